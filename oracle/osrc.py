@@ -1,0 +1,115 @@
+"""OSRC block-diagonal preconditioner of Sec. 2.3, FP64, sparse direct
+solves (test infrastructure only).
+
+Continuous maps (eq. OSRC_DtN_NtD_maps): with X = Delta_Gamma / k_eps^2,
+  DtN ~ i k sqrt(1 + X),   NtD ~ (i k)^-1 (1 + X)^-1/2,
+k_eps = k + i eps.  Readings taken where the paper is silent:
+  * eps = 0.4 k^(1/3) R_eps^(-2/3) with Re k (the printed exponent -1/3 is
+    dimensionally inconsistent; `eps_exponent` keeps it selectable);
+  * the square root is the rotated-branch-cut Pade approximant with N
+    terms and angle theta:
+      sqrt(1+z) ~ C0 + sum_l A_l z / (1 + B_l z),
+      a_l = 2/(2N+1) sin^2(l pi/(2N+1)),  b_l = cos^2(l pi/(2N+1)),
+      C0  = e^{i theta/2} R_N(e^{-i theta} - 1),  R_N(w) = 1 + sum a_l w/(1 + b_l w),
+      A_l = e^{-i theta/2} a_l / (1 + b_l (e^{-i theta} - 1))^2,
+      B_l = e^{-i theta} b_l / (1 + b_l (e^{-i theta} - 1));
+  * (1+X)^-1/2 = (1+X)^-1 sqrt(1+X);
+  * the wavenumber of block j is the exterior one (superscript + in eq.
+    OSRC_prec_blocks);
+  * discretisation with P1 mass M and stiffness S (Delta_Gamma -> -M^-1 S):
+      DtN (weak)   : i k [C0 M u - sum_l (A_l/k_eps^2) S (M - (B_l/k_eps^2) S)^-1 M u]
+      NtD (strong) : (i k)^-1 (M - S/k_eps^2)^-1 [same bracket]
+  * composition with the Galerkin rows (mass-matrix, strong form): per
+    domain, row1 -> M^-1 DtN_weak(M^-1 row1), row2 -> NtD_strong(M^-1 row2)
+    (eq. OSRC_prec / OSRC_prec_blocks: DtN on the V row, NtD on the W row).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import galerkin, pmchwt
+
+
+def pade_coefficients(N: int, theta: float):
+    l = np.arange(1, N + 1)
+    a = 2.0 / (2 * N + 1) * np.sin(l * np.pi / (2 * N + 1)) ** 2
+    b = np.cos(l * np.pi / (2 * N + 1)) ** 2
+    e = np.exp(-1j * theta)
+    R = 1.0 + np.sum(a * (e - 1) / (1 + b * (e - 1)))
+    C0 = np.exp(0.5j * theta) * R
+    A = np.exp(-0.5j * theta) * a / (1 + b * (e - 1)) ** 2
+    B = e * b / (1 + b * (e - 1))
+    return C0, A, B
+
+
+def pade_sqrt(z, N: int, theta: float):
+    C0, A, B = pade_coefficients(N, theta)
+    z = np.asarray(z, dtype=np.complex128)
+    return C0 + sum(A[i] * z / (1 + B[i] * z) for i in range(N))
+
+
+def damped_wavenumber(k: complex, R_eps: float, eps_exponent: float = 1.0 / 3.0) -> complex:
+    kr = float(np.real(k))
+    eps = 0.4 * kr ** eps_exponent * R_eps ** (-2.0 / 3.0)
+    return complex(k) + 1j * eps
+
+
+class DomainOSRC:
+    def __init__(self, v, t, k, R_eps, n_pade=4, theta=np.pi / 3, eps_exponent=1.0 / 3.0):
+        self.M = galerkin.mass_matrix(v, t).tocsc()
+        self.S = galerkin.stiffness_matrix(v, t).tocsc()
+        self.k = complex(k)
+        self.keps = damped_wavenumber(k, R_eps, eps_exponent)
+        self.C0, self.A, self.B = pade_coefficients(n_pade, theta)
+        k2 = self.keps ** 2
+        self.Minv = spla.splu(self.M)
+        self.shift = [spla.splu((self.M - (Bl / k2) * self.S).astype(np.complex128).tocsc()) for Bl in self.B]
+        self.Mm = spla.splu((self.M - self.S / k2).astype(np.complex128).tocsc())
+
+    def bracket(self, u):
+        k2 = self.keps ** 2
+        Mu = self.M @ u
+        out = self.C0 * Mu
+        for l, lu in enumerate(self.shift):
+            out = out - (self.A[l] / k2) * (self.S @ lu.solve(Mu))
+        return out
+
+    def dtn_weak(self, u):
+        return 1j * self.k * self.bracket(u)
+
+    def ntd_strong(self, u):
+        return self.Mm.solve(self.bracket(u)) / (1j * self.k)
+
+    def minv(self, f):
+        f = np.asarray(f, dtype=np.complex128)
+        return self.Minv.solve(f.real.copy()) + 1j * self.Minv.solve(f.imag.copy())
+
+
+def build(scene, R_eps, n_pade=4, theta=np.pi / 3, eps_exponent=1.0 / 3.0):
+    return [DomainOSRC(d.verts, d.tris, scene.k0, R_eps, n_pade, theta, eps_exponent) for d in scene.domains]
+
+
+def apply(scene, pre, y):
+    """Preconditioner applied to Galerkin rows y (system order)."""
+    n = pmchwt.offsets(scene)
+    out = np.empty_like(y, dtype=np.complex128)
+    for j, d in enumerate(scene.domains):
+        nv = d.verts.shape[0]
+        P = pre[j]
+        r1 = y[n[j]:n[j] + nv]
+        r2 = y[n[j] + nv:n[j + 1]]
+        out[n[j]:n[j] + nv] = P.minv(P.dtn_weak(P.minv(r1)))
+        out[n[j] + nv:n[j + 1]] = P.ntd_strong(P.minv(r2))
+    return out
+
+
+def as_dense(scene, pre):
+    """Dense matrix of the preconditioner (small meshes only)."""
+    N = pmchwt.offsets(scene)[-1]
+    I = np.eye(N, dtype=np.complex128)
+    return np.stack([apply(scene, pre, I[:, c]) for c in range(N)], axis=1)
+
+
+__all__ = ["pade_coefficients", "pade_sqrt", "damped_wavenumber", "DomainOSRC", "build", "apply", "as_dense", "sp"]
