@@ -1,0 +1,298 @@
+"""Benchmark: BEM operator-apply Ginteractions/s on the synthetic rib / fat /
+liver scene (~41k triangles, 0.5 MHz), FP32 matrix-free PMCHWT apply.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one application of the multiple-domain PMCHWT Galerkin operator
+A_hat to a vector (trial gather -> far-field interactions -> projection with
+the Sauter-Schwab near-field correction -> vertex reduction), inputs resident
+in HBM.  An interaction is one Green's-function evaluation at one
+(target point, source point) pair at one wavenumber.  Prints one JSON line.
+Under torchrun each rank runs an independent replica (weak scaling, no
+data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BEM operator-apply Ginteractions/s"
+UNIT = "Ginteractions/s"
+# Algorithmic FP32 work of the far-field kernel per (target point, source
+# point) pair, counted from its source (FFMA = 2 flops; MUFU excluded):
+# one wavenumber 82.2 flops; the fused two-wavenumber pair of own-domain
+# sources 141.5 flops (shared geometry counted once).
+FLOPS_1K = 82.2
+FLOPS_2K = 141.5
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def workload(name):
+    from synth import scenes
+    if name == "rib":
+        s = scenes.rib_scene()
+        desc = "rib/fat/liver scene, 0.5 MHz, ~41k triangles (5 capsule ribs as one bone domain, fat slab, liver)"
+    elif name == "kidney":
+        s = scenes.kidney_scene()
+        desc = "kidney + perinephric fat shell, 1 MHz, ~62k triangles"
+    elif name == "sphere":
+        s = scenes.sphere_scene(3)
+        desc = "unit sphere, icosphere level 3, k0=5, k1=5.25, rho ratio 1.1"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return s, desc
+
+
+def pair_counts(s):
+    P = [6 * d.tris.shape[0] for d in s.domains]
+    tot = sum(P)
+    fused = sum(p * p for p in P)
+    single = tot * tot - fused
+    return single, fused, single + 2 * fused
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.p or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(s, n_rows_per_domain, seed=11):
+    """Time the FP64 oracle's matrix-free apply on sampled output rows of
+    the same scene; returns (interactions, seconds, description)."""
+    import numpy as np
+
+    from oracle import galerkin, pmchwt
+    from synth import scenes
+    galerkin.build()
+    rng = np.random.default_rng(seed)
+    rows = [rng.choice(d.verts.shape[0], size=n_rows_per_domain, replace=False) for d in s.domains]
+    x = scenes.random_complex(2 * s.n_vertices, seed)
+    n_int = 0
+    for j, dj in enumerate(s.domains):
+        for i, di in enumerate(s.domains):
+            e = galerkin.regular_evals(dj.tris, di.tris.shape[0], rows[j], dj.verts.shape[0])
+            n_int += e * (2 if i == j else 1)
+    t0 = time.perf_counter()
+    pmchwt.apply_rows(s, x, rows)
+    dt = time.perf_counter() - t0
+    return n_int, dt, f"{n_rows_per_domain} output vertices per domain (both rows), all sources"
+
+
+def traffic_from_profile():
+    """dram bytes per far-field launch from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "far32_kernel_rib_scene.md")
+    src = os.path.join(ROOT, "paper_1910_01011_gb300", "csrc", "k_apply.cu")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    if not m or not h:
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != h.group(1)[:16]:
+        return None
+    return float(m.group(1))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    s, desc = workload(args.workload)
+    cores = os.cpu_count()
+    vals, times = [], []
+    for _ in range(args.warmup):
+        oracle_sample(s, 1)
+    n_tot, t_tot = 0, 0.0
+    for k in range(args.steps):
+        n, dt, sample = oracle_sample(s, args.ref_rows, seed=100 + k)
+        n_tot += n
+        t_tot += dt
+    value = n_tot / t_tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "n_triangles": s.n_triangles, "n_dofs": s.n_dofs},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step: {sample} (FP64 C oracle, OpenMP)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rib", choices=["rib", "kidney", "sphere"])
+    ap.add_argument("--ref-rows", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1910_01011_gb300.api import Context
+
+    s, desc = workload(args.workload)
+    stream = torch.cuda.current_stream()
+    ctx = Context.from_scene(s, device=local, stream=stream.cuda_stream)
+    N = ctx.n_dofs
+    single, fused, n_int = pair_counts(s)
+    assert n_int == ctx.interactions
+    flops = single * FLOPS_1K + fused * FLOPS_2K
+
+    gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
+    x = torch.complex(torch.randn(N, dtype=torch.float64, device="cuda", generator=gen),
+                      torch.randn(N, dtype=torch.float64, device="cuda", generator=gen))
+    y = torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ctx.apply(x, precision=1, out=y)          # set-up (geometry, near field) outside timing
+    torch.cuda.synchronize()
+    for _ in range(max(3, args.warmup)):
+        ctx.apply(x, precision=1, out=y)
+    torch.cuda.synchronize()
+
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()                      # L2 flush between timed steps (outside the events)
+            starts[k].record(stream)
+            ctx.apply(x, precision=1, out=y)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * n_int * args.steps / (ms / 1e3) / 1e9
+
+    # e2e: the public call with host buffers (pinned), copies inside the timing
+    xh = torch.empty(N, dtype=torch.complex128).pin_memory()
+    yh = torch.empty(N, dtype=torch.complex128).pin_memory()
+    xh.copy_(x.cpu())
+    xa, ya = xh.numpy(), yh.numpy()
+    ctx.apply(xa, precision=1, out=ya)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.apply(xa, precision=1, out=ya)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * n_int * args.steps / e2e_s / 1e9
+
+    far_ms = prof["far_ms"] / max(1, prof["far_launches"])
+    achieved = flops / (far_ms / 1e3) / 1e12
+    traffic = traffic_from_profile()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "n_triangles": s.n_triangles, "n_dofs": N,
+                       "interactions_per_step": n_int, "precision": "FP32 far field, FP64 near field/output",
+                       "l2": "flushed between timed steps (256 MB write)", "replicas": world},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                         "kernel": "far32_kernel", "kernel_ms": far_ms,
+                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FFMA) x 2070 MHz max clock"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 16 * N},
+            "gpu_launches": prof["kernel_launches"],
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, dt, sample = oracle_sample(s, args.ref_rows)
+        line["cpu_baseline"] = {"value": n / dt / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": sample + f", {n:.3g} interactions in {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * bem.h -- C ABI of the GB300 multiple-domain Galerkin BEM library
+ * (Helmholtz transmission problem, PMCHWT multitrace formulation with the
+ * OSRC block-diagonal preconditioner; arXiv 1910.01011).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns BEM_OK (0) or a negative BEM_ERR_* code; the
+ *   message of the last failure is bem_last_error(ctx).  No C++ exception
+ *   crosses this boundary.  A context is used by one host thread at a time.
+ * - Complex numbers are interleaved (re, im) doubles: bem_z.
+ * - Meshes: vertices double[nv][3], triangles int32[nt][3] ordered
+ *   counter-clockwise seen from outside the domain, so that the right-hand
+ *   normal points out of the domain (the normal n^j of the traces, paper
+ *   Sec. 2.1 eq. traces).  Surfaces must be closed, conforming and
+ *   orientable; different domains must not touch (no triple points,
+ *   Sec. 2).  The library copies every input array; the caller keeps
+ *   ownership of its buffers.
+ * - System order of unknowns and rows (paper Sec. 2.2 eq.
+ *   Form2_matrix_format_p2 with the column permutation of Sec. 2.3): per
+ *   domain j, [psi_j (nv_j); phi_j (nv_j)] = [gamma_N^+ p_tot; gamma_D^+ p_tot]
+ *   at the domain's vertices, domains concatenated in creation order.  Rows:
+ *   per domain [row1 (the V row); row2 (the W row)].
+ * - Device pointers (on_device = 1) must be device memory of the context's
+ *   device; work is queued on the context's stream and the call returns
+ *   without synchronising unless stated.  Host pointers (on_device = 0)
+ *   make the call copy through the context's stream and synchronise.
+ */
+#ifndef GBEM_BEM_H
+#define GBEM_BEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bem_ctx bem_ctx;
+typedef struct {
+    double re, im;
+} bem_z;
+
+enum {
+    BEM_OK = 0,
+    BEM_ERR_INVALID_ARG = -1,
+    BEM_ERR_MESH_INVALID = -2,
+    BEM_ERR_OUT_OF_BUDGET = -3,
+    BEM_ERR_NOT_CONVERGED = -4,
+    BEM_ERR_TIMEOUT = -5,
+    BEM_ERR_CUDA = -6,
+    BEM_ERR_STATE = -7
+};
+
+/* Arithmetic of an operator application. */
+enum {
+    BEM_PREC_FP64 = 0, /* FP64 everywhere (the baseline path) */
+    BEM_PREC_FP32 = 1  /* FP32 far field with tile-local phase, FP64 near field and output */
+};
+
+/* Operators for bem_apply. */
+enum {
+    BEM_OP_AHAT = 0,     /* y = A_hat x, the PMCHWT Galerkin system (Sec. 2.2-2.3) */
+    BEM_OP_PREC = 1,     /* y = P x, the OSRC preconditioner on Galerkin rows (Sec. 2.3) */
+    BEM_OP_PREC_AHAT = 2 /* y = P A_hat x */
+};
+
+typedef struct {
+    int32_t n_gauss_singular;  /* Gauss points per direction of the Sauter-Schwab rules (default 6) */
+    int32_t chunk_tiles;       /* source tiles per far-field work item; 0 = automatic */
+    int64_t hbm_budget_bytes;  /* device memory cap for this context; 0 = no cap */
+    int32_t n_pade;            /* OSRC Pade terms (default 4; paper: 4 spheres, 8 anatomy, Sec. 3) */
+    double pade_theta;         /* OSRC branch-cut rotation (default pi/3) */
+    double r_eps;              /* OSRC damping radius R_eps (Sec. 2.3 eq. OSRC_DtN_NtD_maps); <= 0: 1/10 of the largest domain diameter */
+    double eps_exponent;       /* exponent of k in eps = 0.4 k^e R_eps^(-2/3); default 1/3 */
+} bem_opts;
+
+/* Fill opts with the defaults above. */
+int bem_default_opts(bem_opts* opts);
+
+/* Create a context on CUDA device `device`, queueing all work on the CUDA
+ * stream `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * opts may be NULL.  *out receives the context. */
+int bem_create(bem_ctx** out, int device, void* cuda_stream, const bem_opts* opts);
+
+/* Release the context and all device memory it owns.  NULL is a no-op. */
+int bem_destroy(bem_ctx* ctx);
+
+/* Exterior medium Omega^0: wavenumber k0 (Im >= 0) and density rho0
+ * (Sec. 2.1 eq. model). */
+int bem_set_exterior(bem_ctx* ctx, bem_z k0, double rho0);
+
+/* Add a domain Omega^j with its closed surface, interior wavenumber k_j and
+ * density rho_j.  *domain_id receives its index (0, 1, ...).  Returns
+ * BEM_ERR_MESH_INVALID for out-of-range or degenerate triangles or an open
+ * surface (an edge not shared by exactly two triangles). */
+int bem_add_domain(bem_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t nt, bem_z k,
+                   double rho, int32_t* domain_id);
+
+/* Change the material of an existing domain (rebuilds the near field). */
+int bem_set_material(bem_ctx* ctx, int32_t domain_id, bem_z k, double rho);
+
+/* Number of unknowns N = sum_j 2 nv_j. */
+int bem_num_dofs(const bem_ctx* ctx, int64_t* n);
+
+/* Number of Green's-function evaluations of one far-field application of
+ * A_hat (one per quadrature-point pair and wavenumber). */
+int bem_interaction_count(const bem_ctx* ctx, int64_t* n);
+
+/* y = op(x) for n_rhs right-hand sides stored one after another (x, y:
+ * n_rhs * N complex each, system order).  precision: BEM_PREC_*.
+ * x and y must not overlap. */
+int bem_apply(bem_ctx* ctx, int op, const bem_z* x, bem_z* y, int64_t n_rhs, int precision, int on_device);
+
+/* One Calderon block A_k^{ji} = [[-K, V], [W, K']] (App. A) between the
+ * surfaces of test domain j and trial domain i at wavenumber k, in the
+ * paper's order: x = [phi_i; psi_i] (2 nv_i), y = [row1; row2] (2 nv_j).
+ * For i == j the touching pairs use the singular rules. */
+int bem_apply_block(bem_ctx* ctx, int32_t test_domain, int32_t trial_domain, bem_z k, const bem_z* x, bem_z* y,
+                    int precision, int on_device);
+
+/* Incident field: a plane wave amp * exp(i k0 d.x) (d normalised here). */
+int bem_set_plane_wave(bem_ctx* ctx, const double dir[3], bem_z amp);
+
+/* Incident field: n_elem flat pistons (centres, unit normals, radii: host
+ * arrays) radiating by the Rayleigh integral with unit normal velocity,
+ * p = -(i omega rho0 / 2 pi) sum_m w_m int exp(i k0 R)/R dS; omega_rho0 is
+ * omega * rho0.  Piston weights come from bem_set_excitations. */
+int bem_set_transducer(bem_ctx* ctx, const double* centres, const double* normals, const double* radii,
+                       int64_t n_elem, double omega_rho0);
+
+/* Piston weights of n_rhs excitations, w[r * n_elem + m] (host array). */
+int bem_set_excitations(bem_ctx* ctx, const bem_z* w, int64_t n_rhs);
+
+/* Right-hand side b = [<gamma_D p_inc, phi_r>; <gamma_N p_inc, phi_r>] per
+ * domain (Sec. 2.3 eq. Galerkin_disc_rhs1) for every excitation (n_rhs * N
+ * complex; one vector for a plane wave). */
+int bem_rhs(bem_ctx* ctx, bem_z* b, int on_device);
+
+typedef struct {
+    int32_t restart;       /* GMRES restart (paper: 100, Sec. 3) */
+    int32_t max_iter;      /* total inner iterations cap */
+    double tol;            /* target relative residual of the returned traces */
+    int32_t precision;     /* BEM_PREC_FP64: plain FP64 GMRES; BEM_PREC_FP32: FP32 inner, FP64 refinement */
+    int32_t precondition;  /* 1 = OSRC preconditioner */
+    double inner_tol;      /* inner relative tolerance of the mixed-precision path (default 1e-4) */
+    int32_t max_refine;    /* outer refinement cap (default 10) */
+} bem_solve_opts;
+
+typedef struct {
+    int32_t iterations;    /* total inner GMRES iterations */
+    int32_t refinements;   /* outer FP64 refinement steps */
+    double residual;       /* final FP64 relative residual ||b - A_hat u|| / ||b|| */
+    double seconds;        /* wall time of the solve */
+} bem_solve_report;
+
+int bem_default_solve_opts(bem_solve_opts* o);
+
+/* Solve A_hat u = b for every excitation set by bem_set_plane_wave /
+ * bem_set_excitations.  Returns BEM_ERR_NOT_CONVERGED (report filled,
+ * traces kept) when the tolerance is not met. */
+int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* report);
+
+/* Traces of the last solve for excitation `rhs` on domain j:
+ * dirichlet = gamma_D p_tot, neumann = gamma_N^+ p_tot (exterior side;
+ * the interior Neumann trace is rho_j/rho_0 times it, eq. Form1_BCs). */
+int bem_get_traces(bem_ctx* ctx, int32_t domain_id, int64_t rhs, bem_z* dirichlet, bem_z* neumann, int on_device);
+
+/* Kernel timing for measurement: when enabled, the library records CUDA
+ * events on its stream around every far-field kernel launch.
+ * bem_profile_read synchronises the stream and returns the summed far-field
+ * kernel time (ms), the number of far-field launches and the number of
+ * kernels the library launched since the last reset (reset = 1 clears). */
+int bem_profile_enable(bem_ctx* ctx, int enable);
+int bem_profile_read(bem_ctx* ctx, double* far_ms, int64_t* far_launches, int64_t* kernel_launches, int reset);
+
+/* Message of the last error on ctx (never NULL). */
+const char* bem_last_error(const bem_ctx* ctx);
+
+/* Host-only: the library's own quadrature tables, for comparison with an
+ * independent derivation.  which = 0: regular triangle rule (rows l1, l2, w;
+ * point P0 + l1 (P1-P0) + l2 (P2-P0), weights sum to 1); which = 1:
+ * Gauss-Legendre on [0,1] with n points (rows node, weight).  *n_out
+ * receives the number of rows; buf holds 3 * 64 doubles at least. */
+int bem_quadrature_table(int which, int n, double* buf, int* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,103 @@
+"""ctypes binding of the C ABI in include/bem.h (argument marshalling only).
+
+The shared library is built in-tree by build.py.  Nothing here computes any
+part of the method; if the library is missing or fails to load, every call
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgbem.so")
+
+BEM_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "MESH_INVALID", -3: "OUT_OF_BUDGET", -4: "NOT_CONVERGED", -5: "TIMEOUT",
+          -6: "CUDA", -7: "STATE"}
+PREC_FP64, PREC_FP32 = 0, 1
+OP_AHAT, OP_PREC, OP_PREC_AHAT = 0, 1, 2
+
+
+class bem_z(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
+class bem_opts(ctypes.Structure):
+    _fields_ = [("n_gauss_singular", ctypes.c_int32), ("chunk_tiles", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64), ("n_pade", ctypes.c_int32), ("pade_theta", ctypes.c_double),
+                ("r_eps", ctypes.c_double), ("eps_exponent", ctypes.c_double)]
+
+
+class bem_solve_opts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("precondition", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("max_refine", ctypes.c_int32)]
+
+
+class bem_solve_report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("residual", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+class BemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"bem error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "bem_default_opts": [ctypes.POINTER(bem_opts)],
+    "bem_create": [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.POINTER(bem_opts)],
+    "bem_destroy": [_P],
+    "bem_set_exterior": [_P, bem_z, ctypes.c_double],
+    "bem_add_domain": [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, bem_z, ctypes.c_double,
+                       ctypes.POINTER(ctypes.c_int32)],
+    "bem_set_material": [_P, ctypes.c_int32, bem_z, ctypes.c_double],
+    "bem_num_dofs": [_P, ctypes.POINTER(ctypes.c_int64)],
+    "bem_interaction_count": [_P, ctypes.POINTER(ctypes.c_int64)],
+    "bem_apply": [_P, ctypes.c_int, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int],
+    "bem_apply_block": [_P, ctypes.c_int32, ctypes.c_int32, bem_z, _P, _P, ctypes.c_int, ctypes.c_int],
+    "bem_set_plane_wave": [_P, ctypes.POINTER(ctypes.c_double), bem_z],
+    "bem_set_transducer": [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_double],
+    "bem_set_excitations": [_P, _P, ctypes.c_int64],
+    "bem_rhs": [_P, _P, ctypes.c_int],
+    "bem_default_solve_opts": [ctypes.POINTER(bem_solve_opts)],
+    "bem_solve": [_P, ctypes.POINTER(bem_solve_opts), ctypes.POINTER(bem_solve_report)],
+    "bem_get_traces": [_P, ctypes.c_int32, ctypes.c_int64, _P, _P, ctypes.c_int],
+    "bem_last_error": [_P],
+    "bem_profile_enable": [_P, ctypes.c_int],
+    "bem_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
+    "bem_quadrature_table": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_int)],
+}
+
+
+def load(build_if_missing: bool = True):
+    """Load libgbem.so (building it in-tree first if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise ImportError(f"CUDA library not built: {LIB_PATH}")
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == "bem_last_error" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def check(rc, ctx=None):
+    if rc != BEM_OK:
+        msg = load().bem_last_error(ctx).decode() if ctx else ""
+        raise BemError(rc, msg)
+    return rc

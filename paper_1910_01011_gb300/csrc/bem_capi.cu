@@ -1,0 +1,631 @@
+// bem_capi.cu -- the C ABI (include/bem.h): context, device memory, and the
+// operator application pipeline
+//   gather (trial densities) -> far field (FP32 or FP64) -> projection onto
+//   P1 test functions with the touching-pair correction -> vertex reduction.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+#include "internal.h"
+
+using namespace gbem;
+
+// ------------------------------------------------------------------ helpers
+
+#define CK(expr)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) return ctx->fail(BEM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int bem_ctx::fail(int code, const std::string& msg) {
+    err = msg;
+    return code;
+}
+
+void* bem_ctx::dalloc(size_t bytes, int* rc) {
+    if (bytes == 0) bytes = 16;
+    if (opts.hbm_budget_bytes > 0 && (int64_t)(used_bytes + bytes) > opts.hbm_budget_bytes) {
+        *rc = fail(BEM_ERR_OUT_OF_BUDGET, "device memory budget exceeded (" + std::to_string(used_bytes + bytes) +
+                                              " > " + std::to_string(opts.hbm_budget_bytes) + " bytes)");
+        return nullptr;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        *rc = fail(BEM_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return nullptr;
+    }
+    allocs.push_back({p, bytes});
+    used_bytes += bytes;
+    *rc = BEM_OK;
+    return p;
+}
+
+void bem_ctx::dfree(void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < allocs.size(); i++)
+        if (allocs[i].first == p) {
+            used_bytes -= allocs[i].second;
+            cudaFree(p);
+            allocs.erase(allocs.begin() + i);
+            return;
+        }
+}
+
+template <class T>
+static int upload(bem_ctx* ctx, T** dst, const std::vector<T>& v) {
+    int rc;
+    *dst = (T*)ctx->dalloc(v.size() * sizeof(T), &rc);
+    if (rc) return rc;
+    if (!v.empty()) CK(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return BEM_OK;
+}
+
+static void release_device(bem_ctx* ctx) {
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& a : ctx->allocs) cudaFree(a.first);
+    ctx->allocs.clear();
+    ctx->used_bytes = 0;
+    ctx->dev = DeviceGeom();
+    ctx->ready = false;
+    ctx->near_ready = false;
+    ctx->block_cache.clear();
+    ctx->osrc_ready = false;
+    ctx->rhs_ready = false;
+}
+
+// ------------------------------------------------------------------ set-up
+
+int bem_ctx::finalize() {
+    bem_ctx* const ctx = this;
+    if (ready) return BEM_OK;
+    CK(cudaSetDevice(device));
+    if (!build_quadrature(quad, opts.n_gauss_singular)) return fail(BEM_ERR_STATE, "quadrature derivation failed");
+    std::string msg = build_geometry(doms, quad, geo);
+    if (!msg.empty()) return fail(BEM_ERR_MESH_INVALID, msg);
+    const Geometry& g = geo;
+    DeviceGeom& d = dev;
+    int rc;
+    // fp32 / fp64 point and triangle data
+    std::vector<float4> pg32(g.n_pts), tg32(g.n_slots);
+    std::vector<double4> pg64(g.n_pts), tg64(g.n_slots), tc(g.n_tiles);
+    for (int64_t p = 0; p < g.n_pts; p++) {
+        pg32[p] = make_float4((float)g.pt_delta[3 * p], (float)g.pt_delta[3 * p + 1], (float)g.pt_delta[3 * p + 2],
+                              (float)g.pt_w[p]);
+        pg64[p] = make_double4(g.pt_delta[3 * p], g.pt_delta[3 * p + 1], g.pt_delta[3 * p + 2], g.pt_w[p]);
+    }
+    for (int64_t s = 0; s < g.n_slots; s++) {
+        tg32[s] = make_float4((float)g.slot_n[3 * s], (float)g.slot_n[3 * s + 1], (float)g.slot_n[3 * s + 2],
+                              (float)g.slot_h[s]);
+        tg64[s] = make_double4(g.slot_n[3 * s], g.slot_n[3 * s + 1], g.slot_n[3 * s + 2], g.slot_h[s]);
+    }
+    for (int t = 0; t < g.n_tiles; t++)
+        tc[t] = make_double4(g.tile_c[4 * t], g.tile_c[4 * t + 1], g.tile_c[4 * t + 2], g.tile_c[4 * t + 3]);
+    std::vector<int2> dt(g.n_dom);
+    for (int i = 0; i < g.n_dom; i++) dt[i] = make_int2(g.dom_tile_begin[i], g.dom_tile_end[i]);
+    std::vector<int4> sv(g.n_slots);
+    for (int64_t s = 0; s < g.n_slots; s++)
+        sv[s] = make_int4(g.slot_v[4 * s], g.slot_v[4 * s + 1], g.slot_v[4 * s + 2], g.slot_v[4 * s + 3]);
+    if ((rc = upload(this, &d.pg32, pg32)) || (rc = upload(this, &d.tg32, tg32)) || (rc = upload(this, &d.pg64, pg64)) ||
+        (rc = upload(this, &d.tg64, tg64)) || (rc = upload(this, &d.tc, tc)) || (rc = upload(this, &d.tdom, g.tile_dom)) ||
+        (rc = upload(this, &d.tntri, g.tile_ntri)) || (rc = upload(this, &d.dom_tiles, dt)) ||
+        (rc = upload(this, &d.slot_v, sv)) || (rc = upload(this, &d.slot_P, g.slot_P)) ||
+        (rc = upload(this, &d.slot_n, g.slot_n)) || (rc = upload(this, &d.slot_area, g.slot_area)) ||
+        (rc = upload(this, &d.slot_curl, g.slot_curl)) || (rc = upload(this, &d.pt_w, g.pt_w)) ||
+        (rc = upload(this, &d.vc_ptr, g.vc_ptr)) || (rc = upload(this, &d.vc_idx, g.vc_idx)) ||
+        (rc = upload(this, &d.v_dof1, g.v_dof1)) || (rc = upload(this, &d.v_dof2, g.v_dof2)) ||
+        (rc = upload(this, &d.np_ptr, g.np_ptr)) || (rc = upload(this, &d.np_src, g.np_src)) ||
+        (rc = upload(this, &d.np_code, g.np_code)))
+        return rc;
+    // pair target list (for the near build)
+    std::vector<int32_t> ptgt(g.np_src.size());
+    for (int64_t s = 0; s < g.n_slots; s++)
+        for (int64_t i = g.np_ptr[s]; i < g.np_ptr[s + 1]; i++) ptgt[i] = (int32_t)s;
+    if ((rc = upload(this, &d.np_tgt, ptgt))) return rc;
+    for (int r = 1; r <= 3; r++)
+        if ((rc = upload(this, &d.ss_tab[r], quad.ss[r]))) return rc;
+    // working buffers
+    d.pd32 = (float4*)dalloc(g.n_pts * sizeof(float4), &rc); if (rc) return rc;
+    d.tcurl32 = (float4*)dalloc(2 * g.n_slots * sizeof(float4), &rc); if (rc) return rc;
+    d.pd64 = (double4*)dalloc(g.n_pts * sizeof(double4), &rc); if (rc) return rc;
+    d.tcurl64 = (double4*)dalloc(2 * g.n_slots * sizeof(double4), &rc); if (rc) return rc;
+    d.tri_out = (double2*)dalloc(g.n_slots * 6 * sizeof(double2), &rc); if (rc) return rc;
+    d.kdom = (double2*)dalloc(g.n_dom * sizeof(double2), &rc); if (rc) return rc;
+    d.coef = (SlotCoef*)dalloc(g.n_dom * 2 * sizeof(SlotCoef), &rc); if (rc) return rc;
+    d.err = (int*)dalloc(sizeof(int), &rc); if (rc) return rc;
+    d.xs = (double2*)dalloc(g.n_dof * sizeof(double2), &rc); if (rc) return rc;
+    d.ys = (double2*)dalloc(g.n_dof * sizeof(double2), &rc); if (rc) return rc;
+    CK(cudaMemsetAsync(d.err, 0, sizeof(int), stream));
+    ready = true;
+    return upload_materials();
+}
+
+int bem_ctx::upload_materials() {
+    bem_ctx* const ctx = this;
+    std::vector<double2> kd(geo.n_dom);
+    std::vector<SlotCoef> cf(geo.n_dom * 2);
+    for (int i = 0; i < geo.n_dom; i++) {
+        kd[i] = make_double2(doms[i].kre, doms[i].kim);
+        const double r = doms[i].rho / rho0;
+        const double k0r = k0re, k0i = k0im, kr = doms[i].kre, ki = doms[i].kim;
+        cf[2 * i] = SlotCoef{1.0, 1.0, 1.0, 1.0, k0r * k0r - k0i * k0i, 2 * k0r * k0i};
+        cf[2 * i + 1] = SlotCoef{r, 1.0, 1.0, 1.0 / r, kr * kr - ki * ki, 2 * kr * ki};
+    }
+    CK(cudaMemcpyAsync(dev.kdom, kd.data(), kd.size() * sizeof(double2), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(dev.coef, cf.data(), cf.size() * sizeof(SlotCoef), cudaMemcpyHostToDevice, stream));
+    CK(cudaStreamSynchronize(stream));
+    return BEM_OK;
+}
+
+// Near-field corrections: n_slot_k = 2 for the PMCHWT system (exterior and
+// own-domain wavenumbers), 1 for a single Calderon block at wavenumber k.
+int bem_ctx::build_near(NearSet& ns, int n_slot_k, double kre, double kim, const SlotCoef* coef_dev) {
+    bem_ctx* const ctx = this;
+    const int64_t np = (int64_t)geo.np_src.size();
+    int rc;
+    ns.n_pairs = np;
+    ns.nb64 = (double2*)dalloc(std::max<int64_t>(1, np) * 36 * sizeof(double2), &rc); if (rc) return rc;
+    ns.nb32 = (float2*)dalloc(std::max<int64_t>(1, np) * 36 * sizeof(float2), &rc); if (rc) return rc;
+    if (np == 0) return BEM_OK;
+    const int64_t max_batch = 1 << 20;  // bound the raw scratch
+    double2* raw = (double2*)dalloc(std::min(np, max_batch) * n_slot_k * 27 * sizeof(double2), &rc);
+    if (rc) return rc;
+    for (int64_t b0 = 0; b0 < np; b0 += max_batch) {
+        const int64_t nb = std::min(max_batch, np - b0);
+        NearArgs a{};
+        a.n_pairs = nb;
+        a.pair_tgt = dev.np_tgt + b0;
+        a.pair_src = dev.np_src + b0;
+        a.pair_code = dev.np_code + b0;
+        a.slot_P = dev.slot_P;
+        a.slot_n = dev.slot_n;
+        a.slot_area = dev.slot_area;
+        a.slot_curl = dev.slot_curl;
+        for (int r = 1; r <= 3; r++) {
+            a.ss_tab[r] = dev.ss_tab[r];
+            a.ss_n[r] = (int)(quad.ss[r].size() / 5);
+        }
+        a.ss_tab[0] = nullptr;
+        a.ss_n[0] = 0;
+        for (int q = 0; q < QP; q++) {
+            a.rule[3 * q] = quad.l1[q];
+            a.rule[3 * q + 1] = quad.l2[q];
+            a.rule[3 * q + 2] = quad.w[q];
+        }
+        a.k[0] = make_double2(kre, kim);
+        a.k[1] = make_double2(0, 0);
+        a.kdom = dev.kdom;
+        a.slot_dom = (const int*)dev.slot_v;
+        a.n_slot_k = n_slot_k;
+        a.raw = raw;
+        CK(launch_near_build(a, stream));
+        NearCombineArgs c{};
+        c.n_pairs = nb;
+        c.pair_tgt = dev.np_tgt + b0;
+        c.pair_src = dev.np_src + b0;
+        c.slot_n = dev.slot_n;
+        c.slot_curl = dev.slot_curl;
+        c.slot_v = dev.slot_v;
+        c.coef = coef_dev;
+        c.n_slot_k = n_slot_k;
+        c.raw = raw;
+        c.nb64 = ns.nb64 + b0 * 36;
+        c.nb32 = ns.nb32 + b0 * 36;
+        CK(launch_near_combine(c, stream));
+    }
+    CK(cudaStreamSynchronize(stream));
+    dfree(raw);
+    return BEM_OK;
+}
+
+int bem_ctx::ensure_near() {
+    if (near_ready) return BEM_OK;
+    if (pmchwt_near.nb64) { dfree(pmchwt_near.nb64); dfree(pmchwt_near.nb32); pmchwt_near = NearSet(); }
+    int rc = build_near(pmchwt_near, 2, k0re, k0im, dev.coef);
+    if (rc) return rc;
+    near_ready = true;
+    return BEM_OK;
+}
+
+int bem_ctx::ensure_partial(int n_chunks, bool fp64) {
+    size_t need = (size_t)n_chunks * 2 * NCOMP * geo.n_pts * (fp64 ? 8 : 4);
+    if (need <= partial_bytes) return BEM_OK;
+    if (partial) dfree(partial);
+    int rc;
+    partial = dalloc(need, &rc);
+    if (rc) { partial = nullptr; partial_bytes = 0; return rc; }
+    partial_bytes = need;
+    return BEM_OK;
+}
+
+void bem_ctx::chunking(int n_tgt, int n_src, int* n_chunks, int* chunk_tiles) const {
+    int want = std::max(1, (152 * 2 * 8 + n_tgt - 1) / std::max(1, n_tgt));
+    int nc = std::max(want, (n_src + CHUNK_MAX - 1) / CHUNK_MAX);
+    if (opts.chunk_tiles > 0) nc = (n_src + opts.chunk_tiles - 1) / opts.chunk_tiles;
+    nc = std::max(1, std::min(nc, n_src));
+    int ct = (n_src + nc - 1) / nc;
+    ct = std::min(ct, CHUNK_MAX);
+    *chunk_tiles = ct;
+    *n_chunks = (n_src + ct - 1) / ct;
+}
+
+// The pipeline.  x, y: device, system order.  Modes: PMCHWT (all targets,
+// all sources at k0 plus own-domain sources at k_j), or BLOCK (targets of
+// domain j, sources of domain i, one wavenumber).
+int bem_ctx::run_apply(const double2* x, double2* y, int precision, const ApplyMode& m) {
+    bem_ctx* const ctx = this;
+    const Geometry& g = geo;
+    const bool fp64 = precision == BEM_PREC_FP64;
+    const int tgt_b = g.dom_tile_begin[m.tgt_dom_lo], tgt_e = g.dom_tile_end[m.tgt_dom_hi - 1];
+    const int src_b = g.dom_tile_begin[m.src_dom_lo], src_e = g.dom_tile_end[m.src_dom_hi - 1];
+    int n_chunks, chunk_tiles;
+    chunking(tgt_e - tgt_b, src_e - src_b, &n_chunks, &chunk_tiles);
+    int rc = ensure_partial(n_chunks, fp64);
+    if (rc) return rc;
+    // 1. trial densities on the source slots
+    GatherArgs ga{};
+    ga.slot_v = dev.slot_v;
+    ga.v_dof1 = dev.v_dof1;
+    ga.v_dof2 = dev.v_dof2;
+    ga.pt_w = dev.pt_w;
+    ga.slot_curl = dev.slot_curl;
+    ga.x = x;
+    ga.s_begin = (int64_t)src_b * TT;
+    ga.s_end = (int64_t)src_e * TT;
+    for (int q = 0; q < QP; q++)
+        for (int k = 0; k < 3; k++) ga.lam[q][k] = quad.lam[q][k];
+    if (fp64) { ga.pd64 = dev.pd64; ga.tcurl64 = dev.tcurl64; }
+    else { ga.pd32 = dev.pd32; ga.tcurl32 = dev.tcurl32; }
+    CK(launch_gather(ga, stream));
+    // 2. far field
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (profiling) {
+        CK(cudaEventCreate(&ev0));
+        CK(cudaEventCreate(&ev1));
+        CK(cudaEventRecord(ev0, stream));
+    }
+    if (fp64) {
+        FarArgs64 fa{};
+        fa.pg = dev.pg64; fa.tg = dev.tg64; fa.tc = dev.tc; fa.tdom = dev.tdom; fa.tntri = dev.tntri;
+        fa.pd = dev.pd64; fa.tcurl = dev.tcurl64; fa.dom_tiles = dev.dom_tiles; fa.kdom = dev.kdom;
+        fa.k0 = make_double2(m.kre, m.kim);
+        fa.src_begin = src_b; fa.src_end = src_e; fa.tgt_begin = tgt_b; fa.chunk_tiles = chunk_tiles;
+        fa.slot1 = m.slot1; fa.n_pts = g.n_pts; fa.partial = (double*)partial;
+        CK(launch_far64(fa, tgt_e - tgt_b, n_chunks, stream));
+    } else {
+        FarArgs32 fa{};
+        fa.pg = dev.pg32; fa.tg = dev.tg32; fa.tc = dev.tc; fa.tdom = dev.tdom; fa.tntri = dev.tntri;
+        fa.pd = dev.pd32; fa.tcurl = dev.tcurl32; fa.dom_tiles = dev.dom_tiles; fa.kdom = dev.kdom;
+        fa.k0 = make_double2(m.kre, m.kim);
+        fa.src_begin = src_b; fa.src_end = src_e; fa.tgt_begin = tgt_b; fa.chunk_tiles = chunk_tiles;
+        fa.slot1 = m.slot1; fa.n_pts = g.n_pts; fa.partial = (float*)partial; fa.err = dev.err;
+        CK(launch_far32(fa, tgt_e - tgt_b, n_chunks, stream));
+    }
+    if (profiling) {
+        CK(cudaEventRecord(ev1, stream));
+        far_events.push_back({ev0, ev1});
+    }
+    // 3. projection (+ touching-pair correction)
+    ProjectArgs pa{};
+    pa.slot_v = dev.slot_v; pa.pt_w = dev.pt_w; pa.slot_curl = dev.slot_curl; pa.tntri = dev.tntri; pa.tdom = dev.tdom;
+    pa.coef = m.coef; pa.tgt_begin = tgt_b; pa.tgt_end = tgt_e; pa.n_chunks = n_chunks; pa.n_pts = g.n_pts;
+    if (fp64) pa.partial64 = (const double*)partial; else pa.partial32 = (const float*)partial;
+    if (m.near && m.near->n_pairs > 0) {
+        pa.np_ptr = dev.np_ptr; pa.np_src = dev.np_src;
+        if (fp64) pa.nb64 = m.near->nb64; else pa.nb32 = m.near->nb32;
+    }
+    pa.v_dof1 = dev.v_dof1; pa.v_dof2 = dev.v_dof2; pa.x = x; pa.tri_out = dev.tri_out;
+    for (int q = 0; q < QP; q++)
+        for (int k = 0; k < 3; k++) pa.lam[q][k] = quad.lam[q][k];
+    CK(launch_project(pa, stream));
+    // 4. vertex reduction
+    ReduceArgs ra{};
+    ra.vc_ptr = dev.vc_ptr; ra.vc_idx = dev.vc_idx; ra.v_dof1 = dev.v_dof1; ra.v_dof2 = dev.v_dof2;
+    ra.tri_out = dev.tri_out; ra.y = y;
+    ra.v_begin = g.dom_vert_off[m.tgt_dom_lo];
+    ra.v_end = g.dom_vert_off[m.tgt_dom_hi - 1] + g.dom_nv[m.tgt_dom_hi - 1];
+    CK(launch_reduce(ra, stream));
+    launches += 4;
+    return BEM_OK;
+}
+
+int bem_ctx::apply_ahat(const double2* x, double2* y, int precision) {
+    int rc = ensure_near();
+    if (rc) return rc;
+    ApplyMode m;
+    m.tgt_dom_lo = 0; m.tgt_dom_hi = geo.n_dom; m.src_dom_lo = 0; m.src_dom_hi = geo.n_dom;
+    m.kre = k0re; m.kim = k0im; m.slot1 = 1; m.coef = dev.coef; m.near = &pmchwt_near;
+    return run_apply(x, y, precision, m);
+}
+
+int bem_ctx::check_device_error() {
+    bem_ctx* const ctx = this;
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, dev.err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    if (h) {
+        CK(cudaMemsetAsync(dev.err, 0, sizeof(int), stream));
+        return fail(BEM_ERR_TIMEOUT, "a device-side wait timed out (error flag set by a kernel)");
+    }
+    return BEM_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+int bem_default_opts(bem_opts* o) {
+    if (!o) return BEM_ERR_INVALID_ARG;
+    std::memset(o, 0, sizeof *o);
+    o->n_gauss_singular = 6;
+    o->chunk_tiles = 0;
+    o->hbm_budget_bytes = 0;
+    o->n_pade = 4;
+    o->pade_theta = M_PI / 3.0;
+    o->r_eps = 0.0;
+    o->eps_exponent = 1.0 / 3.0;
+    return BEM_OK;
+}
+
+int bem_create(bem_ctx** out, int device, void* cuda_stream, const bem_opts* opts) {
+    if (!out) return BEM_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return BEM_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return BEM_ERR_CUDA;
+    bem_ctx* c = new (std::nothrow) bem_ctx();
+    if (!c) return BEM_ERR_OUT_OF_BUDGET;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    bem_default_opts(&c->opts);
+    if (opts) c->opts = *opts;
+    if (c->opts.n_gauss_singular < 2 || c->opts.n_gauss_singular > 20) {
+        delete c;
+        return BEM_ERR_INVALID_ARG;
+    }
+    *out = c;
+    return BEM_OK;
+}
+
+int bem_destroy(bem_ctx* ctx) {
+    if (!ctx) return BEM_OK;
+    release_device(ctx);
+    delete ctx;
+    return BEM_OK;
+}
+
+int bem_set_exterior(bem_ctx* ctx, bem_z k0, double rho0) {
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (!(rho0 > 0) || !(k0.im >= 0) || !std::isfinite(k0.re)) return ctx->fail(BEM_ERR_INVALID_ARG, "bad exterior medium");
+    ctx->k0re = k0.re;
+    ctx->k0im = k0.im;
+    ctx->rho0 = rho0;
+    if (ctx->ready) {
+        ctx->near_ready = false;
+        ctx->osrc_ready = false;
+        ctx->rhs_ready = false;
+        return ctx->upload_materials();
+    }
+    return BEM_OK;
+}
+
+int bem_add_domain(bem_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t nt, bem_z k,
+                   double rho, int32_t* domain_id) {
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (!verts || !tris || nv < 3 || nt < 4) return ctx->fail(BEM_ERR_INVALID_ARG, "empty or null mesh");
+    if (!(rho > 0) || !(k.im >= 0)) return ctx->fail(BEM_ERR_INVALID_ARG, "bad material");
+    HostDomain d;
+    d.verts.assign(verts, verts + 3 * nv);
+    d.tris.assign(tris, tris + 3 * nt);
+    d.nv = nv;
+    d.nt = nt;
+    d.kre = k.re;
+    d.kim = k.im;
+    d.rho = rho;
+    std::vector<HostDomain> trial = ctx->doms;
+    trial.push_back(d);
+    // validate now (cheap host pass) so that errors surface at the call
+    Quadrature q;
+    if (!build_quadrature(q, 2)) return ctx->fail(BEM_ERR_STATE, "quadrature");
+    Geometry g;
+    std::vector<HostDomain> one{d};
+    std::string msg = build_geometry(one, q, g);
+    if (!msg.empty()) return ctx->fail(BEM_ERR_MESH_INVALID, msg);
+    if (ctx->ready) release_device(ctx);
+    ctx->doms.push_back(d);
+    if (domain_id) *domain_id = (int32_t)ctx->doms.size() - 1;
+    return BEM_OK;
+}
+
+int bem_set_material(bem_ctx* ctx, int32_t id, bem_z k, double rho) {
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (id < 0 || id >= (int32_t)ctx->doms.size()) return ctx->fail(BEM_ERR_INVALID_ARG, "bad domain id");
+    if (!(rho > 0) || !(k.im >= 0)) return ctx->fail(BEM_ERR_INVALID_ARG, "bad material");
+    ctx->doms[id].kre = k.re;
+    ctx->doms[id].kim = k.im;
+    ctx->doms[id].rho = rho;
+    if (ctx->ready) {
+        ctx->near_ready = false;
+        ctx->osrc_ready = false;
+        return ctx->upload_materials();
+    }
+    return BEM_OK;
+}
+
+int bem_num_dofs(const bem_ctx* ctx, int64_t* n) {
+    if (!ctx || !n) return BEM_ERR_INVALID_ARG;
+    int64_t s = 0;
+    for (auto& d : ctx->doms) s += 2 * d.nv;
+    *n = s;
+    return BEM_OK;
+}
+
+int bem_interaction_count(const bem_ctx* ctx, int64_t* n) {
+    if (!ctx || !n) return BEM_ERR_INVALID_ARG;
+    // regular-rule point pairs: all (target, source) points at k0, own-domain pairs at k_j
+    int64_t P = 0, own = 0;
+    for (auto& d : ctx->doms) {
+        P += d.nt * QP;
+        own += (d.nt * QP) * (d.nt * QP);
+    }
+    *n = P * P + own;
+    return BEM_OK;
+}
+
+static int io_in(bem_ctx* ctx, const bem_z* x, int64_t n, int on_device, const double2** out) {
+    if (on_device) {
+        *out = (const double2*)x;
+        return BEM_OK;
+    }
+    CK(cudaMemcpyAsync(ctx->dev.xs, x, n * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+    *out = ctx->dev.xs;
+    return BEM_OK;
+}
+
+int bem_apply(bem_ctx* ctx, int op, const bem_z* x, bem_z* y, int64_t n_rhs, int precision, int on_device) {
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (!x || !y || n_rhs < 1) return ctx->fail(BEM_ERR_INVALID_ARG, "null vector or n_rhs < 1");
+    if (precision != BEM_PREC_FP64 && precision != BEM_PREC_FP32) return ctx->fail(BEM_ERR_INVALID_ARG, "bad precision");
+    if (op < BEM_OP_AHAT || op > BEM_OP_PREC_AHAT) return ctx->fail(BEM_ERR_INVALID_ARG, "bad op");
+    CK(cudaSetDevice(ctx->device));
+    int rc = ctx->finalize();
+    if (rc) return rc;
+    const int64_t N = ctx->geo.n_dof;
+    for (int64_t r = 0; r < n_rhs; r++) {
+        const double2* xd;
+        if ((rc = io_in(ctx, x + r * N, N, on_device, &xd))) return rc;
+        double2* yd = on_device ? (double2*)(y + r * N) : ctx->dev.ys;
+        if (op == BEM_OP_AHAT) rc = ctx->apply_ahat(xd, yd, precision);
+        else if (op == BEM_OP_PREC) rc = ctx->apply_prec(xd, yd);
+        else rc = ctx->apply_prec_ahat(xd, yd, precision);
+        if (rc) return rc;
+        if (!on_device) {
+            CK(cudaMemcpyAsync(y + r * N, yd, N * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            if ((rc = ctx->check_device_error())) return rc;
+        }
+    }
+    return BEM_OK;
+}
+
+int bem_apply_block(bem_ctx* ctx, int32_t j, int32_t i, bem_z k, const bem_z* x, bem_z* y, int precision,
+                    int on_device) {
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    const int nd = (int)ctx->doms.size();
+    if (j < 0 || j >= nd || i < 0 || i >= nd || !x || !y) return ctx->fail(BEM_ERR_INVALID_ARG, "bad block arguments");
+    if (precision != BEM_PREC_FP64 && precision != BEM_PREC_FP32) return ctx->fail(BEM_ERR_INVALID_ARG, "bad precision");
+    CK(cudaSetDevice(ctx->device));
+    int rc = ctx->finalize();
+    if (rc) return rc;
+    const Geometry& g = ctx->geo;
+    // coefficients: plain Calderon block at k on every domain
+    BlockCache* bc = nullptr;
+    for (auto& b : ctx->block_cache)
+        if (b.dom == i && b.kre == k.re && b.kim == k.im) bc = &b;
+    if (!bc) {
+        ctx->block_cache.push_back(BlockCache());
+        bc = &ctx->block_cache.back();
+        bc->dom = i;
+        bc->kre = k.re;
+        bc->kim = k.im;
+        std::vector<SlotCoef> cf(g.n_dom * 2);
+        for (int d = 0; d < g.n_dom; d++) {
+            cf[2 * d] = SlotCoef{1, 1, 1, 1, k.re * k.re - k.im * k.im, 2 * k.re * k.im};
+            cf[2 * d + 1] = SlotCoef{0, 0, 0, 0, 0, 0};
+        }
+        bc->coef = (SlotCoef*)ctx->dalloc(cf.size() * sizeof(SlotCoef), &rc);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(bc->coef, cf.data(), cf.size() * sizeof(SlotCoef), cudaMemcpyHostToDevice, ctx->stream));
+        if ((rc = ctx->build_near(bc->near, 1, k.re, k.im, bc->coef))) return rc;
+    }
+    // scatter x (paper order [phi_i; psi_i]) into a zero system-order vector
+    const int64_t nvi = g.dom_nv[i], nvj = g.dom_nv[j], N = g.n_dof;
+    CK(cudaMemsetAsync(ctx->dev.xs, 0, N * sizeof(double2), ctx->stream));
+    const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const int64_t off_i = g.dom_dof_off[i], off_j = g.dom_dof_off[j];
+    CK(cudaMemcpyAsync(ctx->dev.xs + off_i + nvi, x, nvi * sizeof(double2), kin, ctx->stream));       // phi
+    CK(cudaMemcpyAsync(ctx->dev.xs + off_i, x + nvi, nvi * sizeof(double2), kin, ctx->stream));       // psi
+    ApplyMode m;
+    m.tgt_dom_lo = j; m.tgt_dom_hi = j + 1; m.src_dom_lo = i; m.src_dom_hi = i + 1;
+    m.kre = k.re; m.kim = k.im; m.slot1 = 0; m.coef = bc->coef;
+    m.near = (i == j) ? &bc->near : nullptr;
+    if ((rc = ctx->run_apply(ctx->dev.xs, ctx->dev.ys, precision, m))) return rc;
+    const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(y, ctx->dev.ys + off_j, nvj * sizeof(double2), kout, ctx->stream));            // row1
+    CK(cudaMemcpyAsync(y + nvj, ctx->dev.ys + off_j + nvj, nvj * sizeof(double2), kout, ctx->stream)); // row2
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ctx->check_device_error();
+}
+
+int bem_profile_enable(bem_ctx* ctx, int enable) {
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    ctx->profiling = enable != 0;
+    return BEM_OK;
+}
+
+int bem_profile_read(bem_ctx* ctx, double* far_ms, int64_t* far_launches, int64_t* kernel_launches, int reset) {
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (auto& e : ctx->far_events) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e.first, e.second));
+        ctx->far_ms_acc += ms;
+        ctx->far_count++;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    ctx->far_events.clear();
+    if (far_ms) *far_ms = ctx->far_ms_acc;
+    if (far_launches) *far_launches = ctx->far_count;
+    if (kernel_launches) *kernel_launches = ctx->launches;
+    if (reset) {
+        ctx->far_ms_acc = 0;
+        ctx->far_count = 0;
+        ctx->launches = 0;
+    }
+    return BEM_OK;
+}
+
+const char* bem_last_error(const bem_ctx* ctx) {
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+int bem_quadrature_table(int which, int n, double* buf, int* n_out) {
+    if (!buf || !n_out) return BEM_ERR_INVALID_ARG;
+    if (which == 0) {
+        Quadrature q;
+        if (!build_quadrature(q, 2)) return BEM_ERR_STATE;
+        for (int i = 0; i < QP; i++) {
+            buf[3 * i] = q.l1[i];
+            buf[3 * i + 1] = q.l2[i];
+            buf[3 * i + 2] = q.w[i];
+        }
+        *n_out = QP;
+        return BEM_OK;
+    }
+    if (which == 1) {
+        if (n < 1 || n > 64) return BEM_ERR_INVALID_ARG;
+        std::vector<double> x, w;
+        gauss_legendre01(n, x, w);
+        for (int i = 0; i < n; i++) {
+            buf[2 * i] = x[i];
+            buf[2 * i + 1] = w[i];
+        }
+        *n_out = n;
+        return BEM_OK;
+    }
+    return BEM_ERR_INVALID_ARG;
+}
+
+}  // extern "C"

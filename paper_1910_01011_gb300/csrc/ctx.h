@@ -1,0 +1,111 @@
+// ctx.h -- the opaque bem_ctx behind the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace gbem {
+
+struct DeviceGeom {
+    float4 *pg32 = nullptr, *tg32 = nullptr;
+    double4 *pg64 = nullptr, *tg64 = nullptr, *tc = nullptr;
+    int *tdom = nullptr, *tntri = nullptr;
+    int2* dom_tiles = nullptr;
+    int4* slot_v = nullptr;
+    double *slot_P = nullptr, *slot_n = nullptr, *slot_area = nullptr, *slot_curl = nullptr, *pt_w = nullptr;
+    int64_t* vc_ptr = nullptr;
+    int32_t* vc_idx = nullptr;
+    int64_t *v_dof1 = nullptr, *v_dof2 = nullptr;
+    int64_t* np_ptr = nullptr;
+    int32_t *np_src = nullptr, *np_code = nullptr, *np_tgt = nullptr;
+    double* ss_tab[4] = {nullptr, nullptr, nullptr, nullptr};
+    // working buffers
+    float4 *pd32 = nullptr, *tcurl32 = nullptr;
+    double4 *pd64 = nullptr, *tcurl64 = nullptr;
+    double2* tri_out = nullptr;
+    double2* kdom = nullptr;
+    SlotCoef* coef = nullptr;
+    int* err = nullptr;
+    double2 *xs = nullptr, *ys = nullptr;  // staging vectors (system size)
+};
+
+struct NearSet {
+    int64_t n_pairs = 0;
+    double2* nb64 = nullptr;
+    float2* nb32 = nullptr;
+};
+
+struct BlockCache {
+    int dom = -1;
+    double kre = 0, kim = 0;
+    SlotCoef* coef = nullptr;
+    NearSet near;
+};
+
+struct ApplyMode {
+    int tgt_dom_lo = 0, tgt_dom_hi = 0, src_dom_lo = 0, src_dom_hi = 0;
+    double kre = 0, kim = 0;
+    int slot1 = 0;
+    const SlotCoef* coef = nullptr;
+    const NearSet* near = nullptr;
+};
+
+struct OsrcState;  // k_osrc.cu
+struct SolveState; // bem_solve.cu
+
+}  // namespace gbem
+
+struct bem_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bem_opts opts{};
+    std::string err;
+    double k0re = 1.0, k0im = 0.0, rho0 = 1.0;
+    std::vector<gbem::HostDomain> doms;
+    // device state
+    bool ready = false, near_ready = false, osrc_ready = false, rhs_ready = false;
+    gbem::Quadrature quad;
+    gbem::Geometry geo;
+    gbem::DeviceGeom dev;
+    gbem::NearSet pmchwt_near;
+    std::vector<gbem::BlockCache> block_cache;
+    void* partial = nullptr;
+    size_t partial_bytes = 0;
+    std::vector<std::pair<void*, size_t>> allocs;
+    size_t used_bytes = 0;
+    long long launches = 0;
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> far_events;
+    double far_ms_acc = 0;
+    long long far_count = 0;
+    gbem::OsrcState* osrc = nullptr;
+    gbem::SolveState* solve = nullptr;
+    // incident field
+    int field_kind = 0;  // 0 none, 1 plane wave, 2 transducer
+    double pw_dir[3] = {0, 0, 1};
+    double pw_amp[2] = {1, 0};
+    std::vector<double> tr_c, tr_n, tr_r;
+    double omega_rho0 = 0;
+    std::vector<double> tr_w;  // n_rhs * n_elem * 2
+    int64_t n_rhs = 1;
+
+    int fail(int code, const std::string& msg);
+    void* dalloc(size_t bytes, int* rc);
+    void dfree(void* p);
+    int finalize();
+    int upload_materials();
+    int build_near(gbem::NearSet& ns, int n_slot_k, double kre, double kim, const gbem::SlotCoef* coef_dev);
+    int ensure_near();
+    int ensure_partial(int n_chunks, bool fp64);
+    void chunking(int n_tgt, int n_src, int* n_chunks, int* chunk_tiles) const;
+    int run_apply(const double2* x, double2* y, int precision, const gbem::ApplyMode& m);
+    int apply_ahat(const double2* x, double2* y, int precision);
+    int apply_prec(const double2* x, double2* y);
+    int apply_prec_ahat(const double2* x, double2* y, int precision);
+    int check_device_error();
+};

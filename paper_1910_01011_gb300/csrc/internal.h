@@ -1,0 +1,218 @@
+// internal.h -- data layout shared by the library's translation units.
+//
+// Triangles are stored tile-ordered: each domain's triangles are sorted
+// along a Morton curve of their centroids and cut into tiles of TT
+// triangles (the last tile of a domain is padded).  A tile carries its
+// centre in FP64; every point and plane offset of the tile is stored
+// relative to that centre, so FP32 differences between points of two tiles
+// keep their accuracy (the far-field phase is reconstructed from an FP64
+// tile-pair distance plus an FP32 local offset).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bem.h"
+
+namespace gbem {
+
+constexpr int TT = 32;          // triangles per tile
+constexpr int QP = 6;           // regular-rule points per triangle
+constexpr int TP = TT * QP;     // points per tile = threads of a far-field CTA
+constexpr int NCOMP = 14;       // potentials per target point and wavenumber slot
+constexpr int CHUNK_MAX = 256;  // source tiles per far-field CTA (shared-memory table bound)
+
+// ------------------------------------------------------------------ host geometry
+
+struct Quadrature {
+    double l1[QP], l2[QP], w[QP];  // regular rule (weights sum to 1)
+    double lam[QP][3];             // P1 values at the rule points
+    int ng = 6;                    // Gauss points per singular direction
+    // Sauter-Schwab point tables per relation (1 vertex, 2 edge, 3 identical):
+    // rows (s1, s2, t1, t2, weight * jacobian)
+    std::vector<double> ss[4];
+};
+
+struct HostDomain {
+    std::vector<double> verts;   // nv*3
+    std::vector<int32_t> tris;   // nt*3
+    int64_t nv = 0, nt = 0;
+    double kre = 0, kim = 0, rho = 1;
+};
+
+struct Geometry {
+    int n_dom = 0;
+    int n_tiles = 0;
+    int64_t n_slots = 0, n_pts = 0, n_vert = 0, n_dof = 0, n_tri = 0;
+    std::vector<int> dom_tile_begin, dom_tile_end;
+    std::vector<int64_t> dom_vert_off, dom_dof_off, dom_nv;
+    // per tile
+    std::vector<double> tile_c;     // 4 per tile (x, y, z, radius)
+    std::vector<int> tile_dom, tile_ntri;
+    // per triangle slot (tile order, padded)
+    std::vector<int> slot_v;        // 4 per slot: global vertex ids (pad: -1), domain
+    std::vector<double> slot_P;     // 9 per slot: absolute vertex coordinates
+    std::vector<double> slot_n;     // 3 per slot: unit normal
+    std::vector<double> slot_area;  // 1 per slot
+    std::vector<double> slot_curl;  // 9 per slot: surface curls of the 3 P1 functions
+    std::vector<double> slot_h;     // n . (P0 - tile centre)
+    // per point
+    std::vector<double> pt_delta;   // 3 per point, relative to the tile centre
+    std::vector<double> pt_w;       // rule weight * area (0 for padding)
+    // vertex -> corner CSR (corner = slot*3 + local vertex)
+    std::vector<int64_t> vc_ptr;
+    std::vector<int32_t> vc_idx;
+    std::vector<int64_t> v_dof1, v_dof2;  // system index of psi (row1) and phi (row2) of a vertex
+    // touching pairs, CSR over target slots
+    std::vector<int64_t> np_ptr;
+    std::vector<int32_t> np_src;
+    std::vector<int32_t> np_code;   // rel | pa0<<4 | pa1<<6 | pa2<<8 | pb0<<10 | pb1<<12 | pb2<<14
+    double max_diameter = 0;        // largest domain bounding-box diagonal
+};
+
+// Derive the regular 6-point rule (moment equations), Gauss-Legendre nodes
+// and the Sauter-Schwab tables.  Returns false on a Newton failure.
+bool build_quadrature(Quadrature& q, int n_gauss);
+bool gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
+
+// Validate the meshes and build the tiled geometry.  Returns an empty string
+// on success, else the error message.
+std::string build_geometry(const std::vector<HostDomain>& doms, const Quadrature& q, Geometry& g);
+
+// ------------------------------------------------------------------ device views
+
+struct FarArgs32 {
+    const float4* pg;       // [n_pts]   (dx, dy, dz, w)
+    const float4* tg;       // [n_slots] (nx, ny, nz, h)
+    const double4* tc;      // [n_tiles] centre
+    const int* tdom;        // [n_tiles]
+    const int* tntri;       // [n_tiles]
+    const float4* pd;       // [n_pts]   (sigN re, im, sigD re, im) * w
+    const float4* tcurl;    // [2*n_slots] (Cre, 0), (Cim, 0)
+    const int2* dom_tiles;  // [n_dom] own-domain tile range (slot 1 sources)
+    const double2* kdom;    // [n_dom] slot-1 wavenumber
+    double2 k0;             // slot-0 wavenumber
+    int src_begin, src_end; // slot-0 source tiles
+    int tgt_begin;          // first target tile (grid.x offset)
+    int chunk_tiles;        // source tiles per grid.y index
+    int slot1;              // 1: interior wavenumber on own-domain sources
+    int64_t n_pts;
+    float* partial;         // [grid.y][2][NCOMP][n_pts]
+    int* err;               // device error flag (bounded waits)
+};
+
+struct FarArgs64 {
+    const double4* pg;      // (dx, dy, dz, w)
+    const double4* tg;      // (nx, ny, nz, h)
+    const double4* tc;
+    const int* tdom;
+    const int* tntri;
+    const double4* pd;      // (sigN re, im, sigD re, im) * w
+    const double4* tcurl;   // [2*n_slots] (Cre, 0), (Cim, 0)
+    const int2* dom_tiles;
+    const double2* kdom;
+    double2 k0;
+    int src_begin, src_end, tgt_begin, chunk_tiles, slot1;
+    int64_t n_pts;
+    double* partial;
+};
+
+struct GatherArgs {
+    const int4* slot_v;         // [n_slots] vertex ids (-1 pad), .w = domain
+    const int64_t* v_dof1;      // per global vertex
+    const int64_t* v_dof2;
+    const double* pt_w;         // [n_pts]
+    const double* slot_curl;    // [n_slots*9]
+    const double2* x;           // system-order input
+    int64_t s_begin, s_end;     // slots to gather
+    double lam[QP][3];          // P1 values at the rule points
+    float4* pd32; float4* tcurl32;     // fp32 outputs (may be null)
+    double4* pd64; double4* tcurl64;   // fp64 outputs (may be null)
+};
+
+struct SlotCoef {               // per (domain, slot): row coefficients
+    double cV, cK, cKp, cW;
+    double k2re, k2im;          // k^2 of the slot
+};
+
+struct ProjectArgs {
+    const int4* slot_v;
+    const double* pt_w;
+    const double* slot_curl;
+    const int* tntri;
+    const int* tdom;
+    const SlotCoef* coef;       // [n_dom*2]
+    int tgt_begin, tgt_end;     // target tiles
+    int n_chunks;
+    int64_t n_pts;
+    const float* partial32;     // one of the two is non-null
+    const double* partial64;
+    // touching-pair correction (may be empty)
+    const int64_t* np_ptr;      // [n_slots+1]
+    const int32_t* np_src;
+    const double2* nb64;        // [pair][4][9] combined sub-blocks, FP64
+    const float2* nb32;         // FP32 copy (used by the FP32 path)
+    const int64_t* v_dof1;
+    const int64_t* v_dof2;
+    const double2* x;           // input vector (system order)
+    double2* tri_out;           // [n_slots*3][2] per-corner rows
+    double lam[QP][3];
+};
+
+struct ReduceArgs {
+    const int64_t* vc_ptr;
+    const int32_t* vc_idx;
+    const int64_t* v_dof1;
+    const int64_t* v_dof2;
+    const double2* tri_out;
+    int64_t v_begin, v_end;     // global vertices to produce
+    double2* y;
+};
+
+struct NearArgs {
+    int64_t n_pairs;
+    const int32_t* pair_tgt;    // target slot of each pair
+    const int32_t* pair_src;
+    const int32_t* pair_code;
+    const double* slot_P;       // [n_slots*9]
+    const double* slot_n;       // [n_slots*3]
+    const double* slot_area;
+    const double* slot_curl;
+    const double* ss_tab[4];    // device Sauter-Schwab tables (5 doubles per point)
+    int ss_n[4];
+    double rule[3 * QP];        // regular rule (l1, l2, w)
+    double2 k[2];               // slot wavenumbers: slot 0, slot 1 (per target domain: kdom)
+    const double2* kdom;
+    const int* slot_dom;        // via slot_v.w
+    int n_slot_k;               // 1 or 2
+    double2* raw;               // [pair][slot][27]: V, K, K' (SS minus regular)
+};
+
+struct NearCombineArgs {
+    int64_t n_pairs;
+    const int32_t* pair_tgt;
+    const int32_t* pair_src;
+    const double* slot_n;
+    const double* slot_curl;
+    const int4* slot_v;
+    const SlotCoef* coef;       // [n_dom*2]
+    int n_slot_k;
+    const double2* raw;
+    double2* nb64;
+    float2* nb32;
+};
+
+// launchers (k_apply.cu, k_near.cu)
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
+cudaError_t launch_far32(const FarArgs32& a, int n_tgt_tiles, int n_chunks, cudaStream_t s);
+cudaError_t launch_far64(const FarArgs64& a, int n_tgt_tiles, int n_chunks, cudaStream_t s);
+cudaError_t launch_project(const ProjectArgs& a, cudaStream_t s);
+cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t s);
+cudaError_t launch_near_build(const NearArgs& a, cudaStream_t s);
+cudaError_t launch_near_combine(const NearCombineArgs& a, cudaStream_t s);
+size_t far32_smem_bytes();
+
+}  // namespace gbem

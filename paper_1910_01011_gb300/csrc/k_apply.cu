@@ -1,0 +1,576 @@
+// k_apply.cu -- matrix-free application of the Galerkin boundary operators.
+//
+// Paper App. A (eqs. SLP, DLP, ADJDLP, HYP, green_func) and Sec. 2.3 (eq.
+// Galerkin_disc_lhs): with G = exp(ikr)/(4 pi r), F = G (ik - 1/r)/r and P1
+// trial data phi (Dirichlet) and psi (Neumann), the potentials at a target
+// quadrature point x are
+//   P_V   = sum_y G       w_y psi(y)                       (single layer)
+//   P_K   = sum_y F (y-x).n_y w_y phi(y)                   (double layer)
+//   P_K'  = sum_y F (x-y).n_x w_y psi(y)                   (adjoint double layer)
+//   P_Wc  = sum_y G w_y curl phi(y),  P_Wm = sum_y G (n_x.n_y) w_y phi(y)
+// (the hypersingular operator in its integration-by-parts form), and the
+// Galerkin rows follow by testing with the P1 functions at the target
+// points.  Per trial triangle t the plane offset (y-x).n_t and n_x.n_t are
+// constant, and curl phi is constant, so three per-triangle sums
+// S1 = sum F sigma_D, S2 = sum G w, S3 = sum G sigma_D carry K and W.
+//
+// The FP32 kernel keeps kr accurate for large k|x-y| by reconstructing the
+// distance from the tile-pair centre distance R_c (FP64) and a local
+// offset: with D = c_target - c_source and delta = dx - dy (tile-local),
+//   s = delta.(2D + delta) = r^2 - R_c^2,   r - R_c = s / (r + R_c),
+//   phase = (Re k R_c mod 2 pi, FP64) + Re k (r - R_c).
+#include <cstdio>
+
+#include "internal.h"
+
+namespace gbem {
+
+// ----------------------------------------------------------------- helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok;
+}
+
+// Bulk (TMA) copy global -> shared completing on an mbarrier.  Both
+// addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait: gives up after ~2^31 cycles (about a second), raises the
+// device error flag and lets the caller continue on whatever the buffer
+// holds, so that every thread still reaches every __syncthreads.
+__device__ __forceinline__ void mbar_wait_bounded(uint64_t* b, uint32_t parity, int* err) {
+    if (mbar_try_wait(b, parity)) return;
+    long long t0 = clock64();
+    while (!mbar_try_wait(b, parity)) {
+        if (clock64() - t0 > (1ll << 31)) {
+            atomicExch(err, 1);
+            return;
+        }
+    }
+}
+
+// x - 2 pi round(x / 2 pi) in FP64 (2 pi split in two doubles), as float.
+__device__ __forceinline__ float reduce_phase(double t) {
+    const double two_pi_hi = 6.283185307179586, two_pi_lo = 2.4492935982947064e-16;
+    double n = rint(t * 0.15915494309189535);
+    double r = fma(-n, two_pi_hi, t);
+    r = fma(-n, two_pi_lo, r);
+    return (float)r;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ----------------------------------------------------------------- gather (trial densities)
+
+__global__ void gather_kernel(GatherArgs a) {
+    const int64_t s = a.s_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.s_end) return;
+    int4 v = a.slot_v[s];
+    double2 xs[3], xf[3];
+    bool real = v.x >= 0;
+    for (int k = 0; k < 3; k++) {
+        int vid = k == 0 ? v.x : k == 1 ? v.y : v.z;
+        if (real) {
+            xs[k] = a.x[a.v_dof1[vid]];
+            xf[k] = a.x[a.v_dof2[vid]];
+        } else {
+            xs[k] = make_double2(0, 0);
+            xf[k] = make_double2(0, 0);
+        }
+    }
+    for (int q = 0; q < QP; q++) {
+        double w = real ? a.pt_w[s * QP + q] : 0.0;
+        double sr = 0, si = 0, dr = 0, di = 0;
+        for (int k = 0; k < 3; k++) {
+            sr += a.lam[q][k] * xs[k].x;
+            si += a.lam[q][k] * xs[k].y;
+            dr += a.lam[q][k] * xf[k].x;
+            di += a.lam[q][k] * xf[k].y;
+        }
+        if (a.pd32) a.pd32[s * QP + q] = make_float4((float)(w * sr), (float)(w * si), (float)(w * dr), (float)(w * di));
+        if (a.pd64) a.pd64[s * QP + q] = make_double4(w * sr, w * si, w * dr, w * di);
+    }
+    double cr[3] = {0, 0, 0}, ci[3] = {0, 0, 0};
+    if (real)
+        for (int k = 0; k < 3; k++)
+            for (int c = 0; c < 3; c++) {
+                double cu = a.slot_curl[s * 9 + 3 * k + c];
+                cr[c] += xf[k].x * cu;
+                ci[c] += xf[k].y * cu;
+            }
+    if (a.tcurl32) {
+        a.tcurl32[2 * s] = make_float4((float)cr[0], (float)cr[1], (float)cr[2], 0.f);
+        a.tcurl32[2 * s + 1] = make_float4((float)ci[0], (float)ci[1], (float)ci[2], 0.f);
+    }
+    if (a.tcurl64) {
+        a.tcurl64[2 * s] = make_double4(cr[0], cr[1], cr[2], 0.0);
+        a.tcurl64[2 * s + 1] = make_double4(ci[0], ci[1], ci[2], 0.0);
+    }
+}
+
+// ----------------------------------------------------------------- FP32 far field
+
+struct __align__(16) Stage {
+    float4 pg[TP];      // source points (dx, dy, dz, w)
+    float4 pd[TP];      // densities
+    float4 tg[TT];      // triangles (n, h)
+    float4 tc[2 * TT];  // curl densities
+};
+constexpr uint32_t STAGE_BYTES = sizeof(Stage);
+static_assert(STAGE_BYTES == 7680, "stage layout");
+
+struct Acc {
+    float v[NCOMP];  // PV(2) PK(2) PKp(2) PWm(2) PWc(6)
+};
+
+struct SlotK {
+    float kr, nki, nkil2;  // Re k, -Im k, -Im k * log2(e)
+};
+
+// One source triangle for one wavenumber slot: the six rule points, then
+// the per-triangle terms.  Returns nothing; updates `t` (tile accumulators).
+template <bool TWO>
+__device__ __forceinline__ void triangle_body(const Stage& st, int tl, float dx, float dy, float dz, float nx,
+                                              float ny, float nz, float D2x, float D2y, float D2z, float Rc2,
+                                              float Rc, float nX, float Xx, float Xy, float Xz, float th0,
+                                              float th1, SlotK k0, SlotK k1, Acc& t0, Acc& t1) {
+    float S1r0 = 0, S1i0 = 0, S2r0 = 0, S2i0 = 0, S3r0 = 0, S3i0 = 0;
+    float S1r1 = 0, S1i1 = 0, S2r1 = 0, S2i1 = 0, S3r1 = 0, S3i1 = 0;
+#pragma unroll
+    for (int q = 0; q < QP; q++) {
+        const float4 g = st.pg[tl * QP + q];
+        const float4 d = st.pd[tl * QP + q];
+        const float ex = dx - g.x, ey = dy - g.y, ez = dz - g.z;  // delta = dx - dy
+        const float s = ex * (D2x + ex) + ey * (D2y + ey) + ez * (D2z + ez);
+        const float r2 = Rc2 + s;
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        const float rho = __fdividef(s, r + Rc);            // r - R_c
+        const float ndot = nX - (nx * g.x + ny * g.y + nz * g.z);  // n_x.(x - y)
+        {
+            float sn, cs;
+            __sincosf(fmaf(k0.kr, rho, th0), &sn, &cs);
+            const float a = ex2_approx(k0.nkil2 * r) * rinv;
+            const float Gr = a * cs, Gi = a * sn;
+            const float Gbr = Gr * rinv, Gbi = Gi * rinv;
+            const float u = k0.nki - rinv;
+            const float Fr = Gbr * u - Gbi * k0.kr, Fi = Gbr * k0.kr + Gbi * u;
+            t0.v[0] = fmaf(Gr, d.x, fmaf(-Gi, d.y, t0.v[0]));
+            t0.v[1] = fmaf(Gr, d.y, fmaf(Gi, d.x, t0.v[1]));
+            const float Fnr = Fr * ndot, Fni = Fi * ndot;
+            t0.v[4] = fmaf(Fnr, d.x, fmaf(-Fni, d.y, t0.v[4]));
+            t0.v[5] = fmaf(Fnr, d.y, fmaf(Fni, d.x, t0.v[5]));
+            S1r0 = fmaf(Fr, d.z, fmaf(-Fi, d.w, S1r0));
+            S1i0 = fmaf(Fr, d.w, fmaf(Fi, d.z, S1i0));
+            S2r0 = fmaf(Gr, g.w, S2r0);
+            S2i0 = fmaf(Gi, g.w, S2i0);
+            S3r0 = fmaf(Gr, d.z, fmaf(-Gi, d.w, S3r0));
+            S3i0 = fmaf(Gr, d.w, fmaf(Gi, d.z, S3i0));
+        }
+        if constexpr (TWO) {
+            float sn, cs;
+            __sincosf(fmaf(k1.kr, rho, th1), &sn, &cs);
+            const float a = ex2_approx(k1.nkil2 * r) * rinv;
+            const float Gr = a * cs, Gi = a * sn;
+            const float Gbr = Gr * rinv, Gbi = Gi * rinv;
+            const float u = k1.nki - rinv;
+            const float Fr = Gbr * u - Gbi * k1.kr, Fi = Gbr * k1.kr + Gbi * u;
+            t1.v[0] = fmaf(Gr, d.x, fmaf(-Gi, d.y, t1.v[0]));
+            t1.v[1] = fmaf(Gr, d.y, fmaf(Gi, d.x, t1.v[1]));
+            const float Fnr = Fr * ndot, Fni = Fi * ndot;
+            t1.v[4] = fmaf(Fnr, d.x, fmaf(-Fni, d.y, t1.v[4]));
+            t1.v[5] = fmaf(Fnr, d.y, fmaf(Fni, d.x, t1.v[5]));
+            S1r1 = fmaf(Fr, d.z, fmaf(-Fi, d.w, S1r1));
+            S1i1 = fmaf(Fr, d.w, fmaf(Fi, d.z, S1i1));
+            S2r1 = fmaf(Gr, g.w, S2r1);
+            S2i1 = fmaf(Gi, g.w, S2i1);
+            S3r1 = fmaf(Gr, d.z, fmaf(-Gi, d.w, S3r1));
+            S3i1 = fmaf(Gr, d.w, fmaf(Gi, d.z, S3i1));
+        }
+    }
+    const float4 tg = st.tg[tl];
+    const float4 cre = st.tc[2 * tl], cim = st.tc[2 * tl + 1];
+    const float fK = tg.w - (tg.x * Xx + tg.y * Xy + tg.z * Xz);  // n_t.(y - x)
+    const float nn = nx * tg.x + ny * tg.y + nz * tg.z;            // n_x.n_t
+    t0.v[2] = fmaf(fK, S1r0, t0.v[2]);
+    t0.v[3] = fmaf(fK, S1i0, t0.v[3]);
+    t0.v[6] = fmaf(nn, S3r0, t0.v[6]);
+    t0.v[7] = fmaf(nn, S3i0, t0.v[7]);
+    t0.v[8] = fmaf(S2r0, cre.x, fmaf(-S2i0, cim.x, t0.v[8]));
+    t0.v[9] = fmaf(S2r0, cre.y, fmaf(-S2i0, cim.y, t0.v[9]));
+    t0.v[10] = fmaf(S2r0, cre.z, fmaf(-S2i0, cim.z, t0.v[10]));
+    t0.v[11] = fmaf(S2r0, cim.x, fmaf(S2i0, cre.x, t0.v[11]));
+    t0.v[12] = fmaf(S2r0, cim.y, fmaf(S2i0, cre.y, t0.v[12]));
+    t0.v[13] = fmaf(S2r0, cim.z, fmaf(S2i0, cre.z, t0.v[13]));
+    if constexpr (TWO) {
+        t1.v[2] = fmaf(fK, S1r1, t1.v[2]);
+        t1.v[3] = fmaf(fK, S1i1, t1.v[3]);
+        t1.v[6] = fmaf(nn, S3r1, t1.v[6]);
+        t1.v[7] = fmaf(nn, S3i1, t1.v[7]);
+        t1.v[8] = fmaf(S2r1, cre.x, fmaf(-S2i1, cim.x, t1.v[8]));
+        t1.v[9] = fmaf(S2r1, cre.y, fmaf(-S2i1, cim.y, t1.v[9]));
+        t1.v[10] = fmaf(S2r1, cre.z, fmaf(-S2i1, cim.z, t1.v[10]));
+        t1.v[11] = fmaf(S2r1, cim.x, fmaf(S2i1, cre.x, t1.v[11]));
+        t1.v[12] = fmaf(S2r1, cim.y, fmaf(S2i1, cre.y, t1.v[12]));
+        t1.v[13] = fmaf(S2r1, cim.z, fmaf(S2i1, cre.z, t1.v[13]));
+    }
+}
+
+template <bool TWO>
+__device__ __forceinline__ void tile_body(const Stage& st, int ntri, int skip_tl, float dx, float dy, float dz,
+                                          float nx, float ny, float nz, float4 c0, float4 c1, SlotK k0, SlotK k1,
+                                          Acc& a0, Acc& a1) {
+    const float D2x = c0.x, D2y = c0.y, D2z = c0.z, Rc2 = c0.w, Rc = c1.x, th0 = c1.y, th1 = c1.z;
+    const float Xx = dx + 0.5f * D2x, Xy = dy + 0.5f * D2y, Xz = dz + 0.5f * D2z;  // x - c_source
+    const float nX = nx * Xx + ny * Xy + nz * Xz;
+    Acc t0, t1;
+#pragma unroll
+    for (int c = 0; c < NCOMP; c++) {
+        t0.v[c] = 0.f;
+        if constexpr (TWO) t1.v[c] = 0.f;
+    }
+    for (int tl = 0; tl < ntri; tl++) {
+        if (tl == skip_tl) continue;  // identical triangle: near-field correction only
+        triangle_body<TWO>(st, tl, dx, dy, dz, nx, ny, nz, D2x, D2y, D2z, Rc2, Rc, nX, Xx, Xy, Xz, th0, th1, k0,
+                           k1, t0, t1);
+    }
+#pragma unroll
+    for (int c = 0; c < NCOMP; c++) {
+        a0.v[c] += t0.v[c];
+        if constexpr (TWO) a1.v[c] += t1.v[c];
+    }
+}
+
+__global__ void __launch_bounds__(TP, 2) far32_kernel(FarArgs32 A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    Stage* stage = reinterpret_cast<Stage*>(smem);
+    float4* tab = reinterpret_cast<float4*>(smem + 2 * sizeof(Stage));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * sizeof(Stage) + 2 * CHUNK_MAX * sizeof(float4));
+
+    const int tid = threadIdx.x;
+    const int tt = A.tgt_begin + blockIdx.x;
+    const int sb = A.src_begin + blockIdx.y * A.chunk_tiles;
+    const int se = min(sb + A.chunk_tiles, A.src_end);
+    const int nsrc = max(0, se - sb);
+
+    const int64_t p = (int64_t)tt * TP + tid;
+    const float4 g = A.pg[p];
+    const int mt = tid / QP;
+    const float4 ng = A.tg[(int64_t)tt * TT + mt];
+    const double4 ct = A.tc[tt];
+    const int mydom = A.tdom[tt];
+    const int2 dr = A.dom_tiles[mydom];
+    const double2 kj = A.kdom[mydom];
+    SlotK k0{(float)A.k0.x, (float)-A.k0.y, (float)(-A.k0.y * 1.4426950408889634)};
+    SlotK k1{(float)kj.x, (float)-kj.y, (float)(-kj.y * 1.4426950408889634)};
+
+    // tile-pair table: 2D, R_c^2, R_c and the FP64-reduced phases
+    for (int i = tid; i < nsrc; i += TP) {
+        const int s = sb + i;
+        const double4 cs = A.tc[s];
+        const double Dx = ct.x - cs.x, Dy = ct.y - cs.y, Dz = ct.z - cs.z;
+        const double R = sqrt(Dx * Dx + Dy * Dy + Dz * Dz);
+        const bool own = A.slot1 && s >= dr.x && s < dr.y;
+        tab[2 * i] = make_float4((float)(2 * Dx), (float)(2 * Dy), (float)(2 * Dz), (float)(R * R));
+        tab[2 * i + 1] = make_float4((float)R, reduce_phase(A.k0.x * R), own ? reduce_phase(kj.x * R) : 0.f, 0.f);
+    }
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    auto issue = [&](int i, int buf) {
+        const int s = sb + i;
+        Stage& S = stage[buf];
+        mbar_arrive_expect_tx(&bars[buf], STAGE_BYTES);
+        bulk_g2s(S.pg, A.pg + (int64_t)s * TP, TP * 16, &bars[buf]);
+        bulk_g2s(S.pd, A.pd + (int64_t)s * TP, TP * 16, &bars[buf]);
+        bulk_g2s(S.tg, A.tg + (int64_t)s * TT, TT * 16, &bars[buf]);
+        bulk_g2s(S.tc, A.tcurl + (int64_t)s * 2 * TT, 2 * TT * 16, &bars[buf]);
+    };
+    if (tid == 0) {
+        if (nsrc > 0) issue(0, 0);
+        if (nsrc > 1) issue(1, 1);
+    }
+
+    Acc a0, a1;
+#pragma unroll
+    for (int c = 0; c < NCOMP; c++) {
+        a0.v[c] = 0.f;
+        a1.v[c] = 0.f;
+    }
+    for (int i = 0; i < nsrc; i++) {
+        const int buf = i & 1;
+        mbar_wait_bounded(&bars[buf], (uint32_t)((i >> 1) & 1), A.err);
+        const int s = sb + i;
+        const Stage& st = stage[buf];
+        const int ntri = A.tntri[s];
+        const int skip = (s == tt) ? mt : -1;
+        const float4 c0 = tab[2 * i], c1 = tab[2 * i + 1];
+        if (A.slot1 && s >= dr.x && s < dr.y)
+            tile_body<true>(st, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
+        else
+            tile_body<false>(st, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
+        __syncthreads();
+        if (tid == 0 && i + 2 < nsrc) issue(i + 2, buf);
+    }
+
+    float* out = A.partial + (int64_t)blockIdx.y * 2 * NCOMP * A.n_pts;
+#pragma unroll
+    for (int c = 0; c < NCOMP; c++) {
+        out[(int64_t)c * A.n_pts + p] = a0.v[c];
+        out[(int64_t)(NCOMP + c) * A.n_pts + p] = a1.v[c];
+    }
+}
+
+size_t far32_smem_bytes() { return 2 * sizeof(Stage) + 2 * CHUNK_MAX * sizeof(float4) + 2 * sizeof(uint64_t); }
+
+cudaError_t launch_far32(const FarArgs32& a, int n_tgt_tiles, int n_chunks, cudaStream_t s) {
+    static bool attr = false;
+    size_t smem = far32_smem_bytes();
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(far32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (n_tgt_tiles <= 0 || n_chunks <= 0) return cudaSuccess;
+    far32_kernel<<<dim3(n_tgt_tiles, n_chunks), TP, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- FP64 far field
+
+__global__ void __launch_bounds__(TP) far64_kernel(FarArgs64 A) {
+    const int tid = threadIdx.x;
+    const int tt = A.tgt_begin + blockIdx.x;
+    const int sb = A.src_begin + blockIdx.y * A.chunk_tiles;
+    const int se = min(sb + A.chunk_tiles, A.src_end);
+    const int64_t p = (int64_t)tt * TP + tid;
+    const double4 g = A.pg[p];
+    const int mt = tid / QP;
+    const double4 ng = A.tg[(int64_t)tt * TT + mt];
+    const double4 ct = A.tc[tt];
+    const int mydom = A.tdom[tt];
+    const int2 dr = A.dom_tiles[mydom];
+    double2 ks[2] = {A.k0, A.kdom[mydom]};
+    double acc[2][NCOMP];
+    for (int sl = 0; sl < 2; sl++)
+        for (int c = 0; c < NCOMP; c++) acc[sl][c] = 0.0;
+    for (int s = sb; s < se; s++) {
+        const double4 cs = A.tc[s];
+        const double Dx = ct.x - cs.x, Dy = ct.y - cs.y, Dz = ct.z - cs.z;
+        const double Xx = g.x + Dx, Xy = g.y + Dy, Xz = g.z + Dz;  // x - c_source
+        const int ntri = A.tntri[s];
+        const int nsl = (A.slot1 && s >= dr.x && s < dr.y) ? 2 : 1;
+        for (int tl = 0; tl < ntri; tl++) {
+            if (s == tt && tl == mt) continue;
+            const int64_t ts = (int64_t)s * TT + tl;
+            const double4 tg = A.tg[ts];
+            const double4 cre = A.tcurl[2 * ts], cim = A.tcurl[2 * ts + 1];
+            const double fK = tg.w - (tg.x * Xx + tg.y * Xy + tg.z * Xz);
+            const double nn = ng.x * tg.x + ng.y * tg.y + ng.z * tg.z;
+            for (int sl = 0; sl < nsl; sl++) {
+                const double kr = ks[sl].x, ki = ks[sl].y;
+                double S1r = 0, S1i = 0, S2r = 0, S2i = 0, S3r = 0, S3i = 0;
+                for (int q = 0; q < QP; q++) {
+                    const double4 y = A.pg[ts * QP + q];
+                    const double4 d = A.pd[ts * QP + q];
+                    const double ex = Xx - y.x, ey = Xy - y.y, ez = Xz - y.z;  // x - y
+                    const double r = sqrt(ex * ex + ey * ey + ez * ez);
+                    const double rinv = 1.0 / r;
+                    double sn, cs2;
+                    sincos(kr * r, &sn, &cs2);
+                    const double a = exp(-ki * r) * rinv;
+                    const double Gr = a * cs2, Gi = a * sn;
+                    const double u = -ki - rinv;
+                    const double Fr = (Gr * u - Gi * kr) * rinv, Fi = (Gr * kr + Gi * u) * rinv;
+                    const double ndot = ng.x * ex + ng.y * ey + ng.z * ez;
+                    acc[sl][0] += Gr * d.x - Gi * d.y;
+                    acc[sl][1] += Gr * d.y + Gi * d.x;
+                    acc[sl][4] += ndot * (Fr * d.x - Fi * d.y);
+                    acc[sl][5] += ndot * (Fr * d.y + Fi * d.x);
+                    S1r += Fr * d.z - Fi * d.w;
+                    S1i += Fr * d.w + Fi * d.z;
+                    S2r += Gr * y.w;
+                    S2i += Gi * y.w;
+                    S3r += Gr * d.z - Gi * d.w;
+                    S3i += Gr * d.w + Gi * d.z;
+                }
+                acc[sl][2] += fK * S1r;
+                acc[sl][3] += fK * S1i;
+                acc[sl][6] += nn * S3r;
+                acc[sl][7] += nn * S3i;
+                acc[sl][8] += S2r * cre.x - S2i * cim.x;
+                acc[sl][9] += S2r * cre.y - S2i * cim.y;
+                acc[sl][10] += S2r * cre.z - S2i * cim.z;
+                acc[sl][11] += S2r * cim.x + S2i * cre.x;
+                acc[sl][12] += S2r * cim.y + S2i * cre.y;
+                acc[sl][13] += S2r * cim.z + S2i * cre.z;
+            }
+        }
+    }
+    double* out = A.partial + (int64_t)blockIdx.y * 2 * NCOMP * A.n_pts;
+    for (int sl = 0; sl < 2; sl++)
+        for (int c = 0; c < NCOMP; c++) out[(int64_t)(sl * NCOMP + c) * A.n_pts + p] = acc[sl][c];
+}
+
+cudaError_t launch_far64(const FarArgs64& a, int n_tgt_tiles, int n_chunks, cudaStream_t s) {
+    if (n_tgt_tiles <= 0 || n_chunks <= 0) return cudaSuccess;
+    far64_kernel<<<dim3(n_tgt_tiles, n_chunks), TP, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- projection onto P1 test functions
+
+__global__ void project_kernel(ProjectArgs a) {
+    const int64_t s = (int64_t)a.tgt_begin * TT + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (int64_t)a.tgt_end * TT) return;
+    const int4 v = a.slot_v[s];
+    if (v.x < 0) return;
+    const int dom = v.w;
+    const double inv4pi = 0.07957747154594767;
+    double r1[3][2] = {{0, 0}, {0, 0}, {0, 0}}, r2[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int sl = 0; sl < 2; sl++) {
+        const SlotCoef cf = a.coef[dom * 2 + sl];
+        if (cf.cV == 0 && cf.cK == 0 && cf.cKp == 0 && cf.cW == 0) continue;
+        double wc[6] = {0, 0, 0, 0, 0, 0};
+        for (int q = 0; q < QP; q++) {
+            const int64_t p = s * QP + q;
+            double P[NCOMP];
+            for (int c = 0; c < NCOMP; c++) {
+                double sum = 0;
+                for (int ch = 0; ch < a.n_chunks; ch++) {
+                    const int64_t idx = ((int64_t)(ch * 2 + sl) * NCOMP + c) * a.n_pts + p;
+                    sum += a.partial32 ? (double)a.partial32[idx] : a.partial64[idx];
+                }
+                P[c] = sum;
+            }
+            const double w = a.pt_w[p] * inv4pi;
+            // row1 potential: cV PV - cK PK ; row2 (pointwise part): cKp PKp - cW k^2 PWm
+            const double t1r = cf.cV * P[0] - cf.cK * P[2], t1i = cf.cV * P[1] - cf.cK * P[3];
+            const double kwr = cf.k2re * P[6] - cf.k2im * P[7], kwi = cf.k2re * P[7] + cf.k2im * P[6];
+            const double t2r = cf.cKp * P[4] - cf.cW * kwr, t2i = cf.cKp * P[5] - cf.cW * kwi;
+            for (int k = 0; k < 3; k++) {
+                const double wl = w * a.lam[q][k];
+                r1[k][0] += wl * t1r;
+                r1[k][1] += wl * t1i;
+                r2[k][0] += wl * t2r;
+                r2[k][1] += wl * t2i;
+            }
+            for (int c = 0; c < 6; c++) wc[c] += w * P[8 + c];
+        }
+        for (int k = 0; k < 3; k++) {
+            const double* cu = &a.slot_curl[s * 9 + 3 * k];
+            r2[k][0] += cf.cW * (cu[0] * wc[0] + cu[1] * wc[1] + cu[2] * wc[2]);
+            r2[k][1] += cf.cW * (cu[0] * wc[3] + cu[1] * wc[4] + cu[2] * wc[5]);
+        }
+    }
+    // touching pairs: combined 3x3 sub-blocks (row1<-psi, row1<-phi, row2<-psi, row2<-phi)
+    if (a.np_ptr) {
+        for (int64_t pi = a.np_ptr[s]; pi < a.np_ptr[s + 1]; pi++) {
+            const int4 vt = a.slot_v[a.np_src[pi]];
+            const int vid[3] = {vt.x, vt.y, vt.z};
+            double2 xs[3], xf[3];
+            for (int b = 0; b < 3; b++) {
+                xs[b] = a.x[a.v_dof1[vid[b]]];
+                xf[b] = a.x[a.v_dof2[vid[b]]];
+            }
+            for (int blk = 0; blk < 4; blk++)
+                for (int k = 0; k < 3; k++)
+                    for (int b = 0; b < 3; b++) {
+                        double br, bi;
+                        if (a.nb32) {
+                            const float2 B = a.nb32[(pi * 4 + blk) * 9 + 3 * k + b];
+                            br = B.x;
+                            bi = B.y;
+                        } else {
+                            const double2 B = a.nb64[(pi * 4 + blk) * 9 + 3 * k + b];
+                            br = B.x;
+                            bi = B.y;
+                        }
+                        const double2 xv = (blk & 1) ? xf[b] : xs[b];
+                        double* dst = blk < 2 ? r1[k] : r2[k];
+                        dst[0] += br * xv.x - bi * xv.y;
+                        dst[1] += br * xv.y + bi * xv.x;
+                    }
+        }
+    }
+    for (int k = 0; k < 3; k++) {
+        a.tri_out[(s * 3 + k) * 2] = make_double2(r1[k][0], r1[k][1]);
+        a.tri_out[(s * 3 + k) * 2 + 1] = make_double2(r2[k][0], r2[k][1]);
+    }
+}
+
+cudaError_t launch_project(const ProjectArgs& a, cudaStream_t s) {
+    int64_t n = (int64_t)(a.tgt_end - a.tgt_begin) * TT;
+    if (n <= 0) return cudaSuccess;
+    project_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- vertex reduction
+
+__global__ void reduce_kernel(ReduceArgs a) {
+    const int64_t v = a.v_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.v_end) return;
+    double s1r = 0, s1i = 0, s2r = 0, s2i = 0;
+    for (int64_t i = a.vc_ptr[v]; i < a.vc_ptr[v + 1]; i++) {
+        const int64_t c = a.vc_idx[i];
+        const double2 u = a.tri_out[c * 2], w = a.tri_out[c * 2 + 1];
+        s1r += u.x;
+        s1i += u.y;
+        s2r += w.x;
+        s2i += w.y;
+    }
+    a.y[a.v_dof1[v]] = make_double2(s1r, s1i);
+    a.y[a.v_dof2[v]] = make_double2(s2r, s2i);
+}
+
+cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t s) {
+    int64_t n = a.v_end - a.v_begin;
+    if (n <= 0) return cudaSuccess;
+    reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s) {
+    int64_t n = a.s_end - a.s_begin;
+    if (n <= 0) return cudaSuccess;
+    gather_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gbem
