@@ -43,6 +43,9 @@ def workload(name):
     if name == "rib":
         s = scenes.rib_scene()
         desc = "rib/fat/liver scene, 0.5 MHz, ~41k triangles (5 capsule ribs as one bone domain, fat slab, liver)"
+    elif name == "rib_small":
+        s = scenes.rib_scene(h=6e-3)
+        desc = "rib/fat/liver scene at 6 mm element size (~8k triangles; profiling case)"
     elif name == "kidney":
         s = scenes.kidney_scene()
         desc = "kidney + perinephric fat shell, 1 MHz, ~62k triangles"
@@ -182,8 +185,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rib", choices=["rib", "kidney", "sphere"])
-    ap.add_argument("--ref-rows", type=int, default=3)
+    ap.add_argument("--workload", default="rib", choices=["rib", "rib_small", "kidney", "sphere"])
+    ap.add_argument("--ref-rows", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
