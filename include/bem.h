@@ -118,6 +118,27 @@ int bem_apply(bem_ctx* ctx, int op, const bem_z* x, bem_z* y, int64_t n_rhs, int
 int bem_apply_block(bem_ctx* ctx, int32_t test_domain, int32_t trial_domain, bem_z k, const bem_z* x, bem_z* y,
                     int precision, int on_device);
 
+/* Allocation-free variant of bem_apply(BEM_OP_AHAT, BEM_PREC_FP32) for one
+ * vector.  The paper has no counterpart: this exists for callers that
+ * cannot let the library allocate device memory during the call, such as a
+ * process whose device memory is reserved by another allocator or a
+ * latency-critical loop that must not enter the CUDA allocator.
+ * x, y: device pointers (N complex each, system order, must not overlap),
+ * work queued on the context's stream, no synchronisation.
+ * The context must already be prepared by an earlier allocating call
+ * (bem_apply on it); otherwise BEM_ERR_STATE, and nothing is allocated.
+ * The far-field scratch is a fixed 64 MiB array inside the library (held on
+ * every GPU that loads the library until exit); target tiles are processed
+ * in batches that fit it.  A problem whose single target tile needs more than
+ * that scratch is rejected with BEM_ERR_OUT_OF_BUDGET.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (other streams or other
+ * contexts on the same device) race on it and must be serialised by the
+ * caller.  The scratch is fully rewritten by every call; nothing needs to be
+ * cleared between calls. */
+int bem_apply_noalloc(bem_ctx* ctx, const bem_z* x, bem_z* y);
+
 /* Incident field: a plane wave amp * exp(i k0 d.x) (d normalised here). */
 int bem_set_plane_wave(bem_ctx* ctx, const double dir[3], bem_z amp);
 
