@@ -145,6 +145,7 @@ int bem_ctx::finalize() {
     d.err = (int*)dalloc(sizeof(int), &rc); if (rc) return rc;
     d.xs = (double2*)dalloc(g.n_dof * sizeof(double2), &rc); if (rc) return rc;
     d.ys = (double2*)dalloc(g.n_dof * sizeof(double2), &rc); if (rc) return rc;
+    d.ys2 = (double2*)dalloc(g.n_dof * sizeof(double2), &rc); if (rc) return rc;
     CK(cudaMemsetAsync(d.err, 0, sizeof(int), stream));
     ready = true;
     return upload_materials();

@@ -6,8 +6,13 @@
 #include <cmath>
 #include <cstring>
 
+#include <chrono>
+#include <complex>
+#include <vector>
+
 #include "ctx.h"
 #include "internal.h"
+#include "krylov.h"
 
 using namespace gbem;
 
@@ -67,15 +72,196 @@ __global__ void plane_wave_kernel(PlaneWaveArgs a) {
     }
 }
 
+struct PistonArgs {
+    const double4* pg;   // (dx, dy, dz, w)
+    const double4* tc;
+    const int4* slot_v;
+    const double* slot_n;
+    const double4* disc; // [n_elem * nq] (x, y, z, weight)
+    int n_elem, nq;
+    const double2* w;    // [n_rhs][n_elem] piston weights
+    int n_rhs;
+    double2 k0;
+    double2 pref;        // -i omega rho0 / (2 pi)
+    int64_t n_slots;
+    double lam[QP][3];
+    double2* tri_out;    // [n_rhs][n_slots*3][2]
+};
+
+// Per slot and excitation: <p_inc, phi_k> and <dp_inc/dn, phi_k> with the
+// Rayleigh sum over piston discs (baffled-piston reading of the transducer
+// field; the paper defers it to its ref. elwin2015, Sec. 3.2).
+__global__ void piston_kernel(PistonArgs a) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int rhs = blockIdx.y;
+    if (s >= a.n_slots) return;
+    if (a.slot_v[s].x < 0) return;
+    const double4 c = a.tc[s / TT];
+    const double nx = a.slot_n[3 * s], ny = a.slot_n[3 * s + 1], nz = a.slot_n[3 * s + 2];
+    const double2* wr = a.w + (int64_t)rhs * a.n_elem;
+    double r[3][2][2] = {};
+    for (int q = 0; q < QP; q++) {
+        const double4 g = a.pg[s * QP + q];
+        const double x = c.x + g.x, y = c.y + g.y, z = c.z + g.z;
+        double pr = 0, pi = 0, dr = 0, di = 0;
+        for (int m = 0; m < a.n_elem; m++) {
+            double er = 0, ei = 0, fr = 0, fi = 0;
+            for (int j = 0; j < a.nq; j++) {
+                const double4 d = a.disc[(int64_t)m * a.nq + j];
+                const double ex = x - d.x, ey = y - d.y, ez = z - d.z;
+                const double R = sqrt(ex * ex + ey * ey + ez * ez);
+                const double Ri = 1.0 / R;
+                double sn, cs;
+                sincos(a.k0.x * R, &sn, &cs);
+                const double amp = exp(-a.k0.y * R) * Ri * d.w;
+                const double gr = amp * cs, gi = amp * sn;          // w exp(ikR)/R
+                er += gr;
+                ei += gi;
+                // d/dn: exp(ikR)/R (ik - 1/R) (x-y).n / R
+                const double ur = -a.k0.y - Ri, ui = a.k0.x;
+                const double dn = (ex * nx + ey * ny + ez * nz) * Ri;
+                fr += (gr * ur - gi * ui) * dn;
+                fi += (gr * ui + gi * ur) * dn;
+            }
+            const double2 wm = wr[m];
+            pr += wm.x * er - wm.y * ei;
+            pi += wm.x * ei + wm.y * er;
+            dr += wm.x * fr - wm.y * fi;
+            di += wm.x * fi + wm.y * fr;
+        }
+        const double Pr = a.pref.x * pr - a.pref.y * pi, Pi = a.pref.x * pi + a.pref.y * pr;
+        const double Dr = a.pref.x * dr - a.pref.y * di, Di = a.pref.x * di + a.pref.y * dr;
+        for (int k = 0; k < 3; k++) {
+            const double wl = g.w * a.lam[q][k];
+            r[k][0][0] += wl * Pr;
+            r[k][0][1] += wl * Pi;
+            r[k][1][0] += wl * Dr;
+            r[k][1][1] += wl * Di;
+        }
+    }
+    double2* out = a.tri_out + (int64_t)rhs * a.n_slots * 6;
+    for (int k = 0; k < 3; k++) {
+        out[(s * 3 + k) * 2] = make_double2(r[k][0][0], r[k][0][1]);
+        out[(s * 3 + k) * 2 + 1] = make_double2(r[k][1][0], r[k][1][1]);
+    }
+}
+
+struct SolveState {
+    Krylov kry;
+    double2* b = nullptr;       // [n_rhs][N]
+    double2* u = nullptr;       // [n_rhs][N] solutions
+    double2* r = nullptr;       // work
+    double2* d = nullptr;       // work
+    double2* pb = nullptr;      // work
+    double2* tri_rhs = nullptr; // [n_rhs][n_slots*6]
+    double4* disc = nullptr;
+    double2* wdev = nullptr;
+    int64_t n_rhs_alloc = 0;
+    int64_t n_rhs_solved = 0;
+};
+
 }  // namespace gbem
 
-int bem_ctx::apply_prec(const double2*, double2*) {
-    return fail(BEM_ERR_STATE, "the OSRC preconditioner is not available in this build");
+// Right-hand sides of every excitation into S->b (device).
+static int build_rhs(bem_ctx* ctx) {
+    const Geometry& g = ctx->geo;
+    SolveState* S = ctx->solve;
+    const int64_t N = g.n_dof, nr = ctx->field_kind == 2 ? ctx->n_rhs : 1;
+    int rc;
+    if (S->n_rhs_alloc < nr) {
+        for (void* p : {(void*)S->b, (void*)S->u, (void*)S->tri_rhs}) ctx->dfree(p);
+        S->b = (double2*)ctx->dalloc(nr * N * sizeof(double2), &rc); if (rc) return rc;
+        S->u = (double2*)ctx->dalloc(nr * N * sizeof(double2), &rc); if (rc) return rc;
+        S->tri_rhs = (double2*)ctx->dalloc(nr * g.n_slots * 6 * sizeof(double2), &rc); if (rc) return rc;
+        S->n_rhs_alloc = nr;
+    }
+    if (ctx->field_kind == 1) {
+        PlaneWaveArgs a{};
+        a.pg = ctx->dev.pg64; a.tc = ctx->dev.tc; a.slot_v = ctx->dev.slot_v; a.slot_n = ctx->dev.slot_n;
+        for (int i = 0; i < 3; i++) a.d[i] = ctx->pw_dir[i];
+        a.amp = make_double2(ctx->pw_amp[0], ctx->pw_amp[1]);
+        a.k0 = make_double2(ctx->k0re, ctx->k0im);
+        a.n_slots = g.n_slots;
+        for (int q = 0; q < QP; q++)
+            for (int k = 0; k < 3; k++) a.lam[q][k] = ctx->quad.lam[q][k];
+        a.tri_out = S->tri_rhs;
+        CK(cudaMemsetAsync(S->tri_rhs, 0, g.n_slots * 6 * sizeof(double2), ctx->stream));
+        plane_wave_kernel<<<(unsigned)((g.n_slots + 127) / 128), 128, 0, ctx->stream>>>(a);
+        ctx->launches++;
+    } else if (ctx->field_kind == 2) {
+        // piston disc points: n_r Gauss radii x n_t angles per piston
+        const int n_r = 4, n_t = 8, nq = n_r * n_t;
+        const int64_t ne = (int64_t)ctx->tr_r.size();
+        std::vector<double> gx, gw;
+        gauss_legendre01(n_r, gx, gw);
+        std::vector<double4> disc(ne * nq);
+        for (int64_t m = 0; m < ne; m++) {
+            const double* c = &ctx->tr_c[3 * m];
+            const double* nn = &ctx->tr_n[3 * m];
+            const double a = ctx->tr_r[m];
+            const double ax[3] = {std::fabs(nn[2]) > 0.9 ? 1.0 : 0.0, 0.0, std::fabs(nn[2]) > 0.9 ? 0.0 : 1.0};
+            double e1[3] = {ax[1] * nn[2] - ax[2] * nn[1], ax[2] * nn[0] - ax[0] * nn[2], ax[0] * nn[1] - ax[1] * nn[0]};
+            const double l = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+            for (int i = 0; i < 3; i++) e1[i] /= l;
+            const double e2[3] = {nn[1] * e1[2] - nn[2] * e1[1], nn[2] * e1[0] - nn[0] * e1[2], nn[0] * e1[1] - nn[1] * e1[0]};
+            for (int i = 0; i < n_r; i++)
+                for (int j = 0; j < n_t; j++) {
+                    const double th = 2.0 * M_PI * (j + 0.5) / n_t, rr = a * gx[i];
+                    const double w = gw[i] * gx[i] * (2.0 * M_PI / n_t) * a * a;
+                    double4& d = disc[m * nq + i * n_t + j];
+                    d.x = c[0] + rr * (std::cos(th) * e1[0] + std::sin(th) * e2[0]);
+                    d.y = c[1] + rr * (std::cos(th) * e1[1] + std::sin(th) * e2[1]);
+                    d.z = c[2] + rr * (std::cos(th) * e1[2] + std::sin(th) * e2[2]);
+                    d.w = w;
+                }
+        }
+        ctx->dfree(S->disc);
+        ctx->dfree(S->wdev);
+        S->disc = (double4*)ctx->dalloc(disc.size() * sizeof(double4), &rc); if (rc) return rc;
+        S->wdev = (double2*)ctx->dalloc(ctx->tr_w.size() * sizeof(double), &rc); if (rc) return rc;
+        CK(cudaMemcpyAsync(S->disc, disc.data(), disc.size() * sizeof(double4), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(S->wdev, ctx->tr_w.data(), ctx->tr_w.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        PistonArgs a{};
+        a.pg = ctx->dev.pg64; a.tc = ctx->dev.tc; a.slot_v = ctx->dev.slot_v; a.slot_n = ctx->dev.slot_n;
+        a.disc = S->disc; a.n_elem = (int)ne; a.nq = nq; a.w = S->wdev; a.n_rhs = (int)nr;
+        a.k0 = make_double2(ctx->k0re, ctx->k0im);
+        a.pref = make_double2(0.0, -ctx->omega_rho0 / (2.0 * M_PI));
+        a.n_slots = g.n_slots;
+        for (int q = 0; q < QP; q++)
+            for (int k = 0; k < 3; k++) a.lam[q][k] = ctx->quad.lam[q][k];
+        a.tri_out = S->tri_rhs;
+        CK(cudaMemsetAsync(S->tri_rhs, 0, nr * g.n_slots * 6 * sizeof(double2), ctx->stream));
+        piston_kernel<<<dim3((unsigned)((g.n_slots + 63) / 64), (unsigned)nr), 64, 0, ctx->stream>>>(a);
+        ctx->launches++;
+    } else {
+        return ctx->fail(BEM_ERR_STATE, "no incident field set");
+    }
+    CK(cudaGetLastError());
+    for (int64_t r = 0; r < nr; r++) {
+        ReduceArgs ra{};
+        ra.vc_ptr = ctx->dev.vc_ptr; ra.vc_idx = ctx->dev.vc_idx; ra.v_dof1 = ctx->dev.v_dof1;
+        ra.v_dof2 = ctx->dev.v_dof2; ra.tri_out = S->tri_rhs + r * g.n_slots * 6; ra.v_begin = 0;
+        ra.v_end = g.n_vert; ra.y = S->b + r * N;
+        CK(launch_reduce(ra, ctx->stream));
+        ctx->launches++;
+    }
+    ctx->rhs_ready = true;
+    return BEM_OK;
 }
 
-int bem_ctx::apply_prec_ahat(const double2*, double2*, int) {
-    return fail(BEM_ERR_STATE, "the OSRC preconditioner is not available in this build");
+static int ensure_solve_state(bem_ctx* ctx) {
+    if (!ctx->solve) ctx->solve = new SolveState();
+    SolveState* S = ctx->solve;
+    const int64_t N = ctx->geo.n_dof;
+    int rc;
+    if (!S->r) {
+        S->r = (double2*)ctx->dalloc(N * sizeof(double2), &rc); if (rc) return rc;
+        S->d = (double2*)ctx->dalloc(N * sizeof(double2), &rc); if (rc) return rc;
+        S->pb = (double2*)ctx->dalloc(N * sizeof(double2), &rc); if (rc) return rc;
+    }
+    return BEM_OK;
 }
+
 
 extern "C" {
 
@@ -122,31 +308,12 @@ int bem_rhs(bem_ctx* ctx, bem_z* b, int on_device) {
     CK(cudaSetDevice(ctx->device));
     int rc = ctx->finalize();
     if (rc) return rc;
-    if (ctx->field_kind != 1) return ctx->fail(BEM_ERR_STATE, "no plane wave set (transducer right-hand sides are not available in this build)");
-    const Geometry& g = ctx->geo;
-    PlaneWaveArgs a{};
-    a.pg = ctx->dev.pg64;
-    a.tc = ctx->dev.tc;
-    a.slot_v = ctx->dev.slot_v;
-    a.slot_n = ctx->dev.slot_n;
-    for (int i = 0; i < 3; i++) a.d[i] = ctx->pw_dir[i];
-    a.amp = make_double2(ctx->pw_amp[0], ctx->pw_amp[1]);
-    a.k0 = make_double2(ctx->k0re, ctx->k0im);
-    a.n_slots = g.n_slots;
-    for (int q = 0; q < QP; q++)
-        for (int k = 0; k < 3; k++) a.lam[q][k] = ctx->quad.lam[q][k];
-    a.tri_out = ctx->dev.tri_out;
-    plane_wave_kernel<<<(unsigned)((g.n_slots + 127) / 128), 128, 0, ctx->stream>>>(a);
-    CK(cudaGetLastError());
-    ReduceArgs ra{};
-    ra.vc_ptr = ctx->dev.vc_ptr; ra.vc_idx = ctx->dev.vc_idx; ra.v_dof1 = ctx->dev.v_dof1; ra.v_dof2 = ctx->dev.v_dof2;
-    ra.tri_out = ctx->dev.tri_out; ra.v_begin = 0; ra.v_end = g.n_vert;
-    ra.y = on_device ? (double2*)b : ctx->dev.ys;
-    CK(launch_reduce(ra, ctx->stream));
-    if (!on_device) {
-        CK(cudaMemcpyAsync(b, ctx->dev.ys, g.n_dof * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
-    }
+    if ((rc = ensure_solve_state(ctx))) return rc;
+    if ((rc = build_rhs(ctx))) return rc;
+    const int64_t n = (ctx->field_kind == 2 ? ctx->n_rhs : 1) * ctx->geo.n_dof;
+    CK(cudaMemcpyAsync(b, ctx->solve->b, n * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
     return BEM_OK;
 }
 
@@ -163,14 +330,118 @@ int bem_default_solve_opts(bem_solve_opts* o) {
     return BEM_OK;
 }
 
-int bem_solve(bem_ctx* ctx, const bem_solve_opts*, bem_solve_report*) {
+int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     if (!ctx) return BEM_ERR_INVALID_ARG;
-    return ctx->fail(BEM_ERR_STATE, "bem_solve is not available in this build");
+    bem_solve_opts o;
+    bem_default_solve_opts(&o);
+    if (opts) o = *opts;
+    if (o.restart < 1 || o.max_iter < 1 || !(o.tol > 0) || (o.precision != BEM_PREC_FP64 && o.precision != BEM_PREC_FP32))
+        return ctx->fail(BEM_ERR_INVALID_ARG, "bad solve options");
+    CK(cudaSetDevice(ctx->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = ctx->finalize();
+    if (rc) return rc;
+    if ((rc = ctx->ensure_near())) return rc;
+    if ((rc = ensure_solve_state(ctx))) return rc;
+    if ((rc = build_rhs(ctx))) return rc;
+    SolveState* S = ctx->solve;
+    const int64_t N = ctx->geo.n_dof, nr = ctx->field_kind == 2 ? ctx->n_rhs : 1;
+    if ((rc = S->kry.ensure(ctx, N, o.restart))) return rc;
+    bem_solve_report R{};
+    bool converged = true;
+    auto op_for = [&](int prec) {
+        return [ctx, prec, &o](const double2* x, double2* y) -> int {
+            return o.precondition ? ctx->apply_prec_ahat(x, y, prec) : ctx->apply_ahat(x, y, prec);
+        };
+    };
+    for (int64_t r = 0; r < nr; r++) {
+        const double2* b = S->b + r * N;
+        double2* u = S->u + r * N;
+        double bnorm;
+        if ((rc = S->kry.norm(ctx, b, &bnorm))) return rc;
+        // right-hand side of the system GMRES sees
+        auto rhs_of = [&](const double2* v) -> const double2* {
+            if (!o.precondition) return v;
+            rc = ctx->apply_prec(v, S->pb);
+            return S->pb;
+        };
+        if (o.precision == BEM_PREC_FP64) {
+            // plain FP64: GMRES on (P) A_hat u = (P) b until the true residual meets tol
+            CK(cudaMemsetAsync(u, 0, N * sizeof(double2), ctx->stream));
+            const double2* sb = rhs_of(b);
+            if (rc) return rc;
+            int it = 0;
+            double rel = 1;
+            double inner = o.tol;
+            for (int attempt = 0; attempt < 4; attempt++) {
+                int its = 0;
+                if ((rc = S->kry.gmres(ctx, op_for(BEM_PREC_FP64), sb, u, o.restart, inner, o.max_iter - it, &its, &rel,
+                                       attempt == 0)))
+                    return rc;
+                it += its;
+                // true FP64 residual of the unpreconditioned system
+                if ((rc = ctx->apply_ahat(u, S->r, BEM_PREC_FP64))) return rc;
+                if ((rc = S->kry.axpby(ctx, 1.0, b, -1.0, S->r, S->r))) return rc;
+                double rn;
+                if ((rc = S->kry.norm(ctx, S->r, &rn))) return rc;
+                rel = rn / bnorm;
+                if (rel <= o.tol || it >= o.max_iter) break;
+                inner *= 0.1;
+            }
+            R.iterations += it;
+            R.residual = std::max(R.residual, rel);
+            converged &= rel <= o.tol;
+        } else {
+            // mixed: FP32 inner GMRES, FP64 residual refinement
+            CK(cudaMemsetAsync(u, 0, N * sizeof(double2), ctx->stream));
+            CK(cudaMemcpyAsync(S->r, b, N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+            double rel = 1.0;
+            int it = 0, ref = 0;
+            for (; ref <= o.max_refine; ref++) {
+                double rn;
+                if ((rc = S->kry.norm(ctx, S->r, &rn))) return rc;
+                rel = rn / bnorm;
+                if (rel <= o.tol || it >= o.max_iter) break;
+                if (ref == o.max_refine) break;
+                const double2* sr = rhs_of(S->r);
+                if (rc) return rc;
+                int its = 0;
+                double irel = 0;
+                if ((rc = S->kry.gmres(ctx, op_for(BEM_PREC_FP32), sr, S->d, o.restart, o.inner_tol, o.max_iter - it,
+                                       &its, &irel, true)))
+                    return rc;
+                it += its;
+                if ((rc = S->kry.axpby(ctx, 1.0, u, 1.0, S->d, u))) return rc;
+                if ((rc = ctx->apply_ahat(u, S->r, BEM_PREC_FP64))) return rc;
+                if ((rc = S->kry.axpby(ctx, 1.0, b, -1.0, S->r, S->r))) return rc;
+            }
+            R.iterations += it;
+            R.refinements += ref;
+            R.residual = std::max(R.residual, rel);
+            converged &= rel <= o.tol;
+        }
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    if ((rc = ctx->check_device_error())) return rc;
+    S->n_rhs_solved = nr;
+    R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) *rep = R;
+    if (!converged) return ctx->fail(BEM_ERR_NOT_CONVERGED, "GMRES did not reach the requested residual");
+    return BEM_OK;
 }
 
-int bem_get_traces(bem_ctx* ctx, int32_t, int64_t, bem_z*, bem_z*, int) {
+int bem_get_traces(bem_ctx* ctx, int32_t dom, int64_t rhs, bem_z* dirichlet, bem_z* neumann, int on_device) {
     if (!ctx) return BEM_ERR_INVALID_ARG;
-    return ctx->fail(BEM_ERR_STATE, "no solve has run");
+    if (!ctx->solve || ctx->solve->n_rhs_solved == 0) return ctx->fail(BEM_ERR_STATE, "no solve has run");
+    if (dom < 0 || dom >= ctx->geo.n_dom || rhs < 0 || rhs >= ctx->solve->n_rhs_solved || !dirichlet || !neumann)
+        return ctx->fail(BEM_ERR_INVALID_ARG, "bad trace request");
+    const int64_t N = ctx->geo.n_dof, off = ctx->geo.dom_dof_off[dom], nv = ctx->geo.dom_nv[dom];
+    const double2* u = ctx->solve->u + rhs * N;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(neumann, u + off, nv * sizeof(double2), k, ctx->stream));
+    CK(cudaMemcpyAsync(dirichlet, u + off + nv, nv * sizeof(double2), k, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return BEM_OK;
 }
 
 }  // extern "C"

@@ -31,7 +31,7 @@ struct DeviceGeom {
     double2* kdom = nullptr;
     SlotCoef* coef = nullptr;
     int* err = nullptr;
-    double2 *xs = nullptr, *ys = nullptr;  // staging vectors (system size)
+    double2 *xs = nullptr, *ys = nullptr, *ys2 = nullptr;  // staging vectors (system size)
 };
 
 struct NearSet {

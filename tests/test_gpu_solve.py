@@ -1,0 +1,140 @@
+"""Parity of the OSRC preconditioner, the transducer right-hand side and the
+GPU solves (plain FP64 GMRES and FP32-inner GMRES with FP64 residual
+refinement) with the FP64 oracle, through the C ABI.  Bars: solved traces
+within 1e-6 (relative l2) of the oracle's dense solution; the preconditioner
+to 1e-9 (its sparse solves run to a 1e-12 relative residual)."""
+import numpy as np
+import pytest
+
+from oracle import gmres, mie, osrc, pmchwt, rayleigh
+from synth import scenes
+
+pytestmark = pytest.mark.gpu
+
+R_EPS = 0.2
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1910_01011_gb300 import api, build
+    build.build()
+    return api
+
+
+def ctx_for(api, s, **kw):
+    kw.setdefault("r_eps", R_EPS)
+    return api.Context.from_scene(s, **kw)
+
+
+@pytest.mark.parametrize("name,npade", [("sphere", 4), ("two", 8), ("shell", 4)])
+def test_preconditioner_matches_oracle(api, name, npade):
+    s = {"sphere": lambda: scenes.sphere_scene(2), "two": lambda: scenes.two_sphere_scene(1),
+         "shell": lambda: scenes.shell_scene(1)}[name]()
+    pre = osrc.build(s, R_eps=R_EPS, n_pade=npade)
+    c = ctx_for(api, s, n_pade=npade)
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal(c.n_dofs) + 1j * rng.standard_normal(c.n_dofs)
+    assert rel(c.apply(x, op=api.PREC), osrc.apply(s, pre, x)) < 1e-9
+    A = pmchwt.assemble(s)
+    ref = osrc.apply(s, pre, A @ x)
+    assert rel(c.apply(x, op=api.PREC_AHAT, precision=api.FP64), ref) < 1e-9
+    assert rel(c.apply(x, op=api.PREC_AHAT, precision=api.FP32), ref) < 2e-5
+
+
+@pytest.fixture(scope="module")
+def sphere_ref():
+    s = scenes.sphere_scene(3)
+    u, A, b = pmchwt.solve(s, pmchwt.plane_wave(s.k0, (0, 0, 1)))
+    return s, u, A, b
+
+
+def _traces(c, s):
+    out = []
+    for j, d in enumerate(s.domains):
+        D, Nn = c.traces(j)
+        out.append(np.concatenate([Nn, D]))
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("precision,precondition", [(0, 1), (1, 1), (0, 0)])
+def test_sphere_solve_matches_oracle(api, sphere_ref, precision, precondition):
+    """Config-1 sphere (icosphere level 3, k0=5, k1=5.25, density ratio 1.1,
+    plane wave +z): GPU traces within 1e-6 of the oracle's dense solve."""
+    s, u, A, b = sphere_ref
+    c = ctx_for(api, s, n_pade=4)
+    c.set_plane_wave((0, 0, 1))
+    assert rel(c.rhs(), b) < 1e-13
+    rep = c.solve(precision=precision, precondition=precondition, tol=1e-10, restart=100, max_iter=3000)
+    assert rep["converged"], rep
+    ug = _traces(c, s)
+    assert rel(ug, u) < 1e-6, rep
+    if precondition:
+        assert rep["iterations"] < 120, rep
+    if precision == 1:
+        assert rep["refinements"] >= 1
+
+
+def test_solve_mie_accuracy(api, sphere_ref):
+    """End to end on the GPU: traces of the mixed-precision solve against the
+    Mie series (the paper's < 3 % at about 6-8 elements per wavelength)."""
+    s, u, A, b = sphere_ref
+    c = ctx_for(api, s)
+    c.set_plane_wave((0, 0, 1))
+    c.solve(precision=1, tol=1e-8)
+    d = s.domains[0]
+    D, Nn = c.traces(0)
+    pts = d.verts / np.linalg.norm(d.verts, axis=1)[:, None]
+    eD, eN = mie.surface_traces(pts, 1.0, s.k0, d.k, s.rho0, d.rho)
+    assert rel(D, eD) < 0.03 and rel(Nn, eN) < 0.03
+
+
+def test_multi_domain_mixed_solve(api):
+    s = scenes.shell_scene(1)
+    u, A, b = pmchwt.solve(s, pmchwt.plane_wave(s.k0, s.plane_wave_dir))
+    c = ctx_for(api, s)
+    c.set_plane_wave(s.plane_wave_dir)
+    rep = c.solve(precision=1, tol=1e-10)
+    assert rep["converged"]
+    assert rel(_traces(c, s), u) < 1e-6
+
+
+def small_transducer(n=6, seed=3):
+    tr = scenes.bowl_transducer(seed=seed, n_elem=n, R=4.0, aperture=3.0, piston_radius=0.3, gap=0.05)
+    return tr
+
+
+def test_transducer_rhs_and_multi_rhs_solve(api):
+    """Rayleigh pistons (one excitation per piston and one focused set) on the
+    two-sphere scene: right-hand sides against the oracle, and each solve of
+    the batch equal to the oracle's dense solve of that excitation."""
+    s = scenes.two_sphere_scene(1)
+    tr = small_transducer()
+    k0 = s.k0
+    omega, rho0 = 2.0, 1.3
+    W = np.vstack([np.eye(tr["radii"].size), scenes.focusing_weights(tr, k0)[None, :]]).astype(complex)
+    c = ctx_for(api, s)
+    c.set_transducer(tr["centres"], tr["normals"], tr["radii"], omega * rho0)
+    c.set_excitations(W)
+    B = c.rhs(W.shape[0])
+    A = pmchwt.assemble(s)
+    for r in range(W.shape[0]):
+        ref = pmchwt.rhs(s, rayleigh.field(tr, W[r], k0, omega, rho0))
+        assert rel(B[r], ref) < 1e-12
+    rep = c.solve(precision=1, tol=1e-10)
+    assert rep["converged"]
+    for r in (0, W.shape[0] - 1):
+        u = np.linalg.solve(A, B[r])
+        got = np.concatenate([np.concatenate([c.traces(j, r)[1], c.traces(j, r)[0]]) for j in range(2)])
+        assert rel(got, u) < 1e-6
+
+
+def test_solve_reports_not_converged(api):
+    s = scenes.sphere_scene(2)
+    c = ctx_for(api, s)
+    c.set_plane_wave((0, 0, 1))
+    rep = c.solve(precision=0, precondition=0, tol=1e-12, max_iter=5, restart=5)
+    assert not rep["converged"] and rep["iterations"] <= 5
