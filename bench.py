@@ -28,12 +28,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "BEM operator-apply Ginteractions/s"
 UNIT = "Ginteractions/s"
-# Algorithmic FP32 work of the far-field kernel per (target point, source
-# point) pair, counted from its source (FFMA = 2 flops; MUFU excluded):
-# one wavenumber 82.2 flops; the fused two-wavenumber pair of own-domain
-# sources 141.5 flops (shared geometry counted once).
-FLOPS_1K = 82.2
-FLOPS_2K = 141.5
+# Algorithmic FP32 work of far32_kernel per (target point, source point)
+# pair, counted from its source (FFMA = 2 flops, FADD/FMUL = 1; MUFU
+# excluded): shared geometry 21 flops + per-triangle shared terms 11/6;
+# per wavenumber 52 flops (54 when Im k != 0: the exp(-Im k r) factor) +
+# per-triangle 32/6.
+FL_SHARED = 21.0 + 11.0 / 6.0
+FL_SLOT_LOSSLESS = 52.0 + 32.0 / 6.0
+FL_SLOT_LOSSY = 54.0 + 32.0 / 6.0
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
@@ -63,6 +65,18 @@ def pair_counts(s):
     fused = sum(p * p for p in P)
     single = tot * tot - fused
     return single, fused, single + 2 * fused
+
+
+def algorithmic_flops(s):
+    """FP32 flops of one far32 launch on scene s (see the constants above)."""
+    slot0 = FL_SLOT_LOSSY if complex(s.k0).imag != 0 else FL_SLOT_LOSSLESS
+    P = [6 * d.tris.shape[0] for d in s.domains]
+    tot = sum(P)
+    fl = 0.0
+    for d, p in zip(s.domains, P):
+        slot1 = FL_SLOT_LOSSY if complex(d.k).imag != 0 else FL_SLOT_LOSSLESS
+        fl += p * (tot - p) * (FL_SHARED + slot0) + p * p * (FL_SHARED + slot0 + slot1)
+    return fl
 
 
 class ClockSampler:
@@ -211,7 +225,7 @@ def main():
     N = ctx.n_dofs
     single, fused, n_int = pair_counts(s)
     assert n_int == ctx.interactions
-    flops = single * FLOPS_1K + fused * FLOPS_2K
+    flops = algorithmic_flops(s)
 
     gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
     x = torch.complex(torch.randn(N, dtype=torch.float64, device="cuda", generator=gen),

@@ -140,6 +140,17 @@ __global__ void gather_kernel(GatherArgs a) {
 }
 
 // ----------------------------------------------------------------- FP32 far field
+//
+// One CTA = one target tile (TP threads, one target point each) against a
+// contiguous range of source tiles.  Source tiles stream through an
+// NSTAGE-deep ring of shared-memory stages filled by bulk (TMA) copies that
+// complete on per-stage mbarriers.  There is no CTA-wide barrier in the
+// loop: each warp counts itself out of a stage when it has finished the
+// tile in it, and the last warp to leave a stage refills it with the tile
+// NSTAGE ahead, so warps drift freely within the ring.
+
+constexpr int NSTAGE = 4;
+constexpr int NWARP = TP / 32;
 
 struct __align__(16) Stage {
     float4 pg[TP];      // source points (dx, dy, dz, w)
@@ -150,6 +161,13 @@ struct __align__(16) Stage {
 constexpr uint32_t STAGE_BYTES = sizeof(Stage);
 static_assert(STAGE_BYTES == 7680, "stage layout");
 
+struct FarSmem {
+    Stage st[NSTAGE];
+    float4 tab[2 * CHUNK_MAX];
+    uint64_t full[NSTAGE];
+    int cnt[NSTAGE];
+};
+
 struct Acc {
     float v[NCOMP];  // PV(2) PK(2) PKp(2) PWm(2) PWc(6)
 };
@@ -158,102 +176,57 @@ struct SlotK {
     float kr, nki, nkil2;  // Re k, -Im k, -Im k * log2(e)
 };
 
-// One source triangle for one wavenumber slot: the six rule points, then
-// the per-triangle terms.  Returns nothing; updates `t` (tile accumulators).
-template <bool TWO>
-__device__ __forceinline__ void triangle_body(const Stage& st, int tl, float dx, float dy, float dz, float nx,
-                                              float ny, float nz, float D2x, float D2y, float D2z, float Rc2,
-                                              float Rc, float nX, float Xx, float Xy, float Xz, float th0,
-                                              float th1, SlotK k0, SlotK k1, Acc& t0, Acc& t1) {
-    float S1r0 = 0, S1i0 = 0, S2r0 = 0, S2i0 = 0, S3r0 = 0, S3i0 = 0;
-    float S1r1 = 0, S1i1 = 0, S2r1 = 0, S2i1 = 0, S3r1 = 0, S3i1 = 0;
-#pragma unroll
-    for (int q = 0; q < QP; q++) {
-        const float4 g = st.pg[tl * QP + q];
-        const float4 d = st.pd[tl * QP + q];
-        const float ex = dx - g.x, ey = dy - g.y, ez = dz - g.z;  // delta = dx - dy
-        const float s = ex * (D2x + ex) + ey * (D2y + ey) + ez * (D2z + ez);
-        const float r2 = Rc2 + s;
-        const float rinv = rsqrtf(r2);
-        const float r = r2 * rinv;
-        const float rho = __fdividef(s, r + Rc);            // r - R_c
-        const float ndot = nX - (nx * g.x + ny * g.y + nz * g.z);  // n_x.(x - y)
-        {
-            float sn, cs;
-            __sincosf(fmaf(k0.kr, rho, th0), &sn, &cs);
-            const float a = ex2_approx(k0.nkil2 * r) * rinv;
-            const float Gr = a * cs, Gi = a * sn;
-            const float Gbr = Gr * rinv, Gbi = Gi * rinv;
-            const float u = k0.nki - rinv;
-            const float Fr = Gbr * u - Gbi * k0.kr, Fi = Gbr * k0.kr + Gbi * u;
-            t0.v[0] = fmaf(Gr, d.x, fmaf(-Gi, d.y, t0.v[0]));
-            t0.v[1] = fmaf(Gr, d.y, fmaf(Gi, d.x, t0.v[1]));
-            const float Fnr = Fr * ndot, Fni = Fi * ndot;
-            t0.v[4] = fmaf(Fnr, d.x, fmaf(-Fni, d.y, t0.v[4]));
-            t0.v[5] = fmaf(Fnr, d.y, fmaf(Fni, d.x, t0.v[5]));
-            S1r0 = fmaf(Fr, d.z, fmaf(-Fi, d.w, S1r0));
-            S1i0 = fmaf(Fr, d.w, fmaf(Fi, d.z, S1i0));
-            S2r0 = fmaf(Gr, g.w, S2r0);
-            S2i0 = fmaf(Gi, g.w, S2i0);
-            S3r0 = fmaf(Gr, d.z, fmaf(-Gi, d.w, S3r0));
-            S3i0 = fmaf(Gr, d.w, fmaf(Gi, d.z, S3i0));
-        }
-        if constexpr (TWO) {
-            float sn, cs;
-            __sincosf(fmaf(k1.kr, rho, th1), &sn, &cs);
-            const float a = ex2_approx(k1.nkil2 * r) * rinv;
-            const float Gr = a * cs, Gi = a * sn;
-            const float Gbr = Gr * rinv, Gbi = Gi * rinv;
-            const float u = k1.nki - rinv;
-            const float Fr = Gbr * u - Gbi * k1.kr, Fi = Gbr * k1.kr + Gbi * u;
-            t1.v[0] = fmaf(Gr, d.x, fmaf(-Gi, d.y, t1.v[0]));
-            t1.v[1] = fmaf(Gr, d.y, fmaf(Gi, d.x, t1.v[1]));
-            const float Fnr = Fr * ndot, Fni = Fi * ndot;
-            t1.v[4] = fmaf(Fnr, d.x, fmaf(-Fni, d.y, t1.v[4]));
-            t1.v[5] = fmaf(Fnr, d.y, fmaf(Fni, d.x, t1.v[5]));
-            S1r1 = fmaf(Fr, d.z, fmaf(-Fi, d.w, S1r1));
-            S1i1 = fmaf(Fr, d.w, fmaf(Fi, d.z, S1i1));
-            S2r1 = fmaf(Gr, g.w, S2r1);
-            S2i1 = fmaf(Gi, g.w, S2i1);
-            S3r1 = fmaf(Gr, d.z, fmaf(-Gi, d.w, S3r1));
-            S3i1 = fmaf(Gr, d.w, fmaf(Gi, d.z, S3i1));
-        }
-    }
-    const float4 tg = st.tg[tl];
-    const float4 cre = st.tc[2 * tl], cim = st.tc[2 * tl + 1];
-    const float fK = tg.w - (tg.x * Xx + tg.y * Xy + tg.z * Xz);  // n_t.(y - x)
-    const float nn = nx * tg.x + ny * tg.y + nz * tg.z;            // n_x.n_t
-    t0.v[2] = fmaf(fK, S1r0, t0.v[2]);
-    t0.v[3] = fmaf(fK, S1i0, t0.v[3]);
-    t0.v[6] = fmaf(nn, S3r0, t0.v[6]);
-    t0.v[7] = fmaf(nn, S3i0, t0.v[7]);
-    t0.v[8] = fmaf(S2r0, cre.x, fmaf(-S2i0, cim.x, t0.v[8]));
-    t0.v[9] = fmaf(S2r0, cre.y, fmaf(-S2i0, cim.y, t0.v[9]));
-    t0.v[10] = fmaf(S2r0, cre.z, fmaf(-S2i0, cim.z, t0.v[10]));
-    t0.v[11] = fmaf(S2r0, cim.x, fmaf(S2i0, cre.x, t0.v[11]));
-    t0.v[12] = fmaf(S2r0, cim.y, fmaf(S2i0, cre.y, t0.v[12]));
-    t0.v[13] = fmaf(S2r0, cim.z, fmaf(S2i0, cre.z, t0.v[13]));
-    if constexpr (TWO) {
-        t1.v[2] = fmaf(fK, S1r1, t1.v[2]);
-        t1.v[3] = fmaf(fK, S1i1, t1.v[3]);
-        t1.v[6] = fmaf(nn, S3r1, t1.v[6]);
-        t1.v[7] = fmaf(nn, S3i1, t1.v[7]);
-        t1.v[8] = fmaf(S2r1, cre.x, fmaf(-S2i1, cim.x, t1.v[8]));
-        t1.v[9] = fmaf(S2r1, cre.y, fmaf(-S2i1, cim.y, t1.v[9]));
-        t1.v[10] = fmaf(S2r1, cre.z, fmaf(-S2i1, cim.z, t1.v[10]));
-        t1.v[11] = fmaf(S2r1, cim.x, fmaf(S2i1, cre.x, t1.v[11]));
-        t1.v[12] = fmaf(S2r1, cim.y, fmaf(S2i1, cre.y, t1.v[12]));
-        t1.v[13] = fmaf(S2r1, cim.z, fmaf(S2i1, cre.z, t1.v[13]));
-    }
+struct TriSums {
+    float S1r, S1i, S2r, S2i, S3r, S3i;
+};
+
+// Contribution of one source point at one wavenumber.  LOSSY: Im k != 0
+// (exp(-Im k r) evaluated); otherwise the amplitude is 1/r.
+template <bool LOSSY>
+__device__ __forceinline__ void slot_point(const SlotK& k, float th, float rho, float r, float rinv, float ndot,
+                                           const float4& g, const float4& d, Acc& t, TriSums& S) {
+    float sn, cs;
+    __sincosf(fmaf(k.kr, rho, th), &sn, &cs);
+    const float a = LOSSY ? ex2_approx(k.nkil2 * r) * rinv : rinv;
+    const float Gr = a * cs, Gi = a * sn;
+    const float Gbr = Gr * rinv, Gbi = Gi * rinv;
+    const float u = k.nki - rinv;
+    const float Fr = Gbr * u - Gbi * k.kr, Fi = Gbr * k.kr + Gbi * u;   // G (ik - 1/r) / r
+    t.v[0] = fmaf(Gr, d.x, fmaf(-Gi, d.y, t.v[0]));
+    t.v[1] = fmaf(Gr, d.y, fmaf(Gi, d.x, t.v[1]));
+    const float Fnr = Fr * ndot, Fni = Fi * ndot;
+    t.v[4] = fmaf(Fnr, d.x, fmaf(-Fni, d.y, t.v[4]));
+    t.v[5] = fmaf(Fnr, d.y, fmaf(Fni, d.x, t.v[5]));
+    S.S1r = fmaf(Fr, d.z, fmaf(-Fi, d.w, S.S1r));
+    S.S1i = fmaf(Fr, d.w, fmaf(Fi, d.z, S.S1i));
+    S.S2r = fmaf(Gr, g.w, S.S2r);
+    S.S2i = fmaf(Gi, g.w, S.S2i);
+    S.S3r = fmaf(Gr, d.z, fmaf(-Gi, d.w, S.S3r));
+    S.S3i = fmaf(Gr, d.w, fmaf(Gi, d.z, S.S3i));
 }
 
-template <bool TWO>
+// Per-triangle terms: K through (y-x).n_t, W through curl phi and n_x.n_t.
+__device__ __forceinline__ void slot_triangle(float fK, float nn, const float4& cre, const float4& cim,
+                                              const TriSums& S, Acc& t) {
+    t.v[2] = fmaf(fK, S.S1r, t.v[2]);
+    t.v[3] = fmaf(fK, S.S1i, t.v[3]);
+    t.v[6] = fmaf(nn, S.S3r, t.v[6]);
+    t.v[7] = fmaf(nn, S.S3i, t.v[7]);
+    t.v[8] = fmaf(S.S2r, cre.x, fmaf(-S.S2i, cim.x, t.v[8]));
+    t.v[9] = fmaf(S.S2r, cre.y, fmaf(-S.S2i, cim.y, t.v[9]));
+    t.v[10] = fmaf(S.S2r, cre.z, fmaf(-S.S2i, cim.z, t.v[10]));
+    t.v[11] = fmaf(S.S2r, cim.x, fmaf(S.S2i, cre.x, t.v[11]));
+    t.v[12] = fmaf(S.S2r, cim.y, fmaf(S.S2i, cre.y, t.v[12]));
+    t.v[13] = fmaf(S.S2r, cim.z, fmaf(S.S2i, cre.z, t.v[13]));
+}
+
+template <bool TWO, bool L0, bool L1>
 __device__ __forceinline__ void tile_body(const Stage& st, int ntri, int skip_tl, float dx, float dy, float dz,
-                                          float nx, float ny, float nz, float4 c0, float4 c1, SlotK k0, SlotK k1,
-                                          Acc& a0, Acc& a1) {
+                                          float nx, float ny, float nz, float4 c0, float4 c1, const SlotK& k0,
+                                          const SlotK& k1, Acc& a0, Acc& a1) {
     const float D2x = c0.x, D2y = c0.y, D2z = c0.z, Rc2 = c0.w, Rc = c1.x, th0 = c1.y, th1 = c1.z;
-    const float Xx = dx + 0.5f * D2x, Xy = dy + 0.5f * D2y, Xz = dz + 0.5f * D2z;  // x - c_source
-    const float nX = nx * Xx + ny * Xy + nz * Xz;
+    const float Xx = fmaf(0.5f, D2x, dx), Xy = fmaf(0.5f, D2y, dy), Xz = fmaf(0.5f, D2z, dz);  // x - c_source
+    const float nD = 0.5f * (nx * D2x + ny * D2y + nz * D2z);                                 // n_x.D
     Acc t0, t1;
 #pragma unroll
     for (int c = 0; c < NCOMP; c++) {
@@ -262,8 +235,27 @@ __device__ __forceinline__ void tile_body(const Stage& st, int ntri, int skip_tl
     }
     for (int tl = 0; tl < ntri; tl++) {
         if (tl == skip_tl) continue;  // identical triangle: near-field correction only
-        triangle_body<TWO>(st, tl, dx, dy, dz, nx, ny, nz, D2x, D2y, D2z, Rc2, Rc, nX, Xx, Xy, Xz, th0, th1, k0,
-                           k1, t0, t1);
+        TriSums S0{0, 0, 0, 0, 0, 0}, S1{0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int q = 0; q < QP; q++) {
+            const float4 g = st.pg[tl * QP + q];
+            const float4 d = st.pd[tl * QP + q];
+            const float ex = dx - g.x, ey = dy - g.y, ez = dz - g.z;            // delta = dx - dy
+            const float s = ex * (D2x + ex) + ey * (D2y + ey) + ez * (D2z + ez);  // r^2 - R_c^2
+            const float r2 = Rc2 + s;
+            const float rinv = rsqrtf(r2);
+            const float r = r2 * rinv;
+            const float rho = __fdividef(s, r + Rc);                           // r - R_c
+            const float ndot = fmaf(nx, ex, fmaf(ny, ey, fmaf(nz, ez, nD)));    // n_x.(x - y)
+            slot_point<L0>(k0, th0, rho, r, rinv, ndot, g, d, t0, S0);
+            if constexpr (TWO) slot_point<L1>(k1, th1, rho, r, rinv, ndot, g, d, t1, S1);
+        }
+        const float4 tg = st.tg[tl];
+        const float4 cre = st.tc[2 * tl], cim = st.tc[2 * tl + 1];
+        const float fK = tg.w - (tg.x * Xx + tg.y * Xy + tg.z * Xz);  // n_t.(y - x)
+        const float nn = nx * tg.x + ny * tg.y + nz * tg.z;            // n_x.n_t
+        slot_triangle(fK, nn, cre, cim, S0, t0);
+        if constexpr (TWO) slot_triangle(fK, nn, cre, cim, S1, t1);
     }
 #pragma unroll
     for (int c = 0; c < NCOMP; c++) {
@@ -273,12 +265,10 @@ __device__ __forceinline__ void tile_body(const Stage& st, int ntri, int skip_tl
 }
 
 __global__ void __launch_bounds__(TP, 2) far32_kernel(FarArgs32 A) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    Stage* stage = reinterpret_cast<Stage*>(smem);
-    float4* tab = reinterpret_cast<float4*>(smem + 2 * sizeof(Stage));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * sizeof(Stage) + 2 * CHUNK_MAX * sizeof(float4));
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FarSmem& sm = *reinterpret_cast<FarSmem*>(smem_raw);
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int tt = A.tgt_begin + blockIdx.x;
     const int sb = A.src_begin + blockIdx.y * A.chunk_tiles;
     const int se = min(sb + A.chunk_tiles, A.src_end);
@@ -292,8 +282,9 @@ __global__ void __launch_bounds__(TP, 2) far32_kernel(FarArgs32 A) {
     const int mydom = A.tdom[tt];
     const int2 dr = A.dom_tiles[mydom];
     const double2 kj = A.kdom[mydom];
-    SlotK k0{(float)A.k0.x, (float)-A.k0.y, (float)(-A.k0.y * 1.4426950408889634)};
-    SlotK k1{(float)kj.x, (float)-kj.y, (float)(-kj.y * 1.4426950408889634)};
+    const SlotK k0{(float)A.k0.x, (float)-A.k0.y, (float)(-A.k0.y * 1.4426950408889634)};
+    const SlotK k1{(float)kj.x, (float)-kj.y, (float)(-kj.y * 1.4426950408889634)};
+    const bool lossy0 = A.k0.y != 0.0, lossy1 = kj.y != 0.0;
 
     // tile-pair table: 2D, R_c^2, R_c and the FP64-reduced phases
     for (int i = tid; i < nsrc; i += TP) {
@@ -302,29 +293,29 @@ __global__ void __launch_bounds__(TP, 2) far32_kernel(FarArgs32 A) {
         const double Dx = ct.x - cs.x, Dy = ct.y - cs.y, Dz = ct.z - cs.z;
         const double R = sqrt(Dx * Dx + Dy * Dy + Dz * Dz);
         const bool own = A.slot1 && s >= dr.x && s < dr.y;
-        tab[2 * i] = make_float4((float)(2 * Dx), (float)(2 * Dy), (float)(2 * Dz), (float)(R * R));
-        tab[2 * i + 1] = make_float4((float)R, reduce_phase(A.k0.x * R), own ? reduce_phase(kj.x * R) : 0.f, 0.f);
+        sm.tab[2 * i] = make_float4((float)(2 * Dx), (float)(2 * Dy), (float)(2 * Dz), (float)(R * R));
+        sm.tab[2 * i + 1] = make_float4((float)R, reduce_phase(A.k0.x * R), own ? reduce_phase(kj.x * R) : 0.f, 0.f);
     }
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int s = 0; s < NSTAGE; s++) {
+            mbar_init(&sm.full[s], 1);
+            sm.cnt[s] = 0;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    auto issue = [&](int i, int buf) {
+    auto issue = [&](int i, int st) {
         const int s = sb + i;
-        Stage& S = stage[buf];
-        mbar_arrive_expect_tx(&bars[buf], STAGE_BYTES);
-        bulk_g2s(S.pg, A.pg + (int64_t)s * TP, TP * 16, &bars[buf]);
-        bulk_g2s(S.pd, A.pd + (int64_t)s * TP, TP * 16, &bars[buf]);
-        bulk_g2s(S.tg, A.tg + (int64_t)s * TT, TT * 16, &bars[buf]);
-        bulk_g2s(S.tc, A.tcurl + (int64_t)s * 2 * TT, 2 * TT * 16, &bars[buf]);
+        Stage& S = sm.st[st];
+        mbar_arrive_expect_tx(&sm.full[st], STAGE_BYTES);
+        bulk_g2s(S.pg, A.pg + (int64_t)s * TP, TP * 16, &sm.full[st]);
+        bulk_g2s(S.pd, A.pd + (int64_t)s * TP, TP * 16, &sm.full[st]);
+        bulk_g2s(S.tg, A.tg + (int64_t)s * TT, TT * 16, &sm.full[st]);
+        bulk_g2s(S.tc, A.tcurl + (int64_t)s * 2 * TT, 2 * TT * 16, &sm.full[st]);
     };
-    if (tid == 0) {
-        if (nsrc > 0) issue(0, 0);
-        if (nsrc > 1) issue(1, 1);
-    }
+    if (tid == 0)
+        for (int i = 0; i < min(NSTAGE, nsrc); i++) issue(i, i);
 
     Acc a0, a1;
 #pragma unroll
@@ -333,19 +324,35 @@ __global__ void __launch_bounds__(TP, 2) far32_kernel(FarArgs32 A) {
         a1.v[c] = 0.f;
     }
     for (int i = 0; i < nsrc; i++) {
-        const int buf = i & 1;
-        mbar_wait_bounded(&bars[buf], (uint32_t)((i >> 1) & 1), A.err);
+        const int st = i % NSTAGE;
+        mbar_wait_bounded(&sm.full[st], (uint32_t)((i / NSTAGE) & 1), A.err);
         const int s = sb + i;
-        const Stage& st = stage[buf];
+        const Stage& S = sm.st[st];
         const int ntri = A.tntri[s];
         const int skip = (s == tt) ? mt : -1;
-        const float4 c0 = tab[2 * i], c1 = tab[2 * i + 1];
-        if (A.slot1 && s >= dr.x && s < dr.y)
-            tile_body<true>(st, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
-        else
-            tile_body<false>(st, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
-        __syncthreads();
-        if (tid == 0 && i + 2 < nsrc) issue(i + 2, buf);
+        const float4 c0 = sm.tab[2 * i], c1 = sm.tab[2 * i + 1];
+        const bool two = A.slot1 && s >= dr.x && s < dr.y;
+        if (two) {
+            if (lossy0) {
+                if (lossy1) tile_body<true, true, true>(S, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
+                else tile_body<true, true, false>(S, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
+            } else {
+                if (lossy1) tile_body<true, false, true>(S, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
+                else tile_body<true, false, false>(S, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
+            }
+        } else {
+            if (lossy0) tile_body<false, true, false>(S, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
+            else tile_body<false, false, false>(S, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
+        }
+        // leave the stage; the last warp out refills it with the tile NSTAGE ahead
+        __syncwarp();
+        if (lane == 0) {
+            const int old = atomicAdd(&sm.cnt[st], 1);
+            if (old == NWARP - 1) {
+                sm.cnt[st] = 0;
+                if (i + NSTAGE < nsrc) issue(i + NSTAGE, st);
+            }
+        }
     }
 
     float* out = A.partial + (int64_t)blockIdx.y * 2 * NCOMP * A.n_pts;
@@ -356,7 +363,7 @@ __global__ void __launch_bounds__(TP, 2) far32_kernel(FarArgs32 A) {
     }
 }
 
-size_t far32_smem_bytes() { return 2 * sizeof(Stage) + 2 * CHUNK_MAX * sizeof(float4) + 2 * sizeof(uint64_t); }
+size_t far32_smem_bytes() { return sizeof(FarSmem); }
 
 cudaError_t launch_far32(const FarArgs32& a, int n_tgt_tiles, int n_chunks, cudaStream_t s) {
     static bool attr = false;

@@ -55,8 +55,8 @@ struct OsrcState {
     int* flags = nullptr;              // [max_sys] active
     // stage vectors, [2][n] or [2*n_pade][n]
     double2 *u = nullptr, *g = nullptr, *w = nullptr, *br = nullptr;
-    double tol = 1e-12;
-    int max_iter = 2000;
+    double tol = 1e-11;
+    int max_iter = 20000;
     long long iters_last = 0;
 };
 
@@ -467,7 +467,7 @@ static int cocg_solve(bem_ctx* ctx, int n_sys) {
     std::vector<double> sc(8 * n_sys);
     int it = 0;
     for (; it < o->max_iter;) {
-        for (int k = 0; k < 16; k++, it++) {
+        for (int k = 0; k < 32; k++, it++) {
             a.it = it;
             cocg_spmv<<<grid, SP_THREADS, 0, ctx->stream>>>(a);
             cocg_update<<<grid, SP_THREADS, 0, ctx->stream>>>(a);

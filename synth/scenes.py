@@ -142,6 +142,14 @@ def rib_scene(h: float = 2.65e-3, freq: float = 0.5e6) -> Scene:
     return s
 
 
+def rib_scene_resolved(h: float = 2.65e-3) -> Scene:
+    """The rib scene at the frequency where its ~41k-triangle mesh resolves
+    about 6 elements per wavelength (0.1 MHz; k h ~ 1), for solve timings."""
+    s = rib_scene(h=h, freq=0.1e6)
+    s.name = "rib_fat_liver_0.1MHz"
+    return s
+
+
 def kidney_scene(h: float = 1.8e-3, freq: float = 1.0e6) -> Scene:
     """Ellipsoidal kidney (110 x 60 x 40 mm) inside a hollow perinephric fat
     shell whose inner surface is offset 1 mm and outer surface 8 mm from the
