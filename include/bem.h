@@ -139,6 +139,15 @@ int bem_apply_block(bem_ctx* ctx, int32_t test_domain, int32_t trial_domain, bem
  * cleared between calls. */
 int bem_apply_noalloc(bem_ctx* ctx, const bem_z* x, bem_z* y);
 
+/* Dense complex product on the tensor cores: Y = A X with A (m x k),
+ * X (n_rhs x k, each right-hand side contiguous) and Y (n_rhs x m), all
+ * complex64 (interleaved float re, im) device arrays.  Split-BF16 x3 with
+ * FP32 accumulation (the GEMM of the assembled-operator path, SURVEY row
+ * a11): each real part P ~ P_hi + P_lo in BF16 and the three leading
+ * products kept.  Work and scratch use the context's stream and budget; the
+ * call synchronises. */
+int bem_zgemm_bf16x3(bem_ctx* ctx, int64_t m, int64_t k, int64_t n_rhs, const void* A, const void* X, void* Y);
+
 /* Incident field: a plane wave amp * exp(i k0 d.x) (d normalised here). */
 int bem_set_plane_wave(bem_ctx* ctx, const double dir[3], bem_z amp);
 
