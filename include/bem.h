@@ -54,7 +54,9 @@ enum {
 /* Arithmetic of an operator application. */
 enum {
     BEM_PREC_FP64 = 0, /* FP64 everywhere (the baseline path) */
-    BEM_PREC_FP32 = 1  /* FP32 far field with tile-local phase, FP64 near field and output */
+    BEM_PREC_FP32 = 1, /* FP32 far field with tile-local phase, FP64 near field and output */
+    BEM_PREC_BF16X3 = 2 /* assembled complex64 A_hat (set-up once, N^2 x 16 bytes of device memory)
+                           applied to all right-hand sides at once by the split-BF16x3 tensor-core GEMM */
 };
 
 /* Operators for bem_apply. */

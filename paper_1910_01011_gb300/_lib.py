@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libgbem.so")
 BEM_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "MESH_INVALID", -3: "OUT_OF_BUDGET", -4: "NOT_CONVERGED", -5: "TIMEOUT",
           -6: "CUDA", -7: "STATE"}
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_BF16X3 = 0, 1, 2
 OP_AHAT, OP_PREC, OP_PREC_AHAT = 0, 1, 2
 
 

@@ -70,6 +70,8 @@ static int upload(bem_ctx* ctx, T** dst, const std::vector<T>& v) {
     return BEM_OK;
 }
 
+void destroy_solver_state(bem_ctx* ctx);  // bem_solve.cu / k_sparse.cu (objects only; memory is freed here)
+
 static void release_device(bem_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
@@ -82,6 +84,14 @@ static void release_device(bem_ctx* ctx) {
     ctx->block_cache.clear();
     ctx->osrc_ready = false;
     ctx->rhs_ready = false;
+    ctx->asm_ready = false;
+    ctx->asm_planes = nullptr;
+    ctx->asm_work = nullptr;
+    ctx->asm_work_bytes = 0;
+    ctx->partial = nullptr;
+    ctx->partial_bytes = 0;
+    ctx->pmchwt_near = NearSet();
+    destroy_solver_state(ctx);
 }
 
 // ------------------------------------------------------------------ set-up
@@ -415,6 +425,7 @@ int bem_set_exterior(bem_ctx* ctx, bem_z k0, double rho0) {
         ctx->near_ready = false;
         ctx->osrc_ready = false;
         ctx->rhs_ready = false;
+        ctx->asm_ready = false;
         return ctx->upload_materials();
     }
     return BEM_OK;
@@ -458,6 +469,7 @@ int bem_set_material(bem_ctx* ctx, int32_t id, bem_z k, double rho) {
     if (ctx->ready) {
         ctx->near_ready = false;
         ctx->osrc_ready = false;
+        ctx->asm_ready = false;
         return ctx->upload_materials();
     }
     return BEM_OK;
@@ -496,12 +508,41 @@ static int io_in(bem_ctx* ctx, const bem_z* x, int64_t n, int on_device, const d
 int bem_apply(bem_ctx* ctx, int op, const bem_z* x, bem_z* y, int64_t n_rhs, int precision, int on_device) {
     if (!ctx) return BEM_ERR_INVALID_ARG;
     if (!x || !y || n_rhs < 1) return ctx->fail(BEM_ERR_INVALID_ARG, "null vector or n_rhs < 1");
-    if (precision != BEM_PREC_FP64 && precision != BEM_PREC_FP32) return ctx->fail(BEM_ERR_INVALID_ARG, "bad precision");
+    if (precision != BEM_PREC_FP64 && precision != BEM_PREC_FP32 && precision != BEM_PREC_BF16X3)
+        return ctx->fail(BEM_ERR_INVALID_ARG, "bad precision");
     if (op < BEM_OP_AHAT || op > BEM_OP_PREC_AHAT) return ctx->fail(BEM_ERR_INVALID_ARG, "bad op");
     CK(cudaSetDevice(ctx->device));
     int rc = ctx->finalize();
     if (rc) return rc;
     const int64_t N = ctx->geo.n_dof;
+    if (precision == BEM_PREC_BF16X3 && op != BEM_OP_PREC) {
+        // all right-hand sides in one tensor-core GEMM on the assembled operator
+        const double2* xd = (const double2*)x;
+        double2* yd = (double2*)y;
+        double2* stage = nullptr;
+        if (!on_device) {
+            stage = (double2*)ctx->dalloc((size_t)2 * n_rhs * N * sizeof(double2), &rc);
+            if (rc) return rc;
+            CK(cudaMemcpyAsync(stage, x, n_rhs * N * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+            xd = stage;
+            yd = stage + n_rhs * N;
+        }
+        rc = ctx->apply_assembled(xd, yd, n_rhs);
+        for (int64_t r = 0; !rc && op == BEM_OP_PREC_AHAT && r < n_rhs; r++) {
+            CK(cudaMemcpyAsync(ctx->dev.ys2, yd + r * N, N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+            rc = ctx->apply_prec(ctx->dev.ys2, yd + r * N);
+        }
+        if (!rc && !on_device) {
+            CK(cudaMemcpyAsync(y, yd, n_rhs * N * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+        if (stage) {
+            cudaStreamSynchronize(ctx->stream);
+            ctx->dfree(stage);
+        }
+        if (rc) return rc;
+        return on_device ? BEM_OK : ctx->check_device_error();
+    }
     for (int64_t r = 0; r < n_rhs; r++) {
         const double2* xd;
         if ((rc = io_in(ctx, x + r * N, N, on_device, &xd))) return rc;

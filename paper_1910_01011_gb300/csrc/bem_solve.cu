@@ -249,6 +249,16 @@ static int build_rhs(bem_ctx* ctx) {
     return BEM_OK;
 }
 
+void destroy_osrc_state(bem_ctx* ctx);
+
+// Drop the solver objects after their device memory was released with the
+// rest of the context's allocations.
+void destroy_solver_state(bem_ctx* ctx) {
+    delete ctx->solve;
+    ctx->solve = nullptr;
+    destroy_osrc_state(ctx);
+}
+
 static int ensure_solve_state(bem_ctx* ctx) {
     if (!ctx->solve) ctx->solve = new SolveState();
     SolveState* S = ctx->solve;

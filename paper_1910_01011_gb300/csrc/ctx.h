@@ -1,6 +1,7 @@
 // ctx.h -- the opaque bem_ctx behind the C ABI.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -83,6 +84,12 @@ struct bem_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> far_events;
     double far_ms_acc = 0;
     long long far_count = 0;
+    // assembled operator (split-BF16 planes) for BEM_PREC_BF16X3
+    bool asm_ready = false;
+    __nv_bfloat16* asm_planes = nullptr;
+    int64_t asm_mpad = 0, asm_kpad = 0;
+    void* asm_work = nullptr;
+    size_t asm_work_bytes = 0;
     gbem::OsrcState* osrc = nullptr;
     gbem::SolveState* solve = nullptr;
     // incident field
@@ -108,4 +115,6 @@ struct bem_ctx {
     int apply_prec(const double2* x, double2* y);
     int apply_prec_ahat(const double2* x, double2* y, int precision);
     int check_device_error();
+    int ensure_assembled();
+    int apply_assembled(const double2* x, double2* y, int64_t n_rhs);
 };

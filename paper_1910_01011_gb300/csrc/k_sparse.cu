@@ -328,6 +328,12 @@ using namespace gbem;
 
 // ---------------------------------------------------------------- host set-up
 
+void destroy_osrc_state(bem_ctx* ctx) {
+    delete ctx->osrc;
+    ctx->osrc = nullptr;
+    ctx->osrc_ready = false;
+}
+
 static int osrc_build(bem_ctx* ctx) {
     if (ctx->osrc_ready) return BEM_OK;
     int rc = ctx->finalize();
