@@ -55,8 +55,8 @@ enum {
 enum {
     BEM_PREC_FP64 = 0, /* FP64 everywhere (the baseline path) */
     BEM_PREC_FP32 = 1, /* FP32 far field with tile-local phase, FP64 near field and output */
-    BEM_PREC_BF16X3 = 2 /* assembled complex64 A_hat (set-up once, N^2 x 16 bytes of device memory)
-                           applied to all right-hand sides at once by the split-BF16x3 tensor-core GEMM */
+    BEM_PREC_BF16X3 = 2 /* assembled complex64 A_hat (set-up once; N^2 x 12 bytes of BF16 planes kept)
+                           applied to all right-hand sides at once by the split-BF16 tensor-core GEMM */
 };
 
 /* Operators for bem_apply. */
@@ -143,10 +143,9 @@ int bem_apply_noalloc(bem_ctx* ctx, const bem_z* x, bem_z* y);
 
 /* Dense complex product on the tensor cores: Y = A X with A (m x k),
  * X (n_rhs x k, each right-hand side contiguous) and Y (n_rhs x m), all
- * complex64 (interleaved float re, im) device arrays.  Split-BF16 x3 with
- * FP32 accumulation (the GEMM of the assembled-operator path, SURVEY row
- * a11): each real part P ~ P_hi + P_lo in BF16 and the three leading
- * products kept.  Work and scratch use the context's stream and budget; the
+ * complex64 (interleaved float re, im) device arrays.  Split BF16 with FP32
+ * accumulation (the GEMM of the assembled-operator path): each real part
+ * split into three BF16 terms and the six products down to ~2^-24 kept.  Work and scratch use the context's stream and budget; the
  * call synchronises. */
 int bem_zgemm_bf16x3(bem_ctx* ctx, int64_t m, int64_t k, int64_t n_rhs, const void* A, const void* X, void* Y);
 

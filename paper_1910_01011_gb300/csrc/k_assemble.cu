@@ -193,6 +193,9 @@ __global__ void c64_to_c128(int64_t n, const float2* x, double2* y) {
 int gemm_bf16x3(bem_ctx* ctx, const __nv_bfloat16* Aplanes, int64_t m, int64_t k, int64_t mpad, int64_t kpad,
                 const float2* X, int64_t n_rhs, float2* Y, __nv_bfloat16* xplanes, int64_t nbpad);
 int split_a(bem_ctx* ctx, const float2* A, int64_t m, int64_t k, int64_t mpad, int64_t kpad, __nv_bfloat16* P);
+int gemm_a_planes();
+int gemm_b_planes();
+int gemm_k_align();
 
 }  // namespace gbem
 
@@ -212,7 +215,8 @@ int bem_ctx::ensure_assembled() {
     if (rc) return rc;
     const Geometry& g = geo;
     const int64_t n = g.n_dof;
-    const int64_t mpad = (n + 127) / 128 * 128, kpad = (n + 63) / 64 * 64;
+    const int64_t ka = gemm_k_align();
+    const int64_t mpad = (n + 127) / 128 * 128, kpad = (n + ka - 1) / ka * ka;
     if (asm_planes) { dfree(asm_planes); asm_planes = nullptr; }
     float2* A = (float2*)dalloc((size_t)n * n * sizeof(float2), &rc);
     if (rc) return rc;
@@ -236,7 +240,7 @@ int bem_ctx::ensure_assembled() {
                                                                          dev.v_dof2, pmchwt_near.nb32, n, A);
         CK(cudaGetLastError());
     }
-    asm_planes = (__nv_bfloat16*)dalloc((size_t)4 * mpad * kpad * 2, &rc);
+    asm_planes = (__nv_bfloat16*)dalloc((size_t)gemm_a_planes() * mpad * kpad * 2, &rc);
     if (rc) { dfree(A); return rc; }
     if ((rc = split_a(this, A, n, n, mpad, kpad, asm_planes))) { dfree(A); return rc; }
     CK(cudaStreamSynchronize(stream));
@@ -256,7 +260,7 @@ int bem_ctx::apply_assembled(const double2* x, double2* y, int64_t n_rhs) {
     if (rc) return rc;
     const int64_t n = geo.n_dof;
     const int64_t nbpad = (n_rhs + 63) / 64 * 128;
-    const size_t need = (size_t)n_rhs * n * sizeof(float2) * 2 + (size_t)2 * nbpad * asm_kpad * 2;
+    const size_t need = (size_t)n_rhs * n * sizeof(float2) * 2 + (size_t)gemm_b_planes() * nbpad * asm_kpad * 2;
     if (need > asm_work_bytes) {
         if (asm_work) dfree(asm_work);
         asm_work = dalloc(need, &rc);

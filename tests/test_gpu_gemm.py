@@ -1,6 +1,7 @@
-"""The tcgen05 split-BF16x3 complex GEMM (assembled-operator path) against
-an FP64 product of the same complex64 inputs.  Bar: relative l2 <= 3e-5
-per right-hand side (the split keeps all terms above ~2^-16 relative)."""
+"""The tcgen05 split-BF16 complex GEMM (assembled-operator path) against
+an FP64 product of the same complex64 inputs.  Bar: relative l2 <= 5e-6
+per right-hand side: the three-term split keeps all terms above ~2^-24 and
+the accumulation is flushed to round-to-nearest FP32 every 256 of K."""
 import ctypes
 
 import numpy as np
@@ -33,7 +34,7 @@ def test_zgemm_bf16x3(ctx, m, k, n):
     ref = X.astype(np.complex128) @ A.astype(np.complex128).T
     err = np.linalg.norm(Y - ref, axis=1) / np.linalg.norm(ref, axis=1)
     print("max rel err", err.max())
-    assert err.max() < 3e-5
+    assert err.max() < 5e-6
 
 
 from oracle import pmchwt  # noqa: E402
