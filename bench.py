@@ -40,6 +40,16 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
+def _measured_bf16():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        return 1900.0  # fallback figure of the profiling recipe
+
+
+BF16_PEAK_TFLOPS = _measured_bf16()
+
+
 def workload(name):
     from synth import scenes
     if name == "rib":
@@ -169,6 +179,74 @@ def traffic_from_profile():
     return float(m.group(1))
 
 
+def solve_metrics(local, reps=12):
+    """Config-1 sphere (icosphere level 3, k0 = 5, k1 = 5.25, density ratio
+    1.1, plane wave): seconds per right-hand side of the FP32-inner / FP64-
+    refined solve against the plain FP64 GPU solve, both to an FP64 relative
+    residual of 1e-9 (traces within 1e-6 of each other), and the p50 / p99
+    latency of repeated mixed solves."""
+    import numpy as np
+
+    from paper_1910_01011_gb300.api import Context
+    from synth import scenes
+    s = scenes.sphere_scene(3)
+    c = Context.from_scene(s, device=local, n_pade=4, r_eps=0.2)
+    c.set_plane_wave((0, 0, 1))
+    c.solve(precision=1, tol=1e-9)  # set-up (near field, preconditioner) outside timing
+    t64 = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        r64 = c.solve(precision=0, tol=1e-9)
+        t64.append(time.perf_counter() - t0)
+    u64 = np.concatenate(c.traces(0))
+    t32 = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        r32 = c.solve(precision=1, tol=1e-9)
+        t32.append(time.perf_counter() - t0)
+    u32 = np.concatenate(c.traces(0))
+    c.close()
+    return {"workload": "unit sphere, icosphere level 3 (1280 triangles), k0=5, k1=5.25, rho ratio 1.1, plane wave",
+            "tol_fp64_residual": 1e-9, "fp64_s_per_rhs": float(np.median(t64)), "mixed_s_per_rhs": float(np.median(t32)),
+            "mixed_p50_s": float(np.percentile(t32, 50)), "mixed_p99_s": float(np.percentile(t32, 99)),
+            "speedup_vs_fp64": float(np.median(t64) / np.median(t32)),
+            "trace_rel_diff_mixed_vs_fp64": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
+            "iterations": {"fp64": r64["iterations"], "mixed": r32["iterations"], "refinements": r32["refinements"]}}
+
+
+def assembled_metrics(ctx, s, n_int, local, n_rhs=256):
+    """Config-3 form on the same scene: A_hat assembled once in complex64 and
+    applied to n_rhs right-hand sides by the split-BF16 tensor-core GEMM."""
+    import torch
+
+    from paper_1910_01011_gb300.api import BF16X3
+    N = ctx.n_dofs
+    g = torch.Generator(device="cuda").manual_seed(7)
+    X = torch.complex(torch.randn(n_rhs, N, dtype=torch.float64, device="cuda", generator=g),
+                      torch.randn(n_rhs, N, dtype=torch.float64, device="cuda", generator=g))
+    t0 = time.perf_counter()
+    ctx.apply(X[:1].contiguous(), precision=BF16X3)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    Y = ctx.apply(X, precision=BF16X3)
+    ts = []
+    for _ in range(5):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.apply(X, precision=BF16X3, out=Y)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = sorted(ts)[len(ts) // 2]
+    tflop = 48.0 * N * N * n_rhs / 1e12       # 12 split products x 2 flops x N x 2R x N
+    return {"workload": f"same scene, {n_rhs} right-hand sides, assembled complex64 A_hat, split-BF16 (3 terms, 6 products) tcgen05 GEMM",
+            "assembly_s": setup, "ms_per_apply": ms, "pair_rhs_per_s": n_int * n_rhs / (ms / 1e3),
+            "roofline": {"bound": "tensor", "achieved": tflop / (ms / 1e3), "peak": BF16_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": tflop / (ms / 1e3) / BF16_PEAK_TFLOPS,
+                         "peak_basis": "MEASURED_PEAKS.json bf16_tflops (burst)"}}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -202,6 +280,7 @@ def main():
     ap.add_argument("--workload", default="rib", choices=["rib", "rib_small", "kidney", "sphere"])
     ap.add_argument("--ref-rows", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the solve and assembled-GEMM measurements")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -300,6 +379,9 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 16 * N},
             "gpu_launches": prof["kernel_launches"],
             "clocks": clk.summary()}
+    if not args.no_extras:
+        line["assembled"] = assembled_metrics(ctx, s, n_int, local)
+        line["solve"] = solve_metrics(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt, sample = oracle_sample(s, args.ref_rows)
         line["cpu_baseline"] = {"value": n / dt / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
