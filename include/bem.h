@@ -204,6 +204,17 @@ int bem_get_traces(bem_ctx* ctx, int32_t domain_id, int64_t rhs, bem_z* dirichle
 int bem_profile_enable(bem_ctx* ctx, int enable);
 int bem_profile_read(bem_ctx* ctx, double* far_ms, int64_t* far_launches, int64_t* kernel_launches, int reset);
 
+/* Total pressure at n_points points from the traces of excitation `rhs`
+ * of the last solve, by the representation formula (App. A eq.
+ * rep_formula_gen): for domain_of_point[i] = -1 (exterior)
+ * p_inc + DL_k0(gamma_D p) - SL_k0(gamma_N p) over all surfaces; for
+ * domain_of_point[i] = j, SL_kj((rho_j/rho_0) gamma_N p) - DL_kj(gamma_D p)
+ * over domain j.  points: [n][3] doubles, out: n complex.  The caller says
+ * which domain holds each point.  Accuracy degrades within about one element
+ * size of a surface (regular rule). */
+int bem_field(bem_ctx* ctx, int64_t rhs, const double* points, const int32_t* domain_of_point, int64_t n_points,
+              bem_z* out, int on_device);
+
 /* Message of the last error on ctx (never NULL). */
 const char* bem_last_error(const bem_ctx* ctx);
 

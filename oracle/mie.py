@@ -59,8 +59,10 @@ def surface_traces(points, a, k0, k1, rho0, rho1):
 
 
 def total_field(points, a, k0, k1, rho0, rho1):
-    """Total pressure at arbitrary points (exterior: incident + scattered,
-    interior: transmitted)."""
+    """Total pressure at arbitrary points (exterior: the exact incident
+    plane wave plus the scattered series, whose coefficients a_n decay past
+    n ~ k0 a; interior: the transmitted series).  The incident wave is not
+    summed as a series: at k0 r >> k0 a its series needs ~k0 r terms."""
     n, an, cn = coefficients(a, k0, k1, rho0, rho1)
     r = np.linalg.norm(points, axis=1)
     ct = np.where(r > 0, points[:, 2] / np.where(r > 0, r, 1), 1.0)
@@ -70,7 +72,7 @@ def total_field(points, a, k0, k1, rho0, rho1):
     ext = r >= a
     if ext.any():
         re = r[ext][:, None]
-        out[ext] = (P[ext] * pref * (spherical_jn(n, k0 * re) + an * _h(n, k0 * re))).sum(1)
+        out[ext] = np.exp(1j * k0 * points[ext, 2]) + (P[ext] * pref * an * _h(n, k0 * re)).sum(1)
     if (~ext).any():
         ri = r[~ext][:, None]
         out[~ext] = (P[~ext] * pref * cn * spherical_jn(n, k1 * ri)).sum(1)

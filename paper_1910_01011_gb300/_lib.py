@@ -70,6 +70,7 @@ _SIGS = {
     "bem_default_solve_opts": [ctypes.POINTER(bem_solve_opts)],
     "bem_solve": [_P, ctypes.POINTER(bem_solve_opts), ctypes.POINTER(bem_solve_report)],
     "bem_get_traces": [_P, ctypes.c_int32, ctypes.c_int64, _P, _P, ctypes.c_int],
+    "bem_field": [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, _P, ctypes.c_int],
     "bem_last_error": [_P],
     "bem_profile_enable": [_P, ctypes.c_int],
     "bem_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),

@@ -166,6 +166,14 @@ class Context:
         return d, n
 
 
+    def field(self, points, domain_of_point, rhs=0):
+        """Total pressure at points (representation formula); domain -1 = exterior."""
+        p = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+        d = np.ascontiguousarray(domain_of_point, dtype=np.int32).reshape(-1)
+        out = np.empty(p.shape[0], dtype=np.complex128)
+        self._check(self.lib.bem_field(self.h, int(rhs), p.ctypes.data, d.ctypes.data, p.shape[0], out.ctypes.data, 0))
+        return out
+
     # ---- measurement
     def profile(self, enable=True):
         self._check(self.lib.bem_profile_enable(self.h, 1 if enable else 0))

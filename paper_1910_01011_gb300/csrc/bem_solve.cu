@@ -251,6 +251,21 @@ static int build_rhs(bem_ctx* ctx) {
 
 void destroy_osrc_state(bem_ctx* ctx);
 
+// Traces and incident-field data of excitation `rhs` of the last solve, for
+// the field evaluation (k_field.cu).
+int solve_field_inputs(bem_ctx* ctx, int64_t rhs, const double2** u, const double4** disc, const double2** wts,
+                       int* n_elem, int* nq) {
+    SolveState* S = ctx->solve;
+    if (!S || S->n_rhs_solved == 0) return ctx->fail(BEM_ERR_STATE, "no solve has run");
+    if (rhs < 0 || rhs >= S->n_rhs_solved) return ctx->fail(BEM_ERR_INVALID_ARG, "excitation index out of range");
+    *u = S->u + rhs * ctx->geo.n_dof;
+    *disc = S->disc;
+    *n_elem = ctx->field_kind == 2 ? (int)ctx->tr_r.size() : 0;
+    *nq = ctx->field_kind == 2 ? 32 : 0;
+    *wts = ctx->field_kind == 2 ? S->wdev + rhs * (int64_t)ctx->tr_r.size() : nullptr;
+    return BEM_OK;
+}
+
 // Drop the solver objects after their device memory was released with the
 // rest of the context's allocations.
 void destroy_solver_state(bem_ctx* ctx) {

@@ -1,0 +1,241 @@
+// k_field.cu -- pressure at arbitrary points from the solved traces.
+//
+// Representation formula (paper App. A, eq. rep_formula_gen) with the
+// PMCHWT jump potentials: outside every domain
+//   p_tot(x) = p_inc(x) + DL_k0(gamma_D p_tot)(x) - SL_k0(gamma_N^+ p_tot)(x)
+// over all surfaces, and inside domain j
+//   p^j(x) = SL_kj((rho_j/rho_0) gamma_N^+ p_tot)(x) - DL_kj(gamma_D p_tot)(x)
+// over the surface of domain j (interior traces by eq. Form1_BCs); SL, DL
+// with G = exp(ikr)/(4 pi r).  Surface integrals use the regular rule with
+// the trial densities of the operator application (gather kernel), in FP32
+// with the tile-local phase of the far-field kernel; the regular rule loses
+// accuracy for points within about one element size of a surface.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "ctx.h"
+#include "internal.h"
+
+namespace gbem {
+
+struct FieldArgs {
+    const double* pts;      // [n][3]
+    const int32_t* dom;     // [n] -1 exterior, else domain
+    int64_t n;
+    const float4* pg;       // source points (dx, dy, dz, w)
+    const float4* pd;       // densities (w psi, w phi)
+    const float4* tg;       // triangles (n, h)
+    const double4* tc;
+    const int* tntri;
+    const int* tdom;
+    const double2* kdom;
+    const double* rho_ratio; // [n_dom]
+    double2 k0;
+    int n_tiles;
+    int inc_kind;            // 1 plane wave, 2 pistons
+    double pw_d[3];
+    double2 pw_amp;
+    const double4* disc;     // piston points (x, y, z, weight)
+    const double2* wts;      // piston weights of this excitation
+    int n_elem, nq;
+    double2 pref;
+    double2* out;
+};
+
+__device__ __forceinline__ float f_reduce_phase(double t) {
+    const double two_pi_hi = 6.283185307179586, two_pi_lo = 2.4492935982947064e-16;
+    double nn = rint(t * 0.15915494309189535);
+    double r = fma(-nn, two_pi_hi, t);
+    r = fma(-nn, two_pi_lo, r);
+    return (float)r;
+}
+
+__global__ void __launch_bounds__(TP) field_kernel(FieldArgs a) {
+    __shared__ float4 s_pg[TP], s_pd[TP], s_tg[TT];
+    const int64_t i = (int64_t)blockIdx.x * TP + threadIdx.x;
+    const bool live = i < a.n;
+    double x = 0, y = 0, z = 0;
+    int dom = -1;
+    if (live) {
+        x = a.pts[3 * i];
+        y = a.pts[3 * i + 1];
+        z = a.pts[3 * i + 2];
+        dom = a.dom[i];
+    }
+    const double2 k = dom < 0 ? a.k0 : a.kdom[dom];
+    const float kr = (float)k.x, nki = (float)-k.y, nkil2 = (float)(-k.y * 1.4426950408889634);
+    float slr = 0, sli = 0, dlr = 0, dli = 0;
+    for (int s = 0; s < a.n_tiles; s++) {
+        __syncthreads();
+        const int64_t pb = (int64_t)s * TP;
+        s_pg[threadIdx.x] = a.pg[pb + threadIdx.x];
+        s_pd[threadIdx.x] = a.pd[pb + threadIdx.x];
+        if (threadIdx.x < TT) s_tg[threadIdx.x] = a.tg[(int64_t)s * TT + threadIdx.x];
+        __syncthreads();
+        if (!live || (dom >= 0 && a.tdom[s] != dom)) continue;
+        const double4 c = a.tc[s];
+        const double Dx = x - c.x, Dy = y - c.y, Dz = z - c.z;  // x - c_source
+        const double R = sqrt(Dx * Dx + Dy * Dy + Dz * Dz);
+        const float D2x = (float)(2 * Dx), D2y = (float)(2 * Dy), D2z = (float)(2 * Dz);
+        const float Rc2 = (float)(R * R), Rc = (float)R, th = f_reduce_phase(k.x * R);
+        const int ntri = a.tntri[s];
+        for (int tl = 0; tl < ntri; tl++) {
+            const float4 tgv = s_tg[tl];
+            const float fK = tgv.w - 0.5f * (tgv.x * D2x + tgv.y * D2y + tgv.z * D2z);  // n_t.(y - x)
+            float S1r = 0, S1i = 0;
+#pragma unroll
+            for (int q = 0; q < QP; q++) {
+                const float4 g = s_pg[tl * QP + q];
+                const float4 d = s_pd[tl * QP + q];
+                const float ex = -g.x, ey = -g.y, ez = -g.z;
+                const float sd = ex * (D2x + ex) + ey * (D2y + ey) + ez * (D2z + ez);
+                const float r2 = Rc2 + sd;
+                const float rinv = rsqrtf(r2);
+                const float r = r2 * rinv;
+                const float rho = __fdividef(sd, r + Rc);
+                float sn, cs;
+                __sincosf(fmaf(kr, rho, th), &sn, &cs);
+                const float am = (nki != 0.f ? exp2f(nkil2 * r) : 1.f) * rinv;
+                const float Gr = am * cs, Gi = am * sn;
+                const float u = nki - rinv;
+                const float Fr = (Gr * u - Gi * kr) * rinv, Fi = (Gr * kr + Gi * u) * rinv;
+                slr += Gr * d.x - Gi * d.y;
+                sli += Gr * d.y + Gi * d.x;
+                S1r += Fr * d.z - Fi * d.w;
+                S1i += Fr * d.w + Fi * d.z;
+            }
+            dlr += fK * S1r;
+            dli += fK * S1i;
+        }
+    }
+    if (!live) return;
+    const double inv4pi = 0.07957747154594767;
+    double pr, pi;
+    if (dom >= 0) {
+        const double rr = a.rho_ratio[dom];
+        pr = inv4pi * (rr * slr - dlr);
+        pi = inv4pi * (rr * sli - dli);
+    } else {
+        pr = inv4pi * (dlr - slr);
+        pi = inv4pi * (dli - sli);
+        if (a.inc_kind == 1) {
+            const double ph = a.pw_d[0] * x + a.pw_d[1] * y + a.pw_d[2] * z;
+            double sn, cs;
+            sincos(a.k0.x * ph, &sn, &cs);
+            const double m = exp(-a.k0.y * ph);
+            pr += m * (a.pw_amp.x * cs - a.pw_amp.y * sn);
+            pi += m * (a.pw_amp.x * sn + a.pw_amp.y * cs);
+        } else if (a.inc_kind == 2) {
+            double qr = 0, qi = 0;
+            for (int e = 0; e < a.n_elem; e++) {
+                double er = 0, ei = 0;
+                for (int j = 0; j < a.nq; j++) {
+                    const double4 d = a.disc[(int64_t)e * a.nq + j];
+                    const double ex = x - d.x, ey = y - d.y, ez = z - d.z;
+                    const double R = sqrt(ex * ex + ey * ey + ez * ez);
+                    double sn, cs;
+                    sincos(a.k0.x * R, &sn, &cs);
+                    const double amp = exp(-a.k0.y * R) / R * d.w;
+                    er += amp * cs;
+                    ei += amp * sn;
+                }
+                const double2 w = a.wts[e];
+                qr += w.x * er - w.y * ei;
+                qi += w.x * ei + w.y * er;
+            }
+            pr += a.pref.x * qr - a.pref.y * qi;
+            pi += a.pref.x * qi + a.pref.y * qr;
+        }
+    }
+    a.out[i] = make_double2(pr, pi);
+}
+
+cudaError_t launch_field(const FieldArgs& a, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    field_kernel<<<(unsigned)((a.n + TP - 1) / TP), TP, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gbem
+
+using namespace gbem;
+
+#define CK(expr)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) return ctx->fail(BEM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int solve_field_inputs(bem_ctx* ctx, int64_t rhs, const double2** u, const double4** disc, const double2** wts,
+                       int* n_elem, int* nq);
+
+extern "C" int bem_field(bem_ctx* ctx, int64_t rhs, const double* points, const int32_t* domain_of_point,
+                         int64_t n_points, bem_z* out, int on_device) {
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (n_points < 0 || (n_points > 0 && (!points || !domain_of_point || !out)))
+        return ctx->fail(BEM_ERR_INVALID_ARG, "bad field arguments");
+    if (n_points == 0) return BEM_OK;
+    CK(cudaSetDevice(ctx->device));
+    const double2* u = nullptr;
+    const double4* disc = nullptr;
+    const double2* wts = nullptr;
+    int n_elem = 0, nq = 0;
+    int rc = solve_field_inputs(ctx, rhs, &u, &disc, &wts, &n_elem, &nq);
+    if (rc) return rc;
+    const Geometry& g = ctx->geo;
+    // check the domain ids on the host copy (device ids are checked by the caller's contract)
+    if (!on_device)
+        for (int64_t i = 0; i < n_points; i++)
+            if (domain_of_point[i] < -1 || domain_of_point[i] >= g.n_dom)
+                return ctx->fail(BEM_ERR_INVALID_ARG, "domain id of a point out of range");
+    // trial densities of the traces
+    GatherArgs ga{};
+    ga.slot_v = ctx->dev.slot_v; ga.v_dof1 = ctx->dev.v_dof1; ga.v_dof2 = ctx->dev.v_dof2; ga.pt_w = ctx->dev.pt_w;
+    ga.slot_curl = ctx->dev.slot_curl; ga.x = u; ga.s_begin = 0; ga.s_end = g.n_slots;
+    for (int q = 0; q < QP; q++)
+        for (int kk = 0; kk < 3; kk++) ga.lam[q][kk] = ctx->quad.lam[q][kk];
+    ga.pd32 = ctx->dev.pd32; ga.tcurl32 = ctx->dev.tcurl32;
+    CK(launch_gather(ga, ctx->stream));
+    // point arrays on the device
+    const double* dp = points;
+    const int32_t* dd = domain_of_point;
+    double2* dout = (double2*)out;
+    void* stage = nullptr;
+    if (!on_device) {
+        stage = ctx->dalloc((size_t)n_points * (3 * sizeof(double) + sizeof(int32_t) + sizeof(double2)) + 64, &rc);
+        if (rc) return rc;
+        // 16-byte values first so that every array stays aligned for any n
+        double2* so = (double2*)stage;
+        double* sp = (double*)(so + n_points);
+        int32_t* sd = (int32_t*)(sp + 3 * n_points);
+        CK(cudaMemcpyAsync(sp, points, n_points * 3 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(sd, domain_of_point, n_points * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+        dp = sp;
+        dd = sd;
+        dout = so;
+    }
+    std::vector<double> rr(g.n_dom);
+    for (int j = 0; j < g.n_dom; j++) rr[j] = ctx->doms[j].rho / ctx->rho0;
+    double* drr = (double*)ctx->dalloc(g.n_dom * sizeof(double), &rc);
+    if (rc) { ctx->dfree(stage); return rc; }
+    CK(cudaMemcpyAsync(drr, rr.data(), g.n_dom * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    FieldArgs a{};
+    a.pts = dp; a.dom = dd; a.n = n_points;
+    a.pg = ctx->dev.pg32; a.pd = ctx->dev.pd32; a.tg = ctx->dev.tg32; a.tc = ctx->dev.tc; a.tntri = ctx->dev.tntri;
+    a.tdom = ctx->dev.tdom; a.kdom = ctx->dev.kdom; a.rho_ratio = drr; a.k0 = make_double2(ctx->k0re, ctx->k0im);
+    a.n_tiles = g.n_tiles; a.inc_kind = ctx->field_kind;
+    for (int c = 0; c < 3; c++) a.pw_d[c] = ctx->pw_dir[c];
+    a.pw_amp = make_double2(ctx->pw_amp[0], ctx->pw_amp[1]);
+    a.disc = disc; a.wts = wts; a.n_elem = n_elem; a.nq = nq;
+    a.pref = make_double2(0.0, -ctx->omega_rho0 / (2.0 * M_PI));
+    a.out = dout;
+    CK(launch_field(a, ctx->stream));
+    ctx->launches += 2;
+    if (!on_device) CK(cudaMemcpyAsync(out, dout, n_points * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->dfree(drr);
+    ctx->dfree(stage);
+    return ctx->check_device_error();
+}
