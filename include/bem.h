@@ -55,8 +55,10 @@ enum {
 enum {
     BEM_PREC_FP64 = 0, /* FP64 everywhere (the baseline path) */
     BEM_PREC_FP32 = 1, /* FP32 far field with tile-local phase, FP64 near field and output */
-    BEM_PREC_BF16X3 = 2 /* assembled complex64 A_hat (set-up once; N^2 x 12 bytes of BF16 planes kept)
-                           applied to all right-hand sides at once by the split-BF16 tensor-core GEMM */
+    BEM_PREC_BF16X3 = 2, /* assembled complex64 A_hat (set-up once; N^2 x 12 bytes of BF16 planes kept)
+                            applied to all right-hand sides at once by the split-BF16 tensor-core GEMM */
+    BEM_PREC_FP64_ASSEMBLED = 3 /* assembled complex128 A_hat (set-up once in FP64; N^2 x 16 bytes kept),
+                                   applied by a complex GEMM/GEMV: the fast FP64 residual */
 };
 
 /* Operators for bem_apply. */
@@ -175,6 +177,9 @@ typedef struct {
     int32_t precondition;  /* 1 = OSRC preconditioner */
     double inner_tol;      /* inner relative tolerance of the mixed-precision path (default 1e-4) */
     int32_t max_refine;    /* outer refinement cap (default 10) */
+    int32_t operator_mode; /* 0: matrix-free operators; 1: assembled operators (BF16-split tensor-core
+                              GEMM inside GMRES, complex128 GEMV for FP64 residuals), set up once and
+                              kept on the device for later solves */
 } bem_solve_opts;
 
 typedef struct {

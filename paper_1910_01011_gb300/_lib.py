@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libgbem.so")
 BEM_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "MESH_INVALID", -3: "OUT_OF_BUDGET", -4: "NOT_CONVERGED", -5: "TIMEOUT",
           -6: "CUDA", -7: "STATE"}
-PREC_FP64, PREC_FP32, PREC_BF16X3 = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_BF16X3, PREC_FP64_ASSEMBLED = 0, 1, 2, 3
 OP_AHAT, OP_PREC, OP_PREC_AHAT = 0, 1, 2
 
 
@@ -32,7 +32,7 @@ class bem_opts(ctypes.Structure):
 class bem_solve_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("precondition", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int32)]
+                ("max_refine", ctypes.c_int32), ("operator_mode", ctypes.c_int32)]
 
 
 class bem_solve_report(ctypes.Structure):

@@ -10,7 +10,7 @@ import numpy as np
 from . import _lib
 from ._lib import bem_z, check
 
-FP64, FP32, BF16X3 = _lib.PREC_FP64, _lib.PREC_FP32, _lib.PREC_BF16X3
+FP64, FP32, BF16X3, FP64_ASSEMBLED = _lib.PREC_FP64, _lib.PREC_FP32, _lib.PREC_BF16X3, _lib.PREC_FP64_ASSEMBLED
 AHAT, PREC, PREC_AHAT = _lib.OP_AHAT, _lib.OP_PREC, _lib.OP_PREC_AHAT
 
 

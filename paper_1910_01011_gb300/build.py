@@ -52,7 +52,8 @@ def build(verbose: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     if not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        r = subprocess.run(["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
+        r = subprocess.run(["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas"], capture_output=True,
+                           text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stderr)
         os.replace(tmp, LIB)

@@ -2,6 +2,7 @@
 // operator application pipeline
 //   gather (trial densities) -> far field (FP32 or FP64) -> projection onto
 //   P1 test functions with the touching-pair correction -> vertex reduction.
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -85,6 +86,8 @@ static void release_device(bem_ctx* ctx) {
     ctx->osrc_ready = false;
     ctx->rhs_ready = false;
     ctx->asm_ready = false;
+    ctx->asm64_ready = false;
+    ctx->asm64 = nullptr;
     ctx->asm_planes = nullptr;
     ctx->asm_work = nullptr;
     ctx->asm_work_bytes = 0;
@@ -411,6 +414,7 @@ int bem_create(bem_ctx** out, int device, void* cuda_stream, const bem_opts* opt
 int bem_destroy(bem_ctx* ctx) {
     if (!ctx) return BEM_OK;
     release_device(ctx);
+    if (ctx->cublas) cublasDestroy(ctx->cublas);
     delete ctx;
     return BEM_OK;
 }
@@ -426,6 +430,7 @@ int bem_set_exterior(bem_ctx* ctx, bem_z k0, double rho0) {
         ctx->osrc_ready = false;
         ctx->rhs_ready = false;
         ctx->asm_ready = false;
+        ctx->asm64_ready = false;
         return ctx->upload_materials();
     }
     return BEM_OK;
@@ -470,6 +475,7 @@ int bem_set_material(bem_ctx* ctx, int32_t id, bem_z k, double rho) {
         ctx->near_ready = false;
         ctx->osrc_ready = false;
         ctx->asm_ready = false;
+        ctx->asm64_ready = false;
         return ctx->upload_materials();
     }
     return BEM_OK;
@@ -508,14 +514,14 @@ static int io_in(bem_ctx* ctx, const bem_z* x, int64_t n, int on_device, const d
 int bem_apply(bem_ctx* ctx, int op, const bem_z* x, bem_z* y, int64_t n_rhs, int precision, int on_device) {
     if (!ctx) return BEM_ERR_INVALID_ARG;
     if (!x || !y || n_rhs < 1) return ctx->fail(BEM_ERR_INVALID_ARG, "null vector or n_rhs < 1");
-    if (precision != BEM_PREC_FP64 && precision != BEM_PREC_FP32 && precision != BEM_PREC_BF16X3)
+    if (precision < BEM_PREC_FP64 || precision > BEM_PREC_FP64_ASSEMBLED)
         return ctx->fail(BEM_ERR_INVALID_ARG, "bad precision");
     if (op < BEM_OP_AHAT || op > BEM_OP_PREC_AHAT) return ctx->fail(BEM_ERR_INVALID_ARG, "bad op");
     CK(cudaSetDevice(ctx->device));
     int rc = ctx->finalize();
     if (rc) return rc;
     const int64_t N = ctx->geo.n_dof;
-    if (precision == BEM_PREC_BF16X3 && op != BEM_OP_PREC) {
+    if ((precision == BEM_PREC_BF16X3 || precision == BEM_PREC_FP64_ASSEMBLED) && op != BEM_OP_PREC) {
         // all right-hand sides in one tensor-core GEMM on the assembled operator
         const double2* xd = (const double2*)x;
         double2* yd = (double2*)y;
@@ -527,7 +533,7 @@ int bem_apply(bem_ctx* ctx, int op, const bem_z* x, bem_z* y, int64_t n_rhs, int
             xd = stage;
             yd = stage + n_rhs * N;
         }
-        rc = ctx->apply_assembled(xd, yd, n_rhs);
+        rc = precision == BEM_PREC_BF16X3 ? ctx->apply_assembled(xd, yd, n_rhs) : ctx->apply_assembled64(xd, yd, n_rhs);
         for (int64_t r = 0; !rc && op == BEM_OP_PREC_AHAT && r < n_rhs; r++) {
             CK(cudaMemcpyAsync(ctx->dev.ys2, yd + r * N, N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
             rc = ctx->apply_prec(ctx->dev.ys2, yd + r * N);

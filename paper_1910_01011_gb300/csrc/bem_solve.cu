@@ -352,6 +352,7 @@ int bem_default_solve_opts(bem_solve_opts* o) {
     o->precondition = 1;
     o->inner_tol = 1e-4;
     o->max_refine = 10;
+    o->operator_mode = 0;
     return BEM_OK;
 }
 
@@ -360,7 +361,8 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     bem_solve_opts o;
     bem_default_solve_opts(&o);
     if (opts) o = *opts;
-    if (o.restart < 1 || o.max_iter < 1 || !(o.tol > 0) || (o.precision != BEM_PREC_FP64 && o.precision != BEM_PREC_FP32))
+    if (o.restart < 1 || o.max_iter < 1 || !(o.tol > 0) || (o.precision != BEM_PREC_FP64 && o.precision != BEM_PREC_FP32) ||
+        (o.operator_mode != 0 && o.operator_mode != 1))
         return ctx->fail(BEM_ERR_INVALID_ARG, "bad solve options");
     CK(cudaSetDevice(ctx->device));
     const auto t0 = std::chrono::steady_clock::now();
@@ -374,9 +376,17 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     if ((rc = S->kry.ensure(ctx, N, o.restart))) return rc;
     bem_solve_report R{};
     bool converged = true;
-    auto op_for = [&](int prec) {
-        return [ctx, prec, &o](const double2* x, double2* y) -> int {
-            return o.precondition ? ctx->apply_prec_ahat(x, y, prec) : ctx->apply_ahat(x, y, prec);
+    // the operator of one precision level: matrix-free or assembled, then the preconditioner
+    auto plain = [ctx, &o](const double2* x, double2* y, int prec) -> int {
+        if (o.operator_mode == 1)
+            return prec == BEM_PREC_FP64 ? ctx->apply_assembled64(x, y, 1) : ctx->apply_assembled(x, y, 1);
+        return ctx->apply_ahat(x, y, prec);
+    };
+    auto op_for = [ctx, &o, plain](int prec) {
+        return [ctx, prec, &o, plain](const double2* x, double2* y) -> int {
+            if (!o.precondition) return plain(x, y, prec);
+            int r = plain(x, ctx->dev.ys2, prec);
+            return r ? r : ctx->apply_prec(ctx->dev.ys2, y);
         };
     };
     for (int64_t r = 0; r < nr; r++) {
@@ -405,7 +415,7 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
                     return rc;
                 it += its;
                 // true FP64 residual of the unpreconditioned system
-                if ((rc = ctx->apply_ahat(u, S->r, BEM_PREC_FP64))) return rc;
+                if ((rc = plain(u, S->r, BEM_PREC_FP64))) return rc;
                 if ((rc = S->kry.axpby(ctx, 1.0, b, -1.0, S->r, S->r))) return rc;
                 double rn;
                 if ((rc = S->kry.norm(ctx, S->r, &rn))) return rc;
@@ -437,7 +447,7 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
                     return rc;
                 it += its;
                 if ((rc = S->kry.axpby(ctx, 1.0, u, 1.0, S->d, u))) return rc;
-                if ((rc = ctx->apply_ahat(u, S->r, BEM_PREC_FP64))) return rc;
+                if ((rc = plain(u, S->r, BEM_PREC_FP64))) return rc;
                 if ((rc = S->kry.axpby(ctx, 1.0, b, -1.0, S->r, S->r))) return rc;
             }
             R.iterations += it;

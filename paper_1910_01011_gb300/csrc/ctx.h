@@ -1,6 +1,7 @@
 // ctx.h -- the opaque bem_ctx behind the C ABI.
 #pragma once
 
+#include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -90,6 +91,10 @@ struct bem_ctx {
     int64_t asm_mpad = 0, asm_kpad = 0;
     void* asm_work = nullptr;
     size_t asm_work_bytes = 0;
+    // assembled operator in complex128 (FP64 refinement residuals)
+    bool asm64_ready = false;
+    double2* asm64 = nullptr;
+    cublasHandle_t cublas = nullptr;
     gbem::OsrcState* osrc = nullptr;
     gbem::SolveState* solve = nullptr;
     // incident field
@@ -117,4 +122,6 @@ struct bem_ctx {
     int check_device_error();
     int ensure_assembled();
     int apply_assembled(const double2* x, double2* y, int64_t n_rhs);
+    int ensure_assembled64();
+    int apply_assembled64(const double2* x, double2* y, int64_t n_rhs);
 };

@@ -13,6 +13,7 @@
 // Sauter-Schwab correction block (k_near.cu).  Local blocks are added into
 // the matrix with FP32 atomics (set-up only; the order of additions varies
 // between runs at the level of FP32 rounding).
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -41,6 +42,7 @@ struct AssembleArgs {
     int64_t n;              // matrix dimension (leading dimension)
     float2* A;              // dense, row-major, n x n
     float lam[QP][3];
+    double lam64[QP][3];
 };
 
 __device__ __forceinline__ float a_reduce_phase(double t) {
@@ -163,6 +165,133 @@ __global__ void __launch_bounds__(TT) assemble_kernel(AssembleArgs a) {
     }
 }
 
+// FP64 version of the assembly (straight FP64 distances and transcendentals),
+// for the refinement residual: entries accumulated with FP64 atomics.
+__global__ void __launch_bounds__(TT) assemble64_kernel(AssembleArgs a, const double4* pg64, const double4* tg64,
+                                                        double2* A64) {
+    const int tt = blockIdx.x;
+    const int tl = threadIdx.x;
+    const int64_t ts = (int64_t)tt * TT + tl;
+    const int4 tv = a.slot_v[ts];
+    if (tv.x < 0) return;
+    const int dom = tv.w;
+    const int2 dr = a.dom_tiles[dom];
+    int sb = blockIdx.y * a.chunk_tiles, se = min(sb + a.chunk_tiles, a.n_tiles);
+    if (a.slot == 1) {
+        sb = max(sb, dr.x);
+        se = min(se, dr.y);
+    }
+    if (sb >= se) return;
+    const double2 kd = a.slot == 0 ? a.k0 : a.kdom[dom];
+    const double kr = kd.x, ki = kd.y;
+    const SlotCoef cf = a.coef[dom * 2 + a.slot];
+    const double inv4pi = 0.07957747154594767;
+    const double4 ng = tg64[ts];
+    const double4 ct = a.tc[tt];
+    const int64_t ra[3] = {a.v_dof1[tv.x], a.v_dof1[tv.y], a.v_dof1[tv.z]};
+    const int64_t rb[3] = {a.v_dof2[tv.x], a.v_dof2[tv.y], a.v_dof2[tv.z]};
+    for (int s = sb; s < se; s++) {
+        const double4 cs = a.tc[s];
+        const double Dx = ct.x - cs.x, Dy = ct.y - cs.y, Dz = ct.z - cs.z;
+        const int ntri = a.tntri[s];
+        for (int sl = 0; sl < ntri; sl++) {
+            const int64_t ss = (int64_t)s * TT + sl;
+            if (ss == ts) continue;
+            const double4 sg = tg64[ss];
+            double V[3][3][2] = {}, K[3][3][2] = {}, Kp[3][3][2] = {};
+            for (int qx = 0; qx < QP; qx++) {
+                const double4 x = pg64[ts * QP + qx];
+                const double Xx = x.x + Dx, Xy = x.y + Dy, Xz = x.z + Dz;  // x - c_source
+                const double fK = sg.w - (sg.x * Xx + sg.y * Xy + sg.z * Xz);
+                double hV[3][2] = {}, hK[3][2] = {}, hKp[3][2] = {};
+                for (int qy = 0; qy < QP; qy++) {
+                    const double4 y = pg64[ss * QP + qy];
+                    const double ex = Xx - y.x, ey = Xy - y.y, ez = Xz - y.z;  // x - y
+                    const double r = sqrt(ex * ex + ey * ey + ez * ez);
+                    const double rinv = 1.0 / r;
+                    double sn, c2;
+                    sincos(kr * r, &sn, &c2);
+                    const double am = exp(-ki * r) * rinv;
+                    const double Gr = am * c2, Gi = am * sn;
+                    const double u = -ki - rinv;
+                    const double Fr = (Gr * u - Gi * kr) * rinv, Fi = (Gr * kr + Gi * u) * rinv;
+                    const double ndot = ng.x * ex + ng.y * ey + ng.z * ez;
+                    for (int b = 0; b < 3; b++) {
+                        const double wl = y.w * (double)a.lam64[qy][b];
+                        hV[b][0] += wl * Gr;
+                        hV[b][1] += wl * Gi;
+                        hK[b][0] += wl * Fr;
+                        hK[b][1] += wl * Fi;
+                        hKp[b][0] += wl * ndot * Fr;
+                        hKp[b][1] += wl * ndot * Fi;
+                    }
+                }
+                for (int i = 0; i < 3; i++) {
+                    const double wx = x.w * a.lam64[qx][i] * inv4pi;
+                    for (int b = 0; b < 3; b++) {
+                        V[i][b][0] += wx * hV[b][0];
+                        V[i][b][1] += wx * hV[b][1];
+                        K[i][b][0] += wx * fK * hK[b][0];
+                        K[i][b][1] += wx * fK * hK[b][1];
+                        Kp[i][b][0] += wx * hKp[b][0];
+                        Kp[i][b][1] += wx * hKp[b][1];
+                    }
+                }
+            }
+            double sr = 0, si = 0;
+            for (int i = 0; i < 3; i++)
+                for (int b = 0; b < 3; b++) {
+                    sr += V[i][b][0];
+                    si += V[i][b][1];
+                }
+            const double nn = ng.x * sg.x + ng.y * sg.y + ng.z * sg.z;
+            const int4 sv = a.slot_v[ss];
+            const int vb[3] = {sv.x, sv.y, sv.z};
+            for (int b = 0; b < 3; b++) {
+                const int64_t ca = a.v_dof1[vb[b]], cb = a.v_dof2[vb[b]];
+                for (int i = 0; i < 3; i++) {
+                    double cc = 0;
+                    for (int c = 0; c < 3; c++) cc += a.slot_curl[ts * 9 + 3 * i + c] * a.slot_curl[ss * 9 + 3 * b + c];
+                    const double kvr = cf.k2re * V[i][b][0] - cf.k2im * V[i][b][1];
+                    const double kvi = cf.k2re * V[i][b][1] + cf.k2im * V[i][b][0];
+                    double* e;
+                    e = reinterpret_cast<double*>(&A64[ra[i] * a.n + ca]);
+                    atomicAdd(e, cf.cV * V[i][b][0]);
+                    atomicAdd(e + 1, cf.cV * V[i][b][1]);
+                    e = reinterpret_cast<double*>(&A64[ra[i] * a.n + cb]);
+                    atomicAdd(e, -cf.cK * K[i][b][0]);
+                    atomicAdd(e + 1, -cf.cK * K[i][b][1]);
+                    e = reinterpret_cast<double*>(&A64[rb[i] * a.n + ca]);
+                    atomicAdd(e, cf.cKp * Kp[i][b][0]);
+                    atomicAdd(e + 1, cf.cKp * Kp[i][b][1]);
+                    e = reinterpret_cast<double*>(&A64[rb[i] * a.n + cb]);
+                    atomicAdd(e, cf.cW * (cc * sr - nn * kvr));
+                    atomicAdd(e + 1, cf.cW * (cc * si - nn * kvi));
+                }
+            }
+        }
+    }
+}
+
+__global__ void add_near64_kernel(int64_t n_pairs, const int32_t* pair_tgt, const int32_t* pair_src,
+                                  const int4* slot_v, const int64_t* v_dof1, const int64_t* v_dof2,
+                                  const double2* nb64, int64_t n, double2* A) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pairs) return;
+    const int4 tv = slot_v[pair_tgt[p]], sv = slot_v[pair_src[p]];
+    const int va[3] = {tv.x, tv.y, tv.z}, vb[3] = {sv.x, sv.y, sv.z};
+    for (int blk = 0; blk < 4; blk++)
+        for (int i = 0; i < 3; i++)
+            for (int b = 0; b < 3; b++) {
+                const int64_t row = (blk < 2) ? v_dof1[va[i]] : v_dof2[va[i]];
+                const int64_t col = (blk & 1) ? v_dof2[vb[b]] : v_dof1[vb[b]];
+                const double2 v = nb64[(p * 4 + blk) * 9 + 3 * i + b];
+                double* e = reinterpret_cast<double*>(&A[row * n + col]);
+                atomicAdd(e, v.x);
+                atomicAdd(e + 1, v.y);
+            }
+}
+
 // Touching-pair corrections (combined FP32 blocks) into the dense matrix.
 __global__ void add_near_kernel(int64_t n_pairs, const int32_t* pair_tgt, const int32_t* pair_src, const int4* slot_v,
                                 const int64_t* v_dof1, const int64_t* v_dof2, const float2* nb32, int64_t n,
@@ -227,7 +356,10 @@ int bem_ctx::ensure_assembled() {
     a.dom_tiles = dev.dom_tiles; a.kdom = dev.kdom; a.k0 = make_double2(k0re, k0im);
     a.n_tiles = g.n_tiles; a.chunk_tiles = 16; a.n = n; a.A = A;
     for (int q = 0; q < QP; q++)
-        for (int k = 0; k < 3; k++) a.lam[q][k] = (float)quad.lam[q][k];
+        for (int k = 0; k < 3; k++) {
+            a.lam[q][k] = (float)quad.lam[q][k];
+            a.lam64[q][k] = quad.lam[q][k];
+        }
     const dim3 grid(g.n_tiles, (g.n_tiles + a.chunk_tiles - 1) / a.chunk_tiles);
     for (int sl = 0; sl < 2; sl++) {
         a.slot = sl;
@@ -249,6 +381,69 @@ int bem_ctx::ensure_assembled() {
     asm_mpad = mpad;
     asm_kpad = kpad;
     asm_ready = true;
+    return BEM_OK;
+}
+
+// A_hat assembled in complex128 (FP64 arithmetic), kept for the FP64
+// residual of the refinement: one pass of FP64 interactions at set-up, then
+// every residual is a memory-bound complex GEMM / GEMV (cuBLAS).
+int bem_ctx::ensure_assembled64() {
+    bem_ctx* const ctx = this;
+    if (asm64_ready) return BEM_OK;
+    int rc = ensure_near();
+    if (rc) return rc;
+    const Geometry& g = geo;
+    const int64_t n = g.n_dof;
+    if (asm64) { dfree(asm64); asm64 = nullptr; }
+    asm64 = (double2*)dalloc((size_t)n * n * sizeof(double2), &rc);
+    if (rc) { asm64 = nullptr; return rc; }
+    CK(cudaMemsetAsync(asm64, 0, (size_t)n * n * sizeof(double2), stream));
+    AssembleArgs a{};
+    a.tc = dev.tc; a.tntri = dev.tntri; a.slot_v = dev.slot_v; a.slot_curl = dev.slot_curl;
+    a.v_dof1 = dev.v_dof1; a.v_dof2 = dev.v_dof2; a.coef = dev.coef; a.dom_tiles = dev.dom_tiles; a.kdom = dev.kdom;
+    a.k0 = make_double2(k0re, k0im); a.n_tiles = g.n_tiles; a.chunk_tiles = 8; a.n = n;
+    for (int q = 0; q < QP; q++)
+        for (int k = 0; k < 3; k++) a.lam64[q][k] = quad.lam[q][k];
+    const dim3 grid(g.n_tiles, (g.n_tiles + a.chunk_tiles - 1) / a.chunk_tiles);
+    for (int sl = 0; sl < 2; sl++) {
+        a.slot = sl;
+        assemble64_kernel<<<grid, TT, 0, stream>>>(a, dev.pg64, dev.tg64, asm64);
+        CK(cudaGetLastError());
+    }
+    const int64_t np = pmchwt_near.n_pairs;
+    if (np > 0) {
+        add_near64_kernel<<<(unsigned)((np + 127) / 128), 128, 0, stream>>>(np, dev.np_tgt, dev.np_src, dev.slot_v,
+                                                                           dev.v_dof1, dev.v_dof2, pmchwt_near.nb64,
+                                                                           n, asm64);
+        CK(cudaGetLastError());
+    }
+    if (!cublas) {
+        if (cublasCreate(&cublas) != CUBLAS_STATUS_SUCCESS) return fail(BEM_ERR_CUDA, "cublasCreate failed");
+    }
+    if (cublasSetStream(cublas, stream) != CUBLAS_STATUS_SUCCESS) return fail(BEM_ERR_CUDA, "cublasSetStream failed");
+    CK(cudaStreamSynchronize(stream));
+    launches += 3;
+    asm64_ready = true;
+    return BEM_OK;
+}
+
+// Y = A_hat X (FP64, assembled) for n_rhs system-order vectors.  A is
+// row-major, i.e. column-major A^T for cuBLAS: Y = (A^T)^T X.
+int bem_ctx::apply_assembled64(const double2* x, double2* y, int64_t n_rhs) {
+    int rc = ensure_assembled64();
+    if (rc) return rc;
+    const int64_t n = geo.n_dof;
+    const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+    cublasStatus_t st;
+    if (n_rhs == 1)
+        st = cublasZgemv(cublas, CUBLAS_OP_T, (int)n, (int)n, &one, (const cuDoubleComplex*)asm64, (int)n,
+                         (const cuDoubleComplex*)x, 1, &zero, (cuDoubleComplex*)y, 1);
+    else
+        st = cublasZgemm(cublas, CUBLAS_OP_T, CUBLAS_OP_N, (int)n, (int)n_rhs, (int)n, &one,
+                         (const cuDoubleComplex*)asm64, (int)n, (const cuDoubleComplex*)x, (int)n, &zero,
+                         (cuDoubleComplex*)y, (int)n);
+    if (st != CUBLAS_STATUS_SUCCESS) return fail(BEM_ERR_CUDA, "cuBLAS complex product failed");
+    launches += 1;
     return BEM_OK;
 }
 

@@ -85,3 +85,38 @@ def test_context_rebuilds_after_adding_a_domain():
     got = np.concatenate([np.concatenate([c.traces(j)[1], c.traces(j)[0]]) for j in range(2)])
     assert np.linalg.norm(got - u) / np.linalg.norm(u) < 1e-6
     c.close()
+
+
+@pytest.mark.parametrize("name", ["sphere", "shell"])
+def test_fp64_assembled_operator_matches_oracle(name):
+    """BEM_PREC_FP64_ASSEMBLED: A_hat assembled in complex128 and applied by a
+    complex GEMV/GEMM (the FP64 refinement residual), FP64 bar 1e-11."""
+    from paper_1910_01011_gb300 import api
+    s = {"sphere": lambda: scenes.sphere_scene(2), "shell": lambda: scenes.shell_scene(1)}[name]()
+    A = pmchwt.assemble(s)
+    c = api.Context.from_scene(s)
+    rng = np.random.default_rng(6)
+    for n_rhs in (1, 5):
+        X = rng.standard_normal((n_rhs, A.shape[0])) + 1j * rng.standard_normal((n_rhs, A.shape[0]))
+        Y = c.apply(X, precision=api.FP64_ASSEMBLED)
+        ref = X @ A.T
+        err = np.linalg.norm(Y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert err.max() < 1e-11, err.max()
+    c.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_with_assembled_operators(precision):
+    """bem_solve with operator_mode = 1 (assembled operators for the inner
+    iterations and the FP64 residual): traces within 1e-6 of the oracle."""
+    from paper_1910_01011_gb300 import api
+    s = scenes.sphere_scene(3)
+    u, A, b = pmchwt.solve(s, pmchwt.plane_wave(s.k0, (0, 0, 1)))
+    c = api.Context.from_scene(s, r_eps=0.2)
+    c.set_plane_wave((0, 0, 1))
+    rep = c.solve(precision=precision, tol=1e-10, operator_mode=1)
+    assert rep["converged"], rep
+    D, N = c.traces(0)
+    got = np.concatenate([N, D])
+    assert np.linalg.norm(got - u) / np.linalg.norm(u) < 1e-6
+    c.close()
