@@ -15,12 +15,12 @@ impedance ratio 5.2, taken here as rho = 1900 kg/m^3, c = 4100 m/s with
 Table 1's rib attenuation (47 Np/m at 1 MHz).  The mesh is a cube-sphere
 (synthetic; the paper's meshes are not available).
 
-Run:  python -m paper_1910_01011_gb300.experiments.sphere [--el 4 6 8 10]
+This module runs the GPU solve and evaluates the total field on the grid;
+the comparison with the analytic series lives with the tests
+(tests/sphere_experiment.py), which may use the oracle's Mie routine.
 """
 from __future__ import annotations
 
-import argparse
-import json
 import math
 import time
 
@@ -58,8 +58,9 @@ def field_grid(radius: float, n: int = 200):
 
 
 def run(material: str, el_per_lambda: float, device: int = 0, tol: float = 1e-5, precision: int = 1):
-    """One point of the experiment; returns a dict of measurements."""
-    from oracle import mie  # analytic reference (test infrastructure)
+    """One point of the experiment: solve, then the total field on the grid.
+    Returns the measurements plus `points`, `field` and the sphere's
+    parameters (`radius`, `k0`, `kj`, `rho0`, `rho`) for the comparison."""
     from paper_1910_01011_gb300.api import Context
     s = build_scene(material, el_per_lambda)
     d = s.domains[0]
@@ -71,26 +72,10 @@ def run(material: str, el_per_lambda: float, device: int = 0, tol: float = 1e-5,
     wall = time.perf_counter() - t0
     pts, dom = field_grid(R)
     got = c.field(pts, dom)
-    ref = mie.total_field(pts, R, s.k0, d.k, s.rho0, d.rho)
-    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     c.close()
     return {"material": material, "el_per_lambda": el_per_lambda,
             "el_per_lambda_mean_edge": s.meta["el_per_lambda_actual"], "triangles": int(d.tris.shape[0]),
             "dofs": 2 * int(d.verts.shape[0]), "iterations": rep["iterations"], "refinements": rep["refinements"],
             "converged": rep["converged"], "solve_s": wall, "s_per_iteration": wall / max(1, rep["iterations"]),
-            "field_l2_error": err, "z_ratio": d.rho * (2 * math.pi * s.freq / d.k.real) / (s.rho0 * 1500.0)}
-
-
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--el", type=float, nargs="+", default=[4, 6, 8, 10])
-    ap.add_argument("--materials", nargs="+", default=["fat", "bone"])
-    ap.add_argument("--tol", type=float, default=1e-5)
-    args = ap.parse_args()
-    for m in args.materials:
-        for e in args.el:
-            print(json.dumps(run(m, e, tol=args.tol)))
-
-
-if __name__ == "__main__":
-    main()
+            "z_ratio": d.rho * (2 * math.pi * s.freq / d.k.real) / (s.rho0 * 1500.0),
+            "points": pts, "field": got, "radius": R, "k0": s.k0, "kj": d.k, "rho0": s.rho0, "rho": d.rho}

@@ -9,9 +9,9 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("material", ["fat", "bone"])
 def test_sphere_experiment(material):
-    from paper_1910_01011_gb300.experiments import sphere
-    r4 = sphere.run(material, 4)
-    r6 = sphere.run(material, 6)
+    from sphere_experiment import measure
+    r4 = measure(material, 4)
+    r6 = measure(material, 6)
     print(r4, r6)
     assert r4["converged"] and r6["converged"]
     assert r6["field_l2_error"] < 0.03
