@@ -28,11 +28,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "BEM operator-apply Ginteractions/s"
 UNIT = "Ginteractions/s"
-# Algorithmic FP32 work of far32_kernel per (target point, source point)
-# pair, counted from its source (FFMA = 2 flops, FADD/FMUL = 1; MUFU
-# excluded): shared geometry 21 flops + per-triangle shared terms 11/6;
-# per wavenumber 52 flops (54 when Im k != 0: the exp(-Im k r) factor) +
-# per-triangle 32/6.
+# Algorithmic FP32 work per (target point, source point) pair: the direct
+# evaluation of the interaction formulas (G, F = G (ik - 1/r)/r, the four
+# accumulations; FFMA = 2 flops, FADD/FMUL = 1, MUFU excluded), counted once
+# and kept fixed as the unit of work, so that a kernel which reaches the same
+# result with fewer operations shows a higher achieved rate: shared geometry
+# 21 flops + per-triangle shared terms 11/6; per wavenumber 52 flops (54 when
+# Im k != 0: the exp(-Im k r) factor) + per-triangle 32/6.
 FL_SHARED = 21.0 + 11.0 / 6.0
 FL_SLOT_LOSSLESS = 52.0 + 32.0 / 6.0
 FL_SLOT_LOSSY = 54.0 + 32.0 / 6.0

@@ -76,6 +76,11 @@ typedef struct {
     double pade_theta;         /* OSRC branch-cut rotation (default pi/3) */
     double r_eps;              /* OSRC damping radius R_eps (Sec. 2.3 eq. OSRC_DtN_NtD_maps); <= 0: 1/10 of the largest domain diameter */
     double eps_exponent;       /* exponent of k in eps = 0.4 k^e R_eps^(-2/3); default 1/3 */
+    double osrc_tol;           /* relative residual of the preconditioner's sparse solves in bem_apply
+                                  (default 1e-11); bem_solve uses 1/100 of its own GMRES tolerance */
+    int32_t osrc_solver;       /* sparse solver of the preconditioner: 0 automatic (one CTA per system and
+                                  domain up to 65536 vertices per domain, else grid-wide), 1 one CTA per
+                                  system and domain, 2 grid-wide kernels; same results within osrc_tol */
 } bem_opts;
 
 /* Fill opts with the defaults above. */
@@ -180,6 +185,18 @@ typedef struct {
     int32_t operator_mode; /* 0: matrix-free operators; 1: assembled operators (BF16-split tensor-core
                               GEMM inside GMRES, complex128 GEMV for FP64 residuals), set up once and
                               kept on the device for later solves */
+    int32_t batch_rhs;     /* >1: excitations are solved in blocks of up to batch_rhs right-hand sides,
+                              R independent GMRES runs in lockstep whose operator and preconditioner
+                              applications act on all R columns at once (one GEMM per application with
+                              operator_mode 1); each column stops on its own residual.  0 or 1: one
+                              excitation after another (default).  The results do not depend on it. */
+    int32_t flexible;      /* 1 (default): the preconditioner is applied on the right, u = P y, inside a
+                              flexible GMRES that keeps the preconditioned basis, so its sparse solves may
+                              stop at the loose tolerance prec_tol; GMRES then measures the residual of
+                              A_hat itself.  0: the paper's left composition P A_hat u = P b with plain
+                              GMRES (sparse solves to 1/100 of the GMRES tolerance).  Same solution. */
+    double prec_tol;       /* relative residual of the preconditioner's sparse solves inside the solve;
+                              0 = automatic (1e-2 flexible, 1/100 of the GMRES tolerance otherwise) */
 } bem_solve_opts;
 
 typedef struct {
@@ -201,6 +218,12 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* report
  * the interior Neumann trace is rho_j/rho_0 times it, eq. Form1_BCs). */
 int bem_get_traces(bem_ctx* ctx, int32_t domain_id, int64_t rhs, bem_z* dirichlet, bem_z* neumann, int on_device);
 
+/* The whole solution vector of excitation `rhs` of the last solve, in system
+ * order: per domain j, [gamma_N^+ p_tot (n_v,j); gamma_D p_tot (n_v,j)]
+ * (the unknown [psi; phi] of Sec. 2.3 after the column permutation).
+ * u: bem_num_dofs complex values, host or device (on_device = 1). */
+int bem_get_solution(bem_ctx* ctx, int64_t rhs, bem_z* u, int on_device);
+
 /* Kernel timing for measurement: when enabled, the library records CUDA
  * events on its stream around every far-field kernel launch.
  * bem_profile_read synchronises the stream and returns the summed far-field
@@ -208,6 +231,26 @@ int bem_get_traces(bem_ctx* ctx, int32_t domain_id, int64_t rhs, bem_z* dirichle
  * kernels the library launched since the last reset (reset = 1 clears). */
 int bem_profile_enable(bem_ctx* ctx, int enable);
 int bem_profile_read(bem_ctx* ctx, double* far_ms, int64_t* far_launches, int64_t* kernel_launches, int reset);
+
+/* Device memory of the context: bytes held now and the most it has held. */
+int bem_memory_info(const bem_ctx* ctx, int64_t* used_bytes, int64_t* peak_bytes);
+
+/* Upper estimate of the device bytes a solve of n_exc excitations with
+ * options opts (null: defaults) needs at its peak, from the mesh sizes and
+ * options alone (no device work): geometry, near-field blocks and their
+ * build scratch, far-field partials, right-hand sides, GMRES basis, the
+ * preconditioner's batched vectors and, with operator_mode 1, the assembled
+ * operators. */
+int bem_estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_opts* opts, int64_t* bytes);
+
+/* Autotuner for the far-field launch shape (no counterpart in the paper):
+ * times the whole operator application for source-chunk lengths 8..256
+ * tiles and the built-in heuristic, keeps the fastest in the context
+ * (bem_opts.chunk_tiles) and in a per-process cache keyed by the tile count,
+ * number of domains and lossiness (a cached answer is reused without timing
+ * unless best_ms is requested).  The results do not depend on the choice
+ * beyond rounding order.  chunk_tiles / best_ms may be null. */
+int bem_autotune(bem_ctx* ctx, int precision, int32_t* chunk_tiles, double* best_ms);
 
 /* Total pressure at n_points points from the traces of excitation `rhs`
  * of the last solve, by the representation formula (App. A eq.
@@ -229,6 +272,85 @@ const char* bem_last_error(const bem_ctx* ctx);
  * Gauss-Legendre on [0,1] with n points (rows node, weight).  *n_out
  * receives the number of rows; buf holds 3 * 64 doubles at least. */
 int bem_quadrature_table(int which, int n, double* buf, int* n_out);
+
+/* ---------------------------------------------------------------- serving
+ *
+ * A request loop for planning solves (no counterpart in the paper, which
+ * solves one scene at a time).  A scene is a context with its meshes,
+ * materials and transducer set (bem_set_transducer); the server takes it over
+ * and keeps its device state (geometry, near-field corrections,
+ * preconditioner, assembled operators) resident between requests.  A request
+ * is a set of n_exc piston excitations (weights [n_exc][n_elem] complex) for
+ * one scene.  Requests wait in a FIFO queue and start as soon as one of
+ * `slots` workers and enough of the device-memory budget are free; queued
+ * requests of the scene a worker picks are merged into one solve of up to
+ * max_batch_rhs excitations (bem_solve with batch_rhs), and different scenes
+ * run concurrently on their own streams.  Every device allocation of every
+ * scene draws on one counter limited by hbm_budget_bytes; admission reserves
+ * a solve's estimated need and evicts idle scenes, least recently used
+ * first.  All calls are thread-safe.  Results are the solution vectors of
+ * bem_get_solution, one per excitation, and do not depend on which other
+ * requests shared the batch (within the solve tolerance). */
+typedef struct bem_server bem_server;
+
+enum { BEM_REQ_QUEUED = 0, BEM_REQ_RUNNING = 1, BEM_REQ_DONE = 2, BEM_REQ_FAILED = 3 };
+
+typedef struct {
+    int32_t slots;            /* concurrent solves (worker threads; default 2) */
+    int32_t max_batch_rhs;    /* excitations merged into one solve (default 64) */
+    int64_t hbm_budget_bytes; /* device bytes all scenes may hold together (default 150 GiB; 0 = no limit) */
+    bem_solve_opts solve;     /* options of every solve (default: mixed precision, batch_rhs = max_batch_rhs) */
+} bem_server_opts;
+
+typedef struct {
+    int64_t completed;        /* requests finished successfully */
+    int64_t excitations;      /* excitations of those requests */
+    int64_t failed;
+    int64_t queued;
+    int64_t running;          /* solves on the GPU now */
+    int64_t batches;          /* solves run */
+    double mean_batch_exc;    /* excitations per solve */
+    double p50_ms, p99_ms, max_ms;  /* request latency, submit to result */
+    double p50_wait_ms;       /* submit to start */
+    double requests_per_s;    /* completed requests / (last completion - first submit) */
+    double excitations_per_s;
+    int64_t device_bytes;     /* held by all scenes now */
+    int64_t peak_device_bytes;
+    int64_t evictions;
+} bem_server_stats;
+
+int bem_server_default_opts(bem_server_opts* opts);
+/* Starts the workers.  Errors: INVALID_ARG (bad options), CUDA (no device). */
+int bem_server_create(bem_server** out, int device, const bem_server_opts* opts);
+/* Stops the workers after their current solves and destroys every scene. */
+int bem_server_destroy(bem_server* server);
+/* Takes ownership of ctx (the caller must neither use nor destroy it
+ * afterwards); its device memory counts against the budget from now on.
+ * STATE if ctx has no transducer or no domain. */
+int bem_server_add_scene(bem_server* server, bem_ctx* ctx, int32_t* scene_id);
+/* Sizes of a scene: solution length, pistons, device bytes held now. */
+int bem_server_scene_info(bem_server* server, int32_t scene_id, int64_t* n_dofs, int64_t* n_elem,
+                          int64_t* device_bytes);
+/* Device bytes the server reserves for a solve of n_exc excitations of a
+ * scene (its admission estimate, from the mesh sizes and solve options). */
+int bem_server_estimate(bem_server* server, int32_t scene_id, int64_t n_exc, int64_t* bytes);
+/* Queues a request; weights are copied.  Returns a handle at once. */
+int bem_server_submit(bem_server* server, int32_t scene_id, const bem_z* weights, int64_t n_exc, int64_t* handle);
+int bem_server_poll(bem_server* server, int64_t handle, int32_t* state);
+/* Blocks until the request is done or failed (timeout_s < 0: no limit);
+ * TIMEOUT if it is still queued or running when the time is up. */
+int bem_server_wait(bem_server* server, int64_t handle, double timeout_s, int32_t* state);
+/* Result of a finished request: u [n_exc][n_dofs] (host, may be null), the
+ * solve report of its batch, its latency and the batch's excitation count.
+ * Returns the request's own status (OK, NOT_CONVERGED with u filled,
+ * OUT_OF_BUDGET, ...); STATE if it has not finished.  release = 1 forgets the
+ * request afterwards. */
+int bem_server_result(bem_server* server, int64_t handle, bem_z* u, bem_solve_report* report, double* latency_ms,
+                      int64_t* batch_exc, int release);
+int bem_server_get_stats(bem_server* server, bem_server_stats* stats);
+/* Error text of a failed request ("" if it did not fail); valid until the
+ * request is released. */
+const char* bem_server_error(bem_server* server, int64_t handle);
 
 #ifdef __cplusplus
 }

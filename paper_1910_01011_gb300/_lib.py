@@ -17,6 +17,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "MESH_INVALID", -3: "OUT_OF_BUDGET", -4: "NOT_C
           -6: "CUDA", -7: "STATE"}
 PREC_FP64, PREC_FP32, PREC_BF16X3, PREC_FP64_ASSEMBLED = 0, 1, 2, 3
 OP_AHAT, OP_PREC, OP_PREC_AHAT = 0, 1, 2
+ERR_OUT_OF_BUDGET, ERR_NOT_CONVERGED, ERR_TIMEOUT = -3, -4, -5
 
 
 class bem_z(ctypes.Structure):
@@ -26,18 +27,37 @@ class bem_z(ctypes.Structure):
 class bem_opts(ctypes.Structure):
     _fields_ = [("n_gauss_singular", ctypes.c_int32), ("chunk_tiles", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_int64), ("n_pade", ctypes.c_int32), ("pade_theta", ctypes.c_double),
-                ("r_eps", ctypes.c_double), ("eps_exponent", ctypes.c_double)]
+                ("r_eps", ctypes.c_double), ("eps_exponent", ctypes.c_double), ("osrc_tol", ctypes.c_double),
+                ("osrc_solver", ctypes.c_int32)]
 
 
 class bem_solve_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("precondition", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int32), ("operator_mode", ctypes.c_int32)]
+                ("max_refine", ctypes.c_int32), ("operator_mode", ctypes.c_int32), ("batch_rhs", ctypes.c_int32),
+                ("flexible", ctypes.c_int32), ("prec_tol", ctypes.c_double)]
 
 
 class bem_solve_report(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("residual", ctypes.c_double),
                 ("seconds", ctypes.c_double)]
+
+
+class bem_server_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_batch_rhs", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
+                ("solve", bem_solve_opts)]
+
+
+class bem_server_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("excitations", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("mean_batch_exc", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("p50_wait_ms", ctypes.c_double), ("requests_per_s", ctypes.c_double),
+                ("excitations_per_s", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("peak_device_bytes", ctypes.c_int64), ("evictions", ctypes.c_int64)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 
 class BemError(RuntimeError):
@@ -70,8 +90,26 @@ _SIGS = {
     "bem_default_solve_opts": [ctypes.POINTER(bem_solve_opts)],
     "bem_solve": [_P, ctypes.POINTER(bem_solve_opts), ctypes.POINTER(bem_solve_report)],
     "bem_get_traces": [_P, ctypes.c_int32, ctypes.c_int64, _P, _P, ctypes.c_int],
+    "bem_get_solution": [_P, ctypes.c_int64, _P, ctypes.c_int],
+    "bem_server_default_opts": [ctypes.POINTER(bem_server_opts)],
+    "bem_server_create": [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(bem_server_opts)],
+    "bem_server_destroy": [_P],
+    "bem_server_add_scene": [_P, _P, ctypes.POINTER(ctypes.c_int32)],
+    "bem_server_scene_info": [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_int64)],
+    "bem_server_estimate": [_P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)],
+    "bem_server_submit": [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)],
+    "bem_server_poll": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)],
+    "bem_server_wait": [_P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_int32)],
+    "bem_server_result": [_P, ctypes.c_int64, _P, ctypes.POINTER(bem_solve_report), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
+    "bem_server_error": [_P, ctypes.c_int64],
+    "bem_server_get_stats": [_P, ctypes.POINTER(bem_server_stats)],
     "bem_field": [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, _P, ctypes.c_int],
     "bem_last_error": [_P],
+    "bem_memory_info": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "bem_estimate_solve_bytes": [_P, ctypes.c_int64, ctypes.POINTER(bem_solve_opts), ctypes.POINTER(ctypes.c_int64)],
+    "bem_autotune": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
     "bem_profile_enable": [_P, ctypes.c_int],
     "bem_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
@@ -94,7 +132,7 @@ def load(build_if_missing: bool = True):
     for name, args in _SIGS.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = ctypes.c_char_p if name == "bem_last_error" else ctypes.c_int
+        f.restype = ctypes.c_char_p if name in ("bem_last_error", "bem_server_error") else ctypes.c_int
     _lib = lib
     return lib
 

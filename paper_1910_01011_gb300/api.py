@@ -149,7 +149,10 @@ class Context:
     def solve(self, **kw):
         o = _lib.bem_solve_opts()
         check(self.lib.bem_default_solve_opts(ctypes.byref(o)))
+        names = {f[0] for f in o._fields_}
         for k, v in kw.items():
+            if k not in names:
+                raise TypeError(f"unknown solve option {k!r}")
             setattr(o, k, v)
         r = _lib.bem_solve_report()
         rc = self.lib.bem_solve(self.h, ctypes.byref(o), ctypes.byref(r))
@@ -157,6 +160,12 @@ class Context:
             self._check(rc)
         return {"iterations": r.iterations, "refinements": r.refinements, "residual": r.residual,
                 "seconds": r.seconds, "converged": rc == 0}
+
+    def solution(self, rhs=0):
+        """System-order solution of excitation rhs: per domain [gamma_N; gamma_D]."""
+        u = np.empty(self.n_dofs, dtype=np.complex128)
+        self._check(self.lib.bem_get_solution(self.h, int(rhs), u.ctypes.data, 0))
+        return u
 
     def traces(self, dom, rhs=0):
         nv = self.domains[dom][0]
@@ -174,7 +183,31 @@ class Context:
         self._check(self.lib.bem_field(self.h, int(rhs), p.ctypes.data, d.ctypes.data, p.shape[0], out.ctypes.data, 0))
         return out
 
+    # ---- memory
+    def memory(self):
+        """(bytes held on the device now, most held so far)."""
+        u, p = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.bem_memory_info(self.h, ctypes.byref(u), ctypes.byref(p)))
+        return u.value, p.value
+
+    def estimate_solve_bytes(self, n_exc=1, **solve):
+        o = _lib.bem_solve_opts()
+        check(self.lib.bem_default_solve_opts(ctypes.byref(o)))
+        for k, v in solve.items():
+            setattr(o, k, v)
+        b = ctypes.c_int64()
+        self._check(self.lib.bem_estimate_solve_bytes(self.h, int(n_exc), ctypes.byref(o), ctypes.byref(b)))
+        return b.value
+
     # ---- measurement
+    def autotune(self, precision=FP32, timed=True):
+        """Pick the far-field source-chunk length by timing (bem_autotune)."""
+        ct = ctypes.c_int32()
+        ms = ctypes.c_double()
+        self._check(self.lib.bem_autotune(self.h, int(precision), ctypes.byref(ct),
+                                          ctypes.byref(ms) if timed else None))
+        return {"chunk_tiles": ct.value, "ms": ms.value if timed else None}
+
     def profile(self, enable=True):
         self._check(self.lib.bem_profile_enable(self.h, 1 if enable else 0))
 
@@ -194,3 +227,107 @@ def quadrature_table(which, n=6):
     check(lib.bem_quadrature_table(which, n, buf, ctypes.byref(m)))
     cols = 3 if which == 0 else 2
     return np.array(buf[:m.value * cols]).reshape(m.value, cols)
+
+
+class Server:
+    """Request loop for planning solves (bem_server_*): scenes stay resident on
+    the device, requests of piston excitations are queued, batched per scene
+    and solved concurrently across scenes under one device-memory budget."""
+
+    def __init__(self, device: int = 0, slots: int = 2, max_batch_rhs: int = 64, hbm_budget_bytes: int = 150 << 30,
+                 **solve):
+        self.lib = _lib.load()
+        o = _lib.bem_server_opts()
+        check(self.lib.bem_server_default_opts(ctypes.byref(o)))
+        o.slots, o.max_batch_rhs, o.hbm_budget_bytes = int(slots), int(max_batch_rhs), int(hbm_budget_bytes)
+        names = {f[0] for f in o.solve._fields_}
+        for k, v in solve.items():
+            if k not in names:
+                raise TypeError(f"unknown solve option {k!r}")
+            setattr(o.solve, k, v)
+        h = ctypes.c_void_p()
+        rc = self.lib.bem_server_create(ctypes.byref(h), device, ctypes.byref(o))
+        if rc:
+            raise _lib.BemError(rc, "bem_server_create failed")
+        self.h = h
+        self.device = device
+        self.scenes = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bem_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_context(self, ctx: Context) -> int:
+        """Hand a configured Context (meshes, materials, transducer) to the
+        server, which owns it from then on."""
+        i = ctypes.c_int32()
+        rc = self.lib.bem_server_add_scene(self.h, ctx.h, ctypes.byref(i))
+        if rc:
+            raise _lib.BemError(rc, self.lib.bem_last_error(ctx.h).decode())
+        ctx.h = None  # owned by the server now
+        n, ne, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(self.lib.bem_server_scene_info(self.h, i, ctypes.byref(n), ctypes.byref(ne), ctypes.byref(b)))
+        self.scenes[i.value] = (n.value, ne.value)
+        return i.value
+
+    def add_scene(self, scene, transducer=None, omega_rho0=None, **ctx_opts) -> int:
+        """A synth scene with its transducer (scene.transducer by default)."""
+        c = Context.from_scene(scene, self.device, stream=0, **ctx_opts)
+        tr = transducer if transducer is not None else scene.transducer
+        w = omega_rho0 if omega_rho0 is not None else 2 * np.pi * scene.freq * scene.rho0
+        c.set_transducer(tr["centres"], tr["normals"], tr["radii"], w)
+        return self.add_context(c)
+
+    def estimate(self, scene_id: int, n_exc: int = 1) -> int:
+        """Device bytes admission reserves for a solve of n_exc excitations."""
+        b = ctypes.c_int64()
+        check(self.lib.bem_server_estimate(self.h, int(scene_id), int(n_exc), ctypes.byref(b)))
+        return b.value
+
+    def submit(self, scene_id: int, weights) -> int:
+        W = np.ascontiguousarray(np.atleast_2d(weights), dtype=np.complex128)
+        assert W.shape[1] == self.scenes[scene_id][1], "weights: one per piston"
+        hnd = ctypes.c_int64()
+        check(self.lib.bem_server_submit(self.h, int(scene_id), W.ctypes.data, W.shape[0], ctypes.byref(hnd)))
+        return hnd.value
+
+    def poll(self, handle: int) -> int:
+        st = ctypes.c_int32()
+        check(self.lib.bem_server_poll(self.h, int(handle), ctypes.byref(st)))
+        return st.value
+
+    def wait(self, handle: int, timeout: float = -1.0) -> int:
+        st = ctypes.c_int32()
+        rc = self.lib.bem_server_wait(self.h, int(handle), float(timeout), ctypes.byref(st))
+        if rc not in (0, _lib.ERR_TIMEOUT):
+            check(rc)
+        return st.value
+
+    def result(self, handle: int, n_exc: int, scene_id: int, release: bool = True):
+        """(U [n_exc, n_dofs], report dict); raises on a failed request."""
+        n = self.scenes[scene_id][0]
+        U = np.empty((n_exc, n), dtype=np.complex128)
+        r = _lib.bem_solve_report()
+        lat = ctypes.c_double()
+        be = ctypes.c_int64()
+        rc = self.lib.bem_server_result(self.h, int(handle), U.ctypes.data, ctypes.byref(r), ctypes.byref(lat),
+                                        ctypes.byref(be), 1 if release else 0)
+        if rc:
+            raise _lib.BemError(rc, self.error(handle) or f"request {handle} failed")
+        return U, {"iterations": r.iterations, "refinements": r.refinements, "residual": r.residual,
+                   "seconds": r.seconds, "latency_ms": lat.value, "batch_exc": be.value}
+
+    def error(self, handle: int) -> str:
+        return self.lib.bem_server_error(self.h, int(handle)).decode()
+
+    def stats(self) -> dict:
+        st = _lib.bem_server_stats()
+        check(self.lib.bem_server_get_stats(self.h, ctypes.byref(st)))
+        return {f[0]: getattr(st, f[0]) for f in st._fields_}

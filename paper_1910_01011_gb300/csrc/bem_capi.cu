@@ -11,7 +11,10 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "ctx.h"
@@ -39,14 +42,25 @@ void* bem_ctx::dalloc(size_t bytes, int* rc) {
                                               " > " + std::to_string(opts.hbm_budget_bytes) + " bytes)");
         return nullptr;
     }
+    if (pool) {
+        const int64_t after = pool->fetch_add((int64_t)bytes) + (int64_t)bytes;
+        if (pool_limit > 0 && after > pool_limit) {
+            pool->fetch_sub((int64_t)bytes);
+            *rc = fail(BEM_ERR_OUT_OF_BUDGET, "shared device memory budget exceeded (" + std::to_string(after) +
+                                                  " > " + std::to_string(pool_limit) + " bytes)");
+            return nullptr;
+        }
+    }
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
+        if (pool) pool->fetch_sub((int64_t)bytes);
         *rc = fail(BEM_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         return nullptr;
     }
     allocs.push_back({p, bytes});
     used_bytes += bytes;
+    peak_bytes = std::max(peak_bytes, used_bytes);
     *rc = BEM_OK;
     return p;
 }
@@ -56,6 +70,7 @@ void bem_ctx::dfree(void* p) {
     for (size_t i = 0; i < allocs.size(); i++)
         if (allocs[i].first == p) {
             used_bytes -= allocs[i].second;
+            if (pool) pool->fetch_sub((int64_t)allocs[i].second);
             cudaFree(p);
             allocs.erase(allocs.begin() + i);
             return;
@@ -78,6 +93,7 @@ static void release_device(bem_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto& a : ctx->allocs) cudaFree(a.first);
     ctx->allocs.clear();
+    if (ctx->pool) ctx->pool->fetch_sub((int64_t)ctx->used_bytes);
     ctx->used_bytes = 0;
     ctx->dev = DeviceGeom();
     ctx->ready = false;
@@ -96,6 +112,61 @@ static void release_device(bem_ctx* ctx) {
     ctx->pmchwt_near = NearSet();
     destroy_solver_state(ctx);
 }
+
+namespace gbem {
+
+// Eviction by the request loop: every device allocation of the context goes;
+// the host description (meshes, materials, transducer) stays and the device
+// state is rebuilt on next use.
+void release_device_memory(bem_ctx* ctx) { release_device(ctx); }
+
+// Device bytes a solve of n_exc excitations with options o may need at its
+// peak, from the mesh sizes alone (no device state is needed); every term
+// follows one allocation of the solver, rounded up, with a 10 % margin.
+int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_opts& o) {
+    int64_t T = 0, nv = 0, tiles = 0;
+    for (auto& d : ctx->doms) {
+        T += d.nt;
+        nv += d.nv;
+        tiles += (d.nt + TT - 1) / TT;
+    }
+    const int64_t N = 2 * nv, pts = tiles * TP, slots = tiles * TT, pairs = 16 * T;
+    const int64_t ne = (int64_t)ctx->tr_r.size();
+    int64_t b = 0;
+    // geometry, densities, staging vectors
+    b += pts * 136 + slots * 460 + pairs * 12 + N * 64 + tiles * 64;
+    // near-field blocks (c128 + c64) and their build scratch
+    b += pairs * 36 * 24 + std::min<int64_t>(pairs, 1 << 20) * 2 * 27 * 16;
+    // far-field partial potentials (FP64 residual is the larger)
+    int nc = 1, ct = 1;
+    ctx->chunking((int)tiles, (int)tiles, &nc, &ct);
+    b += (int64_t)nc * 2 * NCOMP * pts * 8;
+    // right-hand sides, solutions, piston data
+    b += n_exc * (2 * N * 16 + slots * 6 * 16 + ne * 16) + ne * 32 * 32 + 3 * N * 16;
+    // GMRES basis and work (per lockstep column)
+    const int64_t R = o.batch_rhs > 1 ? std::min<int64_t>(o.batch_rhs, n_exc) : 1;
+    b += (int64_t)(o.restart + 1) * R * N * 16 + 2 * R * N * 16 + (int64_t)(o.restart + 2) * 120 * R * 16 * 3 + 8 * R;
+    if (o.precondition && o.flexible) b += (int64_t)o.restart * R * N * 16;  // flexible basis
+    b += 4 * R * N * 16;
+    if (o.precondition) {
+        const int64_t L = ctx->opts.n_pade, nnz = 8 * nv, ms = 2 * L * R;
+        b += nnz * 20 + (nv + 1) * 8 + 2 * nv * 8;
+        b += 6 * ms * nv * 16 + ms * (16 + 128 * 4 * 8 + 64) + 4 * R * nv * 16;
+    }
+    if (o.operator_mode == 1) {
+        const int64_t mp = (N + 127) / 128 * 128, kp = (N + 31) / 32 * 32;
+        const int64_t planes = 6 * mp * kp * 2;
+        const int64_t nbpad = (R + 63) / 64 * 128;
+        const int64_t a64 = 16 * N * N;
+        if (o.precision == BEM_PREC_FP32)
+            b += std::max(planes + 8 * N * N, planes + a64) + R * N * 16 + 3 * nbpad * kp * 2;
+        else
+            b += a64;
+    }
+    return b + b / 10 + ((int64_t)64 << 20);
+}
+
+}  // namespace gbem
 
 // ------------------------------------------------------------------ set-up
 
@@ -388,6 +459,8 @@ int bem_default_opts(bem_opts* o) {
     o->pade_theta = M_PI / 3.0;
     o->r_eps = 0.0;
     o->eps_exponent = 1.0 / 3.0;
+    o->osrc_tol = 1e-11;
+    o->osrc_solver = 0;
     return BEM_OK;
 }
 
@@ -403,10 +476,12 @@ int bem_create(bem_ctx** out, int device, void* cuda_stream, const bem_opts* opt
     c->stream = (cudaStream_t)cuda_stream;
     bem_default_opts(&c->opts);
     if (opts) c->opts = *opts;
-    if (c->opts.n_gauss_singular < 2 || c->opts.n_gauss_singular > 20) {
+    if (c->opts.n_gauss_singular < 2 || c->opts.n_gauss_singular > 20 || !(c->opts.osrc_tol > 0) ||
+        !(c->opts.osrc_tol < 1) || c->opts.osrc_solver < 0 || c->opts.osrc_solver > 2) {
         delete c;
         return BEM_ERR_INVALID_ARG;
     }
+    c->osrc_tol = c->opts.osrc_tol;
     *out = c;
     return BEM_OK;
 }
@@ -415,6 +490,7 @@ int bem_destroy(bem_ctx* ctx) {
     if (!ctx) return BEM_OK;
     release_device(ctx);
     if (ctx->cublas) cublasDestroy(ctx->cublas);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return BEM_OK;
 }
@@ -533,11 +609,42 @@ int bem_apply(bem_ctx* ctx, int op, const bem_z* x, bem_z* y, int64_t n_rhs, int
             xd = stage;
             yd = stage + n_rhs * N;
         }
-        rc = precision == BEM_PREC_BF16X3 ? ctx->apply_assembled(xd, yd, n_rhs) : ctx->apply_assembled64(xd, yd, n_rhs);
-        for (int64_t r = 0; !rc && op == BEM_OP_PREC_AHAT && r < n_rhs; r++) {
-            CK(cudaMemcpyAsync(ctx->dev.ys2, yd + r * N, N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
-            rc = ctx->apply_prec(ctx->dev.ys2, yd + r * N);
+        double2* tmp = nullptr;
+        if (op == BEM_OP_PREC_AHAT) {
+            tmp = (double2*)ctx->dalloc((size_t)n_rhs * N * sizeof(double2), &rc);
+            if (rc) return rc;
         }
+        double2* dst = tmp ? tmp : yd;
+        rc = precision == BEM_PREC_BF16X3 ? ctx->apply_assembled(xd, dst, n_rhs) : ctx->apply_assembled64(xd, dst, n_rhs);
+        if (!rc && tmp) rc = ctx->apply_prec_batch(tmp, yd, n_rhs);
+        if (tmp) {
+            cudaStreamSynchronize(ctx->stream);
+            ctx->dfree(tmp);
+        }
+        if (!rc && !on_device) {
+            CK(cudaMemcpyAsync(y, yd, n_rhs * N * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+        if (stage) {
+            cudaStreamSynchronize(ctx->stream);
+            ctx->dfree(stage);
+        }
+        if (rc) return rc;
+        return on_device ? BEM_OK : ctx->check_device_error();
+    }
+    if (op == BEM_OP_PREC && n_rhs > 1) {
+        // every right-hand side in one batched preconditioner application
+        const double2* xd = (const double2*)x;
+        double2* yd = (double2*)y;
+        double2* stage = nullptr;
+        if (!on_device) {
+            stage = (double2*)ctx->dalloc((size_t)2 * n_rhs * N * sizeof(double2), &rc);
+            if (rc) return rc;
+            CK(cudaMemcpyAsync(stage, x, n_rhs * N * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+            xd = stage;
+            yd = stage + n_rhs * N;
+        }
+        rc = ctx->apply_prec_batch(xd, yd, n_rhs);
         if (!rc && !on_device) {
             CK(cudaMemcpyAsync(y, yd, n_rhs * N * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
             CK(cudaStreamSynchronize(ctx->stream));
@@ -641,6 +748,103 @@ int bem_profile_read(bem_ctx* ctx, double* far_ms, int64_t* far_launches, int64_
         ctx->far_count = 0;
         ctx->launches = 0;
     }
+    return BEM_OK;
+}
+
+// Autotuner for the far-field launch shape: the number of source tiles one
+// CTA streams (grid = target tiles x source chunks).  Short chunks give more
+// CTAs (better balance over 152 SMs) but more partial potentials to write and
+// reduce; long chunks the opposite.  Every candidate runs the whole operator
+// application (gather, far field, projection, reduction) on the context's
+// stream, timed with CUDA events after one warm-up run; the fastest is kept
+// in the context's options and a per-process cache keyed by the tile counts.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune_cache;  // (tiles, domains, lossy, precision) -> chunk
+}  // namespace
+
+int bem_autotune(bem_ctx* ctx, int precision, int32_t* chunk_tiles, double* best_ms) {
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (precision != BEM_PREC_FP32 && precision != BEM_PREC_FP64) return ctx->fail(BEM_ERR_INVALID_ARG, "bad precision");
+    CK(cudaSetDevice(ctx->device));
+    int rc = ctx->finalize();
+    if (rc) return rc;
+    if ((rc = ctx->ensure_near())) return rc;
+    const Geometry& g = ctx->geo;
+    bool lossy = ctx->k0im != 0;
+    for (auto& d : ctx->doms) lossy |= d.kim != 0;
+    const auto key = std::make_tuple(g.n_tiles, g.n_dom, (int)lossy, precision);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && !best_ms) {
+            ctx->opts.chunk_tiles = it->second;
+            if (chunk_tiles) *chunk_tiles = it->second;
+            return BEM_OK;
+        }
+    }
+    const int64_t N = g.n_dof;
+    double2* x = (double2*)ctx->dalloc(2 * N * sizeof(double2), &rc);
+    if (rc) return rc;
+    double2* y = x + N;
+    CK(cudaMemsetAsync(x, 0, N * sizeof(double2), ctx->stream));
+    std::vector<int> cand;
+    for (int c : {8, 16, 32, 64, 128, 256})
+        if (c <= CHUNK_MAX && (c <= g.n_tiles || cand.empty())) cand.push_back(c);
+    cand.push_back(0);  // the built-in heuristic
+    const int saved = ctx->opts.chunk_tiles;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = saved;
+    double best_t = 1e300;
+    for (int c : cand) {
+        ctx->opts.chunk_tiles = c;
+        if ((rc = ctx->apply_ahat(x, y, precision))) break;  // warm-up (and partial buffer sizing)
+        CK(cudaEventRecord(e0, ctx->stream));
+        const int reps = 2;
+        for (int r = 0; r < reps && !rc; r++) rc = ctx->apply_ahat(x, y, precision);
+        if (rc) break;
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms / reps < best_t) {
+            best_t = ms / reps;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->dfree(x);
+    if (rc) {
+        ctx->opts.chunk_tiles = saved;
+        return rc;
+    }
+    ctx->opts.chunk_tiles = best;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    if (chunk_tiles) *chunk_tiles = best;
+    if (best_ms) *best_ms = best_t;
+    return ctx->check_device_error();
+}
+
+int bem_memory_info(const bem_ctx* ctx, int64_t* used, int64_t* peak) {
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (used) *used = (int64_t)ctx->used_bytes;
+    if (peak) *peak = (int64_t)ctx->peak_bytes;
+    return BEM_OK;
+}
+
+int bem_estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_opts* opts, int64_t* bytes) {
+    if (!ctx || !bytes || n_exc < 1) return BEM_ERR_INVALID_ARG;
+    bem_solve_opts o;
+    bem_default_solve_opts(&o);
+    if (opts) o = *opts;
+    *bytes = estimate_solve_bytes(ctx, n_exc, o);
     return BEM_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 
+#include <algorithm>
 #include <chrono>
 #include <complex>
 #include <vector>
@@ -153,6 +154,9 @@ struct SolveState {
     double2* r = nullptr;       // work
     double2* d = nullptr;       // work
     double2* pb = nullptr;      // work
+    // batched solves: [batch][N] work blocks
+    double2 *bt = nullptr, *bpb = nullptr, *bd = nullptr, *br = nullptr;
+    int64_t batch_alloc = 0;
     double2* tri_rhs = nullptr; // [n_rhs][n_slots*6]
     double4* disc = nullptr;
     double2* wdev = nullptr;
@@ -250,6 +254,7 @@ static int build_rhs(bem_ctx* ctx) {
 }
 
 void destroy_osrc_state(bem_ctx* ctx);
+void set_osrc_tolerance(bem_ctx* ctx, double tol);
 
 // Traces and incident-field data of excitation `rhs` of the last solve, for
 // the field evaluation (k_field.cu).
@@ -265,6 +270,18 @@ int solve_field_inputs(bem_ctx* ctx, int64_t rhs, const double2** u, const doubl
     *wts = ctx->field_kind == 2 ? S->wdev + rhs * (int64_t)ctx->tr_r.size() : nullptr;
     return BEM_OK;
 }
+
+namespace gbem {
+// Solutions rhs0 .. rhs0+n-1 of the last solve into host memory (system order).
+int copy_solution(bem_ctx* ctx, int64_t rhs0, int64_t n, double2* host) {
+    SolveState* S = ctx->solve;
+    if (!S || rhs0 < 0 || rhs0 + n > S->n_rhs_solved) return ctx->fail(BEM_ERR_STATE, "no such solution");
+    const int64_t N = ctx->geo.n_dof;
+    CK(cudaMemcpyAsync(host, S->u + rhs0 * N, n * N * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return BEM_OK;
+}
+}  // namespace gbem
 
 // Drop the solver objects after their device memory was released with the
 // rest of the context's allocations.
@@ -353,6 +370,115 @@ int bem_default_solve_opts(bem_solve_opts* o) {
     o->inner_tol = 1e-4;
     o->max_refine = 10;
     o->operator_mode = 0;
+    o->batch_rhs = 0;
+    o->flexible = 1;
+    o->prec_tol = 0.0;
+    return BEM_OK;
+}
+
+// Work blocks for batched solves of up to R right-hand sides.
+static int ensure_batch_state(bem_ctx* ctx, int64_t R) {
+    SolveState* S = ctx->solve;
+    if (S->batch_alloc >= R) return BEM_OK;
+    for (void* p : {(void*)S->bt, (void*)S->bpb, (void*)S->bd, (void*)S->br}) ctx->dfree(p);
+    S->bt = S->bpb = S->bd = S->br = nullptr;
+    S->batch_alloc = 0;
+    const size_t bytes = (size_t)R * ctx->geo.n_dof * sizeof(double2);
+    int rc;
+    S->bt = (double2*)ctx->dalloc(bytes, &rc); if (rc) return rc;
+    S->bpb = (double2*)ctx->dalloc(bytes, &rc); if (rc) return rc;
+    S->bd = (double2*)ctx->dalloc(bytes, &rc); if (rc) return rc;
+    S->br = (double2*)ctx->dalloc(bytes, &rc); if (rc) return rc;
+    S->batch_alloc = R;
+    return BEM_OK;
+}
+
+// Solve R = nb right-hand sides b[R][N] into u[R][N] with R GMRES runs in
+// lockstep (same method, tolerances and stopping rule per column as the
+// one-at-a-time path).
+static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, double2* u, int64_t R,
+                       bem_solve_report* rep, bool* converged) {
+    SolveState* S = ctx->solve;
+    const int64_t N = ctx->geo.n_dof;
+    int rc;
+    if ((rc = ensure_batch_state(ctx, R))) return rc;
+    if ((rc = S->kry.ensure(ctx, N, o.restart, R))) return rc;
+    auto plain = [ctx, &o, N](const double2* X, double2* Y, int prec, int64_t nr) -> int {
+        if (o.operator_mode == 1)
+            return prec == BEM_PREC_FP64 ? ctx->apply_assembled64(X, Y, nr) : ctx->apply_assembled(X, Y, nr);
+        for (int64_t r = 0; r < nr; r++) {
+            int e = ctx->apply_ahat(X + r * N, Y + r * N, prec);
+            if (e) return e;
+        }
+        return BEM_OK;
+    };
+    const bool left = o.precondition && !o.flexible;
+    auto op_for = [ctx, left, plain, S, R](int prec) {
+        return [ctx, prec, left, plain, S, R](const double2* X, double2* Y) -> int {
+            if (!left) return plain(X, Y, prec, R);
+            int e = plain(X, S->bt, prec, R);
+            return e ? e : ctx->apply_prec_batch(S->bt, Y, R);
+        };
+    };
+    const Krylov::Op right = [ctx, R](const double2* X, double2* Y) -> int { return ctx->apply_prec_batch(X, Y, R); };
+    const Krylov::Op* rp = (o.precondition && o.flexible) ? &right : nullptr;
+    auto rhs_of = [&](const double2* v) -> const double2* {
+        if (!left) return v;
+        rc = ctx->apply_prec_batch(v, S->bpb, R);
+        return S->bpb;
+    };
+    auto residual = [&](std::vector<double>& rel, const std::vector<double>& bn) -> int {
+        // br = b - A_hat u in FP64, relative column norms
+        int e = plain(u, S->br, BEM_PREC_FP64, R);
+        if (e) return e;
+        if ((e = S->kry.axpby(ctx, 1.0, b, -1.0, S->br, S->br, R * N))) return e;
+        std::vector<double> rn(R);
+        if ((e = S->kry.norms(ctx, S->br, R, rn.data()))) return e;
+        for (int64_t r = 0; r < R; r++) rel[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+        return BEM_OK;
+    };
+    std::vector<double> bn(R), rel(R, 1.0), irel(R);
+    std::vector<int> its(R);
+    if ((rc = S->kry.norms(ctx, b, R, bn.data()))) return rc;
+    CK(cudaMemsetAsync(u, 0, R * N * sizeof(double2), ctx->stream));
+    int it = 0;
+    double worst = 0;
+    if (o.precision == BEM_PREC_FP64) {
+        const double2* sb = rhs_of(b);
+        if (rc) return rc;
+        double inner = o.tol;
+        for (int attempt = 0; attempt < 4; attempt++) {
+            if ((rc = S->kry.gmres_batch(ctx, op_for(BEM_PREC_FP64), sb, u, R, o.restart, inner, o.max_iter - it,
+                                         its.data(), irel.data(), attempt == 0, rp)))
+                return rc;
+            it += *std::max_element(its.begin(), its.end());
+            for (int64_t r = 0; r < R; r++) rep->iterations += its[r];
+            if ((rc = residual(rel, bn))) return rc;
+            worst = *std::max_element(rel.begin(), rel.end());
+            if (worst <= o.tol || it >= o.max_iter) break;
+            inner *= 0.1;
+        }
+    } else {
+        CK(cudaMemcpyAsync(S->br, b, R * N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+        for (int64_t r = 0; r < R; r++) rel[r] = bn[r] > 0 ? 1.0 : 0.0;
+        int ref = 0;
+        for (; ref <= o.max_refine; ref++) {
+            worst = *std::max_element(rel.begin(), rel.end());
+            if (worst <= o.tol || it >= o.max_iter || ref == o.max_refine) break;
+            const double2* sr = rhs_of(S->br);
+            if (rc) return rc;
+            if ((rc = S->kry.gmres_batch(ctx, op_for(BEM_PREC_FP32), sr, S->bd, R, o.restart, o.inner_tol,
+                                         o.max_iter - it, its.data(), irel.data(), true, rp)))
+                return rc;
+            it += *std::max_element(its.begin(), its.end());
+            for (int64_t r = 0; r < R; r++) rep->iterations += its[r];
+            if ((rc = S->kry.axpby(ctx, 1.0, u, 1.0, S->bd, u, R * N))) return rc;
+            if ((rc = residual(rel, bn))) return rc;
+        }
+        rep->refinements += ref;
+    }
+    rep->residual = std::max(rep->residual, worst);
+    *converged &= worst <= o.tol;
     return BEM_OK;
 }
 
@@ -362,7 +488,8 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     bem_default_solve_opts(&o);
     if (opts) o = *opts;
     if (o.restart < 1 || o.max_iter < 1 || !(o.tol > 0) || (o.precision != BEM_PREC_FP64 && o.precision != BEM_PREC_FP32) ||
-        (o.operator_mode != 0 && o.operator_mode != 1))
+        (o.operator_mode != 0 && o.operator_mode != 1) || o.batch_rhs < 0 || o.flexible < 0 || o.flexible > 1 ||
+        !(o.prec_tol >= 0) || o.prec_tol >= 1)
         return ctx->fail(BEM_ERR_INVALID_ARG, "bad solve options");
     CK(cudaSetDevice(ctx->device));
     const auto t0 = std::chrono::steady_clock::now();
@@ -374,6 +501,15 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     SolveState* S = ctx->solve;
     const int64_t N = ctx->geo.n_dof, nr = ctx->field_kind == 2 ? ctx->n_rhs : 1;
     if ((rc = S->kry.ensure(ctx, N, o.restart))) return rc;
+    // the preconditioner only has to be a fixed linear map to the accuracy the
+    // GMRES it sits in needs: two orders below that GMRES's tolerance
+    struct TolScope {
+        bem_ctx* c;
+        double saved;
+        ~TolScope() { set_osrc_tolerance(c, saved); }
+    } tol_scope{ctx, ctx->osrc_tol};
+    const double gm_tol = o.precision == BEM_PREC_FP64 ? o.tol : std::max(o.inner_tol, o.tol);
+    set_osrc_tolerance(ctx, o.prec_tol > 0 ? o.prec_tol : o.flexible ? 1e-2 : std::max(1e-13, 0.01 * gm_tol));
     bem_solve_report R{};
     bool converged = true;
     // the operator of one precision level: matrix-free or assembled, then the preconditioner
@@ -382,21 +518,31 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
             return prec == BEM_PREC_FP64 ? ctx->apply_assembled64(x, y, 1) : ctx->apply_assembled(x, y, 1);
         return ctx->apply_ahat(x, y, prec);
     };
-    auto op_for = [ctx, &o, plain](int prec) {
-        return [ctx, prec, &o, plain](const double2* x, double2* y) -> int {
-            if (!o.precondition) return plain(x, y, prec);
+    const bool left = o.precondition && !o.flexible;
+    auto op_for = [ctx, left, plain](int prec) {
+        return [ctx, prec, left, plain](const double2* x, double2* y) -> int {
+            if (!left) return plain(x, y, prec);
             int r = plain(x, ctx->dev.ys2, prec);
             return r ? r : ctx->apply_prec(ctx->dev.ys2, y);
         };
     };
-    for (int64_t r = 0; r < nr; r++) {
+    const Krylov::Op right = [ctx](const double2* x, double2* y) -> int { return ctx->apply_prec(x, y); };
+    const Krylov::Op* rp = (o.precondition && o.flexible) ? &right : nullptr;
+    if (o.batch_rhs > 1 && nr > 1) {
+        // blocks of up to batch_rhs excitations, GMRES in lockstep
+        for (int64_t r0 = 0; r0 < nr; r0 += o.batch_rhs) {
+            const int64_t Rb = std::min<int64_t>(o.batch_rhs, nr - r0);
+            if ((rc = solve_block(ctx, o, S->b + r0 * N, S->u + r0 * N, Rb, &R, &converged))) return rc;
+        }
+    }
+    for (int64_t r = 0; r < (o.batch_rhs > 1 && nr > 1 ? 0 : nr); r++) {
         const double2* b = S->b + r * N;
         double2* u = S->u + r * N;
         double bnorm;
         if ((rc = S->kry.norm(ctx, b, &bnorm))) return rc;
         // right-hand side of the system GMRES sees
         auto rhs_of = [&](const double2* v) -> const double2* {
-            if (!o.precondition) return v;
+            if (!left) return v;
             rc = ctx->apply_prec(v, S->pb);
             return S->pb;
         };
@@ -411,7 +557,7 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
             for (int attempt = 0; attempt < 4; attempt++) {
                 int its = 0;
                 if ((rc = S->kry.gmres(ctx, op_for(BEM_PREC_FP64), sb, u, o.restart, inner, o.max_iter - it, &its, &rel,
-                                       attempt == 0)))
+                                       attempt == 0, rp)))
                     return rc;
                 it += its;
                 // true FP64 residual of the unpreconditioned system
@@ -443,7 +589,7 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
                 int its = 0;
                 double irel = 0;
                 if ((rc = S->kry.gmres(ctx, op_for(BEM_PREC_FP32), sr, S->d, o.restart, o.inner_tol, o.max_iter - it,
-                                       &its, &irel, true)))
+                                       &its, &irel, true, rp)))
                     return rc;
                 it += its;
                 if ((rc = S->kry.axpby(ctx, 1.0, u, 1.0, S->d, u))) return rc;
@@ -462,6 +608,17 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = R;
     if (!converged) return ctx->fail(BEM_ERR_NOT_CONVERGED, "GMRES did not reach the requested residual");
+    return BEM_OK;
+}
+
+int bem_get_solution(bem_ctx* ctx, int64_t rhs, bem_z* u, int on_device) {
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (!ctx->solve || ctx->solve->n_rhs_solved == 0) return ctx->fail(BEM_ERR_STATE, "no solve has run");
+    if (rhs < 0 || rhs >= ctx->solve->n_rhs_solved || !u) return ctx->fail(BEM_ERR_INVALID_ARG, "bad solution request");
+    const int64_t N = ctx->geo.n_dof;
+    CK(cudaMemcpyAsync(u, ctx->solve->u + rhs * N, N * sizeof(double2),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return BEM_OK;
 }
 

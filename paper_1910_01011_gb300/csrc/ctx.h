@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <string>
 #include <utility>
 #include <vector>
@@ -80,6 +81,10 @@ struct bem_ctx {
     size_t partial_bytes = 0;
     std::vector<std::pair<void*, size_t>> allocs;
     size_t used_bytes = 0;
+    size_t peak_bytes = 0;                     // largest used_bytes seen
+    std::atomic<int64_t>* pool = nullptr;      // shared device-memory counter (serving), or null
+    int64_t pool_limit = 0;                    // limit of the shared counter (0: none)
+    bool own_stream = false;                   // stream created by the library, destroyed with the context
     long long launches = 0;
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> far_events;
@@ -96,6 +101,7 @@ struct bem_ctx {
     double2* asm64 = nullptr;
     cublasHandle_t cublas = nullptr;
     gbem::OsrcState* osrc = nullptr;
+    double osrc_tol = 1e-11;  // relative residual of the preconditioner's sparse solves
     gbem::SolveState* solve = nullptr;
     // incident field
     int field_kind = 0;  // 0 none, 1 plane wave, 2 transducer
@@ -118,6 +124,7 @@ struct bem_ctx {
     int run_apply(const double2* x, double2* y, int precision, const gbem::ApplyMode& m);
     int apply_ahat(const double2* x, double2* y, int precision);
     int apply_prec(const double2* x, double2* y);
+    int apply_prec_batch(const double2* x, double2* y, int64_t n_rhs);
     int apply_prec_ahat(const double2* x, double2* y, int precision);
     int check_device_error();
     int ensure_assembled();

@@ -181,17 +181,27 @@ struct TriSums {
 };
 
 // Contribution of one source point at one wavenumber.  LOSSY: Im k != 0
-// (exp(-Im k r) evaluated); otherwise the amplitude is 1/r.
+// (exp(-Im k r) evaluated); otherwise the amplitude is 1/r.  With
+// (ik - 1/r)/r = A + iB, A = (-Im k - 1/r)/r, B = Re k / r, the gradient
+// factor is F = G (A + iB); A = -1/r^2 for real k (rinv2 = 1/r^2 is shared
+// by both wavenumbers of a point).
 template <bool LOSSY>
-__device__ __forceinline__ void slot_point(const SlotK& k, float th, float rho, float r, float rinv, float ndot,
-                                           const float4& g, const float4& d, Acc& t, TriSums& S) {
+__device__ __forceinline__ void slot_point(const SlotK& k, float th, float rho, float r2, float rinv, float rinv2,
+                                           float ndot, const float4& g, const float4& d, Acc& t, TriSums& S) {
     float sn, cs;
     __sincosf(fmaf(k.kr, rho, th), &sn, &cs);
-    const float a = LOSSY ? ex2_approx(k.nkil2 * r) * rinv : rinv;
+    const float a = LOSSY ? ex2_approx(k.nkil2 * (r2 * rinv)) * rinv : rinv;
     const float Gr = a * cs, Gi = a * sn;
-    const float Gbr = Gr * rinv, Gbi = Gi * rinv;
-    const float u = k.nki - rinv;
-    const float Fr = Gbr * u - Gbi * k.kr, Fi = Gbr * k.kr + Gbi * u;   // G (ik - 1/r) / r
+    const float B = k.kr * rinv;
+    float Fr, Fi;
+    if constexpr (LOSSY) {
+        const float A = fmaf(rinv, k.nki, -rinv2);
+        Fr = fmaf(A, Gr, -(B * Gi));
+        Fi = fmaf(B, Gr, A * Gi);
+    } else {
+        Fr = -fmaf(rinv2, Gr, B * Gi);
+        Fi = fmaf(B, Gr, -(rinv2 * Gi));
+    }
     t.v[0] = fmaf(Gr, d.x, fmaf(-Gi, d.y, t.v[0]));
     t.v[1] = fmaf(Gr, d.y, fmaf(Gi, d.x, t.v[1]));
     const float Fnr = Fr * ndot, Fni = Fi * ndot;
@@ -244,11 +254,11 @@ __device__ __forceinline__ void tile_body(const Stage& st, int ntri, int skip_tl
             const float s = ex * (D2x + ex) + ey * (D2y + ey) + ez * (D2z + ez);  // r^2 - R_c^2
             const float r2 = Rc2 + s;
             const float rinv = rsqrtf(r2);
-            const float r = r2 * rinv;
-            const float rho = __fdividef(s, r + Rc);                           // r - R_c
+            const float rinv2 = rinv * rinv;
+            const float rho = __fdividef(s, fmaf(r2, rinv, Rc));               // r - R_c = s / (r + R_c)
             const float ndot = fmaf(nx, ex, fmaf(ny, ey, fmaf(nz, ez, nD)));    // n_x.(x - y)
-            slot_point<L0>(k0, th0, rho, r, rinv, ndot, g, d, t0, S0);
-            if constexpr (TWO) slot_point<L1>(k1, th1, rho, r, rinv, ndot, g, d, t1, S1);
+            slot_point<L0>(k0, th0, rho, r2, rinv, rinv2, ndot, g, d, t0, S0);
+            if constexpr (TWO) slot_point<L1>(k1, th1, rho, r2, rinv, rinv2, ndot, g, d, t1, S1);
         }
         const float4 tg = st.tg[tl];
         const float4 cre = st.tc[2 * tl], cim = st.tc[2 * tl + 1];
@@ -366,13 +376,10 @@ __global__ void __launch_bounds__(TP, 2) far32_kernel(FarArgs32 A) {
 size_t far32_smem_bytes() { return sizeof(FarSmem); }
 
 cudaError_t launch_far32(const FarArgs32& a, int n_tgt_tiles, int n_chunks, cudaStream_t s) {
-    static bool attr = false;
-    size_t smem = far32_smem_bytes();
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(far32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    const size_t smem = far32_smem_bytes();
+    static const cudaError_t attr_e =
+        cudaFuncSetAttribute(far32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr_e != cudaSuccess) return attr_e;
     if (n_tgt_tiles <= 0 || n_chunks <= 0) return cudaSuccess;
     far32_kernel<<<dim3(n_tgt_tiles, n_chunks), TP, smem, s>>>(a);
     return cudaGetLastError();

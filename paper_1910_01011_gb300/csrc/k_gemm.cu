@@ -319,16 +319,18 @@ __global__ void split_x_kernel(const float2* X, int64_t n_rhs, int64_t k, int64_
     split3(x, P[idx], P[nbpad * kpad + idx], P[2 * nbpad * kpad + idx]);
 }
 
+// Resolved once (thread-safe static initialisation; contexts on several
+// threads share it).
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+            return (PFN_cuTensorMapEncodeTiled_v12000)p;
+        return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }();
     return fn;
 }
 
@@ -355,13 +357,10 @@ int gemm_bf16x3(bem_ctx* ctx, const __nv_bfloat16* Aplanes, int64_t m, int64_t k
         return ctx->fail(BEM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     const int64_t nx = nbpad * kpad;
     split_x_kernel<<<(unsigned)((nx + 255) / 256), 256, 0, ctx->stream>>>(X, n_rhs, k, nbpad, kpad, xplanes);
-    static bool attr = false;
     const size_t smem = sizeof(GemmSmem) + 1024;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return ctx->fail(BEM_ERR_CUDA, std::string("gemm attribute: ") + cudaGetErrorString(e));
-        attr = true;
-    }
+    static const cudaError_t attr_e =
+        cudaFuncSetAttribute(gemm_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr_e != cudaSuccess) return ctx->fail(BEM_ERR_CUDA, std::string("gemm attribute: ") + cudaGetErrorString(attr_e));
     const dim3 grid((unsigned)(nbpad / GN), (unsigned)(mpad / GM));
     gemm_bf16x3_kernel<<<grid, GEMM_THREADS, smem, ctx->stream>>>(ta, tb, mpad, nbpad, (int)(kpad / GK), (int)m,
                                                                   (int)n_rhs, Y, ctx->dev.err);

@@ -46,19 +46,34 @@ struct OsrcState {
     std::vector<double2> A, B;         // A_l / k_eps^2, B_l / k_eps^2
     double2 inv_keps2{};               // 1 / k_eps^2
     int max_sys = 0;
+    int64_t max_rhs = 0;               // right-hand sides the batched buffers hold
     int nblk = 0;
-    // batched COCG state, [max_sys][n] complex
+    // batched COCG state, [max_sys][n] complex; max_sys = 2 n_pade max_rhs
     double2 *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *b = nullptr;
     double2* beta = nullptr;           // [max_sys] shifts
     double* part = nullptr;            // [max_sys][nblk][4] partial sums
     double* scal = nullptr;            // [max_sys][8]: rho(2 parities) re/im, bnorm2, rnorm2, active
-    int* flags = nullptr;              // [max_sys] active
-    // stage vectors, [2][n] or [2*n_pade][n]
-    double2 *u = nullptr, *g = nullptr, *w = nullptr, *br = nullptr;
+    // stage vectors, [max_rhs][2][n]
+    double2 *u = nullptr, *g = nullptr;
     double tol = 1e-11;
     int max_iter = 20000;
     long long iters_last = 0;
+    // one-CTA-per-(system, domain) solver: domain vertex ranges, status words
+    int n_dom = 0;
+    int64_t max_dom_nv = 0;
+    int64_t* dom_v0 = nullptr;         // [n_dom + 1] vertex offsets
+    unsigned long long* stat = nullptr;  // [0]: iterations (sum over CTAs), [1]: CTAs that did not converge
+    // CUDA graphs of GRAPH_ITERS COCG iterations, per (number of systems, tolerance)
+    struct Graph {
+        int n_sys;
+        double tol;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+    cudaStream_t cap = nullptr;
 };
+
+constexpr int GRAPH_ITERS = 32;
 
 // ---------------------------------------------------------------- kernels
 
@@ -249,6 +264,143 @@ __global__ void cocg_check(double* scal, int n_sys, double tol2) {
     if (sc[6] != 0.0 && sc[5] <= tol2 * sc[4]) sc[6] = 0.0;
 }
 
+// ---- one CTA per (system, domain)
+//
+// M and S are block diagonal over the domains (P1 functions of one surface
+// only couple within it), so every (system, domain) pair is an independent
+// complex-symmetric system that one CTA can iterate on its own: the vectors
+// of a domain stay in L2, the dot products are CTA reductions, and no
+// iteration needs a launch, a grid-wide synchronisation or a host round trip.
+// Each CTA stops on its own relative residual |r_j| <= tol |b_j|, so a
+// system converges to tol on every domain (hence also globally); after
+// max_iter iterations it stops and counts itself in stat[1].
+struct CocgCtaArgs {
+    int64_t n;                 // vertices (vector length per system)
+    const int64_t* rp;
+    const int32_t* ci;
+    const double *vm, *vs, *dm, *ds;
+    const double2* beta;       // [n_sys]
+    const double2* b;          // [n_sys][n]
+    double2 *x, *r, *z, *p, *q;
+    const int64_t* dom_v0;     // [n_dom + 1]
+    int n_dom;
+    double tol2;
+    int max_iter;
+    unsigned long long* stat;
+};
+
+// Sum of NV doubles over the CTA; every thread gets the same result (fixed order).
+template <int NT, int NV>
+__device__ __forceinline__ void cta_sum(double (&v)[NV]) {
+    __shared__ double sh[NT / 32][NV];
+    __shared__ double tot[NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double t = v[k];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[warp][k] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double t = 0;
+        for (int w = 0; w < NT / 32; w++) t += sh[w][threadIdx.x];
+        tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = tot[k];
+    __syncthreads();  // tot and sh are reused by the next call
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) cocg_cta_kernel(CocgCtaArgs a) {
+    const int s = blockIdx.x / a.n_dom, j = blockIdx.x % a.n_dom;
+    const int64_t v0 = a.dom_v0[j], v1 = a.dom_v0[j + 1];
+    const int64_t off = (int64_t)s * a.n;
+    const double2 be = a.beta[s];
+    const double2* b = a.b + off;
+    double2 *x = a.x + off, *r = a.r + off, *z = a.z + off, *p = a.p + off, *q = a.q + off;
+    auto dinv = [&](int64_t i) {
+        return cdiv(make_double2(1.0, 0.0), make_double2(a.dm[i] - be.x * a.ds[i], -be.y * a.ds[i]));
+    };
+    // x = 0, r = b, z = D^-1 b, p = z; rho = r^T z, |b|^2
+    double v3[3] = {0, 0, 0};
+    for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+        const double2 bi = b[i];
+        const double2 zi = cmul(dinv(i), bi);
+        x[i] = make_double2(0, 0);
+        r[i] = bi;
+        z[i] = zi;
+        p[i] = zi;
+        const double2 rz = cmul(bi, zi);
+        v3[0] += rz.x;
+        v3[1] += rz.y;
+        v3[2] += bi.x * bi.x + bi.y * bi.y;
+    }
+    cta_sum<NT, 3>(v3);
+    double2 rho = make_double2(v3[0], v3[1]);
+    const double lim = a.tol2 * v3[2];
+    if (!(v3[2] > 0)) return;  // zero right-hand side: x = 0
+    int it = 0;
+    bool ok = false;
+    while (it < a.max_iter) {
+        it++;
+        // q = (M - beta S) p, p^T q
+        double v2[2] = {0, 0};
+        for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+            double qr = 0, qi = 0;
+            for (int64_t e = a.rp[i]; e < a.rp[i + 1]; e++) {
+                const double2 pj = p[a.ci[e]];
+                const double mr = a.vm[e] - be.x * a.vs[e], mi = -be.y * a.vs[e];
+                qr += mr * pj.x - mi * pj.y;
+                qi += mr * pj.y + mi * pj.x;
+            }
+            q[i] = make_double2(qr, qi);
+            const double2 pi = p[i];
+            v2[0] += pi.x * qr - pi.y * qi;
+            v2[1] += pi.x * qi + pi.y * qr;
+        }
+        cta_sum<NT, 2>(v2);
+        const double2 alpha = cdiv(rho, make_double2(v2[0], v2[1]));
+        // x += alpha p, r -= alpha q, z = D^-1 r; r^T z, |r|^2
+        double w3[3] = {0, 0, 0};
+        for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+            const double2 pi = p[i], qi = q[i];
+            double2 xi = x[i], ri = r[i];
+            const double2 ap = cmul(alpha, pi), aq = cmul(alpha, qi);
+            xi.x += ap.x; xi.y += ap.y;
+            ri.x -= aq.x; ri.y -= aq.y;
+            x[i] = xi;
+            r[i] = ri;
+            const double2 zi = cmul(dinv(i), ri);
+            z[i] = zi;
+            const double2 rz = cmul(ri, zi);
+            w3[0] += rz.x;
+            w3[1] += rz.y;
+            w3[2] += ri.x * ri.x + ri.y * ri.y;
+        }
+        cta_sum<NT, 3>(w3);
+        if (w3[2] <= lim) {
+            ok = true;
+            break;
+        }
+        const double2 rn = make_double2(w3[0], w3[1]);
+        const double2 bt = cdiv(rn, rho);
+        rho = rn;
+        for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+            const double2 zi = z[i], pi = p[i];
+            const double2 bp = cmul(bt, pi);
+            p[i] = make_double2(zi.x + bp.x, zi.y + bp.y);
+        }
+        __syncthreads();  // p is read across rows by the next product
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&a.stat[0], (unsigned long long)it);
+        if (!ok) atomicAdd(&a.stat[1], 1ull);
+    }
+}
+
 // y[s][i] = (M - beta_s S) x[s][i]  (plain SpMV, beta per system)
 __global__ void spmv_shift(int64_t n, const int64_t* rp, const int32_t* ci, const double* vm, const double* vs,
                            double2 beta, const double2* x, double2* y) {
@@ -280,13 +432,15 @@ struct BracketArgs {
     double2* out;
 };
 
+// Right-hand side rb = blockIdx.z of a batch: g, out at [rb][2][n], w at [rb][2][L][n].
 __global__ void bracket_kernel(BracketArgs a) {
     const int64_t i = (int64_t)blockIdx.x * SP_THREADS + threadIdx.x;
     const int row = blockIdx.y;
+    const int64_t rr = (int64_t)blockIdx.z * 2 + row;  // (rhs, row)
     if (i >= a.n) return;
-    double2 acc = cmul(a.C0, a.g[(int64_t)row * a.n + i]);
+    double2 acc = cmul(a.C0, a.g[rr * a.n + i]);
     for (int l = 0; l < a.L; l++) {
-        const double2* wl = a.w + ((int64_t)row * a.L + l) * a.n;
+        const double2* wl = a.w + (rr * a.L + l) * a.n;
         double sr = 0, si = 0;
         for (int64_t e = a.rp[i]; e < a.rp[i + 1]; e++) {
             const double2 wj = wl[a.ci[e]];
@@ -297,23 +451,33 @@ __global__ void bracket_kernel(BracketArgs a) {
         acc.x -= t.x;
         acc.y -= t.y;
     }
-    a.out[(int64_t)row * a.n + i] = cmul(a.post[row], acc);
+    a.out[rr * a.n + i] = cmul(a.post[row], acc);
 }
 
-// gather system-order rows into vertex arrays: out[0][v] = y[dof1[v]], out[1][v] = y[dof2[v]]
+// gather system-order rows (right-hand side blockIdx.y, N = 2n dofs each) into
+// vertex arrays: out[rb][0][v] = y[rb][dof1[v]], out[rb][1][v] = y[rb][dof2[v]]
 __global__ void rows_to_vertex(int64_t n, const int64_t* d1, const int64_t* d2, const double2* y, double2* out) {
     const int64_t v = (int64_t)blockIdx.x * SP_THREADS + threadIdx.x;
+    const int64_t rb = blockIdx.y;
     if (v >= n) return;
-    out[v] = y[d1[v]];
-    out[n + v] = y[d2[v]];
+    out[rb * 2 * n + v] = y[rb * 2 * n + d1[v]];
+    out[rb * 2 * n + n + v] = y[rb * 2 * n + d2[v]];
 }
 
-__global__ void vertex_to_rows(int64_t n, const int64_t* d1, const int64_t* d2, const double2* in0,
-                               const double2* in1, double2* y) {
+__global__ void vertex_to_rows(int64_t n, const int64_t* d1, const int64_t* d2, const double2* in, double2* y) {
     const int64_t v = (int64_t)blockIdx.x * SP_THREADS + threadIdx.x;
+    const int64_t rb = blockIdx.y;
     if (v >= n) return;
-    y[d1[v]] = in0[v];
-    y[d2[v]] = in1[v];
+    y[rb * 2 * n + d1[v]] = in[rb * 2 * n + v];
+    y[rb * 2 * n + d2[v]] = in[rb * 2 * n + n + v];
+}
+
+// Pade right-hand sides: b[(rr L + l)][i] = g[rr][i] for every (rhs, row) pair rr
+__global__ void replicate_rows(int64_t n, int L, const double2* g, double2* b) {
+    const int64_t i = (int64_t)blockIdx.x * SP_THREADS + threadIdx.x;
+    const int64_t sys = blockIdx.y;  // rr * L + l
+    if (i >= n) return;
+    b[sys * n + i] = g[(sys / L) * n + i];
 }
 
 }  // namespace gbem
@@ -329,9 +493,48 @@ using namespace gbem;
 // ---------------------------------------------------------------- host set-up
 
 void destroy_osrc_state(bem_ctx* ctx) {
+    if (ctx->osrc) {
+        for (auto& g : ctx->osrc->graphs) cudaGraphExecDestroy(g.exec);
+        if (ctx->osrc->cap) cudaStreamDestroy(ctx->osrc->cap);
+    }
     delete ctx->osrc;
     ctx->osrc = nullptr;
     ctx->osrc_ready = false;
+}
+
+// Batched buffers for R right-hand sides (2 n_pade R systems); captured
+// graphs hold the old pointers and are dropped when the buffers move.
+static int ensure_osrc_batch(bem_ctx* ctx, OsrcState* o, int64_t R) {
+    if (R <= o->max_rhs) return BEM_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (void* p : {(void*)o->x, (void*)o->r, (void*)o->z, (void*)o->p, (void*)o->q, (void*)o->b, (void*)o->beta,
+                    (void*)o->part, (void*)o->scal, (void*)o->u, (void*)o->g})
+        ctx->dfree(p);
+    o->x = o->r = o->z = o->p = o->q = o->b = o->beta = o->u = o->g = nullptr;
+    o->part = o->scal = nullptr;
+    for (auto& gr : o->graphs) cudaGraphExecDestroy(gr.exec);
+    o->graphs.clear();
+    o->max_rhs = 0;
+    o->max_sys = 0;
+    const int64_t n = o->n;
+    const int64_t ms = 2 * (int64_t)o->n_pade * R;
+    if (ms > 65535) return ctx->fail(BEM_ERR_INVALID_ARG, "too many right-hand sides for one preconditioner batch");
+    int rc;
+    const size_t vec = (size_t)ms * n * sizeof(double2);
+    o->x = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
+    o->r = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
+    o->z = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
+    o->p = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
+    o->q = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
+    o->b = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
+    o->beta = (double2*)ctx->dalloc(ms * sizeof(double2), &rc); if (rc) return rc;
+    o->part = (double*)ctx->dalloc((size_t)ms * o->nblk * 4 * sizeof(double), &rc); if (rc) return rc;
+    o->scal = (double*)ctx->dalloc((size_t)ms * 8 * sizeof(double), &rc); if (rc) return rc;
+    o->u = (double2*)ctx->dalloc((size_t)2 * R * n * sizeof(double2), &rc); if (rc) return rc;
+    o->g = (double2*)ctx->dalloc((size_t)2 * R * n * sizeof(double2), &rc); if (rc) return rc;
+    o->max_sys = (int)ms;
+    o->max_rhs = R;
+    return BEM_OK;
 }
 
 static int osrc_build(bem_ctx* ctx) {
@@ -346,9 +549,11 @@ static int osrc_build(bem_ctx* ctx) {
     } else {
         for (void* p : {(void*)o->rp, (void*)o->ci, (void*)o->vm, (void*)o->vs, (void*)o->dm, (void*)o->ds,
                         (void*)o->x, (void*)o->r, (void*)o->z, (void*)o->p, (void*)o->q, (void*)o->b,
-                        (void*)o->beta, (void*)o->part, (void*)o->scal, (void*)o->u, (void*)o->g, (void*)o->w,
-                        (void*)o->br})
+                        (void*)o->beta, (void*)o->part, (void*)o->scal, (void*)o->u, (void*)o->g,
+                        (void*)o->dom_v0, (void*)o->stat})
             ctx->dfree(p);
+        for (auto& g : o->graphs) cudaGraphExecDestroy(g.exec);
+        if (o->cap) cudaStreamDestroy(o->cap);
         *o = OsrcState();
     }
     // P1 mass and stiffness in one CSR pattern (per domain, block diagonal)
@@ -399,8 +604,15 @@ static int osrc_build(bem_ctx* ctx) {
         cudaError_t e = cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream);
         return e == cudaSuccess ? BEM_OK : ctx->fail(BEM_ERR_CUDA, "osrc upload");
     };
+    std::vector<int64_t> dv0(g.n_dom + 1, 0);
+    for (int d = 0; d < g.n_dom; d++) {
+        dv0[d + 1] = g.dom_vert_off[d] + g.dom_nv[d];
+        o->max_dom_nv = std::max(o->max_dom_nv, g.dom_nv[d]);
+    }
+    o->n_dom = g.n_dom;
+    std::vector<unsigned long long> st0(2, 0ull);
     if ((rc = up(&o->rp, rp)) || (rc = up(&o->ci, ci)) || (rc = up(&o->vm, vm)) || (rc = up(&o->vs, vs)) ||
-        (rc = up(&o->dm, dm)) || (rc = up(&o->ds, ds)))
+        (rc = up(&o->dm, dm)) || (rc = up(&o->ds, ds)) || (rc = up(&o->dom_v0, dv0)) || (rc = up(&o->stat, st0)))
         return rc;
     // Pade coefficients and the damped wavenumber (exterior k0, Sec. 2.3)
     const int N = ctx->opts.n_pade;
@@ -436,31 +648,60 @@ static int osrc_build(bem_ctx* ctx) {
         o->A[l] = make_double2(Al.real(), Al.imag());
         o->B[l] = make_double2(Bl.real(), Bl.imag());
     }
-    // batched state
-    o->max_sys = std::max(2 * N, 2);
     o->nblk = (int)std::min<int64_t>(128, (n + SP_THREADS - 1) / SP_THREADS);
-    const size_t vec = (size_t)o->max_sys * n * sizeof(double2);
-    o->x = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
-    o->r = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
-    o->z = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
-    o->p = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
-    o->q = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
-    o->b = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
-    o->beta = (double2*)ctx->dalloc(o->max_sys * sizeof(double2), &rc); if (rc) return rc;
-    o->part = (double*)ctx->dalloc((size_t)o->max_sys * o->nblk * 4 * sizeof(double), &rc); if (rc) return rc;
-    o->scal = (double*)ctx->dalloc((size_t)o->max_sys * 8 * sizeof(double), &rc); if (rc) return rc;
-    o->u = (double2*)ctx->dalloc(2 * n * sizeof(double2), &rc); if (rc) return rc;
-    o->g = (double2*)ctx->dalloc(2 * n * sizeof(double2), &rc); if (rc) return rc;
-    o->w = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
-    o->br = (double2*)ctx->dalloc(2 * n * sizeof(double2), &rc); if (rc) return rc;
+    if ((rc = ensure_osrc_batch(ctx, o, 1))) return rc;
+    o->tol = ctx->osrc_tol;
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->osrc_ready = true;
     return BEM_OK;
 }
 
 // Solve (M - beta_s S) x_s = b_s for s < n_sys (b already in o->b, shifts
-// in o->beta); solutions in o->x.
+// in o->beta); solutions in o->x.  The iterations run in batches of
+// GRAPH_ITERS as one captured CUDA graph (iteration parity is all the
+// kernels take from the iteration count, so one graph serves every batch);
+// convergence flags are read back between batches.
+static void cocg_iteration_launches(OsrcState* o, CocgArgs a, int n_sys, cudaStream_t st) {
+    const dim3 grid(o->nblk, n_sys);
+    for (int k = 0; k < GRAPH_ITERS; k++) {
+        a.it = k;
+        cocg_spmv<<<grid, SP_THREADS, 0, st>>>(a);
+        cocg_update<<<grid, SP_THREADS, 0, st>>>(a);
+        cocg_direction<<<grid, SP_THREADS, 0, st>>>(a);
+        cocg_check<<<(n_sys + 31) / 32, 32, 0, st>>>(o->scal, n_sys, a.tol2);
+    }
+}
+
+// Domains of up to this many vertices are solved one CTA per (system,
+// domain); larger ones by the grid-wide kernels below.
+constexpr int64_t CTA_SOLVE_MAX_NV = 1 << 16;
+
+static int cocg_solve_grid(bem_ctx* ctx, int n_sys);
+
 static int cocg_solve(bem_ctx* ctx, int n_sys) {
+    OsrcState* o = ctx->osrc;
+    const int mode = ctx->opts.osrc_solver;
+    if (mode == 2 || (mode == 0 && o->max_dom_nv > CTA_SOLVE_MAX_NV)) return cocg_solve_grid(ctx, n_sys);
+    CocgCtaArgs a{};
+    a.n = o->n; a.rp = o->rp; a.ci = o->ci; a.vm = o->vm; a.vs = o->vs; a.dm = o->dm; a.ds = o->ds;
+    a.beta = o->beta; a.b = o->b; a.x = o->x; a.r = o->r; a.z = o->z; a.p = o->p; a.q = o->q;
+    a.dom_v0 = o->dom_v0; a.n_dom = o->n_dom; a.tol2 = o->tol * o->tol; a.max_iter = o->max_iter; a.stat = o->stat;
+    const unsigned ctas = (unsigned)(n_sys * o->n_dom);
+    CK(cudaMemsetAsync(o->stat, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    // wide CTAs while they fit in one wave, narrower ones (more per SM) beyond
+    if (ctas <= 152) cocg_cta_kernel<1024><<<ctas, 1024, 0, ctx->stream>>>(a);
+    else cocg_cta_kernel<256><<<ctas, 256, 0, ctx->stream>>>(a);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    unsigned long long st[2];
+    CK(cudaMemcpyAsync(st, o->stat, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    o->iters_last += (long long)st[0];
+    if (st[1]) return ctx->fail(BEM_ERR_NOT_CONVERGED, "OSRC inner COCG solve did not converge");
+    return BEM_OK;
+}
+
+static int cocg_solve_grid(bem_ctx* ctx, int n_sys) {
     OsrcState* o = ctx->osrc;
     CocgArgs a{};
     a.n = o->n; a.rp = o->rp; a.ci = o->ci; a.vm = o->vm; a.vs = o->vs; a.dm = o->dm; a.ds = o->ds;
@@ -470,18 +711,26 @@ static int cocg_solve(bem_ctx* ctx, int n_sys) {
     cocg_init<<<grid, SP_THREADS, 0, ctx->stream>>>(a);
     cocg_init_scalars<<<n_sys, SP_THREADS, 0, ctx->stream>>>(a);
     ctx->launches += 2;
+    // graph of GRAPH_ITERS iterations for this system count and tolerance
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : o->graphs)
+        if (g.n_sys == n_sys && g.tol == o->tol) exec = g.exec;
+    if (!exec) {
+        if (!o->cap) CK(cudaStreamCreateWithFlags(&o->cap, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(o->cap, cudaStreamCaptureModeThreadLocal));
+        cocg_iteration_launches(o, a, n_sys, o->cap);
+        CK(cudaStreamEndCapture(o->cap, &graph));
+        CK(cudaGraphInstantiate(&exec, graph, 0));
+        CK(cudaGraphDestroy(graph));
+        o->graphs.push_back({n_sys, o->tol, exec});
+    }
     std::vector<double> sc(8 * n_sys);
     int it = 0;
-    for (; it < o->max_iter;) {
-        for (int k = 0; k < 32; k++, it++) {
-            a.it = it;
-            cocg_spmv<<<grid, SP_THREADS, 0, ctx->stream>>>(a);
-            cocg_update<<<grid, SP_THREADS, 0, ctx->stream>>>(a);
-            cocg_direction<<<grid, SP_THREADS, 0, ctx->stream>>>(a);
-            cocg_check<<<(n_sys + 31) / 32, 32, 0, ctx->stream>>>(o->scal, n_sys, a.tol2);
-            ctx->launches += 4;
-        }
-        CK(cudaGetLastError());
+    while (it < o->max_iter) {
+        CK(cudaGraphLaunch(exec, ctx->stream));
+        it += GRAPH_ITERS;
+        ctx->launches += 4 * GRAPH_ITERS;
         CK(cudaMemcpyAsync(sc.data(), o->scal, sc.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         bool any = false;
@@ -495,29 +744,37 @@ static int cocg_solve(bem_ctx* ctx, int n_sys) {
     return BEM_OK;
 }
 
+// Inner tolerance of the preconditioner's sparse solves (relative residual).
+void set_osrc_tolerance(bem_ctx* ctx, double tol) {
+    if (ctx->osrc) ctx->osrc->tol = tol;
+    ctx->osrc_tol = tol;
+}
+
 // y = P x for Galerkin rows x (system order); both device vectors.
 // With u = M^-1 row, the bracket's g = M u is the row itself, so the Pade
 // solves take the rows directly: 2 N_pade + 2 sparse solves per application.
-int bem_ctx::apply_prec(const double2* xin, double2* yout) {
+int bem_ctx::apply_prec(const double2* xin, double2* yout) { return apply_prec_batch(xin, yout, 1); }
+
+// The same for R right-hand sides [R][N] at once: all R (2 N_pade) Pade
+// systems in one batched COCG, then all 2 R closing systems in another.
+int bem_ctx::apply_prec_batch(const double2* xin, double2* yout, int64_t R) {
     bem_ctx* const ctx = this;
     int rc = osrc_build(this);
     if (rc) return rc;
     OsrcState* o = osrc;
+    if ((rc = ensure_osrc_batch(this, o, R))) return rc;
     const int64_t n = o->n;
     const unsigned nb = (unsigned)((n + SP_THREADS - 1) / SP_THREADS);
     const int L = o->n_pade;
-    // rows in vertex order: g[0] = row1, g[1] = row2
-    rows_to_vertex<<<nb, SP_THREADS, 0, stream>>>(n, dev.v_dof1, dev.v_dof2, xin, o->g);
-    // Pade solves w_{i,l} = (M - B_l S)^-1 row_i, systems ordered [row][l]
-    std::vector<double2> be(o->max_sys, make_double2(0, 0));
-    for (int row = 0; row < 2; row++)
-        for (int l = 0; l < L; l++) {
-            CK(cudaMemcpyAsync(o->b + ((int64_t)row * L + l) * n, o->g + (int64_t)row * n, n * sizeof(double2),
-                               cudaMemcpyDeviceToDevice, stream));
-            be[row * L + l] = o->B[l];
-        }
-    CK(cudaMemcpyAsync(o->beta, be.data(), 2 * L * sizeof(double2), cudaMemcpyHostToDevice, stream));
-    if ((rc = cocg_solve(this, 2 * L))) return rc;
+    const int ns = (int)(2 * L * R);
+    // rows in vertex order: g[rb][0] = row1, g[rb][1] = row2
+    rows_to_vertex<<<dim3(nb, (unsigned)R), SP_THREADS, 0, stream>>>(n, dev.v_dof1, dev.v_dof2, xin, o->g);
+    // Pade solves w_{rb,i,l} = (M - B_l S)^-1 row_i, systems ordered [rb][row][l]
+    replicate_rows<<<dim3(nb, (unsigned)ns), SP_THREADS, 0, stream>>>(n, L, o->g, o->b);
+    std::vector<double2> be(ns);
+    for (int s = 0; s < ns; s++) be[s] = o->B[s % L];
+    CK(cudaMemcpyAsync(o->beta, be.data(), ns * sizeof(double2), cudaMemcpyHostToDevice, stream));
+    if ((rc = cocg_solve(this, ns))) return rc;
     // brackets; row 1 scaled by i k (the DtN weak form)
     BracketArgs ba{};
     ba.n = n; ba.rp = o->rp; ba.ci = o->ci; ba.vs = o->vs; ba.g = o->g; ba.w = o->x; ba.L = L; ba.C0 = o->C0;
@@ -525,12 +782,14 @@ int bem_ctx::apply_prec(const double2* xin, double2* yout) {
     ba.post[0] = o->ikk;
     ba.post[1] = make_double2(1.0, 0.0);
     ba.out = o->b;
-    bracket_kernel<<<dim3(nb, 2), SP_THREADS, 0, stream>>>(ba);
+    bracket_kernel<<<dim3(nb, 2, (unsigned)R), SP_THREADS, 0, stream>>>(ba);
     // out1 = M^-1 (i k bracket_1);  out2 = (M - S/k_eps^2)^-1 bracket_2, then / (i k)
-    be[0] = make_double2(0, 0);
-    be[1] = o->inv_keps2;
-    CK(cudaMemcpyAsync(o->beta, be.data(), 2 * sizeof(double2), cudaMemcpyHostToDevice, stream));
-    if ((rc = cocg_solve(this, 2))) return rc;
+    for (int64_t rb = 0; rb < R; rb++) {
+        be[2 * rb] = make_double2(0, 0);
+        be[2 * rb + 1] = o->inv_keps2;
+    }
+    CK(cudaMemcpyAsync(o->beta, be.data(), 2 * R * sizeof(double2), cudaMemcpyHostToDevice, stream));
+    if ((rc = cocg_solve(this, (int)(2 * R)))) return rc;
     const std::complex<double> inv = 1.0 / std::complex<double>(o->ikk.x, o->ikk.y);
     BracketArgs cp{};  // scaled copy (no Pade terms): u_row = post_row * x_row
     cp.n = n; cp.rp = o->rp; cp.ci = o->ci; cp.vs = o->vs; cp.g = o->x; cp.w = nullptr; cp.L = 0;
@@ -538,9 +797,9 @@ int bem_ctx::apply_prec(const double2* xin, double2* yout) {
     cp.post[0] = make_double2(1.0, 0.0);
     cp.post[1] = make_double2(inv.real(), inv.imag());
     cp.out = o->u;
-    bracket_kernel<<<dim3(nb, 2), SP_THREADS, 0, stream>>>(cp);
-    vertex_to_rows<<<nb, SP_THREADS, 0, stream>>>(n, dev.v_dof1, dev.v_dof2, o->u, o->u + n, yout);
-    launches += 4;
+    bracket_kernel<<<dim3(nb, 2, (unsigned)R), SP_THREADS, 0, stream>>>(cp);
+    vertex_to_rows<<<dim3(nb, (unsigned)R), SP_THREADS, 0, stream>>>(n, dev.v_dof1, dev.v_dof2, o->u, yout);
+    launches += 5;
     CK(cudaGetLastError());
     return BEM_OK;
 }

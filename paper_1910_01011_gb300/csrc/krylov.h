@@ -11,16 +11,32 @@ namespace gbem {
 struct Krylov {
     int64_t n = 0;
     int m = 0;
+    int64_t R = 0;  // columns the buffers hold (batched GMRES)
     double2 *V = nullptr, *w = nullptr, *t = nullptr, *part = nullptr, *h = nullptr, *y = nullptr;
+    double2* Z = nullptr;  // preconditioned basis of flexible GMRES, [m][R][n] (allocated on first use)
+    double* sc = nullptr;
 
-    int ensure(bem_ctx* ctx, int64_t n, int m);
+    int ensure(bem_ctx* ctx, int64_t n, int m, int64_t R = 1);
     void release(bem_ctx* ctx);
     int dot(bem_ctx* ctx, const double2* a, const double2* b, std::complex<double>* out);
     int norm(bem_ctx* ctx, const double2* a, double* out);
+    // out = a x + b z over len entries (default n)
     int axpby(bem_ctx* ctx, std::complex<double> a, const double2* x, std::complex<double> b, const double2* z,
-              double2* out);
-    int gmres(bem_ctx* ctx, const std::function<int(const double2*, double2*)>& op, const double2* b, double2* x,
-              int restart, double tol, int max_iter, int* iters, double* relres, bool zero_guess);
+              double2* out, int64_t len = -1);
+    // Solve op(x) = b.  With prec (flexible GMRES, right preconditioning):
+    // z_j = prec(v_j), the basis grows with op(z_j) and x += Z y, so prec
+    // may change from one application to the next (e.g. inner solves run to
+    // a loose tolerance); residuals are those of op itself.
+    using Op = std::function<int(const double2*, double2*)>;
+    int gmres(bem_ctx* ctx, const Op& op, const double2* b, double2* x, int restart, double tol, int max_iter,
+              int* iters, double* relres, bool zero_guess, const Op* prec = nullptr);
+    int ensure_flexible(bem_ctx* ctx);
+    // column norms of R vectors [R][n] (host out[R])
+    int norms(bem_ctx* ctx, const double2* a, int64_t R, double* out);
+    // R independent GMRES runs in lockstep: op maps [R][n] to [R][n] column
+    // by column; column r stops once its own residual meets tol.
+    int gmres_batch(bem_ctx* ctx, const Op& op, const double2* B, double2* X, int64_t R, int restart, double tol,
+                    int max_iter, int* iters, double* relres, bool zero_guess, const Op* prec = nullptr);
 };
 
 }  // namespace gbem

@@ -152,3 +152,20 @@ def test_memory_budget_is_enforced(api):
     with pytest.raises(BemError) as e:
         c.apply(np.ones(c.n_dofs, dtype=complex))
     assert e.value.code == -3
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotuned_launch_shape_keeps_parity(api, prec):
+    """The autotuner's chosen source-chunk length is one of the candidates and
+    the operator it then applies still meets the precision's bar; a second
+    context of the same size reuses the cached choice."""
+    s = ragged_scene()
+    A = pmchwt.assemble(s)
+    c = ctx_for(api, s)
+    t = c.autotune(prec)
+    assert t["chunk_tiles"] in (0, 8, 16, 32, 64, 128, 256) and t["ms"] > 0
+    x = scenes.random_complex(A.shape[0], 9)
+    assert rel(c.apply(x, precision=prec), A @ x) < TOL[prec]
+    c2 = ctx_for(api, s)
+    assert c2.autotune(prec, timed=False)["chunk_tiles"] == t["chunk_tiles"]
+    assert rel(c2.apply(x, precision=prec), A @ x) < TOL[prec]
