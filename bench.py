@@ -181,12 +181,12 @@ def traffic_from_profile():
     return float(m.group(1))
 
 
-def solve_metrics(local, reps=12):
+def sphere_solve_metrics(local, reps=12):
     """Config-1 sphere (icosphere level 3, k0 = 5, k1 = 5.25, density ratio
-    1.1, plane wave): seconds per right-hand side of the FP32-inner / FP64-
-    refined solve against the plain FP64 GPU solve, both to an FP64 relative
-    residual of 1e-9 (traces within 1e-6 of each other), and the p50 / p99
-    latency of repeated mixed solves."""
+    1.1, plane wave): seconds per solve of the mixed path (FP32 operator
+    inside a flexible GMRES, FP64 residual refinement) against the plain FP64
+    GPU path, both to an FP64 relative residual of 1e-9, and the p50 / p99 of
+    repeated mixed solves."""
     import numpy as np
 
     from paper_1910_01011_gb300.api import Context
@@ -200,13 +200,13 @@ def solve_metrics(local, reps=12):
         t0 = time.perf_counter()
         r64 = c.solve(precision=0, tol=1e-9)
         t64.append(time.perf_counter() - t0)
-    u64 = np.concatenate(c.traces(0))
+    u64 = c.solution(0)
     t32 = []
     for _ in range(reps):
         t0 = time.perf_counter()
         r32 = c.solve(precision=1, tol=1e-9)
         t32.append(time.perf_counter() - t0)
-    u32 = np.concatenate(c.traces(0))
+    u32 = c.solution(0)
     c.close()
     return {"workload": "unit sphere, icosphere level 3 (1280 triangles), k0=5, k1=5.25, rho ratio 1.1, plane wave",
             "tol_fp64_residual": 1e-9, "fp64_s_per_rhs": float(np.median(t64)), "mixed_s_per_rhs": float(np.median(t32)),
@@ -214,6 +214,127 @@ def solve_metrics(local, reps=12):
             "speedup_vs_fp64": float(np.median(t64) / np.median(t32)),
             "trace_rel_diff_mixed_vs_fp64": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
             "iterations": {"fp64": r64["iterations"], "mixed": r32["iterations"], "refinements": r32["refinements"]}}
+
+
+def rib_solve_metrics(local, n_rhs=8, tol=1e-8):
+    """The rib / fat / liver scene at the frequency its mesh resolves (0.1 MHz,
+    41k triangles, k h ~ 1), random-phase piston excitations of the 256-piston
+    bowl: seconds per right-hand side of the mixed, batched form (n_rhs
+    excitations in lockstep; split-BF16 tensor-core GEMM on the assembled
+    operator inside a flexible GMRES, OSRC preconditioner with loose sparse
+    solves, FP64 residual refinement on the assembled complex128 operator)
+    against the plain FP64 GPU path (FP64 assembled operator, the same
+    preconditioner, one excitation at a time), both to an FP64 relative
+    residual of tol; the traces of the two paths agree to the reported
+    difference.  Operator assembly and preconditioner set-up are reported
+    separately (they are kept on the device for later requests)."""
+    import numpy as np
+    import torch
+
+    from paper_1910_01011_gb300.api import BF16X3, FP64_ASSEMBLED, Context
+    from synth import scenes
+    s = scenes.rib_scene_resolved()
+    tr = s.transducer
+    c = Context.from_scene(s, device=local, n_pade=8)
+    c.set_transducer(tr["centres"], tr["normals"], tr["radii"], 2 * np.pi * s.freq * s.rho0)
+    W = np.exp(2j * np.pi * np.random.default_rng(3).random((n_rhs, tr["radii"].size)))
+    N = c.n_dofs
+    x = torch.zeros(N, dtype=torch.complex128, device="cuda")
+    t0 = time.perf_counter()
+    c.apply(x, precision=FP64_ASSEMBLED)
+    c.apply(x, precision=BF16X3)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    c.set_excitations(W[:1])
+    t0 = time.perf_counter()
+    r64 = c.solve(precision=0, operator_mode=1, tol=tol)
+    t64 = time.perf_counter() - t0
+    u64 = c.solution(0)
+    c.set_excitations(W)
+    t0 = time.perf_counter()
+    rb = c.solve(precision=1, operator_mode=1, tol=tol, batch_rhs=n_rhs)
+    tb = time.perf_counter() - t0
+    ub = c.solution(0)
+    c.close()
+    return {"workload": f"rib/fat/liver scene, 0.1 MHz, {s.n_triangles} triangles (N={N}), {n_rhs} random-phase "
+                        "excitations of the 256-piston bowl, n_pade 8",
+            "tol_fp64_residual": tol, "setup_s": setup,
+            "fp64_s_per_rhs": t64, "mixed_batched_s_per_rhs": tb / n_rhs, "speedup_vs_fp64": t64 / (tb / n_rhs),
+            "trace_rel_diff_mixed_vs_fp64": float(np.linalg.norm(ub - u64) / np.linalg.norm(u64)),
+            "iterations": {"fp64": r64["iterations"], "mixed_per_rhs": rb["iterations"] / n_rhs,
+                           "refinements": rb["refinements"]},
+            "residual": {"fp64": r64["residual"], "mixed": rb["residual"]}}
+
+
+def serving_metrics(local, n_req=12, max_exc=8, rate=20.0, budget=150 << 30, tol=1e-6):
+    """Serving trace: Poisson arrivals (mean `rate`/s) of planning solves over
+    a pool of scenes (1k and 5k-triangle spheres, a 10k-triangle rib scene, a
+    20k-triangle kidney scene, each at k h ~ 1), each request with 1..max_exc
+    random-phase piston excitations, through the request loop (2 workers,
+    device-resident scene cache, admission by the HBM budget; mixed precision
+    with batched excitations, FP64 refinement to tol).  The cache is warmed
+    with one request per scene before the trace (set-up not in the
+    latencies).  Baseline: the same excitations solved one at a time by the
+    plain FP64 GPU path, timed on one excitation per scene and summed over the
+    trace's excitations."""
+    import numpy as np
+
+    from paper_1910_01011_gb300.api import Context, Server
+    from synth import serving
+    reqs, weights = serving.trace(n_req, rate=rate, max_exc=max_exc)
+    keys = sorted({k for _, k, _ in reqs})
+    built = {k: serving.POOL[k]() for k in keys}
+    srv = Server(device=local, slots=2, max_batch_rhs=64, hbm_budget_bytes=budget, precision=1, operator_mode=1,
+                 tol=tol, max_iter=20000, max_refine=20)
+    ids = {k: srv.add_scene(built[k], omega_rho0=built[k].meta["omega_rho0"], n_pade=8) for k in keys}
+    for k in keys:  # warm the cache (geometry, near field, assembled operators, preconditioner)
+        h = srv.submit(ids[k], np.ones((1, srv.scenes[ids[k]][1])))
+        srv.wait(h)
+        srv.result(h, 1, ids[k])
+    warm = srv.stats()
+    t0 = time.perf_counter()
+    hs = []
+    for i, (ta, k, ne) in enumerate(reqs):
+        dt = t0 + ta - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        hs.append((srv.submit(ids[k], weights(i, srv.scenes[ids[k]][1])), k, ne))
+    lat, fails, its = [], [], {}
+    for h, k, ne in hs:
+        srv.wait(h)
+        try:
+            _, rep = srv.result(h, ne, ids[k])
+            lat.append(rep["latency_ms"])
+            its.setdefault(k, []).append(rep["iterations"] / max(1, rep["batch_exc"]))
+        except Exception as e:  # reported, not hidden
+            fails.append(f"{k}: {e}")
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    # plain FP64 GPU path, one excitation at a time, per scene
+    t64 = {}
+    for k in keys:
+        sc = built[k]
+        c = Context.from_scene(sc, device=local, n_pade=8)
+        tr = sc.transducer
+        c.set_transducer(tr["centres"], tr["normals"], tr["radii"], sc.meta["omega_rho0"])
+        c.set_excitations(weights(0, tr["radii"].size)[:1])
+        c.solve(precision=0, operator_mode=1, tol=tol, max_iter=20000)  # set-up
+        t1 = time.perf_counter()
+        c.solve(precision=0, operator_mode=1, tol=tol, max_iter=20000)
+        t64[k] = time.perf_counter() - t1
+        c.close()
+    n_exc = sum(ne for _, _, ne in reqs)
+    seq = sum(ne * t64[k] for _, k, ne in reqs)
+    return {"workload": f"{n_req} requests, Poisson {rate}/s, 1..{max_exc} excitations each "
+                        f"({n_exc} total), scenes {keys}, tol {tol}, budget {budget / 2**30:.0f} GiB",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "wall_s": wall, "excitations_per_s": n_exc / wall, "requests_per_s": n_req / wall,
+            "batches": st["batches"] - warm["batches"], "peak_device_gib": st["peak_device_bytes"] / 2**30,
+            "fp64_sequential_s_estimate": seq, "fp64_sequential_excitations_per_s": n_exc / seq,
+            "speedup_vs_fp64_sequential": seq / wall, "fp64_s_per_rhs": t64,
+            "mixed_iterations_per_excitation": {k: float(np.mean(v)) for k, v in its.items()},
+            "failed_requests": fails}
 
 
 def assembled_metrics(ctx, s, n_int, local, n_rhs=256):
@@ -247,6 +368,39 @@ def assembled_metrics(ctx, s, n_int, local, n_rhs=256):
             "roofline": {"bound": "tensor", "achieved": tflop / (ms / 1e3), "peak": BF16_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": tflop / (ms / 1e3) / BF16_PEAK_TFLOPS,
                          "peak_basis": "MEASURED_PEAKS.json bf16_tflops (burst)"}}
+
+
+def prec_step(args, s, desc, local, world):
+    """One OSRC preconditioner application to R right-hand sides per step
+    (n_pade 8, sparse solves to a 10 % relative residual, as inside the
+    flexible GMRES)."""
+    import torch
+
+    from paper_1910_01011_gb300.api import PREC, Context
+    ctx = Context.from_scene(s, device=local, stream=torch.cuda.current_stream().cuda_stream, n_pade=8,
+                             osrc_tol=0.1)
+    N, R = ctx.n_dofs, args.prec_rhs
+    g = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.complex(torch.randn(R, N, dtype=torch.float64, device="cuda", generator=g),
+                      torch.randn(R, N, dtype=torch.float64, device="cuda", generator=g))
+    Y = torch.empty_like(X)
+    for _ in range(max(3, args.warmup)):
+        ctx.apply(X, op=PREC, out=Y)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.apply(X, op=PREC, out=Y)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    prof = ctx.profile_read(reset=True)
+    ctx.close()
+    print(json.dumps({"metric": "OSRC preconditioner applications (right-hand sides) per s", "value": R * args.steps / dt,
+                      "unit": "RHS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+                      "config": {"workload": desc, "n_rhs": R, "n_pade": 8, "osrc_tol": 0.1},
+                      "gpu_launches": prof["kernel_launches"]}))
 
 
 def run_reference(args, rank, world):
@@ -283,6 +437,11 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the solve and assembled-GEMM measurements")
+    ap.add_argument("--quick", action="store_true", help="skip the rib-scene solve and the serving trace")
+    ap.add_argument("--step", default="apply", choices=["apply", "prec"],
+                    help="apply: the operator application (the headline metric); prec: one OSRC preconditioner "
+                         "application to --prec-rhs right-hand sides (for profiling the sparse solves)")
+    ap.add_argument("--prec-rhs", type=int, default=8)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -302,6 +461,8 @@ def main():
 
     s, desc = workload(args.workload)
     stream = torch.cuda.current_stream()
+    if args.step == "prec":
+        return prec_step(args, s, desc, local, world)
     ctx = Context.from_scene(s, device=local, stream=stream.cuda_stream)
     N = ctx.n_dofs
     single, fused, n_int = pair_counts(s)
@@ -382,8 +543,16 @@ def main():
             "gpu_launches": prof["kernel_launches"],
             "clocks": clk.summary()}
     if not args.no_extras:
-        line["assembled"] = assembled_metrics(ctx, s, n_int, local)
-        line["solve"] = solve_metrics(local)
+        def extra(name, fn, *a):
+            try:
+                line[name] = fn(*a)
+            except Exception as e:  # the line still prints; the failure is part of it
+                line[name] = {"error": f"{type(e).__name__}: {e}"}
+        extra("assembled", assembled_metrics, ctx, s, n_int, local)
+        extra("solve_sphere", sphere_solve_metrics, local)
+        if not args.quick:
+            extra("solve", rib_solve_metrics, local)
+            extra("serving", serving_metrics, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt, sample = oracle_sample(s, args.ref_rows)
         line["cpu_baseline"] = {"value": n / dt / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",

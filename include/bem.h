@@ -180,7 +180,8 @@ typedef struct {
     double tol;            /* target relative residual of the returned traces */
     int32_t precision;     /* BEM_PREC_FP64: plain FP64 GMRES; BEM_PREC_FP32: FP32 inner, FP64 refinement */
     int32_t precondition;  /* 1 = OSRC preconditioner */
-    double inner_tol;      /* inner relative tolerance of the mixed-precision path (default 1e-4) */
+    double inner_tol;      /* inner relative tolerance of the mixed-precision path (default 1e-4; an inner
+                              solve that only needs a smaller reduction to reach tol stops there) */
     int32_t max_refine;    /* outer refinement cap (default 10) */
     int32_t operator_mode; /* 0: matrix-free operators; 1: assembled operators (BF16-split tensor-core
                               GEMM inside GMRES, complex128 GEMV for FP64 residuals), set up once and
@@ -196,7 +197,7 @@ typedef struct {
                               A_hat itself.  0: the paper's left composition P A_hat u = P b with plain
                               GMRES (sparse solves to 1/100 of the GMRES tolerance).  Same solution. */
     double prec_tol;       /* relative residual of the preconditioner's sparse solves inside the solve;
-                              0 = automatic (1e-2 flexible, 1/100 of the GMRES tolerance otherwise) */
+                              0 = automatic (1e-1 flexible, 1/100 of the GMRES tolerance otherwise) */
 } bem_solve_opts;
 
 typedef struct {

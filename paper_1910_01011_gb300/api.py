@@ -318,9 +318,12 @@ class Server:
         lat = ctypes.c_double()
         be = ctypes.c_int64()
         rc = self.lib.bem_server_result(self.h, int(handle), U.ctypes.data, ctypes.byref(r), ctypes.byref(lat),
-                                        ctypes.byref(be), 1 if release else 0)
+                                        ctypes.byref(be), 0)
+        msg = self.error(handle) if rc else ""
+        if release:
+            self.lib.bem_server_result(self.h, int(handle), None, None, None, None, 1)
         if rc:
-            raise _lib.BemError(rc, self.error(handle) or f"request {handle} failed")
+            raise _lib.BemError(rc, msg or f"request {handle} failed")
         return U, {"iterations": r.iterations, "refinements": r.refinements, "residual": r.residual,
                    "seconds": r.seconds, "latency_ms": lat.value, "batch_exc": be.value}
 

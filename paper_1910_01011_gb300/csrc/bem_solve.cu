@@ -376,6 +376,14 @@ int bem_default_solve_opts(bem_solve_opts* o) {
     return BEM_OK;
 }
 
+// Relative tolerance of one inner (FP32-operator) solve of the refinement
+// when the FP64 residual is at rel: inner_tol, or looser once a smaller
+// reduction already reaches the target (half of tol / rel), at most 1/2.
+static double inner_tolerance(const bem_solve_opts& o, double rel) {
+    const double need = rel > 0 ? 0.5 * o.tol / rel : o.inner_tol;
+    return std::min(0.5, std::max(o.inner_tol, need));
+}
+
 // Work blocks for batched solves of up to R right-hand sides.
 static int ensure_batch_state(bem_ctx* ctx, int64_t R) {
     SolveState* S = ctx->solve;
@@ -461,14 +469,20 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
     } else {
         CK(cudaMemcpyAsync(S->br, b, R * N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
         for (int64_t r = 0; r < R; r++) rel[r] = bn[r] > 0 ? 1.0 : 0.0;
-        int ref = 0;
+        int ref = 0, inner_prec = BEM_PREC_FP32;
+        double prev = 2.0;
         for (; ref <= o.max_refine; ref++) {
             worst = *std::max_element(rel.begin(), rel.end());
             if (worst <= o.tol || it >= o.max_iter || ref == o.max_refine) break;
+            // stalled refinement (reduced-precision operator error too large
+            // for this conditioning): the remaining inner solves run in FP64
+            if (worst > 0.5 * prev) inner_prec = BEM_PREC_FP64;
+            prev = worst;
             const double2* sr = rhs_of(S->br);
             if (rc) return rc;
-            if ((rc = S->kry.gmres_batch(ctx, op_for(BEM_PREC_FP32), sr, S->bd, R, o.restart, o.inner_tol,
-                                         o.max_iter - it, its.data(), irel.data(), true, rp)))
+            if ((rc = S->kry.gmres_batch(ctx, op_for(inner_prec), sr, S->bd, R, o.restart,
+                                         inner_tolerance(o, worst), o.max_iter - it, its.data(), irel.data(), true,
+                                         rp)))
                 return rc;
             it += *std::max_element(its.begin(), its.end());
             for (int64_t r = 0; r < R; r++) rep->iterations += its[r];
@@ -509,7 +523,7 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
         ~TolScope() { set_osrc_tolerance(c, saved); }
     } tol_scope{ctx, ctx->osrc_tol};
     const double gm_tol = o.precision == BEM_PREC_FP64 ? o.tol : std::max(o.inner_tol, o.tol);
-    set_osrc_tolerance(ctx, o.prec_tol > 0 ? o.prec_tol : o.flexible ? 1e-2 : std::max(1e-13, 0.01 * gm_tol));
+    set_osrc_tolerance(ctx, o.prec_tol > 0 ? o.prec_tol : o.flexible ? 1e-1 : std::max(1e-13, 0.01 * gm_tol));
     bem_solve_report R{};
     bool converged = true;
     // the operator of one precision level: matrix-free or assembled, then the preconditioner
@@ -576,20 +590,24 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
             // mixed: FP32 inner GMRES, FP64 residual refinement
             CK(cudaMemsetAsync(u, 0, N * sizeof(double2), ctx->stream));
             CK(cudaMemcpyAsync(S->r, b, N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
-            double rel = 1.0;
-            int it = 0, ref = 0;
+            double rel = 1.0, prev = 2.0;
+            int it = 0, ref = 0, inner_prec = BEM_PREC_FP32;
             for (; ref <= o.max_refine; ref++) {
                 double rn;
                 if ((rc = S->kry.norm(ctx, S->r, &rn))) return rc;
                 rel = rn / bnorm;
                 if (rel <= o.tol || it >= o.max_iter) break;
                 if (ref == o.max_refine) break;
+                // refinement stalls when the reduced-precision operator's error
+                // times the conditioning is near 1: finish in FP64
+                if (rel > 0.5 * prev) inner_prec = BEM_PREC_FP64;
+                prev = rel;
                 const double2* sr = rhs_of(S->r);
                 if (rc) return rc;
                 int its = 0;
                 double irel = 0;
-                if ((rc = S->kry.gmres(ctx, op_for(BEM_PREC_FP32), sr, S->d, o.restart, o.inner_tol, o.max_iter - it,
-                                       &its, &irel, true, rp)))
+                if ((rc = S->kry.gmres(ctx, op_for(inner_prec), sr, S->d, o.restart, inner_tolerance(o, rel),
+                                       o.max_iter - it, &its, &irel, true, rp)))
                     return rc;
                 it += its;
                 if ((rc = S->kry.axpby(ctx, 1.0, u, 1.0, S->d, u))) return rc;

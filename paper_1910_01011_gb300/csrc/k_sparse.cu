@@ -61,6 +61,9 @@ struct OsrcState {
     // one-CTA-per-(system, domain) solver: domain vertex ranges, status words
     int n_dom = 0;
     int64_t max_dom_nv = 0;
+    int ell_w = 0;                     // ELL width (max nonzeros per row), 0 if too wide
+    int32_t* ell_ci = nullptr;         // [ell_w][n] column indices (padding: the row itself)
+    double *ell_m = nullptr, *ell_s = nullptr;  // [ell_w][n] mass / stiffness values (padding: 0)
     int64_t* dom_v0 = nullptr;         // [n_dom + 1] vertex offsets
     unsigned long long* stat = nullptr;  // [0]: iterations (sum over CTAs), [1]: CTAs that did not converge
     // CUDA graphs of GRAPH_ITERS COCG iterations, per (number of systems, tolerance)
@@ -276,9 +279,9 @@ __global__ void cocg_check(double* scal, int n_sys, double tol2) {
 // max_iter iterations it stops and counts itself in stat[1].
 struct CocgCtaArgs {
     int64_t n;                 // vertices (vector length per system)
-    const int64_t* rp;
-    const int32_t* ci;
-    const double *vm, *vs, *dm, *ds;
+    const int32_t* eci;        // ELL [W][n]
+    const double *em, *es;     // ELL [W][n]
+    const double *dm, *ds;
     const double2* beta;       // [n_sys]
     const double2* b;          // [n_sys][n]
     double2 *x, *r, *z, *p, *q;
@@ -313,11 +316,15 @@ __device__ __forceinline__ void cta_sum(double (&v)[NV]) {
     __syncthreads();  // tot and sh are reused by the next call
 }
 
-template <int NT>
+// Rows a thread handles together: U rows NT apart, so that the loads of all
+// U rows (W coalesced ELL entries each) are in flight at once.
+constexpr int CTA_U = 4;
+
+template <int NT, int W>
 __global__ void __launch_bounds__(NT) cocg_cta_kernel(CocgCtaArgs a) {
     const int s = blockIdx.x / a.n_dom, j = blockIdx.x % a.n_dom;
     const int64_t v0 = a.dom_v0[j], v1 = a.dom_v0[j + 1];
-    const int64_t off = (int64_t)s * a.n;
+    const int64_t n = a.n, off = (int64_t)s * n;
     const double2 be = a.beta[s];
     const double2* b = a.b + off;
     double2 *x = a.x + off, *r = a.r + off, *z = a.z + off, *p = a.p + off, *q = a.q + off;
@@ -348,18 +355,34 @@ __global__ void __launch_bounds__(NT) cocg_cta_kernel(CocgCtaArgs a) {
         it++;
         // q = (M - beta S) p, p^T q
         double v2[2] = {0, 0};
-        for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
-            double qr = 0, qi = 0;
-            for (int64_t e = a.rp[i]; e < a.rp[i + 1]; e++) {
-                const double2 pj = p[a.ci[e]];
-                const double mr = a.vm[e] - be.x * a.vs[e], mi = -be.y * a.vs[e];
-                qr += mr * pj.x - mi * pj.y;
-                qi += mr * pj.y + mi * pj.x;
+        for (int64_t i0 = v0 + threadIdx.x; i0 < v1; i0 += CTA_U * NT) {
+            double qr[CTA_U], qi[CTA_U];
+#pragma unroll
+            for (int u = 0; u < CTA_U; u++) {
+                qr[u] = 0;
+                qi[u] = 0;
+                const int64_t i = i0 + (int64_t)u * NT;
+                if (i < v1) {
+#pragma unroll
+                    for (int k = 0; k < W; k++) {
+                        const int64_t e = (int64_t)k * n + i;
+                        const double2 pj = p[a.eci[e]];
+                        const double mr = a.em[e] - be.x * a.es[e], mi = -be.y * a.es[e];
+                        qr[u] += mr * pj.x - mi * pj.y;
+                        qi[u] += mr * pj.y + mi * pj.x;
+                    }
+                }
             }
-            q[i] = make_double2(qr, qi);
-            const double2 pi = p[i];
-            v2[0] += pi.x * qr - pi.y * qi;
-            v2[1] += pi.x * qi + pi.y * qr;
+#pragma unroll
+            for (int u = 0; u < CTA_U; u++) {
+                const int64_t i = i0 + (int64_t)u * NT;
+                if (i < v1) {
+                    q[i] = make_double2(qr[u], qi[u]);
+                    const double2 pi = p[i];
+                    v2[0] += pi.x * qr[u] - pi.y * qi[u];
+                    v2[1] += pi.x * qi[u] + pi.y * qr[u];
+                }
+            }
         }
         cta_sum<NT, 2>(v2);
         const double2 alpha = cdiv(rho, make_double2(v2[0], v2[1]));
@@ -550,7 +573,7 @@ static int osrc_build(bem_ctx* ctx) {
         for (void* p : {(void*)o->rp, (void*)o->ci, (void*)o->vm, (void*)o->vs, (void*)o->dm, (void*)o->ds,
                         (void*)o->x, (void*)o->r, (void*)o->z, (void*)o->p, (void*)o->q, (void*)o->b,
                         (void*)o->beta, (void*)o->part, (void*)o->scal, (void*)o->u, (void*)o->g,
-                        (void*)o->dom_v0, (void*)o->stat})
+                        (void*)o->dom_v0, (void*)o->stat, (void*)o->ell_ci, (void*)o->ell_m, (void*)o->ell_s})
             ctx->dfree(p);
         for (auto& g : o->graphs) cudaGraphExecDestroy(g.exec);
         if (o->cap) cudaStreamDestroy(o->cap);
@@ -604,6 +627,30 @@ static int osrc_build(bem_ctx* ctx) {
         cudaError_t e = cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream);
         return e == cudaSuccess ? BEM_OK : ctx->fail(BEM_ERR_CUDA, "osrc upload");
     };
+    // ELL copy of the pattern for the one-CTA solver (width = most nonzeros in a row)
+    int64_t wmax = 0;
+    for (int64_t i = 0; i < n; i++) wmax = std::max(wmax, rp[i + 1] - rp[i]);
+    const int ell_w = wmax <= 8 ? 8 : wmax <= 12 ? 12 : wmax <= 16 ? 16 : 0;
+    std::vector<int32_t> eci;
+    std::vector<double> em, es;
+    if (ell_w) {
+        eci.assign((size_t)ell_w * n, 0);
+        em.assign((size_t)ell_w * n, 0.0);
+        es.assign((size_t)ell_w * n, 0.0);
+        for (int64_t i = 0; i < n; i++)
+            for (int k = 0; k < ell_w; k++) {
+                const int64_t e = rp[i] + k;
+                const size_t d = (size_t)k * n + i;
+                if (e < rp[i + 1]) {
+                    eci[d] = ci[e];
+                    em[d] = vm[e];
+                    es[d] = vs[e];
+                } else {
+                    eci[d] = (int32_t)i;
+                }
+            }
+    }
+    o->ell_w = ell_w;
     std::vector<int64_t> dv0(g.n_dom + 1, 0);
     for (int d = 0; d < g.n_dom; d++) {
         dv0[d + 1] = g.dom_vert_off[d] + g.dom_nv[d];
@@ -614,6 +661,7 @@ static int osrc_build(bem_ctx* ctx) {
     if ((rc = up(&o->rp, rp)) || (rc = up(&o->ci, ci)) || (rc = up(&o->vm, vm)) || (rc = up(&o->vs, vs)) ||
         (rc = up(&o->dm, dm)) || (rc = up(&o->ds, ds)) || (rc = up(&o->dom_v0, dv0)) || (rc = up(&o->stat, st0)))
         return rc;
+    if (ell_w && ((rc = up(&o->ell_ci, eci)) || (rc = up(&o->ell_m, em)) || (rc = up(&o->ell_s, es)))) return rc;
     // Pade coefficients and the damped wavenumber (exterior k0, Sec. 2.3)
     const int N = ctx->opts.n_pade;
     if (N < 1 || N > 16) return ctx->fail(BEM_ERR_INVALID_ARG, "n_pade must be in 1..16");
@@ -680,17 +728,24 @@ static int cocg_solve_grid(bem_ctx* ctx, int n_sys);
 
 static int cocg_solve(bem_ctx* ctx, int n_sys) {
     OsrcState* o = ctx->osrc;
+    // automatic: one CTA per (system, domain) once there are enough of them
+    // to fill two waves of the 152 SMs (many right-hand sides at once); for a
+    // few systems the grid-wide kernels, which spread each system over many
+    // SMs, finish sooner
     const int mode = ctx->opts.osrc_solver;
-    if (mode == 2 || (mode == 0 && o->max_dom_nv > CTA_SOLVE_MAX_NV)) return cocg_solve_grid(ctx, n_sys);
+    const bool big = o->max_dom_nv > CTA_SOLVE_MAX_NV || o->ell_w == 0;
+    if (mode == 2 || (mode == 0 && (big || (int64_t)n_sys * o->n_dom < 2 * 152))) return cocg_solve_grid(ctx, n_sys);
     CocgCtaArgs a{};
-    a.n = o->n; a.rp = o->rp; a.ci = o->ci; a.vm = o->vm; a.vs = o->vs; a.dm = o->dm; a.ds = o->ds;
+    a.n = o->n; a.eci = o->ell_ci; a.em = o->ell_m; a.es = o->ell_s; a.dm = o->dm; a.ds = o->ds;
     a.beta = o->beta; a.b = o->b; a.x = o->x; a.r = o->r; a.z = o->z; a.p = o->p; a.q = o->q;
     a.dom_v0 = o->dom_v0; a.n_dom = o->n_dom; a.tol2 = o->tol * o->tol; a.max_iter = o->max_iter; a.stat = o->stat;
     const unsigned ctas = (unsigned)(n_sys * o->n_dom);
     CK(cudaMemsetAsync(o->stat, 0, 2 * sizeof(unsigned long long), ctx->stream));
-    // wide CTAs while they fit in one wave, narrower ones (more per SM) beyond
-    if (ctas <= 152) cocg_cta_kernel<1024><<<ctas, 1024, 0, ctx->stream>>>(a);
-    else cocg_cta_kernel<256><<<ctas, 256, 0, ctx->stream>>>(a);
+    constexpr int NT = 256;
+    if (o->ell_w == 8) cocg_cta_kernel<NT, 8><<<ctas, NT, 0, ctx->stream>>>(a);
+    else if (o->ell_w == 12) cocg_cta_kernel<NT, 12><<<ctas, NT, 0, ctx->stream>>>(a);
+    else if (mode == 1 && o->ell_w == 0) return ctx->fail(BEM_ERR_INVALID_ARG, "mesh rows too wide for the one-CTA solver");
+    else cocg_cta_kernel<NT, 16><<<ctas, NT, 0, ctx->stream>>>(a);
     ctx->launches += 1;
     CK(cudaGetLastError());
     unsigned long long st[2];
