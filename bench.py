@@ -266,7 +266,7 @@ def rib_solve_metrics(local, n_rhs=8, tol=1e-8):
             "residual": {"fp64": r64["residual"], "mixed": rb["residual"]}}
 
 
-def serving_metrics(local, n_req=12, max_exc=8, rate=20.0, budget=150 << 30, tol=1e-6):
+def serving_metrics(local, n_req=12, max_exc=8, rate=20.0, budget=150 << 30, tol=1e-6, rank=0, world=1):
     """Serving trace: Poisson arrivals (mean `rate`/s) of planning solves over
     a pool of scenes (1k and 5k-triangle spheres, a 10k-triangle rib scene, a
     20k-triangle kidney scene, each at k h ~ 1), each request with 1..max_exc
@@ -282,6 +282,15 @@ def serving_metrics(local, n_req=12, max_exc=8, rate=20.0, budget=150 << 30, tol
     from paper_1910_01011_gb300.api import Context, Server
     from synth import serving
     reqs, weights = serving.trace(n_req, rate=rate, max_exc=max_exc)
+    # replicas: each rank serves its contiguous share of the trace
+    b, e = shard(len(reqs), rank, world)
+    if world > 1:
+        t_b = reqs[b][0] if b < e else 0.0
+        reqs = [(t - t_b, k, ne) for t, k, ne in reqs[b:e]]
+        weights = (lambda w0, off: (lambda i, n_elem: w0(i + off, n_elem)))(weights, b)
+        n_req = len(reqs)
+    if not reqs:
+        return {"requests": 0}
     keys = sorted({k for _, k, _ in reqs})
     built = {k: serving.POOL[k]() for k in keys}
     srv = Server(device=local, slots=2, max_batch_rhs=64, hbm_budget_bytes=budget, precision=1, operator_mode=1,
@@ -368,6 +377,32 @@ def assembled_metrics(ctx, s, n_int, local, n_rhs=256):
             "roofline": {"bound": "tensor", "achieved": tflop / (ms / 1e3), "peak": BF16_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": tflop / (ms / 1e3) / BF16_PEAK_TFLOPS,
                          "peak_basis": "MEASURED_PEAKS.json bf16_tflops (burst)"}}
+
+
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest x over all ranks (timings: the job is as slow as its
+    slowest replica); x itself on one process."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank in at most seconds_max (weak scaling)."""
+    return world * units_per_rank / seconds_max
+
+
+def shard(n: int, rank: int, world: int):
+    """[begin, end) of rank's share of n independent items (excitations or
+    requests), contiguous and balanced to within one item."""
+    q, r = divmod(n, world)
+    b = rank * q + min(rank, r)
+    return b, b + q + (1 if rank < r else 0)
 
 
 def prec_step(args, s, desc, local, world):
@@ -498,13 +533,9 @@ def main():
         dist.barrier()
     prof = ctx.profile_read(reset=True)
     ctx.profile(False)
-    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, ends)), world)
     ms_per_step = ms / args.steps
-    value = world * n_int * args.steps / (ms / 1e3) / 1e9
+    value = job_rate(n_int * args.steps, world, ms / 1e3) / 1e9
 
     # e2e: the public call with host buffers (pinned), copies inside the timing
     xh = torch.empty(N, dtype=torch.complex128).pin_memory()
@@ -519,12 +550,8 @@ def main():
     for _ in range(args.steps):
         ctx.apply(xa, precision=1, out=ya)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * n_int * args.steps / e2e_s / 1e9
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = job_rate(n_int * args.steps, world, e2e_s) / 1e9
 
     far_ms = prof["far_ms"] / max(1, prof["far_launches"])
     achieved = flops / (far_ms / 1e3) / 1e12
@@ -552,7 +579,7 @@ def main():
         extra("solve_sphere", sphere_solve_metrics, local)
         if not args.quick:
             extra("solve", rib_solve_metrics, local)
-            extra("serving", serving_metrics, local)
+            extra("serving", serving_metrics, local, 12, 8, 20.0, 150 << 30, 1e-6, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt, sample = oracle_sample(s, args.ref_rows)
         line["cpu_baseline"] = {"value": n / dt / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",

@@ -517,11 +517,18 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     if ((rc = S->kry.ensure(ctx, N, o.restart))) return rc;
     // the preconditioner only has to be a fixed linear map to the accuracy the
     // GMRES it sits in needs: two orders below that GMRES's tolerance
+    // inside a flexible GMRES the preconditioner may be any map, so a sparse
+    // solve that stops short (iteration cap, breakdown) keeps its iterate
     struct TolScope {
         bem_ctx* c;
         double saved;
-        ~TolScope() { set_osrc_tolerance(c, saved); }
-    } tol_scope{ctx, ctx->osrc_tol};
+        bool strict;
+        ~TolScope() {
+            set_osrc_tolerance(c, saved);
+            c->osrc_strict = strict;
+        }
+    } tol_scope{ctx, ctx->osrc_tol, ctx->osrc_strict};
+    ctx->osrc_strict = !(o.precondition && o.flexible);
     const double gm_tol = o.precision == BEM_PREC_FP64 ? o.tol : std::max(o.inner_tol, o.tol);
     set_osrc_tolerance(ctx, o.prec_tol > 0 ? o.prec_tol : o.flexible ? 1e-1 : std::max(1e-13, 0.01 * gm_tol));
     bem_solve_report R{};

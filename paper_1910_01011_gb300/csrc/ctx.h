@@ -102,6 +102,7 @@ struct bem_ctx {
     cublasHandle_t cublas = nullptr;
     gbem::OsrcState* osrc = nullptr;
     double osrc_tol = 1e-11;  // relative residual of the preconditioner's sparse solves
+    bool osrc_strict = true;  // a sparse solve that stops short of osrc_tol is an error (false: keep its iterate)
     gbem::SolveState* solve = nullptr;
     // incident field
     int field_kind = 0;  // 0 none, 1 plane wave, 2 transducer

@@ -211,13 +211,13 @@ void bem_server::worker() {
         int rc = bem_set_excitations(ctx, (const bem_z*)W.data(), n);
         if (!rc) rc = bem_solve(ctx, &opts.solve, &rep);
         const bool converged_fail = rc == BEM_ERR_NOT_CONVERGED;
+        std::string err = rc ? bem_last_error(ctx) : std::string();
         std::vector<double2> U;
         if (!rc || converged_fail) {
+            // the solutions (kept also when the tolerance was not met, if the solve finished)
             U.resize((size_t)n * s->n_dofs);
-            const int rc2 = copy_solution(ctx, 0, n, U.data());
-            if (rc2) rc = rc2;
+            if (copy_solution(ctx, 0, n, U.data())) U.clear();
         }
-        const std::string err = rc ? bem_last_error(ctx) : std::string();
         const auto t1 = Clock::now();
 
         lk.lock();
