@@ -60,6 +60,9 @@ def workload(name):
     elif name == "rib_small":
         s = scenes.rib_scene(h=6e-3)
         desc = "rib/fat/liver scene at 6 mm element size (~8k triangles; profiling case)"
+    elif name == "rib_resolved":
+        s = scenes.rib_scene_resolved()
+        desc = "rib/fat/liver scene, 0.1 MHz (k h ~ 1), ~41k triangles (the solve-time workload)"
     elif name == "kidney":
         s = scenes.kidney_scene()
         desc = "kidney + perinephric fat shell, 1 MHz, ~62k triangles"
@@ -468,7 +471,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rib", choices=["rib", "rib_small", "kidney", "sphere"])
+    ap.add_argument("--workload", default="rib", choices=["rib", "rib_small", "rib_resolved", "kidney", "sphere"])
     ap.add_argument("--ref-rows", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the solve and assembled-GEMM measurements")
@@ -477,6 +480,8 @@ def main():
                     help="apply: the operator application (the headline metric); prec: one OSRC preconditioner "
                          "application to --prec-rhs right-hand sides (for profiling the sparse solves)")
     ap.add_argument("--prec-rhs", type=int, default=8)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in far-field launch shape instead of the autotuned one")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -511,6 +516,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ctx.apply(x, precision=1, out=y)          # set-up (geometry, near field) outside timing
     torch.cuda.synchronize()
+    tuned = None if args.no_autotune else ctx.autotune(1)   # launch shape picked by timing (bem_autotune)
     for _ in range(max(3, args.warmup)):
         ctx.apply(x, precision=1, out=y)
     torch.cuda.synchronize()
@@ -561,7 +567,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "n_triangles": s.n_triangles, "n_dofs": N,
                        "interactions_per_step": n_int, "precision": "FP32 far field, FP64 near field/output",
-                       "l2": "flushed between timed steps (256 MB write)", "replicas": world},
+                       "l2": "flushed between timed steps (256 MB write)", "replicas": world,
+                       "far_field_chunk_tiles": (tuned or {}).get("chunk_tiles", "built-in")},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                          "kernel": "far32_kernel", "kernel_ms": far_ms,

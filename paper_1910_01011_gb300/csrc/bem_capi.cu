@@ -818,6 +818,13 @@ int bem_autotune(bem_ctx* ctx, int precision, int32_t* chunk_tiles, double* best
     cudaEventDestroy(e1);
     cudaStreamSynchronize(ctx->stream);
     ctx->dfree(x);
+    // the partial-potential buffer was sized for the largest candidate; the
+    // next application allocates what the chosen shape needs
+    if (ctx->partial) {
+        ctx->dfree(ctx->partial);
+        ctx->partial = nullptr;
+        ctx->partial_bytes = 0;
+    }
     if (rc) {
         ctx->opts.chunk_tiles = saved;
         return rc;
