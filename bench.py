@@ -416,7 +416,7 @@ def prec_step(args, s, desc, local, world):
 
     from paper_1910_01011_gb300.api import PREC, Context
     ctx = Context.from_scene(s, device=local, stream=torch.cuda.current_stream().cuda_stream, n_pade=8,
-                             osrc_tol=0.1)
+                             osrc_tol=0.1, osrc_solver=args.osrc_solver)
     N, R = ctx.n_dofs, args.prec_rhs
     g = torch.Generator(device="cuda").manual_seed(5)
     X = torch.complex(torch.randn(R, N, dtype=torch.float64, device="cuda", generator=g),
@@ -437,7 +437,8 @@ def prec_step(args, s, desc, local, world):
     print(json.dumps({"metric": "OSRC preconditioner applications (right-hand sides) per s", "value": R * args.steps / dt,
                       "unit": "RHS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
-                      "config": {"workload": desc, "n_rhs": R, "n_pade": 8, "osrc_tol": 0.1},
+                      "config": {"workload": desc, "n_rhs": R, "n_pade": 8, "osrc_tol": 0.1,
+                                 "osrc_solver": ["automatic", "one CTA per system", "grid-wide", "cluster per system"][args.osrc_solver]},
                       "gpu_launches": prof["kernel_launches"]}))
 
 
@@ -480,6 +481,9 @@ def main():
                     help="apply: the operator application (the headline metric); prec: one OSRC preconditioner "
                          "application to --prec-rhs right-hand sides (for profiling the sparse solves)")
     ap.add_argument("--prec-rhs", type=int, default=8)
+    ap.add_argument("--osrc-solver", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="sparse solver of the preconditioner step: 0 automatic, 1 one CTA per system, 2 grid-wide, "
+                         "3 one thread-block cluster per system")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in far-field launch shape instead of the autotuned one")
     args = ap.parse_args()

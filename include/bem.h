@@ -78,9 +78,10 @@ typedef struct {
     double eps_exponent;       /* exponent of k in eps = 0.4 k^e R_eps^(-2/3); default 1/3 */
     double osrc_tol;           /* relative residual of the preconditioner's sparse solves in bem_apply
                                   (default 1e-11); bem_solve uses 1/100 of its own GMRES tolerance */
-    int32_t osrc_solver;       /* sparse solver of the preconditioner: 0 automatic (one CTA per system and
-                                  domain up to 65536 vertices per domain, else grid-wide), 1 one CTA per
-                                  system and domain, 2 grid-wide kernels; same results within osrc_tol */
+    int32_t osrc_solver;       /* sparse solver of the preconditioner: 0 automatic (by the number of systems
+                                  and the domain sizes), 1 one CTA per system and domain, 2 grid-wide
+                                  kernels, 3 one 8-CTA thread-block cluster per system and domain; same
+                                  results within osrc_tol */
 } bem_opts;
 
 /* Fill opts with the defaults above. */

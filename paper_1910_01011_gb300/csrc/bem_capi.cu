@@ -109,6 +109,8 @@ static void release_device(bem_ctx* ctx) {
     ctx->asm_work_bytes = 0;
     ctx->partial = nullptr;
     ctx->partial_bytes = 0;
+    ctx->far_work = nullptr;
+    for (int& k : ctx->far_work_key) k = -1;
     ctx->pmchwt_near = NearSet();
     destroy_solver_state(ctx);
 }
@@ -333,6 +335,37 @@ int bem_ctx::ensure_partial(int n_chunks, bool fp64) {
     return BEM_OK;
 }
 
+// Launch order of the far-field work items: every (target tile, source chunk)
+// pair, heaviest first (cost = source triangles, twice for sources in the
+// target's own domain, which carry both wavenumbers), so that the light items
+// fill the last wave instead of a long one trailing alone.
+int bem_ctx::ensure_far_work(int tgt_b, int tgt_e, int src_b, int src_e, int chunk_tiles, int n_chunks, int slot1) {
+    const int key[6] = {tgt_b, tgt_e, src_b, src_e, chunk_tiles, slot1};
+    if (far_work && std::equal(key, key + 6, far_work_key)) return BEM_OK;
+    const Geometry& g = geo;
+    const int n_tgt = tgt_e - tgt_b;
+    std::vector<std::pair<int64_t, int>> cost((size_t)n_tgt * n_chunks);
+    for (int t = 0; t < n_tgt; t++) {
+        const int d = g.tile_dom[tgt_b + t];
+        const int own_b = g.dom_tile_begin[d], own_e = g.dom_tile_end[d];
+        for (int c = 0; c < n_chunks; c++) {
+            const int sb = src_b + c * chunk_tiles, se = std::min(sb + chunk_tiles, src_e);
+            int64_t w = 0;
+            for (int s = sb; s < se; s++) w += (int64_t)g.tile_ntri[s] * (1 + (slot1 && s >= own_b && s < own_e));
+            cost[(size_t)t * n_chunks + c] = {-w, t * n_chunks + c};
+        }
+    }
+    std::stable_sort(cost.begin(), cost.end());
+    std::vector<int2> work(cost.size());
+    for (size_t i = 0; i < cost.size(); i++) work[i] = make_int2(cost[i].second / n_chunks, cost[i].second % n_chunks);
+    if (far_work) dfree(far_work);
+    far_work = nullptr;
+    int rc = upload(this, &far_work, work);
+    if (rc) return rc;
+    std::copy(key, key + 6, far_work_key);
+    return BEM_OK;
+}
+
 void bem_ctx::chunking(int n_tgt, int n_src, int* n_chunks, int* chunk_tiles) const {
     int want = std::max(1, (152 * 2 * 8 + n_tgt - 1) / std::max(1, n_tgt));
     int nc = std::max(want, (n_src + CHUNK_MAX - 1) / CHUNK_MAX);
@@ -394,6 +427,8 @@ int bem_ctx::run_apply(const double2* x, double2* y, int precision, const ApplyM
         fa.k0 = make_double2(m.kre, m.kim);
         fa.src_begin = src_b; fa.src_end = src_e; fa.tgt_begin = tgt_b; fa.chunk_tiles = chunk_tiles;
         fa.slot1 = m.slot1; fa.n_pts = g.n_pts; fa.partial = (float*)partial; fa.err = dev.err;
+        if ((rc = ensure_far_work(tgt_b, tgt_e, src_b, src_e, chunk_tiles, n_chunks, m.slot1))) return rc;
+        fa.work = far_work;
         CK(launch_far32(fa, tgt_e - tgt_b, n_chunks, stream));
     }
     if (profiling) {
@@ -477,7 +512,7 @@ int bem_create(bem_ctx** out, int device, void* cuda_stream, const bem_opts* opt
     bem_default_opts(&c->opts);
     if (opts) c->opts = *opts;
     if (c->opts.n_gauss_singular < 2 || c->opts.n_gauss_singular > 20 || !(c->opts.osrc_tol > 0) ||
-        !(c->opts.osrc_tol < 1) || c->opts.osrc_solver < 0 || c->opts.osrc_solver > 2) {
+        !(c->opts.osrc_tol < 1) || c->opts.osrc_solver < 0 || c->opts.osrc_solver > 3) {
         delete c;
         return BEM_ERR_INVALID_ARG;
     }

@@ -79,6 +79,9 @@ struct bem_ctx {
     std::vector<gbem::BlockCache> block_cache;
     void* partial = nullptr;
     size_t partial_bytes = 0;
+    // far-field work list (heaviest (target tile, chunk) first) and the launch it was built for
+    int2* far_work = nullptr;
+    int far_work_key[6] = {-1, -1, -1, -1, -1, -1};
     std::vector<std::pair<void*, size_t>> allocs;
     size_t used_bytes = 0;
     size_t peak_bytes = 0;                     // largest used_bytes seen
@@ -121,6 +124,7 @@ struct bem_ctx {
     int build_near(gbem::NearSet& ns, int n_slot_k, double kre, double kim, const gbem::SlotCoef* coef_dev);
     int ensure_near();
     int ensure_partial(int n_chunks, bool fp64);
+    int ensure_far_work(int tgt_b, int tgt_e, int src_b, int src_e, int chunk_tiles, int n_chunks, int slot1);
     void chunking(int n_tgt, int n_src, int* n_chunks, int* chunk_tiles) const;
     int run_apply(const double2* x, double2* y, int precision, const gbem::ApplyMode& m);
     int apply_ahat(const double2* x, double2* y, int precision);

@@ -102,6 +102,8 @@ struct FarArgs32 {
     int64_t n_pts;
     float* partial;         // [grid.y][2][NCOMP][n_pts]
     int* err;               // device error flag (bounded waits)
+    const int2* work;       // null: grid (target tiles, chunks); else [n_work] (target tile offset, chunk)
+                            // in launch order, heaviest first, on a 1-D grid
 };
 
 struct FarArgs64 {

@@ -279,8 +279,14 @@ __global__ void __launch_bounds__(TP, 2) far32_kernel(FarArgs32 A) {
     FarSmem& sm = *reinterpret_cast<FarSmem*>(smem_raw);
 
     const int tid = threadIdx.x, lane = tid & 31;
-    const int tt = A.tgt_begin + blockIdx.x;
-    const int sb = A.src_begin + blockIdx.y * A.chunk_tiles;
+    int tx = blockIdx.x, cy = blockIdx.y;
+    if (A.work) {
+        const int2 w = A.work[blockIdx.x];
+        tx = w.x;
+        cy = w.y;
+    }
+    const int tt = A.tgt_begin + tx;
+    const int sb = A.src_begin + cy * A.chunk_tiles;
     const int se = min(sb + A.chunk_tiles, A.src_end);
     const int nsrc = max(0, se - sb);
 
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(TP, 2) far32_kernel(FarArgs32 A) {
         }
     }
 
-    float* out = A.partial + (int64_t)blockIdx.y * 2 * NCOMP * A.n_pts;
+    float* out = A.partial + (int64_t)cy * 2 * NCOMP * A.n_pts;
 #pragma unroll
     for (int c = 0; c < NCOMP; c++) {
         out[(int64_t)c * A.n_pts + p] = a0.v[c];
@@ -381,7 +387,8 @@ cudaError_t launch_far32(const FarArgs32& a, int n_tgt_tiles, int n_chunks, cuda
         cudaFuncSetAttribute(far32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr_e != cudaSuccess) return attr_e;
     if (n_tgt_tiles <= 0 || n_chunks <= 0) return cudaSuccess;
-    far32_kernel<<<dim3(n_tgt_tiles, n_chunks), TP, smem, s>>>(a);
+    if (a.work) far32_kernel<<<(unsigned)((int64_t)n_tgt_tiles * n_chunks), TP, smem, s>>>(a);
+    else far32_kernel<<<dim3(n_tgt_tiles, n_chunks), TP, smem, s>>>(a);
     return cudaGetLastError();
 }
 

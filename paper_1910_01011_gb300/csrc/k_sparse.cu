@@ -18,6 +18,7 @@
 // preconditioner is a fixed linear map to within that tolerance.
 // M and S share the P1 vertex-adjacency pattern; the matrix of a system is
 // formed on the fly as M_ij - beta S_ij.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -443,6 +444,160 @@ __global__ void __launch_bounds__(NT) cocg_cta_kernel(CocgCtaArgs a) {
     }
 }
 
+// ---- one thread-block cluster per (system, domain)
+//
+// For a few systems the one-CTA solver leaves most SMs idle and the
+// grid-wide kernels pay four launches per iteration.  Here the CL CTAs of a
+// cluster (on CL SMs) share one (system, domain): each owns a contiguous
+// slice of the domain's rows, the three reductions of an iteration go through
+// distributed shared memory (each CTA writes its partial sums, the cluster
+// barrier publishes them, every CTA adds the CL partials in rank order, so all
+// CTAs hold bit-identical scalars and take identical branches), and the
+// barrier after the direction update makes the new p visible to the other
+// CTAs' products (read through L2).  Every CTA of a cluster executes the same
+// sequence of cluster barriers: the loop bounds and exits depend only on
+// those shared scalars and on max_iter.
+constexpr int CL = 8;
+
+namespace cg = cooperative_groups;
+
+template <int NT, int NV>
+__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, double (&v)[NV], double (*buf)[NV], int& phase) {
+    __shared__ double sh[NT / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double t = v[k];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[warp][k] = t;
+    }
+    __syncthreads();
+    double* mine = buf[phase];
+    if (threadIdx.x < NV) {
+        double t = 0;
+        for (int w = 0; w < NT / 32; w++) t += sh[w][threadIdx.x];
+        mine[threadIdx.x] = t;
+    }
+    cl.sync();  // publishes every CTA's partial sums (release / acquire at cluster scope)
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double t = 0;
+        for (int r = 0; r < CL; r++) t += cl.map_shared_rank(mine, r)[k];
+        v[k] = t;
+    }
+    phase ^= 1;  // the next sum writes the other buffer, so no second barrier is needed
+}
+
+template <int NT, int W>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) cocg_cluster_kernel(CocgCtaArgs a) {
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ double buf2[2][2], buf3[2][3];
+    int ph2 = 0, ph3 = 0;
+    const int item = blockIdx.x / CL, rank = (int)cl.block_rank();
+    const int s = item / a.n_dom, j = item % a.n_dom;
+    const int64_t d0 = a.dom_v0[j], d1 = a.dom_v0[j + 1];
+    const int64_t per = (d1 - d0 + CL - 1) / CL;
+    const int64_t v0 = min(d1, d0 + rank * per), v1 = min(d1, v0 + per);
+    const int64_t n = a.n, off = (int64_t)s * n;
+    const double2 be = a.beta[s];
+    const double2* b = a.b + off;
+    double2 *x = a.x + off, *r = a.r + off, *z = a.z + off, *p = a.p + off, *q = a.q + off;
+    auto dinv = [&](int64_t i) {
+        return cdiv(make_double2(1.0, 0.0), make_double2(a.dm[i] - be.x * a.ds[i], -be.y * a.ds[i]));
+    };
+    double v3[3] = {0, 0, 0};
+    for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+        const double2 bi = b[i];
+        const double2 zi = cmul(dinv(i), bi);
+        x[i] = make_double2(0, 0);
+        r[i] = bi;
+        z[i] = zi;
+        p[i] = zi;
+        const double2 rz = cmul(bi, zi);
+        v3[0] += rz.x;
+        v3[1] += rz.y;
+        v3[2] += bi.x * bi.x + bi.y * bi.y;
+    }
+    cluster_sum<NT, 3>(cl, v3, buf3, ph3);  // also publishes the initial p
+    double2 rho = make_double2(v3[0], v3[1]);
+    const double lim = a.tol2 * v3[2];
+    int it = 0;
+    bool ok = !(v3[2] > 0);  // zero right-hand side: x = 0 is exact
+    while (!ok && it < a.max_iter) {
+        it++;
+        double v2[2] = {0, 0};
+        for (int64_t i0 = v0 + threadIdx.x; i0 < v1; i0 += CTA_U * NT) {
+            double qr[CTA_U], qi[CTA_U];
+#pragma unroll
+            for (int u = 0; u < CTA_U; u++) {
+                qr[u] = 0;
+                qi[u] = 0;
+                const int64_t i = i0 + (int64_t)u * NT;
+                if (i < v1) {
+#pragma unroll
+                    for (int k = 0; k < W; k++) {
+                        const int64_t e = (int64_t)k * n + i;
+                        const double2 pj = __ldcg(p + a.eci[e]);  // other CTAs' rows: read through L2
+                        const double mr = a.em[e] - be.x * a.es[e], mi = -be.y * a.es[e];
+                        qr[u] += mr * pj.x - mi * pj.y;
+                        qi[u] += mr * pj.y + mi * pj.x;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CTA_U; u++) {
+                const int64_t i = i0 + (int64_t)u * NT;
+                if (i < v1) {
+                    q[i] = make_double2(qr[u], qi[u]);
+                    const double2 pi = p[i];
+                    v2[0] += pi.x * qr[u] - pi.y * qi[u];
+                    v2[1] += pi.x * qi[u] + pi.y * qr[u];
+                }
+            }
+        }
+        cluster_sum<NT, 2>(cl, v2, buf2, ph2);
+        const double2 alpha = cdiv(rho, make_double2(v2[0], v2[1]));
+        if (!isfinite(alpha.x) || !isfinite(alpha.y)) break;  // breakdown, identical in every CTA: keep x
+        double w3[3] = {0, 0, 0};
+        for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+            const double2 pi = p[i], qi = q[i];
+            double2 xi = x[i], ri = r[i];
+            const double2 ap = cmul(alpha, pi), aq = cmul(alpha, qi);
+            xi.x += ap.x; xi.y += ap.y;
+            ri.x -= aq.x; ri.y -= aq.y;
+            x[i] = xi;
+            r[i] = ri;
+            const double2 zi = cmul(dinv(i), ri);
+            z[i] = zi;
+            const double2 rz = cmul(ri, zi);
+            w3[0] += rz.x;
+            w3[1] += rz.y;
+            w3[2] += ri.x * ri.x + ri.y * ri.y;
+        }
+        cluster_sum<NT, 3>(cl, w3, buf3, ph3);
+        if (w3[2] <= lim) {
+            ok = true;
+            break;
+        }
+        const double2 rn = make_double2(w3[0], w3[1]);
+        const double2 bt = cdiv(rn, rho);
+        if (!isfinite(bt.x) || !isfinite(bt.y)) break;
+        rho = rn;
+        for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+            const double2 zi = z[i], pi = p[i];
+            const double2 bp = cmul(bt, pi);
+            p[i] = make_double2(zi.x + bp.x, zi.y + bp.y);
+        }
+        cl.sync();  // the new p, read across CTAs by the next product
+    }
+    // no CTA may leave while another still reads its shared memory
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        atomicAdd(&a.stat[0], (unsigned long long)it);
+        if (!ok) atomicAdd(&a.stat[1], 1ull);
+    }
+}
+
 // y[s][i] = (M - beta_s S) x[s][i]  (plain SpMV, beta per system)
 __global__ void spmv_shift(int64_t n, const int64_t* rp, const int32_t* ci, const double* vm, const double* vs,
                            double2 beta, const double2* x, double2* y) {
@@ -753,7 +908,10 @@ static int cocg_solve(bem_ctx* ctx, int n_sys) {
     // SMs, finish sooner
     const int mode = ctx->opts.osrc_solver;
     const bool big = o->max_dom_nv > CTA_SOLVE_MAX_NV || o->ell_w == 0;
-    if (mode == 2 || (mode == 0 && (big || (int64_t)n_sys * o->n_dom < 2 * 152))) return cocg_solve_grid(ctx, n_sys);
+    if (mode == 2 || (mode == 0 && big)) return cocg_solve_grid(ctx, n_sys);
+    // automatic: a cluster of CL CTAs per (system, domain) while the clusters
+    // fit in about two waves; one CTA per (system, domain) beyond
+    const bool clustered = mode == 3 || (mode == 0 && (int64_t)n_sys * o->n_dom * CL <= 2 * 3 * 152);
     CocgCtaArgs a{};
     a.n = o->n; a.eci = o->ell_ci; a.em = o->ell_m; a.es = o->ell_s; a.dm = o->dm; a.ds = o->ds;
     a.beta = o->beta; a.b = o->b; a.x = o->x; a.r = o->r; a.z = o->z; a.p = o->p; a.q = o->q;
@@ -762,11 +920,24 @@ static int cocg_solve(bem_ctx* ctx, int n_sys) {
     a.max_iter = ctx->osrc_strict ? o->max_iter : std::min(o->max_iter, 2000);
     const unsigned ctas = (unsigned)(n_sys * o->n_dom);
     CK(cudaMemsetAsync(o->stat, 0, 2 * sizeof(unsigned long long), ctx->stream));
-    constexpr int NT = 256;
-    if (o->ell_w == 8) cocg_cta_kernel<NT, 8><<<ctas, NT, 0, ctx->stream>>>(a);
-    else if (o->ell_w == 12) cocg_cta_kernel<NT, 12><<<ctas, NT, 0, ctx->stream>>>(a);
-    else if (mode == 1 && o->ell_w == 0) return ctx->fail(BEM_ERR_INVALID_ARG, "mesh rows too wide for the one-CTA solver");
-    else cocg_cta_kernel<NT, 16><<<ctas, NT, 0, ctx->stream>>>(a);
+    if ((mode == 1 || mode == 3) && o->ell_w == 0)
+        return ctx->fail(BEM_ERR_INVALID_ARG, "mesh rows too wide for the CTA solvers");
+    // up to one wave: 1024 threads per CTA (one CTA per SM, shortest iterations);
+    // beyond: 256 threads, three CTAs per SM
+    if (clustered) {
+        const unsigned grid = ctas * CL;
+        if (o->ell_w == 8) cocg_cluster_kernel<256, 8><<<grid, 256, 0, ctx->stream>>>(a);
+        else if (o->ell_w == 12) cocg_cluster_kernel<256, 12><<<grid, 256, 0, ctx->stream>>>(a);
+        else cocg_cluster_kernel<256, 16><<<grid, 256, 0, ctx->stream>>>(a);
+    } else if (ctas <= 152) {
+        if (o->ell_w == 8) cocg_cta_kernel<1024, 8><<<ctas, 1024, 0, ctx->stream>>>(a);
+        else if (o->ell_w == 12) cocg_cta_kernel<1024, 12><<<ctas, 1024, 0, ctx->stream>>>(a);
+        else cocg_cta_kernel<1024, 16><<<ctas, 1024, 0, ctx->stream>>>(a);
+    } else {
+        if (o->ell_w == 8) cocg_cta_kernel<256, 8><<<ctas, 256, 0, ctx->stream>>>(a);
+        else if (o->ell_w == 12) cocg_cta_kernel<256, 12><<<ctas, 256, 0, ctx->stream>>>(a);
+        else cocg_cta_kernel<256, 16><<<ctas, 256, 0, ctx->stream>>>(a);
+    }
     ctx->launches += 1;
     CK(cudaGetLastError());
     unsigned long long st[2];

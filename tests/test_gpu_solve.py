@@ -31,9 +31,11 @@ def ctx_for(api, s, **kw):
 
 
 @pytest.mark.parametrize("name,npade,solver", [("sphere", 4, 0), ("two", 8, 0), ("shell", 4, 0), ("two", 8, 2),
-                                                ("shell", 4, 2)])
+                                                ("shell", 4, 2), ("two", 8, 1), ("shell", 4, 1), ("two", 8, 3),
+                                                ("shell", 4, 3)])
 def test_preconditioner_matches_oracle(api, name, npade, solver):
-    """Both sparse solvers (one CTA per system and domain; grid-wide kernels)."""
+    """Every sparse solver: automatic, one CTA per system and domain, grid-wide
+    kernels, one thread-block cluster per system and domain."""
     s = {"sphere": lambda: scenes.sphere_scene(2), "two": lambda: scenes.two_sphere_scene(1),
          "shell": lambda: scenes.shell_scene(1)}[name]()
     pre = osrc.build(s, R_eps=R_EPS, n_pade=npade)
@@ -145,12 +147,13 @@ def test_solve_reports_not_converged(api):
     assert not rep["converged"] and rep["iterations"] <= 5
 
 
-def test_batched_preconditioner_matches_single(api):
+@pytest.mark.parametrize("solver", [0, 1, 3])
+def test_batched_preconditioner_matches_single(api, solver):
     """The preconditioner applied to several right-hand sides in one batch
     equals the oracle's column by column."""
     s = scenes.two_sphere_scene(1)
     pre = osrc.build(s, R_eps=R_EPS, n_pade=8)
-    c = ctx_for(api, s, n_pade=8)
+    c = ctx_for(api, s, n_pade=8, osrc_solver=solver)
     X = scenes.random_complex(c.n_dofs * 5, 21).reshape(5, c.n_dofs)
     Y = c.apply(X, op=api.PREC)
     for r in range(5):
