@@ -370,6 +370,118 @@ int gemm_bf16x3(bem_ctx* ctx, const __nv_bfloat16* Aplanes, int64_t m, int64_t k
     return BEM_OK;
 }
 
+// ---- few right-hand sides: split-BF16 GEMV on the CUDA cores
+//
+// For R < 16 the tensor-core GEMM would pad R to a 128-column tile and spend
+// most of its time on padding; the operator then reads 12 bytes per entry
+// (six BF16 planes) from HBM and does a handful of FMAs per entry, so a
+// streaming kernel on the CUDA cores runs at memory speed instead.  One warp
+// per row; each lane reads 8 consecutive entries of every plane (16-byte
+// loads), rebuilds a = hi + mid + lo in FP32 and accumulates a x for the R
+// right-hand sides, promoting its FP32 sums to FP64 every 32 entries (the
+// same purpose as the GEMM's promotion every 256 of K); the warp then adds
+// its lanes in a fixed order.
+
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+template <int R>
+__global__ void __launch_bounds__(256) gemv_split_kernel(const __nv_bfloat16* __restrict__ P, int64_t m, int64_t k,
+                                                         int64_t mpad, int64_t kpad, const float2* __restrict__ X,
+                                                         int64_t ldx, float2* __restrict__ Y, int64_t ldy) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
+    if (i >= m) return;  // warp-uniform
+    const int64_t plane = mpad * kpad;
+    const uint4* rows[6];
+#pragma unroll
+    for (int t = 0; t < 6; t++) rows[t] = reinterpret_cast<const uint4*>(P + t * plane + i * kpad);
+    double ar[R], ai[R];
+    float fr[R], fi[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) ar[r] = ai[r] = fr[r] = fi[r] = 0;
+    int cnt = 0;
+    for (int64_t j0 = (int64_t)lane * 8; j0 < k; j0 += 256) {
+        uint4 v[6];
+#pragma unroll
+        for (int t = 0; t < 6; t++) v[t] = __ldcs(rows[t] + (j0 >> 3));  // streamed once: do not keep in L1
+        float are[8], aim[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const int w = e >> 1;
+            const uint32_t q0 = (&v[0].x)[w], q1 = (&v[1].x)[w], q2 = (&v[2].x)[w];
+            const uint32_t q3 = (&v[3].x)[w], q4 = (&v[4].x)[w], q5 = (&v[5].x)[w];
+            if (e & 1) {
+                are[e] = bf_hi(q0) + (bf_hi(q1) + bf_hi(q2));
+                aim[e] = bf_hi(q3) + (bf_hi(q4) + bf_hi(q5));
+            } else {
+                are[e] = bf_lo(q0) + (bf_lo(q1) + bf_lo(q2));
+                aim[e] = bf_lo(q3) + (bf_lo(q4) + bf_lo(q5));
+            }
+        }
+        const int ne = (k - j0) < 8 ? (int)(k - j0) : 8;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const float2* xr = X + r * ldx + j0;
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                if (e < ne) {
+                    const float2 xv = __ldg(xr + e);
+                    fr[r] = fmaf(are[e], xv.x, fmaf(-aim[e], xv.y, fr[r]));
+                    fi[r] = fmaf(are[e], xv.y, fmaf(aim[e], xv.x, fi[r]));
+                }
+            }
+        }
+        if (++cnt == 4) {
+            cnt = 0;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                ar[r] += fr[r];
+                ai[r] += fi[r];
+                fr[r] = fi[r] = 0;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        double a = ar[r] + fr[r], b = ai[r] + fi[r];
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) Y[r * ldy + i] = make_float2((float)a, (float)b);
+    }
+}
+
+// Y (n_rhs x m) = A X for few right-hand sides from the six planes of A
+// (kpad a multiple of 8; X is n_rhs x k complex64, rhs-major).
+int gemv_bf16x3(bem_ctx* ctx, const __nv_bfloat16* Aplanes, int64_t m, int64_t k, int64_t mpad, int64_t kpad,
+                const float2* X, int64_t n_rhs, float2* Y) {
+    const unsigned grid = (unsigned)((m + 7) / 8);
+    for (int64_t r0 = 0; r0 < n_rhs;) {
+        const int64_t left = n_rhs - r0;
+        const float2* x = X + r0 * k;
+        float2* y = Y + r0 * m;
+        if (left >= 8) {
+            gemv_split_kernel<8><<<grid, 256, 0, ctx->stream>>>(Aplanes, m, k, mpad, kpad, x, k, y, m);
+            r0 += 8;
+        } else if (left >= 4) {
+            gemv_split_kernel<4><<<grid, 256, 0, ctx->stream>>>(Aplanes, m, k, mpad, kpad, x, k, y, m);
+            r0 += 4;
+        } else if (left >= 2) {
+            gemv_split_kernel<2><<<grid, 256, 0, ctx->stream>>>(Aplanes, m, k, mpad, kpad, x, k, y, m);
+            r0 += 2;
+        } else {
+            gemv_split_kernel<1><<<grid, 256, 0, ctx->stream>>>(Aplanes, m, k, mpad, kpad, x, k, y, m);
+            r0 += 1;
+        }
+        ctx->launches += 1;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ctx->fail(BEM_ERR_CUDA, std::string("gemv launch: ") + cudaGetErrorString(e));
+    return BEM_OK;
+}
+
 int gemm_a_planes() { return A_TILES; }
 int gemm_b_planes() { return NSPLIT; }
 int gemm_k_align() { return GK; }

@@ -902,16 +902,15 @@ static int cocg_solve_grid(bem_ctx* ctx, int n_sys);
 
 static int cocg_solve(bem_ctx* ctx, int n_sys) {
     OsrcState* o = ctx->osrc;
-    // automatic: one CTA per (system, domain) once there are enough of them
-    // to fill two waves of the 152 SMs (many right-hand sides at once); for a
-    // few systems the grid-wide kernels, which spread each system over many
-    // SMs, finish sooner
+    // the grid-wide kernels serve domains too large or rows too wide for the CTA solvers
     const int mode = ctx->opts.osrc_solver;
     const bool big = o->max_dom_nv > CTA_SOLVE_MAX_NV || o->ell_w == 0;
     if (mode == 2 || (mode == 0 && big)) return cocg_solve_grid(ctx, n_sys);
-    // automatic: a cluster of CL CTAs per (system, domain) while the clusters
-    // fit in about two waves; one CTA per (system, domain) beyond
-    const bool clustered = mode == 3 || (mode == 0 && (int64_t)n_sys * o->n_dom * CL <= 2 * 3 * 152);
+    // automatic: a cluster of CL CTAs per (system, domain).  Measured on the
+    // 41k-triangle rib scene (n_pade 8, 10 % tolerance), per application to 1 /
+    // 8 / 16 right-hand sides: clusters 6.4 / 27.3 / 49.6 ms, one CTA per
+    // system 24.0 / 51.3 / 68.1 ms, grid-wide kernels 11.9 / 99.3 / 201 ms.
+    const bool clustered = mode == 3 || mode == 0;
     CocgCtaArgs a{};
     a.n = o->n; a.eci = o->ell_ci; a.em = o->ell_m; a.es = o->ell_s; a.dm = o->dm; a.ds = o->ds;
     a.beta = o->beta; a.b = o->b; a.x = o->x; a.r = o->r; a.z = o->z; a.p = o->p; a.q = o->q;
