@@ -219,7 +219,7 @@ def sphere_solve_metrics(local, reps=12):
             "iterations": {"fp64": r64["iterations"], "mixed": r32["iterations"], "refinements": r32["refinements"]}}
 
 
-def rib_solve_metrics(local, n_rhs=8, tol=1e-8):
+def rib_solve_metrics(local, n_rhs=16, tol=1e-8):
     """The rib / fat / liver scene at the frequency its mesh resolves (0.1 MHz,
     41k triangles, k h ~ 1), random-phase piston excitations of the 256-piston
     bowl: seconds per right-hand side of the mixed, batched form (n_rhs

@@ -376,11 +376,12 @@ int gemm_bf16x3(bem_ctx* ctx, const __nv_bfloat16* Aplanes, int64_t m, int64_t k
 // most of its time on padding; the operator then reads 12 bytes per entry
 // (six BF16 planes) from HBM and does a handful of FMAs per entry, so a
 // streaming kernel on the CUDA cores runs at memory speed instead.  One warp
-// per row; each lane reads 8 consecutive entries of every plane (16-byte
-// loads), rebuilds a = hi + mid + lo in FP32 and accumulates a x for the R
-// right-hand sides, promoting its FP32 sums to FP64 every 32 entries (the
-// same purpose as the GEMM's promotion every 256 of K); the warp then adds
-// its lanes in a fixed order.
+// per row.  A step covers 256 entries: lane l takes the pairs at
+// 2l + 64e (e = 0..3), so every load of a plane (two BF16 per lane) and of x
+// (two complex values per lane, 16 bytes) is contiguous across the warp.  Each
+// entry is rebuilt as hi + mid + lo in FP32; the FP32 sums are promoted to
+// FP64 after every step (the purpose of the GEMM's promotion every 256 of K)
+// and the warp adds its lanes in a fixed order.
 
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
@@ -393,58 +394,45 @@ __global__ void __launch_bounds__(256) gemv_split_kernel(const __nv_bfloat16* __
     const int64_t i = (int64_t)blockIdx.x * 8 + warp;
     if (i >= m) return;  // warp-uniform
     const int64_t plane = mpad * kpad;
-    const uint4* rows[6];
+    const uint32_t* rows[6];
 #pragma unroll
-    for (int t = 0; t < 6; t++) rows[t] = reinterpret_cast<const uint4*>(P + t * plane + i * kpad);
+    for (int t = 0; t < 6; t++) rows[t] = reinterpret_cast<const uint32_t*>(P + t * plane + i * kpad);
     double ar[R], ai[R];
-    float fr[R], fi[R];
 #pragma unroll
-    for (int r = 0; r < R; r++) ar[r] = ai[r] = fr[r] = fi[r] = 0;
-    int cnt = 0;
-    for (int64_t j0 = (int64_t)lane * 8; j0 < k; j0 += 256) {
-        uint4 v[6];
+    for (int r = 0; r < R; r++) ar[r] = ai[r] = 0;
+    for (int64_t j0 = 0; j0 < k; j0 += 256) {
+        float fr[R], fi[R];
 #pragma unroll
-        for (int t = 0; t < 6; t++) v[t] = __ldcs(rows[t] + (j0 >> 3));  // streamed once: do not keep in L1
-        float are[8], aim[8];
+        for (int r = 0; r < R; r++) fr[r] = fi[r] = 0;
 #pragma unroll
-        for (int e = 0; e < 8; e++) {
-            const int w = e >> 1;
-            const uint32_t q0 = (&v[0].x)[w], q1 = (&v[1].x)[w], q2 = (&v[2].x)[w];
-            const uint32_t q3 = (&v[3].x)[w], q4 = (&v[4].x)[w], q5 = (&v[5].x)[w];
-            if (e & 1) {
-                are[e] = bf_hi(q0) + (bf_hi(q1) + bf_hi(q2));
-                aim[e] = bf_hi(q3) + (bf_hi(q4) + bf_hi(q5));
-            } else {
-                are[e] = bf_lo(q0) + (bf_lo(q1) + bf_lo(q2));
-                aim[e] = bf_lo(q3) + (bf_lo(q4) + bf_lo(q5));
-            }
-        }
-        const int ne = (k - j0) < 8 ? (int)(k - j0) : 8;
+        for (int e = 0; e < 4; e++) {
+            const int64_t j = j0 + 64 * e + 2 * lane;  // this lane's pair (j, j + 1); kpad is a multiple of 32
+            if (j >= kpad) break;
+            uint32_t q[6];
 #pragma unroll
-        for (int r = 0; r < R; r++) {
-            const float2* xr = X + r * ldx + j0;
-#pragma unroll
-            for (int e = 0; e < 8; e++) {
-                if (e < ne) {
-                    const float2 xv = __ldg(xr + e);
-                    fr[r] = fmaf(are[e], xv.x, fmaf(-aim[e], xv.y, fr[r]));
-                    fi[r] = fmaf(are[e], xv.y, fmaf(aim[e], xv.x, fi[r]));
-                }
-            }
-        }
-        if (++cnt == 4) {
-            cnt = 0;
+            for (int t = 0; t < 6; t++) q[t] = __ldcs(rows[t] + (j >> 1));  // streamed once: do not keep in L1
+            const float re0 = bf_lo(q[0]) + (bf_lo(q[1]) + bf_lo(q[2])), re1 = bf_hi(q[0]) + (bf_hi(q[1]) + bf_hi(q[2]));
+            const float im0 = bf_lo(q[3]) + (bf_lo(q[4]) + bf_lo(q[5])), im1 = bf_hi(q[3]) + (bf_hi(q[4]) + bf_hi(q[5]));
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                ar[r] += fr[r];
-                ai[r] += fi[r];
-                fr[r] = fi[r] = 0;
+                const float2* xr = X + r * ldx;
+                const float2 x0 = j < k ? __ldg(xr + j) : make_float2(0.f, 0.f);
+                const float2 x1 = j + 1 < k ? __ldg(xr + j + 1) : make_float2(0.f, 0.f);
+                fr[r] = fmaf(re0, x0.x, fmaf(-im0, x0.y, fr[r]));
+                fi[r] = fmaf(re0, x0.y, fmaf(im0, x0.x, fi[r]));
+                fr[r] = fmaf(re1, x1.x, fmaf(-im1, x1.y, fr[r]));
+                fi[r] = fmaf(re1, x1.y, fmaf(im1, x1.x, fi[r]));
             }
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            ar[r] += fr[r];
+            ai[r] += fi[r];
         }
     }
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        double a = ar[r] + fr[r], b = ai[r] + fi[r];
+        double a = ar[r], b = ai[r];
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
             b += __shfl_xor_sync(0xffffffffu, b, o);
