@@ -322,8 +322,6 @@ __global__ void c64_to_c128(int64_t n, const float2* x, double2* y) {
 int gemm_bf16x3(bem_ctx* ctx, const __nv_bfloat16* Aplanes, int64_t m, int64_t k, int64_t mpad, int64_t kpad,
                 const float2* X, int64_t n_rhs, float2* Y, __nv_bfloat16* xplanes, int64_t nbpad);
 int split_a(bem_ctx* ctx, const float2* A, int64_t m, int64_t k, int64_t mpad, int64_t kpad, __nv_bfloat16* P);
-int gemv_bf16x3(bem_ctx* ctx, const __nv_bfloat16* Aplanes, int64_t m, int64_t k, int64_t mpad, int64_t kpad,
-                const float2* X, int64_t n_rhs, float2* Y);
 int gemm_a_planes();
 int gemm_b_planes();
 int gemm_k_align();
@@ -469,12 +467,7 @@ int bem_ctx::apply_assembled(const double2* x, double2* y, int64_t n_rhs) {
     __nv_bfloat16* xp = (__nv_bfloat16*)(ys + n_rhs * n);
     const int64_t tot = n_rhs * n;
     c128_to_c64<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(tot, x, xs);
-    if (n_rhs < 16) {
-        // few right-hand sides: memory-bound GEMV on the CUDA cores
-        if ((rc = gemv_bf16x3(this, asm_planes, n, n, asm_mpad, asm_kpad, xs, n_rhs, ys))) return rc;
-    } else if ((rc = gemm_bf16x3(this, asm_planes, n, n, asm_mpad, asm_kpad, xs, n_rhs, ys, xp, nbpad))) {
-        return rc;
-    }
+    if ((rc = gemm_bf16x3(this, asm_planes, n, n, asm_mpad, asm_kpad, xs, n_rhs, ys, xp, nbpad))) return rc;
     c64_to_c128<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(tot, ys, y);
     launches += 2;
     CK(cudaGetLastError());

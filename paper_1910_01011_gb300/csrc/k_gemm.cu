@@ -370,106 +370,6 @@ int gemm_bf16x3(bem_ctx* ctx, const __nv_bfloat16* Aplanes, int64_t m, int64_t k
     return BEM_OK;
 }
 
-// ---- few right-hand sides: split-BF16 GEMV on the CUDA cores
-//
-// For R < 16 the tensor-core GEMM would pad R to a 128-column tile and spend
-// most of its time on padding; the operator then reads 12 bytes per entry
-// (six BF16 planes) from HBM and does a handful of FMAs per entry, so a
-// streaming kernel on the CUDA cores runs at memory speed instead.  One warp
-// per row.  A step covers 256 entries: lane l takes the pairs at
-// 2l + 64e (e = 0..3), so every load of a plane (two BF16 per lane) and of x
-// (two complex values per lane, 16 bytes) is contiguous across the warp.  Each
-// entry is rebuilt as hi + mid + lo in FP32; the FP32 sums are promoted to
-// FP64 after every step (the purpose of the GEMM's promotion every 256 of K)
-// and the warp adds its lanes in a fixed order.
-
-__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
-__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
-
-template <int R>
-__global__ void __launch_bounds__(256) gemv_split_kernel(const __nv_bfloat16* __restrict__ P, int64_t m, int64_t k,
-                                                         int64_t mpad, int64_t kpad, const float2* __restrict__ X,
-                                                         int64_t ldx, float2* __restrict__ Y, int64_t ldy) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
-    if (i >= m) return;  // warp-uniform
-    const int64_t plane = mpad * kpad;
-    const uint32_t* rows[6];
-#pragma unroll
-    for (int t = 0; t < 6; t++) rows[t] = reinterpret_cast<const uint32_t*>(P + t * plane + i * kpad);
-    double ar[R], ai[R];
-#pragma unroll
-    for (int r = 0; r < R; r++) ar[r] = ai[r] = 0;
-    for (int64_t j0 = 0; j0 < k; j0 += 256) {
-        float fr[R], fi[R];
-#pragma unroll
-        for (int r = 0; r < R; r++) fr[r] = fi[r] = 0;
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const int64_t j = j0 + 64 * e + 2 * lane;  // this lane's pair (j, j + 1); kpad is a multiple of 32
-            if (j >= kpad) break;
-            uint32_t q[6];
-#pragma unroll
-            for (int t = 0; t < 6; t++) q[t] = __ldcs(rows[t] + (j >> 1));  // streamed once: do not keep in L1
-            const float re0 = bf_lo(q[0]) + (bf_lo(q[1]) + bf_lo(q[2])), re1 = bf_hi(q[0]) + (bf_hi(q[1]) + bf_hi(q[2]));
-            const float im0 = bf_lo(q[3]) + (bf_lo(q[4]) + bf_lo(q[5])), im1 = bf_hi(q[3]) + (bf_hi(q[4]) + bf_hi(q[5]));
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                const float2* xr = X + r * ldx;
-                const float2 x0 = j < k ? __ldg(xr + j) : make_float2(0.f, 0.f);
-                const float2 x1 = j + 1 < k ? __ldg(xr + j + 1) : make_float2(0.f, 0.f);
-                fr[r] = fmaf(re0, x0.x, fmaf(-im0, x0.y, fr[r]));
-                fi[r] = fmaf(re0, x0.y, fmaf(im0, x0.x, fi[r]));
-                fr[r] = fmaf(re1, x1.x, fmaf(-im1, x1.y, fr[r]));
-                fi[r] = fmaf(re1, x1.y, fmaf(im1, x1.x, fi[r]));
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-            ar[r] += fr[r];
-            ai[r] += fi[r];
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        double a = ar[r], b = ai[r];
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-        }
-        if (lane == 0) Y[r * ldy + i] = make_float2((float)a, (float)b);
-    }
-}
-
-// Y (n_rhs x m) = A X for few right-hand sides from the six planes of A
-// (kpad a multiple of 8; X is n_rhs x k complex64, rhs-major).
-int gemv_bf16x3(bem_ctx* ctx, const __nv_bfloat16* Aplanes, int64_t m, int64_t k, int64_t mpad, int64_t kpad,
-                const float2* X, int64_t n_rhs, float2* Y) {
-    const unsigned grid = (unsigned)((m + 7) / 8);
-    for (int64_t r0 = 0; r0 < n_rhs;) {
-        const int64_t left = n_rhs - r0;
-        const float2* x = X + r0 * k;
-        float2* y = Y + r0 * m;
-        if (left >= 8) {
-            gemv_split_kernel<8><<<grid, 256, 0, ctx->stream>>>(Aplanes, m, k, mpad, kpad, x, k, y, m);
-            r0 += 8;
-        } else if (left >= 4) {
-            gemv_split_kernel<4><<<grid, 256, 0, ctx->stream>>>(Aplanes, m, k, mpad, kpad, x, k, y, m);
-            r0 += 4;
-        } else if (left >= 2) {
-            gemv_split_kernel<2><<<grid, 256, 0, ctx->stream>>>(Aplanes, m, k, mpad, kpad, x, k, y, m);
-            r0 += 2;
-        } else {
-            gemv_split_kernel<1><<<grid, 256, 0, ctx->stream>>>(Aplanes, m, k, mpad, kpad, x, k, y, m);
-            r0 += 1;
-        }
-        ctx->launches += 1;
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return ctx->fail(BEM_ERR_CUDA, std::string("gemv launch: ") + cudaGetErrorString(e));
-    return BEM_OK;
-}
-
 int gemm_a_planes() { return A_TILES; }
 int gemm_b_planes() { return NSPLIT; }
 int gemm_k_align() { return GK; }

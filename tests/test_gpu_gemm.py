@@ -52,7 +52,7 @@ def test_assembled_operator_matches_oracle(name):
     A = pmchwt.assemble(s)
     c = api.Context.from_scene(s)
     rng = np.random.default_rng(4)
-    for n_rhs in (1, 3, 8, 15, 70):  # split-BF16 GEMV below 16 right-hand sides (8+4+2+1 groups), tcgen05 GEMM above
+    for n_rhs in (1, 3, 8, 15, 70):
         X = rng.standard_normal((n_rhs, A.shape[0])) + 1j * rng.standard_normal((n_rhs, A.shape[0]))
         Y = c.apply(X, precision=api.BF16X3)
         ref = X @ A.T
