@@ -438,7 +438,8 @@ def prec_step(args, s, desc, local, world):
                       "unit": "RHS/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
                       "config": {"workload": desc, "n_rhs": R, "n_pade": 8, "osrc_tol": 0.1,
-                                 "osrc_solver": ["automatic", "one CTA per system", "grid-wide", "cluster per system"][args.osrc_solver]},
+                                 "osrc_solver": ["automatic", "one CTA per system", "grid-wide", "cluster per system",
+                                                 "cluster per group of shifts"][args.osrc_solver]},
                       "gpu_launches": prof["kernel_launches"]}))
 
 
@@ -481,9 +482,9 @@ def main():
                     help="apply: the operator application (the headline metric); prec: one OSRC preconditioner "
                          "application to --prec-rhs right-hand sides (for profiling the sparse solves)")
     ap.add_argument("--prec-rhs", type=int, default=8)
-    ap.add_argument("--osrc-solver", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--osrc-solver", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="sparse solver of the preconditioner step: 0 automatic, 1 one CTA per system, 2 grid-wide, "
-                         "3 one thread-block cluster per system")
+                         "3 one thread-block cluster per system, 4 one cluster per group of Pade shifts")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in far-field launch shape instead of the autotuned one")
     args = ap.parse_args()

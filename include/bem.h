@@ -80,8 +80,9 @@ typedef struct {
                                   (default 1e-11); bem_solve uses 1/100 of its own GMRES tolerance */
     int32_t osrc_solver;       /* sparse solver of the preconditioner: 0 automatic (by the number of systems
                                   and the domain sizes), 1 one CTA per system and domain, 2 grid-wide
-                                  kernels, 3 one 8-CTA thread-block cluster per system and domain; same
-                                  results within osrc_tol */
+                                  kernels, 3 one 8-CTA thread-block cluster per system and domain, 4 as 3
+                                  with the Pade shifts of one right-hand side in one cluster; same results
+                                  within osrc_tol */
 } bem_opts;
 
 /* Fill opts with the defaults above. */

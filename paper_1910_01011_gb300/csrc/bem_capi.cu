@@ -512,7 +512,7 @@ int bem_create(bem_ctx** out, int device, void* cuda_stream, const bem_opts* opt
     bem_default_opts(&c->opts);
     if (opts) c->opts = *opts;
     if (c->opts.n_gauss_singular < 2 || c->opts.n_gauss_singular > 20 || !(c->opts.osrc_tol > 0) ||
-        !(c->opts.osrc_tol < 1) || c->opts.osrc_solver < 0 || c->opts.osrc_solver > 3) {
+        !(c->opts.osrc_tol < 1) || c->opts.osrc_solver < 0 || c->opts.osrc_solver > 4) {
         delete c;
         return BEM_ERR_INVALID_ARG;
     }

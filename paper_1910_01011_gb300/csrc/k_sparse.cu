@@ -458,6 +458,8 @@ __global__ void __launch_bounds__(NT) cocg_cta_kernel(CocgCtaArgs a) {
 // sequence of cluster barriers: the loop bounds and exits depend only on
 // those shared scalars and on max_iter.
 constexpr int CL = 8;
+// whether the automatic choice groups the Pade shifts of a right-hand side in one cluster
+constexpr bool SHIFT_GROUPS_AUTO = false;
 
 namespace cg = cooperative_groups;
 
@@ -595,6 +597,211 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) cocg_cluster_ke
     if (rank == 0 && threadIdx.x == 0) {
         atomicAdd(&a.stat[0], (unsigned long long)it);
         if (!ok) atomicAdd(&a.stat[1], 1ull);
+    }
+}
+
+// ---- the Pade shifts of one right-hand side together: one cluster per (group, domain)
+//
+// The 2 N_pade Pade systems of a right-hand side come in groups of N_pade
+// that share the right-hand side (one row of the bracket) and the matrices,
+// differing only in the shift B_l.  One cluster iterates all L shifts of a
+// group at once: every ELL entry of M and S is loaded once for the L
+// products, the reductions of the L systems travel together, and there are L
+// times fewer clusters to schedule.  Each shift is still its own COCG (its
+// own alpha, beta and stopping test); a shift that has converged or broken
+// down stops changing x, while the others go on.  The shared scalars live in
+// shared memory, identical in every CTA of the cluster.
+
+// As cluster_sum, but the NV totals go to shared memory (res[NV]) instead of registers.
+template <int NT, int NV>
+__device__ __forceinline__ void cluster_sum_to(cg::cluster_group& cl, const double (&v)[NV], double (*buf)[NV],
+                                               int& phase, double* res) {
+    __shared__ double sh[NT / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double t = v[k];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[warp][k] = t;
+    }
+    __syncthreads();
+    double* mine = buf[phase];
+    if (threadIdx.x < NV) {
+        double t = 0;
+        for (int w = 0; w < NT / 32; w++) t += sh[w][threadIdx.x];
+        mine[threadIdx.x] = t;
+    }
+    cl.sync();
+    if (threadIdx.x < NV) {
+        double t = 0;
+        for (int r = 0; r < CL; r++) t += cl.map_shared_rank(mine, r)[threadIdx.x];
+        res[threadIdx.x] = t;
+    }
+    __syncthreads();
+    phase ^= 1;
+}
+
+template <int NT, int W, int L>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) cocg_cluster_shift_kernel(CocgCtaArgs a) {
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ double bufA[2][2 * L], bufB[2][3 * L];
+    __shared__ double resA[2 * L], resB[3 * L];
+    __shared__ double2 rho[L], alpha[L], bt[L];
+    __shared__ double lim[L];
+    __shared__ double2 be[L];
+    __shared__ int act[L], brk[L];
+    int phA = 0, phB = 0;
+    const int item = blockIdx.x / CL, rank = (int)cl.block_rank();
+    const int grp = item / a.n_dom, j = item % a.n_dom;
+    const int64_t d0 = a.dom_v0[j], d1 = a.dom_v0[j + 1];
+    const int64_t per = (d1 - d0 + CL - 1) / CL;
+    const int64_t v0 = min(d1, d0 + rank * per), v1 = min(d1, v0 + per);
+    const int64_t n = a.n, off0 = (int64_t)grp * L * n;  // system grp*L + l at off0 + l*n
+    const double2* b = a.b + off0;                       // the shared right-hand side (first shift's copy)
+    if (threadIdx.x < L) {
+        be[threadIdx.x] = a.beta[grp * L + threadIdx.x];
+        brk[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    // x = 0, r = b, z = D_l^-1 b, p = z; per shift r^T z, and |b|^2
+    {
+        double v[3 * L];
+#pragma unroll
+        for (int t = 0; t < 3 * L; t++) v[t] = 0;
+        for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+            const double2 bi = b[i];
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                const int64_t o = off0 + l * n + i;
+                const double2 zi = cmul(cdiv(make_double2(1.0, 0.0),
+                                             make_double2(a.dm[i] - be[l].x * a.ds[i], -be[l].y * a.ds[i])), bi);
+                a.x[o] = make_double2(0, 0);
+                a.r[o] = bi;
+                a.z[o] = zi;
+                a.p[o] = zi;
+                const double2 rz = cmul(bi, zi);
+                v[3 * l] += rz.x;
+                v[3 * l + 1] += rz.y;
+                v[3 * l + 2] += bi.x * bi.x + bi.y * bi.y;
+            }
+        }
+        cluster_sum_to<NT, 3 * L>(cl, v, bufB, phB, resB);  // also publishes the initial p
+    }
+    if (threadIdx.x < L) {
+        const int l = threadIdx.x;
+        rho[l] = make_double2(resB[3 * l], resB[3 * l + 1]);
+        lim[l] = a.tol2 * resB[3 * l + 2];
+        act[l] = resB[3 * l + 2] > 0;
+    }
+    __syncthreads();
+    int it = 0, open = 0;
+    for (int l = 0; l < L; l++) open += act[l];
+    while (open > 0 && it < a.max_iter) {
+        it++;
+        // q_l = (M - beta_l S) p_l and p_l^T q_l, every shift from one pass over the ELL entries
+        double v2[2 * L];
+#pragma unroll
+        for (int t = 0; t < 2 * L; t++) v2[t] = 0;
+        for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+            double qr[L], qi[L];
+#pragma unroll
+            for (int l = 0; l < L; l++) qr[l] = qi[l] = 0;
+#pragma unroll
+            for (int k = 0; k < W; k++) {
+                const int64_t e = (int64_t)k * n + i;
+                const int64_t c = a.eci[e];
+                const double m = a.em[e], sv = a.es[e];
+#pragma unroll
+                for (int l = 0; l < L; l++) {
+                    const double2 pj = __ldcg(a.p + off0 + l * n + c);  // other CTAs' rows: read through L2
+                    const double mr = m - be[l].x * sv, mi = -be[l].y * sv;
+                    qr[l] += mr * pj.x - mi * pj.y;
+                    qi[l] += mr * pj.y + mi * pj.x;
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                const int64_t o = off0 + l * n + i;
+                a.q[o] = make_double2(qr[l], qi[l]);
+                const double2 pi = a.p[o];
+                v2[2 * l] += pi.x * qr[l] - pi.y * qi[l];
+                v2[2 * l + 1] += pi.x * qi[l] + pi.y * qr[l];
+            }
+        }
+        cluster_sum_to<NT, 2 * L>(cl, v2, bufA, phA, resA);
+        if (threadIdx.x < L) {
+            const int l = threadIdx.x;
+            alpha[l] = cdiv(rho[l], make_double2(resA[2 * l], resA[2 * l + 1]));
+            if (act[l] && (!isfinite(alpha[l].x) || !isfinite(alpha[l].y))) {
+                act[l] = 0;  // breakdown: keep x
+                brk[l] = 1;
+            }
+        }
+        __syncthreads();
+        double v3[3 * L];
+#pragma unroll
+        for (int t = 0; t < 3 * L; t++) v3[t] = 0;
+        for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                if (!act[l]) continue;
+                const int64_t o = off0 + l * n + i;
+                const double2 pi = a.p[o], qi = a.q[o];
+                double2 xi = a.x[o], ri = a.r[o];
+                const double2 ap = cmul(alpha[l], pi), aq = cmul(alpha[l], qi);
+                xi.x += ap.x; xi.y += ap.y;
+                ri.x -= aq.x; ri.y -= aq.y;
+                a.x[o] = xi;
+                a.r[o] = ri;
+                const double2 zi = cmul(cdiv(make_double2(1.0, 0.0),
+                                             make_double2(a.dm[i] - be[l].x * a.ds[i], -be[l].y * a.ds[i])), ri);
+                a.z[o] = zi;
+                const double2 rz = cmul(ri, zi);
+                v3[3 * l] += rz.x;
+                v3[3 * l + 1] += rz.y;
+                v3[3 * l + 2] += ri.x * ri.x + ri.y * ri.y;
+            }
+        }
+        cluster_sum_to<NT, 3 * L>(cl, v3, bufB, phB, resB);
+        if (threadIdx.x < L) {
+            const int l = threadIdx.x;
+            if (act[l]) {
+                if (resB[3 * l + 2] <= lim[l]) {
+                    act[l] = 0;  // converged
+                } else {
+                    const double2 rn = make_double2(resB[3 * l], resB[3 * l + 1]);
+                    bt[l] = cdiv(rn, rho[l]);
+                    if (!isfinite(bt[l].x) || !isfinite(bt[l].y)) {
+                        act[l] = 0;
+                        brk[l] = 1;
+                    }
+                    rho[l] = rn;
+                }
+            }
+        }
+        __syncthreads();
+        open = 0;
+        for (int l = 0; l < L; l++) open += act[l];
+        if (open == 0) break;
+        for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+#pragma unroll
+            for (int l = 0; l < L; l++) {
+                if (!act[l]) continue;
+                const int64_t o = off0 + l * n + i;
+                const double2 zi = a.z[o], pi = a.p[o];
+                const double2 bp = cmul(bt[l], pi);
+                a.p[o] = make_double2(zi.x + bp.x, zi.y + bp.y);
+            }
+        }
+        cl.sync();  // the new p, read across CTAs by the next product
+    }
+    cl.sync();  // no CTA may leave while another still reads its shared memory
+    if (rank == 0 && threadIdx.x == 0) {
+        atomicAdd(&a.stat[0], (unsigned long long)it);
+        // shifts still open hit the iteration cap; broken-down ones count too
+        int bad = 0;
+        for (int l = 0; l < L; l++) bad += act[l] || brk[l];
+        if (bad) atomicAdd(&a.stat[1], 1ull);
     }
 }
 
@@ -900,7 +1107,9 @@ constexpr int64_t CTA_SOLVE_MAX_NV = 1 << 16;
 
 static int cocg_solve_grid(bem_ctx* ctx, int n_sys);
 
-static int cocg_solve(bem_ctx* ctx, int n_sys) {
+// shifts > 1: the systems come in groups of `shifts` that share the right-hand
+// side and differ only in the shift (the Pade systems of one bracket row).
+static int cocg_solve(bem_ctx* ctx, int n_sys, int shifts = 1) {
     OsrcState* o = ctx->osrc;
     // the grid-wide kernels serve domains too large or rows too wide for the CTA solvers
     const int mode = ctx->opts.osrc_solver;
@@ -910,7 +1119,10 @@ static int cocg_solve(bem_ctx* ctx, int n_sys) {
     // 41k-triangle rib scene (n_pade 8, 10 % tolerance), per application to 1 /
     // 8 / 16 right-hand sides: clusters 6.4 / 27.3 / 49.6 ms, one CTA per
     // system 24.0 / 51.3 / 68.1 ms, grid-wide kernels 11.9 / 99.3 / 201 ms.
-    const bool clustered = mode == 3 || mode == 0;
+    const bool clustered = mode == 3 || mode == 0 || mode == 4;
+    // the shifts of a group in one cluster (mode 4, or automatic once measured to pay)
+    const bool grouped = clustered && (mode == 4 || (mode == 0 && SHIFT_GROUPS_AUTO)) && (shifts == 4 || shifts == 8) &&
+                         n_sys % shifts == 0;
     CocgCtaArgs a{};
     a.n = o->n; a.eci = o->ell_ci; a.em = o->ell_m; a.es = o->ell_s; a.dm = o->dm; a.ds = o->ds;
     a.beta = o->beta; a.b = o->b; a.x = o->x; a.r = o->r; a.z = o->z; a.p = o->p; a.q = o->q;
@@ -919,11 +1131,22 @@ static int cocg_solve(bem_ctx* ctx, int n_sys) {
     a.max_iter = ctx->osrc_strict ? o->max_iter : std::min(o->max_iter, 2000);
     const unsigned ctas = (unsigned)(n_sys * o->n_dom);
     CK(cudaMemsetAsync(o->stat, 0, 2 * sizeof(unsigned long long), ctx->stream));
-    if ((mode == 1 || mode == 3) && o->ell_w == 0)
+    if ((mode == 1 || mode == 3 || mode == 4) && o->ell_w == 0)
         return ctx->fail(BEM_ERR_INVALID_ARG, "mesh rows too wide for the CTA solvers");
     // up to one wave: 1024 threads per CTA (one CTA per SM, shortest iterations);
     // beyond: 256 threads, three CTAs per SM
-    if (clustered) {
+    if (grouped) {
+        const unsigned grid = (unsigned)(n_sys / shifts * o->n_dom * CL);
+        if (shifts == 8) {
+            if (o->ell_w == 8) cocg_cluster_shift_kernel<256, 8, 8><<<grid, 256, 0, ctx->stream>>>(a);
+            else if (o->ell_w == 12) cocg_cluster_shift_kernel<256, 12, 8><<<grid, 256, 0, ctx->stream>>>(a);
+            else cocg_cluster_shift_kernel<256, 16, 8><<<grid, 256, 0, ctx->stream>>>(a);
+        } else {
+            if (o->ell_w == 8) cocg_cluster_shift_kernel<256, 8, 4><<<grid, 256, 0, ctx->stream>>>(a);
+            else if (o->ell_w == 12) cocg_cluster_shift_kernel<256, 12, 4><<<grid, 256, 0, ctx->stream>>>(a);
+            else cocg_cluster_shift_kernel<256, 16, 4><<<grid, 256, 0, ctx->stream>>>(a);
+        }
+    } else if (clustered) {
         const unsigned grid = ctas * CL;
         if (o->ell_w == 8) cocg_cluster_kernel<256, 8><<<grid, 256, 0, ctx->stream>>>(a);
         else if (o->ell_w == 12) cocg_cluster_kernel<256, 12><<<grid, 256, 0, ctx->stream>>>(a);
@@ -1022,7 +1245,7 @@ int bem_ctx::apply_prec_batch(const double2* xin, double2* yout, int64_t R) {
     std::vector<double2> be(ns);
     for (int s = 0; s < ns; s++) be[s] = o->B[s % L];
     CK(cudaMemcpyAsync(o->beta, be.data(), ns * sizeof(double2), cudaMemcpyHostToDevice, stream));
-    if ((rc = cocg_solve(this, ns))) return rc;
+    if ((rc = cocg_solve(this, ns, L))) return rc;
     // brackets; row 1 scaled by i k (the DtN weak form)
     BracketArgs ba{};
     ba.n = n; ba.rp = o->rp; ba.ci = o->ci; ba.vs = o->vs; ba.g = o->g; ba.w = o->x; ba.L = L; ba.C0 = o->C0;

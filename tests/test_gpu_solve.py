@@ -32,10 +32,11 @@ def ctx_for(api, s, **kw):
 
 @pytest.mark.parametrize("name,npade,solver", [("sphere", 4, 0), ("two", 8, 0), ("shell", 4, 0), ("two", 8, 2),
                                                 ("shell", 4, 2), ("two", 8, 1), ("shell", 4, 1), ("two", 8, 3),
-                                                ("shell", 4, 3)])
+                                                ("shell", 4, 3), ("two", 8, 4), ("shell", 4, 4)])
 def test_preconditioner_matches_oracle(api, name, npade, solver):
     """Every sparse solver: automatic, one CTA per system and domain, grid-wide
-    kernels, one thread-block cluster per system and domain."""
+    kernels, one thread-block cluster per system and domain, one cluster per
+    group of Pade shifts."""
     s = {"sphere": lambda: scenes.sphere_scene(2), "two": lambda: scenes.two_sphere_scene(1),
          "shell": lambda: scenes.shell_scene(1)}[name]()
     pre = osrc.build(s, R_eps=R_EPS, n_pade=npade)
@@ -147,7 +148,7 @@ def test_solve_reports_not_converged(api):
     assert not rep["converged"] and rep["iterations"] <= 5
 
 
-@pytest.mark.parametrize("solver", [0, 1, 3])
+@pytest.mark.parametrize("solver", [0, 1, 3, 4])
 def test_batched_preconditioner_matches_single(api, solver):
     """The preconditioner applied to several right-hand sides in one batch
     equals the oracle's column by column."""
