@@ -57,7 +57,8 @@ def field_grid(radius: float, n: int = 200):
     return pts, np.where(np.linalg.norm(pts, axis=1) < radius, 0, -1).astype(np.int32)
 
 
-def run(material: str, el_per_lambda: float, device: int = 0, tol: float = 1e-5, precision: int = 1):
+def run(material: str, el_per_lambda: float, device: int = 0, tol: float = 1e-5, precision: int = 1,
+        operator_mode: int = 1):
     """One point of the experiment: solve, then the total field on the grid.
     Returns the measurements plus `points`, `field` and the sphere's
     parameters (`radius`, `k0`, `kj`, `rho0`, `rho`) for the comparison."""
@@ -68,7 +69,7 @@ def run(material: str, el_per_lambda: float, device: int = 0, tol: float = 1e-5,
     c = Context.from_scene(s, device=device, n_pade=4, r_eps=R / 10.0)
     c.set_plane_wave((0, 0, 1))
     t0 = time.perf_counter()
-    rep = c.solve(precision=precision, tol=tol, restart=100, max_iter=3000)
+    rep = c.solve(precision=precision, tol=tol, restart=100, max_iter=3000, operator_mode=operator_mode)
     wall = time.perf_counter() - t0
     pts, dom = field_grid(R)
     got = c.field(pts, dom)
