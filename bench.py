@@ -95,11 +95,19 @@ def algorithmic_flops(s):
 
 
 class ClockSampler:
-    def __init__(self, index):
+    """nvidia-smi clock and throttle-reason samples (every 200 ms) during the
+    timed region; kept in `path` when one is given, else in a temporary file
+    that is removed after the summary."""
+
+    def __init__(self, index, path=None):
+        import tempfile
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_{os.getpid()}.csv"
+        self.keep = path is not None
+        if path is None:
+            fd, path = tempfile.mkstemp(prefix="bench_clocks_", suffix=".csv")
+            os.close(fd)
+        self.path = path
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -140,6 +148,8 @@ class ClockSampler:
             for n, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
+        if not self.keep:
+            os.remove(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
@@ -482,6 +492,7 @@ def main():
                     help="apply: the operator application (the headline metric); prec: one OSRC preconditioner "
                          "application to --prec-rhs right-hand sides (for profiling the sparse solves)")
     ap.add_argument("--prec-rhs", type=int, default=8)
+    ap.add_argument("--clocks-log", default=None, help="keep the raw nvidia-smi clock samples in this CSV file")
     ap.add_argument("--osrc-solver", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="sparse solver of the preconditioner step: 0 automatic, 1 one CTA per system, 2 grid-wide, "
                          "3 one thread-block cluster per system, 4 one cluster per group of Pade shifts")
@@ -533,7 +544,7 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_log) as clk:
         for k in range(args.steps):
             flush.zero_()                      # L2 flush between timed steps (outside the events)
             starts[k].record(stream)

@@ -199,7 +199,7 @@ typedef struct {
                               A_hat itself.  0: the paper's left composition P A_hat u = P b with plain
                               GMRES (sparse solves to 1/100 of the GMRES tolerance).  Same solution. */
     double prec_tol;       /* relative residual of the preconditioner's sparse solves inside the solve;
-                              0 = automatic (1e-1 flexible, 1/100 of the GMRES tolerance otherwise) */
+                              0 = automatic (0.3 flexible, 1/100 of the GMRES tolerance otherwise) */
 } bem_solve_opts;
 
 typedef struct {

@@ -530,7 +530,7 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     } tol_scope{ctx, ctx->osrc_tol, ctx->osrc_strict};
     ctx->osrc_strict = !(o.precondition && o.flexible);
     const double gm_tol = o.precision == BEM_PREC_FP64 ? o.tol : std::max(o.inner_tol, o.tol);
-    set_osrc_tolerance(ctx, o.prec_tol > 0 ? o.prec_tol : o.flexible ? 1e-1 : std::max(1e-13, 0.01 * gm_tol));
+    set_osrc_tolerance(ctx, o.prec_tol > 0 ? o.prec_tol : o.flexible ? 0.3 : std::max(1e-13, 0.01 * gm_tol));
     bem_solve_report R{};
     bool converged = true;
     // the operator of one precision level: matrix-free or assembled, then the preconditioner
