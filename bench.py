@@ -310,7 +310,8 @@ def serving_metrics(local, n_req=12, max_exc=8, rate=20.0, budget=150 << 30, tol
     built = {k: serving.POOL[k]() for k in keys}
     srv = Server(device=local, slots=2, max_batch_rhs=64, hbm_budget_bytes=budget, precision=1, operator_mode=1,
                  tol=tol, max_iter=20000, max_refine=20)
-    ids = {k: srv.add_scene(built[k], omega_rho0=built[k].meta["omega_rho0"], n_pade=8) for k in keys}
+    ids = {k: srv.add_scene(built[k], omega_rho0=built[k].meta["omega_rho0"], n_pade=8, r_eps=built[k].meta["r_eps"])
+           for k in keys}
     for k in keys:  # warm the cache (geometry, near field, assembled operators, preconditioner)
         h = srv.submit(ids[k], np.ones((1, srv.scenes[ids[k]][1])))
         srv.wait(h)
@@ -339,7 +340,7 @@ def serving_metrics(local, n_req=12, max_exc=8, rate=20.0, budget=150 << 30, tol
     t64 = {}
     for k in keys:
         sc = built[k]
-        c = Context.from_scene(sc, device=local, n_pade=8)
+        c = Context.from_scene(sc, device=local, n_pade=8, r_eps=sc.meta["r_eps"])
         tr = sc.transducer
         c.set_transducer(tr["centres"], tr["normals"], tr["radii"], sc.meta["omega_rho0"])
         c.set_excitations(weights(0, tr["radii"].size)[:1])

@@ -8,6 +8,8 @@ span the stated ranges (spheres of 1k-5k triangles, rib scenes of 10k-40k,
 kidney scenes of 20k-60k), each with a random number of random-phase piston
 excitations.  The pool uses the small end of each range, with frequencies
 chosen so that every mesh resolves about 6 elements per wavelength (k h ~ 1).
+Each scene carries the OSRC damping radius of the paper's corresponding
+experiment, scaled to the same k R_eps (meta["r_eps"]).
 """
 from __future__ import annotations
 
@@ -26,6 +28,7 @@ def sphere_with_bowl(level: int, k0: float, k1: float, n_elem: int, seed: int) -
     s.domains.append(scenes.Domain("sphere", v, t, complex(k1), 1.1))
     s.transducer = scenes.bowl_transducer(seed=seed, n_elem=n_elem, R=4.0, aperture=4.0, piston_radius=0.2, gap=0.05)
     s.meta["omega_rho0"] = 2.6
+    s.meta["r_eps"] = 0.1  # the paper's sphere value, 5e-4 m for a 5 mm radius, relative to the radius
     return s
 
 
@@ -34,6 +37,7 @@ def rib_10k() -> scenes.Scene:
     s = scenes.rib_scene(h=h, freq=1500.0 / (2 * math.pi * h))
     s.name = "rib_fat_liver_10k"
     s.meta["omega_rho0"] = 2 * math.pi * s.freq * s.rho0
+    s.meta["r_eps"] = 1e-4 * 1e6 / s.freq  # the paper's rib value (1e-4 m at 1 MHz) at the same k R_eps
     return s
 
 
@@ -42,6 +46,7 @@ def kidney_20k() -> scenes.Scene:
     s = scenes.kidney_scene(h=h, freq=1500.0 / (2 * math.pi * h))
     s.name = "kidney_fat_20k"
     s.meta["omega_rho0"] = 2 * math.pi * s.freq * s.rho0
+    s.meta["r_eps"] = 1e-3 * 1e6 / s.freq  # the paper's kidney value (1e-3 m at 1 MHz) at the same k R_eps
     return s
 
 

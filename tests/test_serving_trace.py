@@ -27,4 +27,4 @@ def test_pool_sizes():
         s = make()
         lo, hi = ranges[key.split("_")[0]]
         assert lo <= s.n_triangles <= hi, (key, s.n_triangles)
-        assert s.transducer is not None and s.meta["omega_rho0"] > 0
+        assert s.transducer is not None and s.meta["omega_rho0"] > 0 and s.meta["r_eps"] > 0
