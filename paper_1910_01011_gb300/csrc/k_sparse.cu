@@ -1123,7 +1123,10 @@ static int cocg_solve(bem_ctx* ctx, int n_sys, int shifts = 1) {
     // 41k-triangle rib scene (n_pade 8, 10 % tolerance), per application to 1 /
     // 8 / 16 right-hand sides: clusters 6.4 / 27.3 / 49.6 ms, one CTA per
     // system 24.0 / 51.3 / 68.1 ms, grid-wide kernels 11.9 / 99.3 / 201 ms.
-    const bool clustered = mode == 3 || mode == 0 || mode == 4;
+    // Small domains (under 4,096 vertices, fewer than two rows per thread of a
+    // cluster's CTAs) go to one CTA per system instead: on an 8k-triangle rib
+    // scene one CTA took 0.95 ms where the clusters took 1.56 ms.
+    const bool clustered = mode == 3 || mode == 4 || (mode == 0 && o->max_dom_nv >= 4096);
     // the shifts of a group in one cluster (mode 4, or automatic once measured to pay)
     const bool grouped = clustered && (mode == 4 || (mode == 0 && SHIFT_GROUPS_AUTO)) && (shifts == 4 || shifts == 8) &&
                          n_sys % shifts == 0;
