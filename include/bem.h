@@ -221,6 +221,22 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* report
  * the interior Neumann trace is rho_j/rho_0 times it, eq. Form1_BCs). */
 int bem_get_traces(bem_ctx* ctx, int32_t domain_id, int64_t rhs, bem_z* dirichlet, bem_z* neumann, int on_device);
 
+/* Excitation superposition (no counterpart as an entry point in the paper;
+ * it follows from the linearity of eq. Galerkin_disc_rhs1 in the piston
+ * weights).  bem_solve_basis solves every piston of the transducer alone
+ * (n_elem unit excitations, with the given solve options; use batch_rhs) and
+ * keeps the n_elem solutions on the device; the caller's excitations set by
+ * bem_set_excitations are left as they were.  bem_superpose then returns the
+ * solutions for any weights w [n_exc][n_elem] (complex, host or device) as
+ * u = w x basis, [n_exc][bem_num_dofs], in the system order of
+ * bem_get_solution, with one complex GEMM.  The residual of a superposed
+ * solution is bounded by the basis tolerance times sum |w_m| ||b_m|| /
+ * ||sum w_m b_m||, which for random phases grows like sqrt(n_elem): solve the
+ * basis that much tighter.  STATE if no basis exists for the current
+ * transducer; changing the mesh, materials or transducer drops it. */
+int bem_solve_basis(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* report);
+int bem_superpose(bem_ctx* ctx, const bem_z* w, int64_t n_exc, bem_z* u, int on_device);
+
 /* The whole solution vector of excitation `rhs` of the last solve, in system
  * order: per domain j, [gamma_N^+ p_tot (n_v,j); gamma_D p_tot (n_v,j)]
  * (the unknown [psi; phi] of Sec. 2.3 after the column permutation).

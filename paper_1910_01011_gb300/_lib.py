@@ -91,6 +91,8 @@ _SIGS = {
     "bem_solve": [_P, ctypes.POINTER(bem_solve_opts), ctypes.POINTER(bem_solve_report)],
     "bem_get_traces": [_P, ctypes.c_int32, ctypes.c_int64, _P, _P, ctypes.c_int],
     "bem_get_solution": [_P, ctypes.c_int64, _P, ctypes.c_int],
+    "bem_solve_basis": [_P, ctypes.POINTER(bem_solve_opts), ctypes.POINTER(bem_solve_report)],
+    "bem_superpose": [_P, _P, ctypes.c_int64, _P, ctypes.c_int],
     "bem_server_default_opts": [ctypes.POINTER(bem_server_opts)],
     "bem_server_create": [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(bem_server_opts)],
     "bem_server_destroy": [_P],

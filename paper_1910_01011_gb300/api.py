@@ -161,6 +161,30 @@ class Context:
         return {"iterations": r.iterations, "refinements": r.refinements, "residual": r.residual,
                 "seconds": r.seconds, "converged": rc == 0}
 
+    def solve_basis(self, **kw):
+        """Solve every piston of the transducer alone and keep the solutions
+        for superposition (bem_solve_basis); solve options as for solve()."""
+        o = _lib.bem_solve_opts()
+        check(self.lib.bem_default_solve_opts(ctypes.byref(o)))
+        names = {f[0] for f in o._fields_}
+        for k, v in kw.items():
+            if k not in names:
+                raise TypeError(f"unknown solve option {k!r}")
+            setattr(o, k, v)
+        r = _lib.bem_solve_report()
+        rc = self.lib.bem_solve_basis(self.h, ctypes.byref(o), ctypes.byref(r))
+        if rc not in (0, _lib.ERR_NOT_CONVERGED):
+            self._check(rc)
+        return {"iterations": r.iterations, "refinements": r.refinements, "residual": r.residual,
+                "seconds": r.seconds, "converged": rc == 0}
+
+    def superpose(self, weights):
+        """Solutions (n_exc, n_dofs) for piston weights (n_exc, n_elem) from the basis."""
+        W = np.ascontiguousarray(np.atleast_2d(weights), dtype=np.complex128)
+        U = np.empty((W.shape[0], self.n_dofs), dtype=np.complex128)
+        self._check(self.lib.bem_superpose(self.h, W.ctypes.data, W.shape[0], U.ctypes.data, 0))
+        return U
+
     def solution(self, rhs=0):
         """System-order solution of excitation rhs: per domain [gamma_N; gamma_D]."""
         u = np.empty(self.n_dofs, dtype=np.complex128)

@@ -117,6 +117,8 @@ static void release_device(bem_ctx* ctx) {
 
 namespace gbem {
 
+void invalidate_basis(bem_ctx* ctx);
+
 // Eviction by the request loop: every device allocation of the context goes;
 // the host description (meshes, materials, transducer) stays and the device
 // state is rebuilt on next use.
@@ -536,6 +538,7 @@ int bem_set_exterior(bem_ctx* ctx, bem_z k0, double rho0) {
     ctx->k0re = k0.re;
     ctx->k0im = k0.im;
     ctx->rho0 = rho0;
+    invalidate_basis(ctx);
     if (ctx->ready) {
         ctx->near_ready = false;
         ctx->osrc_ready = false;
@@ -582,6 +585,7 @@ int bem_set_material(bem_ctx* ctx, int32_t id, bem_z k, double rho) {
     ctx->doms[id].kre = k.re;
     ctx->doms[id].kim = k.im;
     ctx->doms[id].rho = rho;
+    invalidate_basis(ctx);
     if (ctx->ready) {
         ctx->near_ready = false;
         ctx->osrc_ready = false;

@@ -162,6 +162,11 @@ struct SolveState {
     double2* wdev = nullptr;
     int64_t n_rhs_alloc = 0;
     int64_t n_rhs_solved = 0;
+    // superposition basis: the solution of every piston alone, [n_elem][N]
+    double2* basis = nullptr;
+    int64_t n_basis = 0;
+    double2* wstage = nullptr;  // staging for superposition weights and outputs
+    size_t wstage_bytes = 0;
 };
 
 }  // namespace gbem
@@ -283,6 +288,13 @@ int copy_solution(bem_ctx* ctx, int64_t rhs0, int64_t n, double2* host) {
 }
 }  // namespace gbem
 
+namespace gbem {
+// A superposition basis belongs to one transducer, mesh and set of materials.
+void invalidate_basis(bem_ctx* ctx) {
+    if (ctx->solve) ctx->solve->n_basis = 0;
+}
+}  // namespace gbem
+
 // Drop the solver objects after their device memory was released with the
 // rest of the context's allocations.
 void destroy_solver_state(bem_ctx* ctx) {
@@ -323,6 +335,7 @@ int bem_set_plane_wave(bem_ctx* ctx, const double dir[3], bem_z amp) {
 int bem_set_transducer(bem_ctx* ctx, const double* c, const double* n, const double* r, int64_t n_elem,
                        double omega_rho0) {
     if (!ctx || !c || !n || !r || n_elem < 1) return BEM_ERR_INVALID_ARG;
+    invalidate_basis(ctx);
     ctx->tr_c.assign(c, c + 3 * n_elem);
     ctx->tr_n.assign(n, n + 3 * n_elem);
     ctx->tr_r.assign(r, r + n_elem);
@@ -633,6 +646,97 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = R;
     if (!converged) return ctx->fail(BEM_ERR_NOT_CONVERGED, "GMRES did not reach the requested residual");
+    return BEM_OK;
+}
+
+// ---- excitation superposition (treatment planning: many phase patterns of one array)
+//
+// The traces are linear in the piston weights (the right-hand side is a sum of
+// the pistons' Rayleigh fields, eq. Galerkin_disc_rhs1, and A_hat does not
+// depend on the excitation), so once the solution u_m of every piston m alone
+// is known, any weight vector w gives u = sum_m w_m u_m: one complex GEMM
+// instead of a solve.
+
+int bem_solve_basis(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    if (ctx->field_kind != 2) return ctx->fail(BEM_ERR_STATE, "set a transducer first");
+    const int64_t ne = (int64_t)ctx->tr_r.size();
+    // unit excitations, restoring the caller's weights afterwards
+    const std::vector<double> saved_w = ctx->tr_w;
+    const int64_t saved_n = ctx->n_rhs;
+    std::vector<double> eye((size_t)2 * ne * ne, 0.0);
+    for (int64_t m = 0; m < ne; m++) eye[(size_t)2 * (m * ne + m)] = 1.0;
+    int rc = bem_set_excitations(ctx, (const bem_z*)eye.data(), ne);
+    if (!rc) rc = bem_solve(ctx, opts, rep);
+    const int solve_rc = rc;
+    if (!rc || rc == BEM_ERR_NOT_CONVERGED) {
+        SolveState* S = ctx->solve;
+        const int64_t N = ctx->geo.n_dof;
+        if (S->n_basis != ne) {
+            ctx->dfree(S->basis);
+            S->basis = (double2*)ctx->dalloc((size_t)ne * N * sizeof(double2), &rc);
+            if (rc) {
+                S->basis = nullptr;
+                S->n_basis = 0;
+            }
+        }
+        if (!rc) {
+            CK(cudaMemcpyAsync(S->basis, S->u, (size_t)ne * N * sizeof(double2), cudaMemcpyDeviceToDevice,
+                               ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            S->n_basis = ne;
+            rc = solve_rc;
+        }
+    }
+    ctx->tr_w = saved_w;
+    ctx->n_rhs = saved_n;
+    ctx->rhs_ready = false;
+    return rc;
+}
+
+int bem_superpose(bem_ctx* ctx, const bem_z* w, int64_t n_exc, bem_z* u, int on_device) {
+    if (!ctx || !w || !u || n_exc < 1) return BEM_ERR_INVALID_ARG;
+    SolveState* S = ctx->solve;
+    const int64_t ne = (int64_t)ctx->tr_r.size();
+    if (!S || !S->basis || S->n_basis != ne || ctx->field_kind != 2)
+        return ctx->fail(BEM_ERR_STATE, "no superposition basis: call bem_solve_basis after bem_set_transducer");
+    CK(cudaSetDevice(ctx->device));
+    const int64_t N = ctx->geo.n_dof;
+    const double2* wd = (const double2*)w;
+    double2* ud = (double2*)u;
+    int rc;
+    if (!on_device) {
+        const size_t need = ((size_t)n_exc * ne + (size_t)n_exc * N) * sizeof(double2);
+        if (need > S->wstage_bytes) {
+            ctx->dfree(S->wstage);
+            S->wstage = (double2*)ctx->dalloc(need, &rc);
+            if (rc) {
+                S->wstage = nullptr;
+                S->wstage_bytes = 0;
+                return rc;
+            }
+            S->wstage_bytes = need;
+        }
+        CK(cudaMemcpyAsync(S->wstage, w, (size_t)n_exc * ne * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+        wd = S->wstage;
+        ud = S->wstage + n_exc * ne;
+    }
+    if (!ctx->cublas) {
+        if (cublasCreate(&ctx->cublas) != CUBLAS_STATUS_SUCCESS) return ctx->fail(BEM_ERR_CUDA, "cublasCreate failed");
+    }
+    if (cublasSetStream(ctx->cublas, ctx->stream) != CUBLAS_STATUS_SUCCESS)
+        return ctx->fail(BEM_ERR_CUDA, "cublasSetStream failed");
+    // column-major view: U^T (N x n_exc) = B^T (N x ne) W^T (ne x n_exc)
+    const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+    if (cublasZgemm(ctx->cublas, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, (int)n_exc, (int)ne, &one,
+                    (const cuDoubleComplex*)S->basis, (int)N, (const cuDoubleComplex*)wd, (int)ne, &zero,
+                    (cuDoubleComplex*)ud, (int)N) != CUBLAS_STATUS_SUCCESS)
+        return ctx->fail(BEM_ERR_CUDA, "cuBLAS superposition product failed");
+    ctx->launches += 1;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(u, ud, (size_t)n_exc * N * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     return BEM_OK;
 }
 
