@@ -1124,9 +1124,13 @@ static int cocg_solve(bem_ctx* ctx, int n_sys, int shifts = 1) {
     // 8 / 16 right-hand sides: clusters 6.4 / 27.3 / 49.6 ms, one CTA per
     // system 24.0 / 51.3 / 68.1 ms, grid-wide kernels 11.9 / 99.3 / 201 ms.
     // Small domains (under 4,096 vertices, fewer than two rows per thread of a
-    // cluster's CTAs) go to one CTA per system instead: on an 8k-triangle rib
-    // scene one CTA took 0.95 ms where the clusters took 1.56 ms.
-    const bool clustered = mode == 3 || mode == 4 || (mode == 0 && o->max_dom_nv >= 4096);
+    // cluster's CTAs) go to one CTA per system once there are enough systems to
+    // occupy the SMs: on an 8k-triangle rib scene (384 systems x domains) one
+    // CTA took 0.95 ms where the clusters took 1.56 ms; with fewer systems than
+    // SMs the clusters spread the work wider (the 1,280-triangle sphere's solve
+    // took 0.13 s with clusters, 0.16 s with one CTA per system).
+    const bool clustered = mode == 3 || mode == 4 ||
+                           (mode == 0 && (o->max_dom_nv >= 4096 || (int64_t)n_sys * o->n_dom < 152));
     // the shifts of a group in one cluster (mode 4, or automatic once measured to pay)
     const bool grouped = clustered && (mode == 4 || (mode == 0 && SHIFT_GROUPS_AUTO)) && (shifts == 4 || shifts == 8) &&
                          n_sys % shifts == 0;
