@@ -603,7 +603,9 @@ def main():
                 line[name] = {"error": f"{type(e).__name__}: {e}"}
         extra("assembled", assembled_metrics, ctx, s, n_int, local)
         extra("solve_sphere", sphere_solve_metrics, local)
-        if not args.quick:
+        if not args.quick and world == 1:
+            # the minutes-long solve and serving measurements run on one GPU; replicas
+            # of them on more GPUs would only repeat the same numbers
             extra("solve", rib_solve_metrics, local)
             extra("serving", serving_metrics, local, 12, 8, 20.0, 150 << 30, 1e-6, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
