@@ -262,6 +262,22 @@ int bem_memory_info(const bem_ctx* ctx, int64_t* used_bytes, int64_t* peak_bytes
  * operators. */
 int bem_estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_opts* opts, int64_t* bytes);
 
+/* Several meshes at once (no counterpart in the paper; for many small
+ * problems, e.g. requests on small meshes, whose single applications leave
+ * most SMs idle): y[i] = A_hat_i x[i] for the n contexts ctxs[i], FP32 far
+ * field, every mesh's far-field work in ONE launch (work items of all meshes,
+ * heaviest first), gathers, projections and reductions around it.  x[i], y[i]
+ * are device vectors of ctxs[i]'s size.  The whole launch sequence is captured
+ * into a CUDA graph owned by ctxs[0] and replayed on ctxs[0]'s stream while
+ * the same contexts, vectors and device buffers are used; any change (another
+ * vector, a context that reallocated, a different member list) captures anew.
+ * The other contexts' pending work on their own streams is waited for first.
+ * The source chunks are sized for the whole group (small meshes get long
+ * chunks), so results match separate bem_apply calls at BEM_PREC_FP32 to FP32
+ * rounding (a different summation order), not bit for bit.
+ * Errors: INVALID_ARG (null pointers, repeated context, mixed devices). */
+int bem_apply_group(bem_ctx* const* ctxs, int32_t n, const bem_z* const* x, bem_z* const* y);
+
 /* Autotuner for the far-field launch shape (no counterpart in the paper):
  * times the whole operator application for source-chunk lengths 8..256
  * tiles and the built-in heuristic, keeps the fastest in the context

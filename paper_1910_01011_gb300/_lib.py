@@ -81,6 +81,7 @@ _SIGS = {
     "bem_interaction_count": [_P, ctypes.POINTER(ctypes.c_int64)],
     "bem_apply": [_P, ctypes.c_int, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int],
     "bem_apply_noalloc": [_P, _P, _P],
+    "bem_apply_group": [_P, ctypes.c_int32, _P, _P],
     "bem_zgemm_bf16x3": [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, _P, _P],
     "bem_apply_block": [_P, ctypes.c_int32, ctypes.c_int32, bem_z, _P, _P, ctypes.c_int, ctypes.c_int],
     "bem_set_plane_wave": [_P, ctypes.POINTER(ctypes.c_double), bem_z],

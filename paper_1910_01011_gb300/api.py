@@ -253,6 +253,24 @@ def quadrature_table(which, n=6):
     return np.array(buf[:m.value * cols]).reshape(m.value, cols)
 
 
+def apply_group(contexts, xs, ys=None):
+    """y_i = A_hat_i x_i for several contexts in one far-field launch, replayed
+    from a captured CUDA graph while the same contexts and tensors are used
+    (bem_apply_group).  xs, ys: complex128 CUDA tensors, one per context."""
+    import torch
+    n = len(contexts)
+    assert n == len(xs) and n > 0
+    ys = [torch.empty_like(x) for x in xs] if ys is None else ys
+    for c, x, y in zip(contexts, xs, ys):
+        assert x.is_cuda and x.dtype == torch.complex128 and x.is_contiguous() and x.numel() == c.n_dofs
+        assert y.is_cuda and y.dtype == torch.complex128 and y.is_contiguous() and y.numel() == c.n_dofs
+    hs = (ctypes.c_void_p * n)(*[c.h.value for c in contexts])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+    contexts[0]._check(contexts[0].lib.bem_apply_group(hs, n, xp, yp))
+    return ys
+
+
 class Server:
     """Request loop for planning solves (bem_server_*): scenes stay resident on
     the device, requests of piston excitations are queued, batched per scene

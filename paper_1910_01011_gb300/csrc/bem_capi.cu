@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -35,6 +36,13 @@ int bem_ctx::fail(int code, const std::string& msg) {
     return code;
 }
 
+// Allocation generations are unique across contexts, so a cached group
+// launch never mistakes a new context at a reused address for the old one.
+static uint64_t next_gen() {
+    static std::atomic<uint64_t> g{0};
+    return ++g;
+}
+
 void* bem_ctx::dalloc(size_t bytes, int* rc) {
     if (bytes == 0) bytes = 16;
     if (opts.hbm_budget_bytes > 0 && (int64_t)(used_bytes + bytes) > opts.hbm_budget_bytes) {
@@ -60,6 +68,7 @@ void* bem_ctx::dalloc(size_t bytes, int* rc) {
     }
     allocs.push_back({p, bytes});
     used_bytes += bytes;
+    gen = next_gen();
     peak_bytes = std::max(peak_bytes, used_bytes);
     *rc = BEM_OK;
     return p;
@@ -69,6 +78,7 @@ void bem_ctx::dfree(void* p) {
     if (!p) return;
     for (size_t i = 0; i < allocs.size(); i++)
         if (allocs[i].first == p) {
+            gen = next_gen();
             used_bytes -= allocs[i].second;
             if (pool) pool->fetch_sub((int64_t)allocs[i].second);
             cudaFree(p);
@@ -88,9 +98,19 @@ static int upload(bem_ctx* ctx, T** dst, const std::vector<T>& v) {
 
 void destroy_solver_state(bem_ctx* ctx);  // bem_solve.cu / k_sparse.cu (objects only; memory is freed here)
 
+static void release_group(bem_ctx* ctx) {
+    if (!ctx->group) return;
+    if (ctx->group->exec) cudaGraphExecDestroy(ctx->group->exec);
+    if (ctx->group->cap) cudaStreamDestroy(ctx->group->cap);
+    delete ctx->group;  // its device buffers belong to ctx->allocs
+    ctx->group = nullptr;
+}
+
 static void release_device(bem_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    release_group(ctx);
+    ctx->gen = next_gen();
     for (auto& a : ctx->allocs) cudaFree(a.first);
     ctx->allocs.clear();
     if (ctx->pool) ctx->pool->fetch_sub((int64_t)ctx->used_bytes);
@@ -379,21 +399,25 @@ void bem_ctx::chunking(int n_tgt, int n_src, int* n_chunks, int* chunk_tiles) co
     *n_chunks = (n_src + ct - 1) / ct;
 }
 
-// The pipeline.  x, y: device, system order.  Modes: PMCHWT (all targets,
-// all sources at k0 plus own-domain sources at k_j), or BLOCK (targets of
-// domain j, sources of domain i, one wavenumber).
-int bem_ctx::run_apply(const double2* x, double2* y, int precision, const ApplyMode& m) {
-    bem_ctx* const ctx = this;
+// Buffers and launch arguments of one operator application (no launches).
+// fill_tiles > 0: the target tiles of all meshes launched together (a group),
+// which the chunking spreads over the SMs instead of this mesh's alone.
+int bem_ctx::plan_apply(const double2* x, double2* y, int precision, const ApplyMode& m, ApplyPlan& P,
+                        int fill_tiles) {
     const Geometry& g = geo;
     const bool fp64 = precision == BEM_PREC_FP64;
+    P = ApplyPlan();
+    P.fp64 = fp64;
     const int tgt_b = g.dom_tile_begin[m.tgt_dom_lo], tgt_e = g.dom_tile_end[m.tgt_dom_hi - 1];
     const int src_b = g.dom_tile_begin[m.src_dom_lo], src_e = g.dom_tile_end[m.src_dom_hi - 1];
     int n_chunks, chunk_tiles;
-    chunking(tgt_e - tgt_b, src_e - src_b, &n_chunks, &chunk_tiles);
+    chunking(fill_tiles > 0 ? fill_tiles : tgt_e - tgt_b, src_e - src_b, &n_chunks, &chunk_tiles);
     int rc = ensure_partial(n_chunks, fp64);
     if (rc) return rc;
+    P.n_tgt = tgt_e - tgt_b;
+    P.n_chunks = n_chunks;
     // 1. trial densities on the source slots
-    GatherArgs ga{};
+    GatherArgs& ga = P.ga;
     ga.slot_v = dev.slot_v;
     ga.v_dof1 = dev.v_dof1;
     ga.v_dof2 = dev.v_dof2;
@@ -406,24 +430,16 @@ int bem_ctx::run_apply(const double2* x, double2* y, int precision, const ApplyM
         for (int k = 0; k < 3; k++) ga.lam[q][k] = quad.lam[q][k];
     if (fp64) { ga.pd64 = dev.pd64; ga.tcurl64 = dev.tcurl64; }
     else { ga.pd32 = dev.pd32; ga.tcurl32 = dev.tcurl32; }
-    CK(launch_gather(ga, stream));
     // 2. far field
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    if (profiling) {
-        CK(cudaEventCreate(&ev0));
-        CK(cudaEventCreate(&ev1));
-        CK(cudaEventRecord(ev0, stream));
-    }
     if (fp64) {
-        FarArgs64 fa{};
+        FarArgs64& fa = P.fa64;
         fa.pg = dev.pg64; fa.tg = dev.tg64; fa.tc = dev.tc; fa.tdom = dev.tdom; fa.tntri = dev.tntri;
         fa.pd = dev.pd64; fa.tcurl = dev.tcurl64; fa.dom_tiles = dev.dom_tiles; fa.kdom = dev.kdom;
         fa.k0 = make_double2(m.kre, m.kim);
         fa.src_begin = src_b; fa.src_end = src_e; fa.tgt_begin = tgt_b; fa.chunk_tiles = chunk_tiles;
         fa.slot1 = m.slot1; fa.n_pts = g.n_pts; fa.partial = (double*)partial;
-        CK(launch_far64(fa, tgt_e - tgt_b, n_chunks, stream));
     } else {
-        FarArgs32 fa{};
+        FarArgs32& fa = P.fa32;
         fa.pg = dev.pg32; fa.tg = dev.tg32; fa.tc = dev.tc; fa.tdom = dev.tdom; fa.tntri = dev.tntri;
         fa.pd = dev.pd32; fa.tcurl = dev.tcurl32; fa.dom_tiles = dev.dom_tiles; fa.kdom = dev.kdom;
         fa.k0 = make_double2(m.kre, m.kim);
@@ -431,14 +447,9 @@ int bem_ctx::run_apply(const double2* x, double2* y, int precision, const ApplyM
         fa.slot1 = m.slot1; fa.n_pts = g.n_pts; fa.partial = (float*)partial; fa.err = dev.err;
         if ((rc = ensure_far_work(tgt_b, tgt_e, src_b, src_e, chunk_tiles, n_chunks, m.slot1))) return rc;
         fa.work = far_work;
-        CK(launch_far32(fa, tgt_e - tgt_b, n_chunks, stream));
-    }
-    if (profiling) {
-        CK(cudaEventRecord(ev1, stream));
-        far_events.push_back({ev0, ev1});
     }
     // 3. projection (+ touching-pair correction)
-    ProjectArgs pa{};
+    ProjectArgs& pa = P.pa;
     pa.slot_v = dev.slot_v; pa.pt_w = dev.pt_w; pa.slot_curl = dev.slot_curl; pa.tntri = dev.tntri; pa.tdom = dev.tdom;
     pa.coef = m.coef; pa.tgt_begin = tgt_b; pa.tgt_end = tgt_e; pa.n_chunks = n_chunks; pa.n_pts = g.n_pts;
     if (fp64) pa.partial64 = (const double*)partial; else pa.partial32 = (const float*)partial;
@@ -449,14 +460,38 @@ int bem_ctx::run_apply(const double2* x, double2* y, int precision, const ApplyM
     pa.v_dof1 = dev.v_dof1; pa.v_dof2 = dev.v_dof2; pa.x = x; pa.tri_out = dev.tri_out;
     for (int q = 0; q < QP; q++)
         for (int k = 0; k < 3; k++) pa.lam[q][k] = quad.lam[q][k];
-    CK(launch_project(pa, stream));
     // 4. vertex reduction
-    ReduceArgs ra{};
+    ReduceArgs& ra = P.ra;
     ra.vc_ptr = dev.vc_ptr; ra.vc_idx = dev.vc_idx; ra.v_dof1 = dev.v_dof1; ra.v_dof2 = dev.v_dof2;
     ra.tri_out = dev.tri_out; ra.y = y;
     ra.v_begin = g.dom_vert_off[m.tgt_dom_lo];
     ra.v_end = g.dom_vert_off[m.tgt_dom_hi - 1] + g.dom_nv[m.tgt_dom_hi - 1];
-    CK(launch_reduce(ra, stream));
+    return BEM_OK;
+}
+
+// The pipeline.  x, y: device, system order.  Modes: PMCHWT (all targets,
+// all sources at k0 plus own-domain sources at k_j), or BLOCK (targets of
+// domain j, sources of domain i, one wavenumber).
+int bem_ctx::run_apply(const double2* x, double2* y, int precision, const ApplyMode& m) {
+    bem_ctx* const ctx = this;
+    ApplyPlan P;
+    int rc = plan_apply(x, y, precision, m, P);
+    if (rc) return rc;
+    CK(launch_gather(P.ga, stream));
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (profiling) {
+        CK(cudaEventCreate(&ev0));
+        CK(cudaEventCreate(&ev1));
+        CK(cudaEventRecord(ev0, stream));
+    }
+    if (P.fp64) CK(launch_far64(P.fa64, P.n_tgt, P.n_chunks, stream));
+    else CK(launch_far32(P.fa32, P.n_tgt, P.n_chunks, stream));
+    if (profiling) {
+        CK(cudaEventRecord(ev1, stream));
+        far_events.push_back({ev0, ev1});
+    }
+    CK(launch_project(P.pa, stream));
+    CK(launch_reduce(P.ra, stream));
     launches += 4;
     return BEM_OK;
 }
@@ -526,6 +561,7 @@ int bem_create(bem_ctx** out, int device, void* cuda_stream, const bem_opts* opt
 int bem_destroy(bem_ctx* ctx) {
     if (!ctx) return BEM_OK;
     release_device(ctx);
+    release_group(ctx);
     if (ctx->cublas) cublasDestroy(ctx->cublas);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -759,6 +795,113 @@ int bem_apply_block(bem_ctx* ctx, int32_t j, int32_t i, bem_z k, const bem_z* x,
     CK(cudaMemcpyAsync(y + nvj, ctx->dev.ys + off_j + nvj, nvj * sizeof(double2), kout, ctx->stream)); // row2
     CK(cudaStreamSynchronize(ctx->stream));
     return ctx->check_device_error();
+}
+
+// Several meshes in one far-field launch (see include/bem.h).
+int bem_apply_group(bem_ctx* const* ctxs, int32_t n, const bem_z* const* x, bem_z* const* y) {
+    if (!ctxs || !x || !y || n < 1 || n > 4096) return BEM_ERR_INVALID_ARG;
+    bem_ctx* const ctx = ctxs[0];
+    if (!ctx) return BEM_ERR_INVALID_ARG;
+    for (int i = 0; i < n; i++) {
+        if (!ctxs[i] || !x[i] || !y[i]) return ctx->fail(BEM_ERR_INVALID_ARG, "null context or vector in the group");
+        if (ctxs[i]->device != ctx->device) return ctx->fail(BEM_ERR_INVALID_ARG, "group contexts on different devices");
+        for (int j = 0; j < i; j++)
+            if (ctxs[j] == ctxs[i]) return ctx->fail(BEM_ERR_INVALID_ARG, "a context appears twice in the group");
+    }
+    CK(cudaSetDevice(ctx->device));
+    // buffers and arguments of every member (no launches yet); the source
+    // chunks are sized for the whole group's target tiles, so small meshes
+    // get long chunks and the group, not each mesh, fills the SMs
+    std::vector<ApplyPlan> P(n);
+    int rc;
+    int fill = 0;
+    for (int i = 0; i < n; i++) {
+        if ((rc = ctxs[i]->finalize())) return ctx->fail(rc, ctxs[i]->err);
+        fill += ctxs[i]->geo.n_tiles;
+    }
+    for (int i = 0; i < n; i++) {
+        bem_ctx* c = ctxs[i];
+        if ((rc = c->finalize()) || (rc = c->ensure_near())) return rc == BEM_OK ? rc : ctx->fail(rc, c->err);
+        ApplyMode m;
+        m.tgt_dom_lo = 0; m.tgt_dom_hi = c->geo.n_dom; m.src_dom_lo = 0; m.src_dom_hi = c->geo.n_dom;
+        m.kre = c->k0re; m.kim = c->k0im; m.slot1 = 1; m.coef = c->dev.coef; m.near = &c->pmchwt_near;
+        if ((rc = c->plan_apply((const double2*)x[i], (double2*)y[i], BEM_PREC_FP32, m, P[i], fill)))
+            return ctx->fail(rc, c->err);
+        if (c != ctx && c->stream != ctx->stream) CK(cudaStreamSynchronize(c->stream));  // its own work first
+    }
+    GroupCache* G = ctx->group;
+    bool valid = G && G->exec && (int)G->ctxs.size() == n;
+    for (int i = 0; valid && i < n; i++)
+        valid = G->ctxs[i] == ctxs[i] && G->gens[i] == ctxs[i]->gen && G->io[2 * i] == x[i] && G->io[2 * i + 1] == y[i];
+    if (!valid) {
+        // the work list over all members, heaviest first (as for one mesh)
+        std::vector<std::pair<int64_t, int4>> items;
+        std::vector<FarArgs32> table(n);
+        for (int i = 0; i < n; i++) {
+            const Geometry& g = ctxs[i]->geo;
+            const FarArgs32& fa = P[i].fa32;
+            table[i] = fa;
+            table[i].work = nullptr;
+            for (int t = 0; t < P[i].n_tgt; t++) {
+                const int d = g.tile_dom[fa.tgt_begin + t];
+                const int own_b = g.dom_tile_begin[d], own_e = g.dom_tile_end[d];
+                for (int cch = 0; cch < P[i].n_chunks; cch++) {
+                    const int sb = fa.src_begin + cch * fa.chunk_tiles, se = std::min(sb + fa.chunk_tiles, fa.src_end);
+                    int64_t w = 0;
+                    for (int sidx = sb; sidx < se; sidx++)
+                        w += (int64_t)g.tile_ntri[sidx] * (1 + (fa.slot1 && sidx >= own_b && sidx < own_e));
+                    items.push_back({-w, make_int4(i, t, cch, 0)});
+                }
+            }
+        }
+        std::stable_sort(items.begin(), items.end(),
+                         [](const std::pair<int64_t, int4>& a, const std::pair<int64_t, int4>& b) { return a.first < b.first; });
+        std::vector<int4> work(items.size());
+        for (size_t k = 0; k < items.size(); k++) work[k] = items[k].second;
+        if (!G) {
+            G = new GroupCache();
+            ctx->group = G;
+        }
+        if (G->exec) {
+            cudaGraphExecDestroy(G->exec);
+            G->exec = nullptr;
+        }
+        ctx->dfree(G->table);
+        ctx->dfree(G->work);
+        G->table = nullptr;
+        G->work = nullptr;
+        if ((rc = upload(ctx, &G->table, table)) || (rc = upload(ctx, &G->work, work))) return rc;
+        G->n_work = (int64_t)work.size();
+        if (!G->cap) CK(cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking));
+        CK(launch_far32_group(G->table, G->work, 0, G->cap));  // one-time kernel attribute, outside the capture
+        CK(cudaStreamSynchronize(ctx->stream));                 // the uploads are done before the graph exists
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(G->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < n && e == cudaSuccess; i++) e = launch_gather(P[i].ga, G->cap);
+        if (e == cudaSuccess) e = launch_far32_group(G->table, G->work, G->n_work, G->cap);
+        for (int i = 0; i < n && e == cudaSuccess; i++) {
+            e = launch_project(P[i].pa, G->cap);
+            if (e == cudaSuccess) e = launch_reduce(P[i].ra, G->cap);
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(G->cap, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return ctx->fail(BEM_ERR_CUDA, std::string("group capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        e = cudaGraphInstantiate(&G->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return ctx->fail(BEM_ERR_CUDA, std::string("group graph: ") + cudaGetErrorString(e));
+        G->ctxs.assign(ctxs, ctxs + n);
+        G->gens.resize(n);
+        for (int i = 0; i < n; i++) G->gens[i] = ctxs[i]->gen;
+        G->io.resize(2 * n);
+        for (int i = 0; i < n; i++) {
+            G->io[2 * i] = x[i];
+            G->io[2 * i + 1] = y[i];
+        }
+    }
+    CK(cudaGraphLaunch(G->exec, ctx->stream));
+    ctx->launches += 1 + 3 * n;
+    return BEM_OK;
 }
 
 int bem_profile_enable(bem_ctx* ctx, int enable) {

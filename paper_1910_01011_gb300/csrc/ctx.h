@@ -58,6 +58,30 @@ struct ApplyMode {
     const NearSet* near = nullptr;
 };
 
+// Launch arguments of one operator application (gather, far field, projection, reduction).
+struct ApplyPlan {
+    GatherArgs ga{};
+    FarArgs32 fa32{};
+    FarArgs64 fa64{};
+    ProjectArgs pa{};
+    ReduceArgs ra{};
+    bool fp64 = false;
+    int n_tgt = 0, n_chunks = 0;
+};
+
+// Several meshes applied together (bem_apply_group): the launch sequence,
+// captured once as a CUDA graph and replayed while nothing it points to moved.
+struct GroupCache {
+    std::vector<bem_ctx*> ctxs;
+    std::vector<uint64_t> gens;      // each context's allocation generation when captured
+    std::vector<const void*> io;     // x and y pointers
+    FarArgs32* table = nullptr;      // device [n] (owned by the first context)
+    int4* work = nullptr;            // device [n_work]
+    int64_t n_work = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+};
+
 struct OsrcState;  // k_osrc.cu
 struct SolveState; // bem_solve.cu
 
@@ -85,6 +109,8 @@ struct bem_ctx {
     std::vector<std::pair<void*, size_t>> allocs;
     size_t used_bytes = 0;
     size_t peak_bytes = 0;                     // largest used_bytes seen
+    uint64_t gen = 0;                          // bumped by every device allocation and release
+    gbem::GroupCache* group = nullptr;         // bem_apply_group state when this context leads a group
     std::atomic<int64_t>* pool = nullptr;      // shared device-memory counter (serving), or null
     int64_t pool_limit = 0;                    // limit of the shared counter (0: none)
     bool own_stream = false;                   // stream created by the library, destroyed with the context
@@ -126,6 +152,8 @@ struct bem_ctx {
     int ensure_partial(int n_chunks, bool fp64);
     int ensure_far_work(int tgt_b, int tgt_e, int src_b, int src_e, int chunk_tiles, int n_chunks, int slot1);
     void chunking(int n_tgt, int n_src, int* n_chunks, int* chunk_tiles) const;
+    int plan_apply(const double2* x, double2* y, int precision, const gbem::ApplyMode& m, gbem::ApplyPlan& P,
+                   int fill_tiles = 0);
     int run_apply(const double2* x, double2* y, int precision, const gbem::ApplyMode& m);
     int apply_ahat(const double2* x, double2* y, int precision);
     int apply_prec(const double2* x, double2* y);

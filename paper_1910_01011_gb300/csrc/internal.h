@@ -210,6 +210,7 @@ struct NearCombineArgs {
 // launchers (k_apply.cu, k_near.cu)
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
 cudaError_t launch_far32(const FarArgs32& a, int n_tgt_tiles, int n_chunks, cudaStream_t s);
+cudaError_t launch_far32_group(const FarArgs32* group, const int4* gwork, int64_t n_work, cudaStream_t s);
 cudaError_t launch_far64(const FarArgs64& a, int n_tgt_tiles, int n_chunks, cudaStream_t s);
 cudaError_t launch_project(const ProjectArgs& a, cudaStream_t s);
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t s);

@@ -274,17 +274,12 @@ __device__ __forceinline__ void tile_body(const Stage& st, int ntri, int skip_tl
     }
 }
 
-__global__ void __launch_bounds__(TP, 2) far32_kernel(FarArgs32 A) {
+// One work item: target tile tx (offset from A.tgt_begin) against source chunk cy.
+__device__ __forceinline__ void far32_item(const FarArgs32& A, int tx, int cy) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     FarSmem& sm = *reinterpret_cast<FarSmem*>(smem_raw);
 
     const int tid = threadIdx.x, lane = tid & 31;
-    int tx = blockIdx.x, cy = blockIdx.y;
-    if (A.work) {
-        const int2 w = A.work[blockIdx.x];
-        tx = w.x;
-        cy = w.y;
-    }
     const int tt = A.tgt_begin + tx;
     const int sb = A.src_begin + cy * A.chunk_tiles;
     const int se = min(sb + A.chunk_tiles, A.src_end);
@@ -379,6 +374,25 @@ __global__ void __launch_bounds__(TP, 2) far32_kernel(FarArgs32 A) {
     }
 }
 
+__global__ void __launch_bounds__(TP, 2) far32_kernel(FarArgs32 A) {
+    int tx = blockIdx.x, cy = blockIdx.y;
+    if (A.work) {
+        const int2 w = A.work[blockIdx.x];
+        tx = w.x;
+        cy = w.y;
+    }
+    far32_item(A, tx, cy);
+}
+
+// Several meshes in one launch: work item blockIdx.x is (mesh, target tile,
+// chunk) = gwork[blockIdx.x], and the mesh's arguments are group[mesh].
+__global__ void __launch_bounds__(TP, 2) far32_group_kernel(const FarArgs32* __restrict__ group,
+                                                            const int4* __restrict__ gwork) {
+    const int4 w = gwork[blockIdx.x];
+    const FarArgs32 A = group[w.x];
+    far32_item(A, w.y, w.z);
+}
+
 size_t far32_smem_bytes() { return sizeof(FarSmem); }
 
 cudaError_t launch_far32(const FarArgs32& a, int n_tgt_tiles, int n_chunks, cudaStream_t s) {
@@ -389,6 +403,16 @@ cudaError_t launch_far32(const FarArgs32& a, int n_tgt_tiles, int n_chunks, cuda
     if (n_tgt_tiles <= 0 || n_chunks <= 0) return cudaSuccess;
     if (a.work) far32_kernel<<<(unsigned)((int64_t)n_tgt_tiles * n_chunks), TP, smem, s>>>(a);
     else far32_kernel<<<dim3(n_tgt_tiles, n_chunks), TP, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far32_group(const FarArgs32* group, const int4* gwork, int64_t n_work, cudaStream_t s) {
+    const size_t smem = far32_smem_bytes();
+    static const cudaError_t attr_e =
+        cudaFuncSetAttribute(far32_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr_e != cudaSuccess) return attr_e;
+    if (n_work <= 0) return cudaSuccess;
+    far32_group_kernel<<<(unsigned)n_work, TP, smem, s>>>(group, gwork);
     return cudaGetLastError();
 }
 

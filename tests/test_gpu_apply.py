@@ -169,3 +169,31 @@ def test_autotuned_launch_shape_keeps_parity(api, prec):
     c2 = ctx_for(api, s)
     assert c2.autotune(prec, timed=False)["chunk_tiles"] == t["chunk_tiles"]
     assert rel(c2.apply(x, precision=prec), A @ x) < TOL[prec]
+
+
+def test_group_apply_matches_single_applies(api):
+    """Several meshes in one far-field launch (bem_apply_group): each result
+    matches that context's own FP32 application and the oracle; the replayed
+    graph gives the same result again, and new vectors are captured anew."""
+    import torch
+    built = [scenes.sphere_scene(2), scenes.two_sphere_scene(1), scenes.shell_scene(1), ragged_scene(),
+             scenes.sphere_scene(1)]
+    ctxs = [ctx_for(api, s) for s in built]
+    xs = [torch.from_numpy(scenes.random_complex(c.n_dofs, 30 + i)).cuda() for i, c in enumerate(ctxs)]
+    ys = api.apply_group(ctxs, xs)
+    torch.cuda.synchronize()
+    first = [y.cpu().numpy() for y in ys]
+    for c, s, x, y in zip(ctxs, built, xs, first):
+        own = c.apply(x.cpu().numpy(), precision=1)
+        assert rel(y, own) < 1e-6
+        A = pmchwt.assemble(s)
+        assert rel(y, A @ x.cpu().numpy()) < TOL[1]
+    ys2 = api.apply_group(ctxs, xs, ys)      # same vectors: the captured graph is replayed
+    torch.cuda.synchronize()
+    for y, y0 in zip(ys2, first):
+        assert np.array_equal(y.cpu().numpy(), y0)
+    xs[2] = torch.from_numpy(scenes.random_complex(ctxs[2].n_dofs, 99)).cuda()   # a new vector: new capture
+    ys3 = api.apply_group(ctxs, xs)
+    torch.cuda.synchronize()
+    assert rel(ys3[2].cpu().numpy(), ctxs[2].apply(xs[2].cpu().numpy(), precision=1)) < 1e-6
+    assert np.array_equal(ys3[0].cpu().numpy(), first[0])
