@@ -77,7 +77,7 @@ typedef struct {
     double r_eps;              /* OSRC damping radius R_eps (Sec. 2.3 eq. OSRC_DtN_NtD_maps); <= 0: 1/10 of the largest domain diameter */
     double eps_exponent;       /* exponent of k in eps = 0.4 k^e R_eps^(-2/3); default 1/3 */
     double osrc_tol;           /* relative residual of the preconditioner's sparse solves in bem_apply
-                                  (default 1e-11); bem_solve uses 1/100 of its own GMRES tolerance */
+                                  (default 1e-11); bem_solve sets its own (bem_solve_opts.prec_tol) */
     int32_t osrc_solver;       /* sparse solver of the preconditioner: 0 automatic (by the number of systems
                                   and the domain sizes), 1 one CTA per system and domain, 2 grid-wide
                                   kernels, 3 one 8-CTA thread-block cluster per system and domain, 4 as 3
