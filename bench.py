@@ -281,7 +281,7 @@ def rib_solve_metrics(local, n_rhs=16, tol=1e-8):
             "residual": {"fp64": r64["residual"], "mixed": rb["residual"]}}
 
 
-def serving_metrics(local, n_req=12, max_exc=8, rate=20.0, budget=150 << 30, tol=1e-6, rank=0, world=1):
+def serving_metrics(local, n_req=12, max_exc=8, rate=20.0, budget=150 << 30, tol=1e-6, rank=0, world=1, slots=2):
     """Serving trace: Poisson arrivals (mean `rate`/s) of planning solves over
     a pool of scenes (1k and 5k-triangle spheres, a 10k-triangle rib scene, a
     20k-triangle kidney scene, each at k h ~ 1), each request with 1..max_exc
@@ -308,7 +308,7 @@ def serving_metrics(local, n_req=12, max_exc=8, rate=20.0, budget=150 << 30, tol
         return {"requests": 0}
     keys = sorted({k for _, k, _ in reqs})
     built = {k: serving.POOL[k]() for k in keys}
-    srv = Server(device=local, slots=2, max_batch_rhs=64, hbm_budget_bytes=budget, precision=1, operator_mode=1,
+    srv = Server(device=local, slots=slots, max_batch_rhs=64, hbm_budget_bytes=budget, precision=1, operator_mode=1,
                  tol=tol, max_iter=20000, max_refine=20)
     ids = {k: srv.add_scene(built[k], omega_rho0=built[k].meta["omega_rho0"], n_pade=8, r_eps=built[k].meta["r_eps"])
            for k in keys}
@@ -352,7 +352,8 @@ def serving_metrics(local, n_req=12, max_exc=8, rate=20.0, budget=150 << 30, tol
     n_exc = sum(ne for _, _, ne in reqs)
     seq = sum(ne * t64[k] for _, k, ne in reqs)
     return {"workload": f"{n_req} requests, Poisson {rate}/s, 1..{max_exc} excitations each "
-                        f"({n_exc} total), scenes {keys}, tol {tol}, budget {budget / 2**30:.0f} GiB",
+                        f"({n_exc} total), scenes {keys}, tol {tol}, budget {budget / 2**30:.0f} GiB, "
+                        f"{slots} workers",
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "wall_s": wall, "excitations_per_s": n_exc / wall, "requests_per_s": n_req / wall,
             "batches": st["batches"] - warm["batches"], "peak_device_gib": st["peak_device_bytes"] / 2**30,
