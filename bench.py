@@ -194,6 +194,48 @@ def traffic_from_profile():
     return float(m.group(1))
 
 
+def kidney_apply_metrics(local, steps=3):
+    """The same operator application on the kidney + perinephric fat scene
+    (61,996 triangles, 1 MHz), autotuned launch shape, L2 flushed between
+    steps."""
+    import torch
+
+    from paper_1910_01011_gb300.api import Context
+    s, desc = workload("kidney")
+    stream = torch.cuda.current_stream()
+    c = Context.from_scene(s, device=local, stream=stream.cuda_stream)
+    N = c.n_dofs
+    g = torch.Generator(device="cuda").manual_seed(99)
+    x = torch.complex(torch.randn(N, dtype=torch.float64, device="cuda", generator=g),
+                      torch.randn(N, dtype=torch.float64, device="cuda", generator=g))
+    y = torch.empty_like(x)
+    c.apply(x, precision=1, out=y)
+    tuned = c.autotune(1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        c.apply(x, precision=1, out=y)
+    c.profile(True)
+    c.profile_read(reset=True)
+    ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c.apply(x, precision=1, out=y)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+    prof = c.profile_read(reset=True)
+    c.close()
+    far_ms = prof["far_ms"] / max(1, prof["far_launches"])
+    achieved = algorithmic_flops(s) / (far_ms / 1e3) / 1e12
+    n_int = pair_counts(s)[2]
+    return {"workload": desc, "value": n_int * steps / (ms / 1e3) / 1e9, "unit": UNIT,
+            "far_field_chunk_tiles": tuned["chunk_tiles"],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "kernel_ms": far_ms}}
+
+
 def sphere_solve_metrics(local, reps=12):
     """Config-1 sphere (icosphere level 3, k0 = 5, k1 = 5.25, density ratio
     1.1, plane wave): seconds per solve of the mixed path (FP32 operator
@@ -605,6 +647,7 @@ def main():
         extra("assembled", assembled_metrics, ctx, s, n_int, local)
         extra("solve_sphere", sphere_solve_metrics, local)
         if not args.quick and world == 1:
+            extra("apply_kidney", kidney_apply_metrics, local)
             # the minutes-long solve and serving measurements run on one GPU; replicas
             # of them on more GPUs would only repeat the same numbers
             extra("solve", rib_solve_metrics, local)

@@ -63,3 +63,18 @@ def test_invalid_arguments_do_not_need_a_gpu(lib):
     assert lib.bem_quadrature_table(1, 0, buf, ctypes.byref(m)) == -1
     assert lib.bem_destroy(None) == 0
     assert lib.bem_default_opts(None) == -1
+    # null contexts and vectors are refused before any device work
+    assert lib.bem_apply_group(None, 1, None, None) == -1
+    assert lib.bem_apply_group(None, 0, None, None) == -1
+    assert lib.bem_solve_basis(None, None, None) == -1
+    assert lib.bem_superpose(None, None, 1, None, 0) == -1
+    assert lib.bem_get_solution(None, 0, None, 0) == -1
+    assert lib.bem_memory_info(None, None, None) == -1
+    assert lib.bem_estimate_solve_bytes(None, 1, None, None) == -1
+    assert lib.bem_autotune(None, 1, None, None) == -1
+    assert lib.bem_server_destroy(None) == 0
+    assert lib.bem_server_submit(None, 0, None, 1, None) == -1
+    from paper_1910_01011_gb300 import _lib
+    o = _lib.bem_server_opts()
+    assert lib.bem_server_default_opts(ctypes.byref(o)) == 0
+    assert o.slots == 2 and o.max_batch_rhs == 64 and o.solve.flexible == 1
