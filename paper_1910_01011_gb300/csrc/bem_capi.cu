@@ -158,7 +158,7 @@ int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_
     const int64_t ne = (int64_t)ctx->tr_r.size();
     int64_t b = 0;
     // geometry, densities, staging vectors
-    b += pts * 136 + slots * 460 + pairs * 12 + N * 64 + tiles * 64;
+    b += pts * 152 + slots * 460 + pairs * 12 + N * 64 + tiles * 64;
     // near-field blocks (c128 + c64) and their build scratch
     b += pairs * 36 * 24 + std::min<int64_t>(pairs, 1 << 20) * 2 * 27 * 16;
     // far-field partial potentials (FP64 residual is the larger)
@@ -212,6 +212,12 @@ int bem_ctx::finalize() {
                               (float)g.pt_w[p]);
         pg64[p] = make_double4(g.pt_delta[3 * p], g.pt_delta[3 * p + 1], g.pt_delta[3 * p + 2], g.pt_w[p]);
     }
+    std::vector<float4> pgp32(g.n_pts);
+    for (int64_t s = 0; s < g.n_slots; s++) {
+        float4 tri[QP];
+        for (int q = 0; q < QP; q++) tri[q] = pg32[s * QP + q];
+        pair_interleave(tri, pgp32.data() + s * QP);
+    }
     for (int64_t s = 0; s < g.n_slots; s++) {
         tg32[s] = make_float4((float)g.slot_n[3 * s], (float)g.slot_n[3 * s + 1], (float)g.slot_n[3 * s + 2],
                               (float)g.slot_h[s]);
@@ -224,7 +230,7 @@ int bem_ctx::finalize() {
     std::vector<int4> sv(g.n_slots);
     for (int64_t s = 0; s < g.n_slots; s++)
         sv[s] = make_int4(g.slot_v[4 * s], g.slot_v[4 * s + 1], g.slot_v[4 * s + 2], g.slot_v[4 * s + 3]);
-    if ((rc = upload(this, &d.pg32, pg32)) || (rc = upload(this, &d.tg32, tg32)) || (rc = upload(this, &d.pg64, pg64)) ||
+    if ((rc = upload(this, &d.pg32, pg32)) || (rc = upload(this, &d.pgp32, pgp32)) || (rc = upload(this, &d.tg32, tg32)) || (rc = upload(this, &d.pg64, pg64)) ||
         (rc = upload(this, &d.tg64, tg64)) || (rc = upload(this, &d.tc, tc)) || (rc = upload(this, &d.tdom, g.tile_dom)) ||
         (rc = upload(this, &d.tntri, g.tile_ntri)) || (rc = upload(this, &d.dom_tiles, dt)) ||
         (rc = upload(this, &d.slot_v, sv)) || (rc = upload(this, &d.slot_P, g.slot_P)) ||
@@ -440,7 +446,7 @@ int bem_ctx::plan_apply(const double2* x, double2* y, int precision, const Apply
         fa.slot1 = m.slot1; fa.n_pts = g.n_pts; fa.partial = (double*)partial;
     } else {
         FarArgs32& fa = P.fa32;
-        fa.pg = dev.pg32; fa.tg = dev.tg32; fa.tc = dev.tc; fa.tdom = dev.tdom; fa.tntri = dev.tntri;
+        fa.pg = dev.pg32; fa.pgp = dev.pgp32; fa.tg = dev.tg32; fa.tc = dev.tc; fa.tdom = dev.tdom; fa.tntri = dev.tntri;
         fa.pd = dev.pd32; fa.tcurl = dev.tcurl32; fa.dom_tiles = dev.dom_tiles; fa.kdom = dev.kdom;
         fa.k0 = make_double2(m.kre, m.kim);
         fa.src_begin = src_b; fa.src_end = src_e; fa.tgt_begin = tgt_b; fa.chunk_tiles = chunk_tiles;

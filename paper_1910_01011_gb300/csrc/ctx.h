@@ -15,7 +15,7 @@
 namespace gbem {
 
 struct DeviceGeom {
-    float4 *pg32 = nullptr, *tg32 = nullptr;
+    float4 *pg32 = nullptr, *pgp32 = nullptr, *tg32 = nullptr;  // pgp32: pg32 pair-interleaved
     double4 *pg64 = nullptr, *tg64 = nullptr, *tc = nullptr;
     int *tdom = nullptr, *tntri = nullptr;
     int2* dom_tiles = nullptr;

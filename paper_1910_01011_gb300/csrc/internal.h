@@ -84,13 +84,32 @@ std::string build_geometry(const std::vector<HostDomain>& doms, const Quadrature
 
 // ------------------------------------------------------------------ device views
 
+// Pair-interleaved storage of the QP points of one triangle, the layout in
+// which the FP32 far field reads its sources (two points per packed FP32
+// instruction): pair j (points 2j and 2j+1) is the float4
+// (x_a, x_b, y_a, y_b) at 2j followed by (z_a, z_b, w_a, w_b) at 2j + 1.
+static_assert(QP % 2 == 0, "points pair up within a triangle");
+__host__ __device__ inline void pair_interleave(const float4 (&pt)[QP], float4* out) {
+    for (int j = 0; j < QP / 2; j++) {
+        const float4 a = pt[2 * j], b = pt[2 * j + 1];
+        out[2 * j] = make_float4(a.x, b.x, a.y, b.y);
+        out[2 * j + 1] = make_float4(a.z, b.z, a.w, b.w);
+    }
+}
+// Point q of a triangle stored pair-interleaved at tri.
+__host__ __device__ inline float4 pair_point(const float4* tri, int q) {
+    const float4 u = tri[q & ~1], v = tri[(q & ~1) + 1];
+    return (q & 1) ? make_float4(u.y, u.w, v.y, v.w) : make_float4(u.x, u.z, v.x, v.z);
+}
+
 struct FarArgs32 {
-    const float4* pg;       // [n_pts]   (dx, dy, dz, w)
+    const float4* pg;       // [n_pts]   (dx, dy, dz, w)          target points
+    const float4* pgp;      // [n_pts]   the same, pair-interleaved  source points
     const float4* tg;       // [n_slots] (nx, ny, nz, h)
     const double4* tc;      // [n_tiles] centre
     const int* tdom;        // [n_tiles]
     const int* tntri;       // [n_tiles]
-    const float4* pd;       // [n_pts]   (sigN re, im, sigD re, im) * w
+    const float4* pd;       // [n_pts]   (sigN re, im, sigD re, im) * w, pair-interleaved
     const float4* tcurl;    // [2*n_slots] (Cre, 0), (Cim, 0)
     const int2* dom_tiles;  // [n_dom] own-domain tile range (slot 1 sources)
     const double2* kdom;    // [n_dom] slot-1 wavenumber
@@ -131,7 +150,7 @@ struct GatherArgs {
     const double2* x;           // system-order input
     int64_t s_begin, s_end;     // slots to gather
     double lam[QP][3];          // P1 values at the rule points
-    float4* pd32; float4* tcurl32;     // fp32 outputs (may be null)
+    float4* pd32; float4* tcurl32;     // fp32 outputs (may be null); pd32 pair-interleaved
     double4* pd64; double4* tcurl64;   // fp64 outputs (may be null)
 };
 

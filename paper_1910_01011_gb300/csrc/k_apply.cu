@@ -109,6 +109,7 @@ __global__ void gather_kernel(GatherArgs a) {
             xf[k] = make_double2(0, 0);
         }
     }
+    float4 p32[QP];
     for (int q = 0; q < QP; q++) {
         double w = real ? a.pt_w[s * QP + q] : 0.0;
         double sr = 0, si = 0, dr = 0, di = 0;
@@ -118,9 +119,10 @@ __global__ void gather_kernel(GatherArgs a) {
             dr += a.lam[q][k] * xf[k].x;
             di += a.lam[q][k] * xf[k].y;
         }
-        if (a.pd32) a.pd32[s * QP + q] = make_float4((float)(w * sr), (float)(w * si), (float)(w * dr), (float)(w * di));
+        p32[q] = make_float4((float)(w * sr), (float)(w * si), (float)(w * dr), (float)(w * di));
         if (a.pd64) a.pd64[s * QP + q] = make_double4(w * sr, w * si, w * dr, w * di);
     }
+    if (a.pd32) pair_interleave(p32, a.pd32 + s * QP);
     double cr[3] = {0, 0, 0}, ci[3] = {0, 0, 0};
     if (real)
         for (int k = 0; k < 3; k++)
@@ -153,8 +155,8 @@ constexpr int NSTAGE = 4;
 constexpr int NWARP = TP / 32;
 
 struct __align__(16) Stage {
-    float4 pg[TP];      // source points (dx, dy, dz, w)
-    float4 pd[TP];      // densities
+    float4 pg[TP];      // source points (dx, dy, dz, w), pair-interleaved
+    float4 pd[TP];      // densities, pair-interleaved
     float4 tg[TT];      // triangles (n, h)
     float4 tc[2 * TT];  // curl densities
 };
@@ -172,71 +174,133 @@ struct Acc {
     float v[NCOMP];  // PV(2) PK(2) PKp(2) PWm(2) PWc(6)
 };
 
-struct SlotK {
-    float kr, nki, nkil2;  // Re k, -Im k, -Im k * log2(e)
+// Source points are processed two at a time, side by side in the two lanes
+// of a float2, so that one packed FP32 instruction (FFMA2 / FADD2 / FMUL2)
+// advances both.  The points of a triangle are stored pair-interleaved:
+// pair j (points 2j and 2j+1) is the float4 (x_a, x_b, y_a, y_b) followed by
+// (z_a, z_b, w_a, w_b), for the source geometry (offsets from the tile
+// centre and weight) and for the gathered densities (the two complex
+// densities in place of x, y and z, w).
+typedef float2 f2;
+
+__device__ __forceinline__ f2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ f2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 neg2(f2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ void sincos_approx(float x, float* s, float* c) {
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(x));
+}
+
+// One wavenumber slot, both lanes.
+struct PairK {
+    f2 kr, nkr, th, ki, nkil2;  // Re k, -Re k, reduced FP64 phase of the tile pair, Im k, -Im k log2(e)
 };
 
-struct TriSums {
-    float S1r, S1i, S2r, S2i, S3r, S3i;
+// Sums over the points of one tile (V, K') and of one triangle (the rest),
+// per lane.  The K' and K sums are kept with the sign of -F, the form in
+// which the gradient factor comes out without a sign flip.
+struct PairTile {
+    f2 Vr, Vi, nKpr, nKpi;
+};
+struct PairTri {
+    f2 nS1r, nS1i, S2r, S2i, S3r, S3i;
 };
 
-// Contribution of one source point at one wavenumber.  LOSSY: Im k != 0
-// (exp(-Im k r) evaluated); otherwise the amplitude is 1/r.  With
-// (ik - 1/r)/r = A + iB, A = (-Im k - 1/r)/r, B = Re k / r, the gradient
-// factor is F = G (A + iB); A = -1/r^2 for real k (rinv2 = 1/r^2 is shared
-// by both wavenumbers of a point).
+// Contribution of two source points at one wavenumber.  With
+// (ik - 1/r)/r = A + iB, B = Re k / r, P = -A = Im k / r + 1/r^2, the
+// gradient factor is F = G (A + iB), so -Re F = P Gr + B Gi and
+// -Im F = P Gi - B Gr.  LOSSY: Im k != 0 (exp(-Im k r) evaluated);
+// otherwise the amplitude is 1/r and P = 1/r^2.
 template <bool LOSSY>
-__device__ __forceinline__ void slot_point(const SlotK& k, float th, float rho, float r2, float rinv, float rinv2,
-                                           float ndot, const float4& g, const float4& d, Acc& t, TriSums& S) {
-    float sn, cs;
-    __sincosf(fmaf(k.kr, rho, th), &sn, &cs);
-    const float a = LOSSY ? ex2_approx(k.nkil2 * (r2 * rinv)) * rinv : rinv;
-    const float Gr = a * cs, Gi = a * sn;
-    const float B = k.kr * rinv;
-    float Fr, Fi;
+__device__ __forceinline__ void pair_slot(const PairK& k, f2 rho, f2 r, f2 rinv, f2 rinv2, f2 ndot, f2 w, f2 d1r,
+                                          f2 d1i, f2 nd1i, f2 d2r, f2 d2i, f2 nd2i, PairTile& T, PairTri& S) {
+    const f2 arg = fma2(k.kr, rho, k.th);
+    f2 sn, cs;
+    sincos_approx(arg.x, &sn.x, &cs.x);
+    sincos_approx(arg.y, &sn.y, &cs.y);
+    f2 a = rinv;
     if constexpr (LOSSY) {
-        const float A = fmaf(rinv, k.nki, -rinv2);
-        Fr = fmaf(A, Gr, -(B * Gi));
-        Fi = fmaf(B, Gr, A * Gi);
-    } else {
-        Fr = -fmaf(rinv2, Gr, B * Gi);
-        Fi = fmaf(B, Gr, -(rinv2 * Gi));
+        const f2 e = mul2(k.nkil2, r);
+        a = mul2(make_float2(ex2_approx(e.x), ex2_approx(e.y)), rinv);
     }
-    t.v[0] = fmaf(Gr, d.x, fmaf(-Gi, d.y, t.v[0]));
-    t.v[1] = fmaf(Gr, d.y, fmaf(Gi, d.x, t.v[1]));
-    const float Fnr = Fr * ndot, Fni = Fi * ndot;
-    t.v[4] = fmaf(Fnr, d.x, fmaf(-Fni, d.y, t.v[4]));
-    t.v[5] = fmaf(Fnr, d.y, fmaf(Fni, d.x, t.v[5]));
-    S.S1r = fmaf(Fr, d.z, fmaf(-Fi, d.w, S.S1r));
-    S.S1i = fmaf(Fr, d.w, fmaf(Fi, d.z, S.S1i));
-    S.S2r = fmaf(Gr, g.w, S.S2r);
-    S.S2i = fmaf(Gi, g.w, S.S2i);
-    S.S3r = fmaf(Gr, d.z, fmaf(-Gi, d.w, S.S3r));
-    S.S3i = fmaf(Gr, d.w, fmaf(Gi, d.z, S.S3i));
+    const f2 Gr = mul2(a, cs), Gi = mul2(a, sn);
+    const f2 B = mul2(k.kr, rinv), nB = mul2(k.nkr, rinv);
+    const f2 P = LOSSY ? fma2(k.ki, rinv, rinv2) : rinv2;
+    const f2 nFr = fma2(P, Gr, mul2(B, Gi));
+    const f2 nFi = fma2(P, Gi, mul2(nB, Gr));
+    T.Vr = fma2(Gr, d1r, fma2(Gi, nd1i, T.Vr));
+    T.Vi = fma2(Gr, d1i, fma2(Gi, d1r, T.Vi));
+    const f2 nFnr = mul2(ndot, nFr), nFni = mul2(ndot, nFi);
+    T.nKpr = fma2(nFnr, d1r, fma2(nFni, nd1i, T.nKpr));
+    T.nKpi = fma2(nFnr, d1i, fma2(nFni, d1r, T.nKpi));
+    S.nS1r = fma2(nFr, d2r, fma2(nFi, nd2i, S.nS1r));
+    S.nS1i = fma2(nFr, d2i, fma2(nFi, d2r, S.nS1i));
+    S.S2r = fma2(Gr, w, S.S2r);
+    S.S2i = fma2(Gi, w, S.S2i);
+    S.S3r = fma2(Gr, d2r, fma2(Gi, nd2i, S.S3r));
+    S.S3i = fma2(Gr, d2i, fma2(Gi, d2r, S.S3i));
 }
 
 // Per-triangle terms: K through (y-x).n_t, W through curl phi and n_x.n_t.
 __device__ __forceinline__ void slot_triangle(float fK, float nn, const float4& cre, const float4& cim,
-                                              const TriSums& S, Acc& t) {
-    t.v[2] = fmaf(fK, S.S1r, t.v[2]);
-    t.v[3] = fmaf(fK, S.S1i, t.v[3]);
-    t.v[6] = fmaf(nn, S.S3r, t.v[6]);
-    t.v[7] = fmaf(nn, S.S3i, t.v[7]);
-    t.v[8] = fmaf(S.S2r, cre.x, fmaf(-S.S2i, cim.x, t.v[8]));
-    t.v[9] = fmaf(S.S2r, cre.y, fmaf(-S.S2i, cim.y, t.v[9]));
-    t.v[10] = fmaf(S.S2r, cre.z, fmaf(-S.S2i, cim.z, t.v[10]));
-    t.v[11] = fmaf(S.S2r, cim.x, fmaf(S.S2i, cre.x, t.v[11]));
-    t.v[12] = fmaf(S.S2r, cim.y, fmaf(S.S2i, cre.y, t.v[12]));
-    t.v[13] = fmaf(S.S2r, cim.z, fmaf(S.S2i, cre.z, t.v[13]));
+                                              const PairTri& P, Acc& t) {
+    const float nS1r = P.nS1r.x + P.nS1r.y, nS1i = P.nS1i.x + P.nS1i.y;
+    const float S2r = P.S2r.x + P.S2r.y, S2i = P.S2i.x + P.S2i.y;
+    const float S3r = P.S3r.x + P.S3r.y, S3i = P.S3i.x + P.S3i.y;
+    t.v[2] = fmaf(-fK, nS1r, t.v[2]);
+    t.v[3] = fmaf(-fK, nS1i, t.v[3]);
+    t.v[6] = fmaf(nn, S3r, t.v[6]);
+    t.v[7] = fmaf(nn, S3i, t.v[7]);
+    t.v[8] = fmaf(S2r, cre.x, fmaf(-S2i, cim.x, t.v[8]));
+    t.v[9] = fmaf(S2r, cre.y, fmaf(-S2i, cim.y, t.v[9]));
+    t.v[10] = fmaf(S2r, cre.z, fmaf(-S2i, cim.z, t.v[10]));
+    t.v[11] = fmaf(S2r, cim.x, fmaf(S2i, cre.x, t.v[11]));
+    t.v[12] = fmaf(S2r, cim.y, fmaf(S2i, cre.y, t.v[12]));
+    t.v[13] = fmaf(S2r, cim.z, fmaf(S2i, cre.z, t.v[13]));
 }
 
+// The target point of a thread: offset d from its tile centre, normal n,
+// with -n and |d|^2, n.d kept for the per-tile constants.
+struct PairTgt {
+    float dx, dy, dz, nx, ny, nz, dd, nd;
+    f2 nnx, nny, nnz;
+};
+
+// One target point against one source tile.  With D = c_target - c_source
+// (c0 carries 2D and R_c^2 = |D|^2, c1 R_c and the reduced phases), a source
+// point offset g from its centre gives x - y = d - g + D and
+//   s = r^2 - R_c^2 = |g|^2 - 2 g.(d + D) + |d|^2 + 2 D.d,
+// a sum whose terms are as small as s itself times R_c / tile size, so that
+// the phase offset r - R_c = s / (r + R_c) keeps FP32 accuracy;
+// n_x.(x - y) = (n.d + n.D) - n.g.
 template <bool TWO, bool L0, bool L1>
-__device__ __forceinline__ void tile_body(const Stage& st, int ntri, int skip_tl, float dx, float dy, float dz,
-                                          float nx, float ny, float nz, float4 c0, float4 c1, const SlotK& k0,
-                                          const SlotK& k1, Acc& a0, Acc& a1) {
-    const float D2x = c0.x, D2y = c0.y, D2z = c0.z, Rc2 = c0.w, Rc = c1.x, th0 = c1.y, th1 = c1.z;
-    const float Xx = fmaf(0.5f, D2x, dx), Xy = fmaf(0.5f, D2y, dy), Xz = fmaf(0.5f, D2z, dz);  // x - c_source
-    const float nD = 0.5f * (nx * D2x + ny * D2y + nz * D2z);                                 // n_x.D
+__device__ __forceinline__ void tile_body(const Stage& st, int ntri, int skip_tl, const PairTgt& X, float4 c0, float4 c1,
+                                          PairK k0, PairK k1, Acc& a0, Acc& a1) {
+    const float D2x = c0.x, D2y = c0.y, D2z = c0.z;
+    const f2 m2x = bc2(-fmaf(2.f, X.dx, D2x)), m2y = bc2(-fmaf(2.f, X.dy, D2y)), m2z = bc2(-fmaf(2.f, X.dz, D2z));
+    const f2 cb = bc2(fmaf(D2x, X.dx, fmaf(D2y, X.dy, fmaf(D2z, X.dz, X.dd))));
+    const f2 cn = bc2(fmaf(0.5f, X.nx * D2x + X.ny * D2y + X.nz * D2z, X.nd));
+    const f2 Rc2 = bc2(c0.w), Rc = bc2(c1.x);
+    k0.th = bc2(c1.y);
+    if constexpr (TWO) k1.th = bc2(c1.z);
+    const float Xx = fmaf(0.5f, D2x, X.dx), Xy = fmaf(0.5f, D2y, X.dy), Xz = fmaf(0.5f, D2z, X.dz);  // x - c_source
+    const f2 z2 = make_float2(0.f, 0.f);
+    PairTile T0{z2, z2, z2, z2}, T1{z2, z2, z2, z2};
     Acc t0, t1;
 #pragma unroll
     for (int c = 0; c < NCOMP; c++) {
@@ -245,27 +309,41 @@ __device__ __forceinline__ void tile_body(const Stage& st, int ntri, int skip_tl
     }
     for (int tl = 0; tl < ntri; tl++) {
         if (tl == skip_tl) continue;  // identical triangle: near-field correction only
-        TriSums S0{0, 0, 0, 0, 0, 0}, S1{0, 0, 0, 0, 0, 0};
+        PairTri S0{z2, z2, z2, z2, z2, z2}, S1{z2, z2, z2, z2, z2, z2};
 #pragma unroll
-        for (int q = 0; q < QP; q++) {
-            const float4 g = st.pg[tl * QP + q];
-            const float4 d = st.pd[tl * QP + q];
-            const float ex = dx - g.x, ey = dy - g.y, ez = dz - g.z;            // delta = dx - dy
-            const float s = ex * (D2x + ex) + ey * (D2y + ey) + ez * (D2z + ez);  // r^2 - R_c^2
-            const float r2 = Rc2 + s;
-            const float rinv = rsqrtf(r2);
-            const float rinv2 = rinv * rinv;
-            const float rho = __fdividef(s, fmaf(r2, rinv, Rc));               // r - R_c = s / (r + R_c)
-            const float ndot = fmaf(nx, ex, fmaf(ny, ey, fmaf(nz, ez, nD)));    // n_x.(x - y)
-            slot_point<L0>(k0, th0, rho, r2, rinv, rinv2, ndot, g, d, t0, S0);
-            if constexpr (TWO) slot_point<L1>(k1, th1, rho, r2, rinv, rinv2, ndot, g, d, t1, S1);
+        for (int j = 0; j < QP / 2; j++) {
+            const float4 GA = st.pg[tl * QP + 2 * j], GB = st.pg[tl * QP + 2 * j + 1];
+            const float4 DA = st.pd[tl * QP + 2 * j], DB = st.pd[tl * QP + 2 * j + 1];
+            const f2 gx = lo2(GA), gy = hi2(GA), gz = lo2(GB), w = hi2(GB);
+            const f2 d1r = lo2(DA), d1i = hi2(DA), d2r = lo2(DB), d2i = hi2(DB);
+            const f2 s = fma2(gx, add2(gx, m2x), fma2(gy, add2(gy, m2y), fma2(gz, add2(gz, m2z), cb)));
+            const f2 r2 = add2(s, Rc2);
+            const f2 rinv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+            const f2 rinv2 = mul2(rinv, rinv);
+            const f2 den = fma2(r2, rinv, Rc);  // r + R_c
+            const f2 rho = mul2(s, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+            const f2 ndot = fma2(X.nnx, gx, fma2(X.nny, gy, fma2(X.nnz, gz, cn)));
+            const f2 r = (L0 || L1) ? mul2(r2, rinv) : z2;
+            const f2 nd1i = neg2(d1i), nd2i = neg2(d2i);
+            pair_slot<L0>(k0, rho, r, rinv, rinv2, ndot, w, d1r, d1i, nd1i, d2r, d2i, nd2i, T0, S0);
+            if constexpr (TWO) pair_slot<L1>(k1, rho, r, rinv, rinv2, ndot, w, d1r, d1i, nd1i, d2r, d2i, nd2i, T1, S1);
         }
         const float4 tg = st.tg[tl];
         const float4 cre = st.tc[2 * tl], cim = st.tc[2 * tl + 1];
         const float fK = tg.w - (tg.x * Xx + tg.y * Xy + tg.z * Xz);  // n_t.(y - x)
-        const float nn = nx * tg.x + ny * tg.y + nz * tg.z;            // n_x.n_t
+        const float nn = X.nx * tg.x + X.ny * tg.y + X.nz * tg.z;      // n_x.n_t
         slot_triangle(fK, nn, cre, cim, S0, t0);
         if constexpr (TWO) slot_triangle(fK, nn, cre, cim, S1, t1);
+    }
+    t0.v[0] += T0.Vr.x + T0.Vr.y;
+    t0.v[1] += T0.Vi.x + T0.Vi.y;
+    t0.v[4] -= T0.nKpr.x + T0.nKpr.y;
+    t0.v[5] -= T0.nKpi.x + T0.nKpi.y;
+    if constexpr (TWO) {
+        t1.v[0] += T1.Vr.x + T1.Vr.y;
+        t1.v[1] += T1.Vi.x + T1.Vi.y;
+        t1.v[4] -= T1.nKpr.x + T1.nKpr.y;
+        t1.v[5] -= T1.nKpi.x + T1.nKpi.y;
     }
 #pragma unroll
     for (int c = 0; c < NCOMP; c++) {
@@ -293,9 +371,13 @@ __device__ __forceinline__ void far32_item(const FarArgs32& A, int tx, int cy) {
     const int mydom = A.tdom[tt];
     const int2 dr = A.dom_tiles[mydom];
     const double2 kj = A.kdom[mydom];
-    const SlotK k0{(float)A.k0.x, (float)-A.k0.y, (float)(-A.k0.y * 1.4426950408889634)};
-    const SlotK k1{(float)kj.x, (float)-kj.y, (float)(-kj.y * 1.4426950408889634)};
+    const PairK k0{bc2((float)A.k0.x), bc2((float)-A.k0.x), bc2(0.f), bc2((float)A.k0.y),
+                   bc2((float)(-A.k0.y * 1.4426950408889634))};
+    const PairK k1{bc2((float)kj.x), bc2((float)-kj.x), bc2(0.f), bc2((float)kj.y),
+                   bc2((float)(-kj.y * 1.4426950408889634))};
     const bool lossy0 = A.k0.y != 0.0, lossy1 = kj.y != 0.0;
+    const PairTgt X{g.x, g.y, g.z, ng.x, ng.y, ng.z, g.x * g.x + g.y * g.y + g.z * g.z,
+                    ng.x * g.x + ng.y * g.y + ng.z * g.z, bc2(-ng.x), bc2(-ng.y), bc2(-ng.z)};
 
     // tile-pair table: 2D, R_c^2, R_c and the FP64-reduced phases
     for (int i = tid; i < nsrc; i += TP) {
@@ -320,7 +402,7 @@ __device__ __forceinline__ void far32_item(const FarArgs32& A, int tx, int cy) {
         const int s = sb + i;
         Stage& S = sm.st[st];
         mbar_arrive_expect_tx(&sm.full[st], STAGE_BYTES);
-        bulk_g2s(S.pg, A.pg + (int64_t)s * TP, TP * 16, &sm.full[st]);
+        bulk_g2s(S.pg, A.pgp + (int64_t)s * TP, TP * 16, &sm.full[st]);
         bulk_g2s(S.pd, A.pd + (int64_t)s * TP, TP * 16, &sm.full[st]);
         bulk_g2s(S.tg, A.tg + (int64_t)s * TT, TT * 16, &sm.full[st]);
         bulk_g2s(S.tc, A.tcurl + (int64_t)s * 2 * TT, 2 * TT * 16, &sm.full[st]);
@@ -345,15 +427,15 @@ __device__ __forceinline__ void far32_item(const FarArgs32& A, int tx, int cy) {
         const bool two = A.slot1 && s >= dr.x && s < dr.y;
         if (two) {
             if (lossy0) {
-                if (lossy1) tile_body<true, true, true>(S, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
-                else tile_body<true, true, false>(S, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
+                if (lossy1) tile_body<true, true, true>(S, ntri, skip, X, c0, c1, k0, k1, a0, a1);
+                else tile_body<true, true, false>(S, ntri, skip, X, c0, c1, k0, k1, a0, a1);
             } else {
-                if (lossy1) tile_body<true, false, true>(S, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
-                else tile_body<true, false, false>(S, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
+                if (lossy1) tile_body<true, false, true>(S, ntri, skip, X, c0, c1, k0, k1, a0, a1);
+                else tile_body<true, false, false>(S, ntri, skip, X, c0, c1, k0, k1, a0, a1);
             }
         } else {
-            if (lossy0) tile_body<false, true, false>(S, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
-            else tile_body<false, false, false>(S, ntri, skip, g.x, g.y, g.z, ng.x, ng.y, ng.z, c0, c1, k0, k1, a0, a1);
+            if (lossy0) tile_body<false, true, false>(S, ntri, skip, X, c0, c1, k0, k1, a0, a1);
+            else tile_body<false, false, false>(S, ntri, skip, X, c0, c1, k0, k1, a0, a1);
         }
         // leave the stage; the last warp out refills it with the tile NSTAGE ahead
         __syncwarp();

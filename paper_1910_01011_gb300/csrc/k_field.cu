@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(TP) field_kernel(FieldArgs a) {
 #pragma unroll
             for (int q = 0; q < QP; q++) {
                 const float4 g = s_pg[tl * QP + q];
-                const float4 d = s_pd[tl * QP + q];
+                const float4 d = pair_point(s_pd + tl * QP, q);
                 const float ex = -g.x, ey = -g.y, ez = -g.z;
                 const float sd = ex * (D2x + ex) + ey * (D2y + ey) + ez * (D2z + ez);
                 const float r2 = Rc2 + sd;

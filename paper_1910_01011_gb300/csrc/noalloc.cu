@@ -95,7 +95,7 @@ extern "C" int bem_apply_noalloc(bem_ctx* ctx, const bem_z* x, bem_z* y) {
         float* base = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(scratch) -
                                                (uintptr_t)((int64_t)tb * TP * (int64_t)sizeof(float)));
         FarArgs32 fa{};
-        fa.pg = ctx->dev.pg32; fa.tg = ctx->dev.tg32; fa.tc = ctx->dev.tc; fa.tdom = ctx->dev.tdom;
+        fa.pg = ctx->dev.pg32; fa.pgp = ctx->dev.pgp32; fa.tg = ctx->dev.tg32; fa.tc = ctx->dev.tc; fa.tdom = ctx->dev.tdom;
         fa.tntri = ctx->dev.tntri; fa.pd = ctx->dev.pd32; fa.tcurl = ctx->dev.tcurl32;
         fa.dom_tiles = ctx->dev.dom_tiles; fa.kdom = ctx->dev.kdom;
         fa.k0 = make_double2(ctx->k0re, ctx->k0im);
