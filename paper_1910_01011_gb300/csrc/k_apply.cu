@@ -212,8 +212,9 @@ struct PairK {
 };
 
 // Sums over the points of one tile (V, K') and of one triangle (the rest),
-// per lane.  The K' and K sums are kept with the sign of -F, the form in
-// which the gradient factor comes out without a sign flip.
+// per lane; they are folded into the chunk's accumulators at the end of
+// their tile or triangle.  The K' and K sums are kept with the sign of -F,
+// the form in which the gradient factor comes out without a sign flip.
 struct PairTile {
     f2 Vr, Vi, nKpr, nKpi;
 };
@@ -301,12 +302,6 @@ __device__ __forceinline__ void tile_body(const Stage& st, int ntri, int skip_tl
     const float Xx = fmaf(0.5f, D2x, X.dx), Xy = fmaf(0.5f, D2y, X.dy), Xz = fmaf(0.5f, D2z, X.dz);  // x - c_source
     const f2 z2 = make_float2(0.f, 0.f);
     PairTile T0{z2, z2, z2, z2}, T1{z2, z2, z2, z2};
-    Acc t0, t1;
-#pragma unroll
-    for (int c = 0; c < NCOMP; c++) {
-        t0.v[c] = 0.f;
-        if constexpr (TWO) t1.v[c] = 0.f;
-    }
     for (int tl = 0; tl < ntri; tl++) {
         if (tl == skip_tl) continue;  // identical triangle: near-field correction only
         PairTri S0{z2, z2, z2, z2, z2, z2}, S1{z2, z2, z2, z2, z2, z2};
@@ -332,23 +327,18 @@ __device__ __forceinline__ void tile_body(const Stage& st, int ntri, int skip_tl
         const float4 cre = st.tc[2 * tl], cim = st.tc[2 * tl + 1];
         const float fK = tg.w - (tg.x * Xx + tg.y * Xy + tg.z * Xz);  // n_t.(y - x)
         const float nn = X.nx * tg.x + X.ny * tg.y + X.nz * tg.z;      // n_x.n_t
-        slot_triangle(fK, nn, cre, cim, S0, t0);
-        if constexpr (TWO) slot_triangle(fK, nn, cre, cim, S1, t1);
+        slot_triangle(fK, nn, cre, cim, S0, a0);
+        if constexpr (TWO) slot_triangle(fK, nn, cre, cim, S1, a1);
     }
-    t0.v[0] += T0.Vr.x + T0.Vr.y;
-    t0.v[1] += T0.Vi.x + T0.Vi.y;
-    t0.v[4] -= T0.nKpr.x + T0.nKpr.y;
-    t0.v[5] -= T0.nKpi.x + T0.nKpi.y;
+    a0.v[0] += T0.Vr.x + T0.Vr.y;
+    a0.v[1] += T0.Vi.x + T0.Vi.y;
+    a0.v[4] -= T0.nKpr.x + T0.nKpr.y;
+    a0.v[5] -= T0.nKpi.x + T0.nKpi.y;
     if constexpr (TWO) {
-        t1.v[0] += T1.Vr.x + T1.Vr.y;
-        t1.v[1] += T1.Vi.x + T1.Vi.y;
-        t1.v[4] -= T1.nKpr.x + T1.nKpr.y;
-        t1.v[5] -= T1.nKpi.x + T1.nKpi.y;
-    }
-#pragma unroll
-    for (int c = 0; c < NCOMP; c++) {
-        a0.v[c] += t0.v[c];
-        if constexpr (TWO) a1.v[c] += t1.v[c];
+        a1.v[0] += T1.Vr.x + T1.Vr.y;
+        a1.v[1] += T1.Vi.x + T1.Vi.y;
+        a1.v[4] -= T1.nKpr.x + T1.nKpr.y;
+        a1.v[5] -= T1.nKpi.x + T1.nKpi.y;
     }
 }
 
@@ -582,12 +572,61 @@ cudaError_t launch_far64(const FarArgs64& a, int n_tgt_tiles, int n_chunks, cuda
 
 // ----------------------------------------------------------------- projection onto P1 test functions
 
-__global__ void project_kernel(ProjectArgs a) {
-    const int64_t s = (int64_t)a.tgt_begin * TT + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= (int64_t)a.tgt_end * TT) return;
+// One CTA per target tile.  Its TP threads first sum, each for its own
+// point, the chunk partials of both slots (reads coalesced across the CTA);
+// then one thread per triangle projects onto the P1 test functions from
+// shared memory.  FP32 partials are summed with a compensated (TwoSum)
+// FP32 sum in chunk order, converted to FP64 once: the GPU's FP64 rate is
+// a small fraction of its FP32 rate, and the compensation carries the
+// rounding error of every addition, so the result matches an FP64 sum of
+// the same FP32 values to ~1e-13 relative.
+__global__ void __launch_bounds__(TP) project_kernel(ProjectArgs a) {
+    __shared__ double Ps[2][NCOMP][TP];
+    const int tile = a.tgt_begin + blockIdx.x;
+    const int tid = threadIdx.x;
+    const int tdom = a.tdom[tile];
+    {
+        const int64_t p = (int64_t)tile * TP + tid;
+        for (int sl = 0; sl < 2; sl++) {
+            const SlotCoef cf = a.coef[tdom * 2 + sl];
+            if (cf.cV == 0 && cf.cK == 0 && cf.cKp == 0 && cf.cW == 0) continue;
+            const int64_t step = 2 * NCOMP * a.n_pts;  // one chunk
+            if (a.partial32) {
+                // all components at once: NCOMP independent loads per chunk
+                const float* src = a.partial32 + (int64_t)sl * NCOMP * a.n_pts + p;
+                float hi[NCOMP], lo[NCOMP];
+#pragma unroll
+                for (int c = 0; c < NCOMP; c++) hi[c] = lo[c] = 0.f;
+                for (int ch = 0; ch < a.n_chunks; ch++, src += step) {
+                    float x[NCOMP];
+#pragma unroll
+                    for (int c = 0; c < NCOMP; c++) x[c] = src[(int64_t)c * a.n_pts];
+#pragma unroll
+                    for (int c = 0; c < NCOMP; c++) {
+                        const float u = hi[c] + x[c];  // TwoSum: hi + x = u + (rounding error)
+                        const float xb = u - hi[c];
+                        lo[c] += (hi[c] - (u - xb)) + (x[c] - xb);
+                        hi[c] = u;
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < NCOMP; c++) Ps[sl][c][tid] = (double)hi[c] + (double)lo[c];
+            } else {
+                for (int c = 0; c < NCOMP; c++) {
+                    const double* src = a.partial64 + ((int64_t)sl * NCOMP + c) * a.n_pts + p;
+                    double sum = 0.0;
+                    for (int ch = 0; ch < a.n_chunks; ch++) sum += src[ch * step];
+                    Ps[sl][c][tid] = sum;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tid >= TT) return;
+    const int64_t s = (int64_t)tile * TT + tid;
     const int4 v = a.slot_v[s];
     if (v.x < 0) return;
-    const int dom = v.w;
+    const int dom = tdom;  // a tile holds triangles of one domain
     const double inv4pi = 0.07957747154594767;
     double r1[3][2] = {{0, 0}, {0, 0}, {0, 0}}, r2[3][2] = {{0, 0}, {0, 0}, {0, 0}};
     for (int sl = 0; sl < 2; sl++) {
@@ -597,14 +636,7 @@ __global__ void project_kernel(ProjectArgs a) {
         for (int q = 0; q < QP; q++) {
             const int64_t p = s * QP + q;
             double P[NCOMP];
-            for (int c = 0; c < NCOMP; c++) {
-                double sum = 0;
-                for (int ch = 0; ch < a.n_chunks; ch++) {
-                    const int64_t idx = ((int64_t)(ch * 2 + sl) * NCOMP + c) * a.n_pts + p;
-                    sum += a.partial32 ? (double)a.partial32[idx] : a.partial64[idx];
-                }
-                P[c] = sum;
-            }
+            for (int c = 0; c < NCOMP; c++) P[c] = Ps[sl][c][tid * QP + q];
             const double w = a.pt_w[p] * inv4pi;
             // row1 potential: cV PV - cK PK ; row2 (pointwise part): cKp PKp - cW k^2 PWm
             const double t1r = cf.cV * P[0] - cf.cK * P[2], t1i = cf.cV * P[1] - cf.cK * P[3];
@@ -662,9 +694,9 @@ __global__ void project_kernel(ProjectArgs a) {
 }
 
 cudaError_t launch_project(const ProjectArgs& a, cudaStream_t s) {
-    int64_t n = (int64_t)(a.tgt_end - a.tgt_begin) * TT;
-    if (n <= 0) return cudaSuccess;
-    project_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a);
+    const int n_tiles = a.tgt_end - a.tgt_begin;
+    if (n_tiles <= 0) return cudaSuccess;
+    project_kernel<<<(unsigned)n_tiles, TP, 0, s>>>(a);
     return cudaGetLastError();
 }
 
