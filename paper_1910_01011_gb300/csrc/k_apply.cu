@@ -579,7 +579,7 @@ cudaError_t launch_far64(const FarArgs64& a, int n_tgt_tiles, int n_chunks, cuda
 // FP32 sum in chunk order, converted to FP64 once: the GPU's FP64 rate is
 // a small fraction of its FP32 rate, and the compensation carries the
 // rounding error of every addition, so the result matches an FP64 sum of
-// the same FP32 values to ~1e-13 relative.
+// the same FP32 values to about 1e-15 of the sum of their magnitudes.
 __global__ void __launch_bounds__(TP) project_kernel(ProjectArgs a) {
     __shared__ double Ps[2][NCOMP][TP];
     const int tile = a.tgt_begin + blockIdx.x;
