@@ -241,7 +241,8 @@ def sphere_solve_metrics(local, reps=12):
     1.1, plane wave): seconds per solve of the mixed path (FP32 operator
     inside a flexible GMRES, FP64 residual refinement) against the plain FP64
     GPU path, both to an FP64 relative residual of 1e-9, and the p50 / p99 of
-    repeated mixed solves."""
+    repeated mixed solves; then the off-surface field of the solution on the
+    200 x 200 grid over +-3 R (the paper's sphere check) through bem_field."""
     import numpy as np
 
     from paper_1910_01011_gb300.api import Context
@@ -262,13 +263,30 @@ def sphere_solve_metrics(local, reps=12):
         r32 = c.solve(precision=1, tol=1e-9)
         t32.append(time.perf_counter() - t0)
     u32 = c.solution(0)
+    # off-surface field on a 200 x 200 grid over +-3 R in the xz-plane, through
+    # the public call with host arrays (copies and synchronisation included)
+    g1 = np.linspace(-3.0, 3.0, 200)
+    X, Z = np.meshgrid(g1, g1, indexing="ij")
+    pts = np.stack([X.ravel(), np.zeros(X.size), Z.ravel()], axis=1)
+    dom = np.where(np.linalg.norm(pts, axis=1) < 1.0, 0, -1).astype(np.int32)
+    c.field(pts, dom)  # warm-up
+    tf = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        c.field(pts, dom)
+        tf.append(time.perf_counter() - t0)
+    n_src = 6 * s.domains[0].tris.shape[0]
     c.close()
+    field = {"grid": "200 x 200 over +-3 R, xz-plane", "points": int(pts.shape[0]),
+             "ms_per_grid": 1e3 * float(np.median(tf)),
+             "ginteractions_per_s": pts.shape[0] * n_src / float(np.median(tf)) / 1e9}
     return {"workload": "unit sphere, icosphere level 3 (1280 triangles), k0=5, k1=5.25, rho ratio 1.1, plane wave",
             "tol_fp64_residual": 1e-9, "fp64_s_per_rhs": float(np.median(t64)), "mixed_s_per_rhs": float(np.median(t32)),
             "mixed_p50_s": float(np.percentile(t32, 50)), "mixed_p99_s": float(np.percentile(t32, 99)),
             "speedup_vs_fp64": float(np.median(t64) / np.median(t32)),
             "trace_rel_diff_mixed_vs_fp64": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
-            "iterations": {"fp64": r64["iterations"], "mixed": r32["iterations"], "refinements": r32["refinements"]}}
+            "iterations": {"fp64": r64["iterations"], "mixed": r32["iterations"], "refinements": r32["refinements"]},
+            "field": field}
 
 
 def rib_solve_metrics(local, n_rhs=16, tol=1e-8):

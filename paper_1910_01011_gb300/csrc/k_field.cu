@@ -42,6 +42,9 @@ struct FieldArgs {
     int n_elem, nq;
     double2 pref;
     double2* out;
+    int chunk_tiles;         // source tiles per grid.y index of the partial kernel
+    int n_chunks;
+    float4* partial;         // [n_chunks][n] (SL re, im, DL re, im) per source chunk
 };
 
 __device__ __forceinline__ float f_reduce_phase(double t) {
@@ -52,7 +55,10 @@ __device__ __forceinline__ float f_reduce_phase(double t) {
     return (float)r;
 }
 
-__global__ void __launch_bounds__(TP) field_kernel(FieldArgs a) {
+// Pass 1: the surface potentials of one block of TP points from one chunk of
+// source tiles (grid: point blocks x source chunks, so that a small set of
+// points still fills the GPU).
+__global__ void __launch_bounds__(TP) field_partial_kernel(FieldArgs a) {
     __shared__ float4 s_pg[TP], s_pd[TP], s_tg[TT];
     const int64_t i = (int64_t)blockIdx.x * TP + threadIdx.x;
     const bool live = i < a.n;
@@ -67,7 +73,8 @@ __global__ void __launch_bounds__(TP) field_kernel(FieldArgs a) {
     const double2 k = dom < 0 ? a.k0 : a.kdom[dom];
     const float kr = (float)k.x, nki = (float)-k.y, nkil2 = (float)(-k.y * 1.4426950408889634);
     float slr = 0, sli = 0, dlr = 0, dli = 0;
-    for (int s = 0; s < a.n_tiles; s++) {
+    const int s_begin = blockIdx.y * a.chunk_tiles, s_end = min(s_begin + a.chunk_tiles, a.n_tiles);
+    for (int s = s_begin; s < s_end; s++) {
         __syncthreads();
         const int64_t pb = (int64_t)s * TP;
         s_pg[threadIdx.x] = a.pg[pb + threadIdx.x];
@@ -110,7 +117,31 @@ __global__ void __launch_bounds__(TP) field_kernel(FieldArgs a) {
             dli += fK * S1i;
         }
     }
-    if (!live) return;
+    if (live) a.partial[(int64_t)blockIdx.y * a.n + i] = make_float4(slr, sli, dlr, dli);
+}
+
+// Pass 2, one thread per point: the chunks summed in chunk order (compensated
+// FP32 sums, converted to FP64 once), the representation formula's
+// combination and the incident field.
+__global__ void field_finish_kernel(FieldArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const double x = a.pts[3 * i], y = a.pts[3 * i + 1], z = a.pts[3 * i + 2];
+    const int dom = a.dom[i];
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int ch = 0; ch < a.n_chunks; ch++) {
+        const float4 v = a.partial[(int64_t)ch * a.n + i];
+        const float xv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const float u = hi[c] + xv[c];  // TwoSum: hi + x = u + (rounding error)
+            const float xb = u - hi[c];
+            lo[c] += (hi[c] - (u - xb)) + (xv[c] - xb);
+            hi[c] = u;
+        }
+    }
+    const double slr = (double)hi[0] + lo[0], sli = (double)hi[1] + lo[1];
+    const double dlr = (double)hi[2] + lo[2], dli = (double)hi[3] + lo[3];
     const double inv4pi = 0.07957747154594767;
     double pr, pi;
     if (dom >= 0) {
@@ -152,9 +183,22 @@ __global__ void __launch_bounds__(TP) field_kernel(FieldArgs a) {
     a.out[i] = make_double2(pr, pi);
 }
 
+// Source chunks per launch: enough CTAs for about eight per SM over the GPU
+// (152 SMs on GB300, read from the device), each chunk at least one tile.
+int field_chunks(int64_t n_points, int n_tiles, int n_sm) {
+    const int64_t blocks = (n_points + TP - 1) / TP;
+    int64_t want = (8LL * n_sm + blocks - 1) / blocks;
+    if (want < 1) want = 1;
+    if (want > n_tiles) want = n_tiles;
+    return (int)want;
+}
+
 cudaError_t launch_field(const FieldArgs& a, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    field_kernel<<<(unsigned)((a.n + TP - 1) / TP), TP, 0, s>>>(a);
+    field_partial_kernel<<<dim3((unsigned)((a.n + TP - 1) / TP), (unsigned)a.n_chunks), TP, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    field_finish_kernel<<<(unsigned)((a.n + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -231,10 +275,18 @@ extern "C" int bem_field(bem_ctx* ctx, int64_t rhs, const double* points, const 
     a.disc = disc; a.wts = wts; a.n_elem = n_elem; a.nq = nq;
     a.pref = make_double2(0.0, -ctx->omega_rho0 / (2.0 * M_PI));
     a.out = dout;
+    int n_sm = 0;
+    CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int want = field_chunks(n_points, g.n_tiles, n_sm);
+    a.chunk_tiles = (g.n_tiles + want - 1) / want;
+    a.n_chunks = (g.n_tiles + a.chunk_tiles - 1) / a.chunk_tiles;
+    a.partial = (float4*)ctx->dalloc((size_t)a.n_chunks * n_points * sizeof(float4), &rc);
+    if (rc) { ctx->dfree(drr); ctx->dfree(stage); return rc; }
     CK(launch_field(a, ctx->stream));
-    ctx->launches += 2;
+    ctx->launches += 3;
     if (!on_device) CK(cudaMemcpyAsync(out, dout, n_points * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->dfree(a.partial);
     ctx->dfree(drr);
     ctx->dfree(stage);
     return ctx->check_device_error();

@@ -72,3 +72,25 @@ def test_field_with_transducer_incident():
     ref = field.total_field(s, u, pts, dom, inc)
     assert rel(got, ref) < 1e-5
     c.close()
+
+
+def test_field_many_points_against_oracle_sample():
+    """A 200 x 200 grid: enough points that each CTA takes a chunk of several
+    source tiles; a seeded sample of the points against the oracle from the
+    same traces."""
+    from paper_1910_01011_gb300 import api
+    s = scenes.sphere_scene(3, k0=5.0, k1=5.25 + 0.1j)
+    c = api.Context.from_scene(s)
+    c.set_plane_wave((0, 0, 1))
+    assert c.solve(precision=0, tol=1e-11)["converged"]
+    D, N = c.traces(0)
+    u = np.concatenate([N, D])
+    pts, dom = grid(200)
+    got = c.field(pts, dom)
+    pick = np.random.default_rng(11).choice(pts.shape[0], size=300, replace=False)
+    ref = field.total_field(s, u, pts[pick], dom[pick], pmchwt.plane_wave(s.k0, (0, 0, 1)))
+    assert rel(got[pick], ref) < 1e-5
+    # the sampled points alone (one source tile per chunk) give the same values
+    alone = c.field(pts[pick], dom[pick])
+    assert rel(got[pick], alone) < 1e-6
+    c.close()
