@@ -129,6 +129,8 @@ static void release_device(bem_ctx* ctx) {
     ctx->asm_work_bytes = 0;
     ctx->partial = nullptr;
     ctx->partial_bytes = 0;
+    ctx->field_buf = nullptr;
+    ctx->field_buf_bytes = 0;
     ctx->far_work = nullptr;
     for (int& k : ctx->far_work_key) k = -1;
     ctx->pmchwt_near = NearSet();

@@ -103,6 +103,8 @@ struct bem_ctx {
     std::vector<gbem::BlockCache> block_cache;
     void* partial = nullptr;
     size_t partial_bytes = 0;
+    void* field_buf = nullptr;  // bem_field scratch (grow-only)
+    size_t field_buf_bytes = 0;
     // far-field work list (heaviest (target tile, chunk) first) and the launch it was built for
     int2* far_work = nullptr;
     int far_work_key[6] = {-1, -1, -1, -1, -1, -1};

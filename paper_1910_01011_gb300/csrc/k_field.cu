@@ -242,18 +242,37 @@ extern "C" int bem_field(bem_ctx* ctx, int64_t rhs, const double* points, const 
         for (int kk = 0; kk < 3; kk++) ga.lam[q][kk] = ctx->quad.lam[q][kk];
     ga.pd32 = ctx->dev.pd32; ga.tcurl32 = ctx->dev.tcurl32;
     CK(launch_gather(ga, ctx->stream));
+    // one grow-only scratch buffer: chunk partials | output | points | rho ratios | domain ids
+    int n_sm = 0;
+    CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int want = field_chunks(n_points, g.n_tiles, n_sm);
+    const int chunk_tiles = (g.n_tiles + want - 1) / want;
+    const int n_chunks = (g.n_tiles + chunk_tiles - 1) / chunk_tiles;
+    auto up16 = [](size_t b) { return (b + 15) / 16 * 16; };
+    const size_t b_part = up16((size_t)n_chunks * n_points * sizeof(float4));
+    const size_t b_out = on_device ? 0 : up16((size_t)n_points * sizeof(double2));
+    const size_t b_pts = on_device ? 0 : up16((size_t)n_points * 3 * sizeof(double));
+    const size_t b_rr = up16((size_t)g.n_dom * sizeof(double));
+    const size_t b_dom = on_device ? 0 : up16((size_t)n_points * sizeof(int32_t));
+    const size_t need = b_part + b_out + b_pts + b_rr + b_dom;
+    if (need > ctx->field_buf_bytes) {
+        ctx->dfree(ctx->field_buf);
+        ctx->field_buf_bytes = 0;
+        ctx->field_buf = ctx->dalloc(need, &rc);
+        if (rc) { ctx->field_buf = nullptr; return rc; }
+        ctx->field_buf_bytes = need;
+    }
+    char* buf = (char*)ctx->field_buf;
+    float4* part = (float4*)buf;
+    double* drr = (double*)(buf + b_part + b_out + b_pts);
     // point arrays on the device
     const double* dp = points;
     const int32_t* dd = domain_of_point;
     double2* dout = (double2*)out;
-    void* stage = nullptr;
     if (!on_device) {
-        stage = ctx->dalloc((size_t)n_points * (3 * sizeof(double) + sizeof(int32_t) + sizeof(double2)) + 64, &rc);
-        if (rc) return rc;
-        // 16-byte values first so that every array stays aligned for any n
-        double2* so = (double2*)stage;
-        double* sp = (double*)(so + n_points);
-        int32_t* sd = (int32_t*)(sp + 3 * n_points);
+        double2* so = (double2*)(buf + b_part);
+        double* sp = (double*)(buf + b_part + b_out);
+        int32_t* sd = (int32_t*)(buf + b_part + b_out + b_pts + b_rr);
         CK(cudaMemcpyAsync(sp, points, n_points * 3 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(sd, domain_of_point, n_points * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
         dp = sp;
@@ -262,8 +281,6 @@ extern "C" int bem_field(bem_ctx* ctx, int64_t rhs, const double* points, const 
     }
     std::vector<double> rr(g.n_dom);
     for (int j = 0; j < g.n_dom; j++) rr[j] = ctx->doms[j].rho / ctx->rho0;
-    double* drr = (double*)ctx->dalloc(g.n_dom * sizeof(double), &rc);
-    if (rc) { ctx->dfree(stage); return rc; }
     CK(cudaMemcpyAsync(drr, rr.data(), g.n_dom * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     FieldArgs a{};
     a.pts = dp; a.dom = dd; a.n = n_points;
@@ -275,19 +292,12 @@ extern "C" int bem_field(bem_ctx* ctx, int64_t rhs, const double* points, const 
     a.disc = disc; a.wts = wts; a.n_elem = n_elem; a.nq = nq;
     a.pref = make_double2(0.0, -ctx->omega_rho0 / (2.0 * M_PI));
     a.out = dout;
-    int n_sm = 0;
-    CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
-    const int want = field_chunks(n_points, g.n_tiles, n_sm);
-    a.chunk_tiles = (g.n_tiles + want - 1) / want;
-    a.n_chunks = (g.n_tiles + a.chunk_tiles - 1) / a.chunk_tiles;
-    a.partial = (float4*)ctx->dalloc((size_t)a.n_chunks * n_points * sizeof(float4), &rc);
-    if (rc) { ctx->dfree(drr); ctx->dfree(stage); return rc; }
+    a.chunk_tiles = chunk_tiles;
+    a.n_chunks = n_chunks;
+    a.partial = part;
     CK(launch_field(a, ctx->stream));
     ctx->launches += 3;
     if (!on_device) CK(cudaMemcpyAsync(out, dout, n_points * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    ctx->dfree(a.partial);
-    ctx->dfree(drr);
-    ctx->dfree(stage);
     return ctx->check_device_error();
 }
