@@ -22,6 +22,7 @@
 #include <cstdio>
 
 #include "internal.h"
+#include "pair_math.h"
 
 namespace gbem {
 
@@ -85,11 +86,6 @@ __device__ __forceinline__ float reduce_phase(double t) {
     return (float)r;
 }
 
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 // ----------------------------------------------------------------- gather (trial densities)
 
@@ -180,31 +176,8 @@ struct Acc {
 // pair j (points 2j and 2j+1) is the float4 (x_a, x_b, y_a, y_b) followed by
 // (z_a, z_b, w_a, w_b), for the source geometry (offsets from the tile
 // centre and weight) and for the gathered densities (the two complex
-// densities in place of x, y and z, w).
-typedef float2 f2;
-
-__device__ __forceinline__ f2 bc2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ f2 lo2(const float4& v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ f2 hi2(const float4& v) { return make_float2(v.z, v.w); }
-__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ f2 neg2(f2 a) { return make_float2(-a.x, -a.y); }
-
-__device__ __forceinline__ float rsqrt_approx(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ void sincos_approx(float x, float* s, float* c) {
-    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(x));
-    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(x));
-}
+// densities in place of x, y and z, w).  The packed helpers are in
+// pair_math.h.
 
 // One wavenumber slot, both lanes.
 struct PairK {

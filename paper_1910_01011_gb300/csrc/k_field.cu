@@ -17,6 +17,7 @@
 
 #include "ctx.h"
 #include "internal.h"
+#include "pair_math.h"
 
 namespace gbem {
 
@@ -24,8 +25,8 @@ struct FieldArgs {
     const double* pts;      // [n][3]
     const int32_t* dom;     // [n] -1 exterior, else domain
     int64_t n;
-    const float4* pg;       // source points (dx, dy, dz, w)
-    const float4* pd;       // densities (w psi, w phi)
+    const float4* pg;       // source points (dx, dy, dz, w), pair-interleaved
+    const float4* pd;       // densities (w psi, w phi), pair-interleaved
     const float4* tg;       // triangles (n, h)
     const double4* tc;
     const int* tntri;
@@ -55,6 +56,62 @@ __device__ __forceinline__ float f_reduce_phase(double t) {
     return (float)r;
 }
 
+// One point against one source tile, two source points per packed FP32
+// instruction: the single-layer sum over the tile and, per triangle, the
+// double-layer sum n_t.(y - x) F sigma_D.  With D = x - c_source (2D in
+// D2x..z), a source offset g from its tile centre gives
+// r^2 - R_c^2 = g.(g - 2D).  As in the far-field kernel, -F is formed:
+// -Re F = P Gr + B Gi, -Im F = P Gi - B Gr with P = Im k / r + 1/r^2,
+// B = Re k / r.
+template <bool LOSSY>
+__device__ __forceinline__ void field_tile(const float4* s_pg, const float4* s_pd, const float4* s_tg, int ntri,
+                                           float D2x, float D2y, float D2z, f2 Rc2, f2 Rc, f2 th, f2 kr, f2 nkr, f2 ki,
+                                           f2 nkil2, float& slr, float& sli, float& dlr, float& dli) {
+    const f2 m2x = bc2(-D2x), m2y = bc2(-D2y), m2z = bc2(-D2z);
+    const f2 z2 = make_float2(0.f, 0.f);
+    f2 Vr = z2, Vi = z2;
+    for (int tl = 0; tl < ntri; tl++) {
+        const float4 tgv = s_tg[tl];
+        const float fK = tgv.w - 0.5f * (tgv.x * D2x + tgv.y * D2y + tgv.z * D2z);  // n_t.(y - x)
+        f2 nS1r = z2, nS1i = z2;
+#pragma unroll
+        for (int j = 0; j < QP / 2; j++) {
+            const float4 GA = s_pg[tl * QP + 2 * j], GB = s_pg[tl * QP + 2 * j + 1];
+            const float4 DA = s_pd[tl * QP + 2 * j], DB = s_pd[tl * QP + 2 * j + 1];
+            const f2 gx = lo2(GA), gy = hi2(GA), gz = lo2(GB);
+            const f2 d1r = lo2(DA), d1i = hi2(DA), d2r = lo2(DB), d2i = hi2(DB);
+            const f2 s = fma2(gx, add2(gx, m2x), fma2(gy, add2(gy, m2y), mul2(gz, add2(gz, m2z))));
+            const f2 r2 = add2(s, Rc2);
+            const f2 rinv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+            const f2 den = fma2(r2, rinv, Rc);  // r + R_c
+            const f2 rho = mul2(s, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+            const f2 arg = fma2(kr, rho, th);
+            f2 sn, cs;
+            sincos_approx(arg.x, &sn.x, &cs.x);
+            sincos_approx(arg.y, &sn.y, &cs.y);
+            const f2 rinv2 = mul2(rinv, rinv);
+            f2 am = rinv;
+            if constexpr (LOSSY) {
+                const f2 e = mul2(nkil2, mul2(r2, rinv));
+                am = mul2(make_float2(ex2_approx(e.x), ex2_approx(e.y)), rinv);
+            }
+            const f2 Gr = mul2(am, cs), Gi = mul2(am, sn);
+            const f2 nd1i = neg2(d1i), nd2i = neg2(d2i);
+            Vr = fma2(Gr, d1r, fma2(Gi, nd1i, Vr));
+            Vi = fma2(Gr, d1i, fma2(Gi, d1r, Vi));
+            const f2 P = LOSSY ? fma2(ki, rinv, rinv2) : rinv2;
+            const f2 B = mul2(kr, rinv), nB = mul2(nkr, rinv);
+            const f2 nFr = fma2(P, Gr, mul2(B, Gi)), nFi = fma2(P, Gi, mul2(nB, Gr));
+            nS1r = fma2(nFr, d2r, fma2(nFi, nd2i, nS1r));
+            nS1i = fma2(nFr, d2i, fma2(nFi, d2r, nS1i));
+        }
+        dlr = fmaf(-fK, nS1r.x + nS1r.y, dlr);
+        dli = fmaf(-fK, nS1i.x + nS1i.y, dli);
+    }
+    slr += Vr.x + Vr.y;
+    sli += Vi.x + Vi.y;
+}
+
 // Pass 1: the surface potentials of one block of TP points from one chunk of
 // source tiles (grid: point blocks x source chunks, so that a small set of
 // points still fills the GPU).
@@ -71,7 +128,9 @@ __global__ void __launch_bounds__(TP) field_partial_kernel(FieldArgs a) {
         dom = a.dom[i];
     }
     const double2 k = dom < 0 ? a.k0 : a.kdom[dom];
-    const float kr = (float)k.x, nki = (float)-k.y, nkil2 = (float)(-k.y * 1.4426950408889634);
+    const bool lossy = k.y != 0.0;
+    const f2 kr2 = bc2((float)k.x), nkr2 = bc2((float)-k.x), ki2 = bc2((float)k.y);
+    const f2 nkil2 = bc2((float)(-k.y * 1.4426950408889634));
     float slr = 0, sli = 0, dlr = 0, dli = 0;
     const int s_begin = blockIdx.y * a.chunk_tiles, s_end = min(s_begin + a.chunk_tiles, a.n_tiles);
     for (int s = s_begin; s < s_end; s++) {
@@ -88,34 +147,12 @@ __global__ void __launch_bounds__(TP) field_partial_kernel(FieldArgs a) {
         const float D2x = (float)(2 * Dx), D2y = (float)(2 * Dy), D2z = (float)(2 * Dz);
         const float Rc2 = (float)(R * R), Rc = (float)R, th = f_reduce_phase(k.x * R);
         const int ntri = a.tntri[s];
-        for (int tl = 0; tl < ntri; tl++) {
-            const float4 tgv = s_tg[tl];
-            const float fK = tgv.w - 0.5f * (tgv.x * D2x + tgv.y * D2y + tgv.z * D2z);  // n_t.(y - x)
-            float S1r = 0, S1i = 0;
-#pragma unroll
-            for (int q = 0; q < QP; q++) {
-                const float4 g = s_pg[tl * QP + q];
-                const float4 d = pair_point(s_pd + tl * QP, q);
-                const float ex = -g.x, ey = -g.y, ez = -g.z;
-                const float sd = ex * (D2x + ex) + ey * (D2y + ey) + ez * (D2z + ez);
-                const float r2 = Rc2 + sd;
-                const float rinv = rsqrtf(r2);
-                const float r = r2 * rinv;
-                const float rho = __fdividef(sd, r + Rc);
-                float sn, cs;
-                __sincosf(fmaf(kr, rho, th), &sn, &cs);
-                const float am = (nki != 0.f ? exp2f(nkil2 * r) : 1.f) * rinv;
-                const float Gr = am * cs, Gi = am * sn;
-                const float u = nki - rinv;
-                const float Fr = (Gr * u - Gi * kr) * rinv, Fi = (Gr * kr + Gi * u) * rinv;
-                slr += Gr * d.x - Gi * d.y;
-                sli += Gr * d.y + Gi * d.x;
-                S1r += Fr * d.z - Fi * d.w;
-                S1i += Fr * d.w + Fi * d.z;
-            }
-            dlr += fK * S1r;
-            dli += fK * S1i;
-        }
+        if (lossy)
+            field_tile<true>(s_pg, s_pd, s_tg, ntri, D2x, D2y, D2z, bc2(Rc2), bc2(Rc), bc2(th), kr2, nkr2, ki2, nkil2,
+                             slr, sli, dlr, dli);
+        else
+            field_tile<false>(s_pg, s_pd, s_tg, ntri, D2x, D2y, D2z, bc2(Rc2), bc2(Rc), bc2(th), kr2, nkr2, ki2, nkil2,
+                              slr, sli, dlr, dli);
     }
     if (live) a.partial[(int64_t)blockIdx.y * a.n + i] = make_float4(slr, sli, dlr, dli);
 }
@@ -284,7 +321,7 @@ extern "C" int bem_field(bem_ctx* ctx, int64_t rhs, const double* points, const 
     CK(cudaMemcpyAsync(drr, rr.data(), g.n_dom * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     FieldArgs a{};
     a.pts = dp; a.dom = dd; a.n = n_points;
-    a.pg = ctx->dev.pg32; a.pd = ctx->dev.pd32; a.tg = ctx->dev.tg32; a.tc = ctx->dev.tc; a.tntri = ctx->dev.tntri;
+    a.pg = ctx->dev.pgp32; a.pd = ctx->dev.pd32; a.tg = ctx->dev.tg32; a.tc = ctx->dev.tc; a.tntri = ctx->dev.tntri;
     a.tdom = ctx->dev.tdom; a.kdom = ctx->dev.kdom; a.rho_ratio = drr; a.k0 = make_double2(ctx->k0re, ctx->k0im);
     a.n_tiles = g.n_tiles; a.inc_kind = ctx->field_kind;
     for (int c = 0; c < 3; c++) a.pw_d[c] = ctx->pw_dir[c];
