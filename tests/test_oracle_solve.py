@@ -114,6 +114,86 @@ def test_osrc_dtn_on_sphere_harmonics():
         assert np.linalg.norm(y - sym * f) / np.linalg.norm(sym * f) < 2e-2
 
 
+def _harmonics(v):
+    z = v[:, 2] / np.linalg.norm(v, axis=1)
+    return ((1, z), (2, 3 * z ** 2 - 1), (3, 5 * z ** 3 - 3 * z))
+
+
+def ntd_symbol(n, P, n_pade=8, theta=np.pi / 3):
+    """(i k)^-1 R(X) / (1 + X) on degree-n harmonics of the unit sphere,
+    X = -n(n+1)/k_eps^2, R the rotated Pade square root: the NtD map of
+    eq. OSRC_DtN_NtD_maps with the (1+X)^-1 sqrt(1+X) reading."""
+    X = -n * (n + 1) / P.keps ** 2
+    return osrc.pade_sqrt(X, n_pade, theta) / (1 + X) / (1j * P.k)
+
+
+def dtn_symbol(n, P, n_pade=8, theta=np.pi / 3):
+    return 1j * P.k * osrc.pade_sqrt(-n * (n + 1) / P.keps ** 2, n_pade, theta)
+
+
+def _ntd_errors(ntd, L, k=5.0):
+    v, t = meshes.icosphere(L)
+    P = osrc.DomainOSRC(v, t, k, R_eps=0.5, n_pade=8)
+    out = []
+    for n, f in _harmonics(v):
+        sym = ntd_symbol(n, P)
+        y = ntd(P, f.astype(complex))
+        out.append(np.linalg.norm(y - sym * f) / np.linalg.norm(sym * f))
+    return np.array(out)
+
+
+def test_osrc_ntd_on_sphere_harmonics():
+    """Discrete NtD (strong form (ik)^-1 (M - S/k_eps^2)^-1 [C0 M u - ...]) on
+    spherical harmonics of degree 1..3 against its symbol
+    (ik)^-1 R(X)/(1+X), X = -n(n+1)/k_eps^2, converging at O(h^2); the
+    symbol itself is within the Pade error of the closed form
+    (ik)^-1 (1+X)^-1/2.  Planted mistakes fail: the (M - S/k_eps^2)^-1 dropped,
+    or the sign of S/k_eps^2 flipped."""
+    import scipy.sparse.linalg as spla
+    errs = {L: _ntd_errors(lambda P, f: P.ntd_strong(f), L) for L in (2, 3, 4)}
+    assert errs[4].max() < 3e-3
+    for L in (2, 3):
+        assert (errs[L] / errs[L + 1]).min() > 3.5
+    v, t = meshes.icosphere(2)
+    P = osrc.DomainOSRC(v, t, 5.0, R_eps=0.5, n_pade=8)
+    for n in (1, 2, 3):
+        closed = 1 / (1j * P.k * np.sqrt(1 - n * (n + 1) / P.keps ** 2))
+        assert abs(ntd_symbol(n, P) - closed) / abs(closed) < 3e-3
+
+    def dropped(P, f):
+        return P.bracket(f) / (1j * P.k)
+
+    def flipped(P, f):
+        return spla.splu((P.M + P.S / P.keps ** 2).astype(complex).tocsc()).solve(P.bracket(f)) / (1j * P.k)
+    assert _ntd_errors(dropped, 3).min() > 0.5
+    assert _ntd_errors(flipped, 3).min() > 0.1
+
+
+def test_osrc_composition_on_sphere_harmonics():
+    """osrc.apply on Galerkin rows [M f; M g] of one sphere: the DtN acts on
+    the V row and the NtD on the W row (eq. OSRC_prec_blocks with the column
+    permutation of Sec. 2.3), giving [DtN_n f; NtD_n g] up to O(h^2); the
+    roles swapped fail."""
+    res = {}
+    for L in (2, 3):
+        s = scenes.sphere_scene(L, k0=5.0)
+        d = s.domains[0]
+        pre = osrc.build(s, R_eps=0.5, n_pade=8)
+        P = pre[0]
+        M = galerkin.mass_matrix(d.verts, d.tris)
+        e, e_swapped = [], []
+        for (n, f), (m, g) in zip(_harmonics(d.verts), _harmonics(d.verts)[::-1]):
+            y = osrc.apply(s, pre, np.concatenate([M @ f, M @ g]).astype(complex))
+            ref = np.concatenate([dtn_symbol(n, P) * f, ntd_symbol(m, P) * g])
+            e.append(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+            swapped = np.concatenate([ntd_symbol(n, P) * f, dtn_symbol(m, P) * g])
+            e_swapped.append(np.linalg.norm(y - swapped) / np.linalg.norm(swapped))
+        res[L] = np.array(e)
+        assert min(e_swapped) > 0.5
+    assert res[3].max() < 0.01
+    assert (res[2] / res[3]).min() > 3.0
+
+
 def test_preconditioned_gmres_same_solution_fewer_iterations(sphere_solves):
     s, u, A, b = sphere_solves[3]
     pre = osrc.build(s, R_eps=0.1, n_pade=4)
@@ -137,17 +217,3 @@ def test_rayleigh_piston_on_axis():
     R1 = np.sqrt(z ** 2 + a ** 2)
     dex = 1000 * 1500 * (1j * k0 * np.exp(1j * k0 * z) - 1j * k0 * z / R1 * np.exp(1j * k0 * R1))
     assert np.abs(dp - dex).max() / np.abs(dex).max() < 1e-9
-
-
-def test_multi_domain_solve_consistency():
-    """Two spheres: the dense solution satisfies the system, the exterior
-    Calderon identity holds for the total field, and each block of A_hat is
-    the paper's Calderon block of its pair."""
-    s = scenes.two_sphere_scene(1)
-    u, A, b = pmchwt.solve(s, pmchwt.plane_wave(s.k0, s.plane_wave_dir))
-    assert np.linalg.norm(A @ u - b) / np.linalg.norm(b) < 1e-12
-    n = pmchwt.offsets(s)
-    d0, d1 = s.domains
-    V, K, Kp, W = galerkin.operator_rows(d0.verts, d0.tris, d1.verts, d1.tris, False, s.k0)
-    ref = np.block([[V, -K], [Kp, W]])
-    assert np.abs(A[n[0]:n[1], n[1]:n[2]] - ref).max() < 1e-15 * np.abs(ref).max() * 10
