@@ -147,7 +147,11 @@ int bem_apply_block(bem_ctx* ctx, int32_t test_domain, int32_t trial_domain, bem
  * share the array: calls that overlap on the GPU (other streams or other
  * contexts on the same device) race on it and must be serialised by the
  * caller.  The scratch is fully rewritten by every call; nothing needs to be
- * cleared between calls. */
+ * cleared between calls.  The call does not synchronise, so a bounded wait
+ * that timed out inside its kernels is not reported by it: the kernel sets
+ * the context's device error flag, and the next call that checks the flag
+ * (bem_apply with on_device = 0, bem_solve, bem_field) returns
+ * BEM_ERR_TIMEOUT and clears it. */
 int bem_apply_noalloc(bem_ctx* ctx, const bem_z* x, bem_z* y);
 
 /* Dense complex product on the tensor cores: Y = A X with A (m x k),
@@ -294,7 +298,9 @@ int bem_autotune(bem_ctx* ctx, int precision, int32_t* chunk_tiles, double* best
  * domain_of_point[i] = j, SL_kj((rho_j/rho_0) gamma_N p) - DL_kj(gamma_D p)
  * over domain j.  points: [n][3] doubles, out: n complex.  The caller says
  * which domain holds each point.  Accuracy degrades within about one element
- * size of a surface (regular rule). */
+ * size of a surface (regular rule).  Domain ids outside [-1, number of
+ * domains) give BEM_ERR_INVALID_ARG: checked on the host for host arrays, by
+ * the kernels for device arrays (those points are skipped and written as NaN). */
 int bem_field(bem_ctx* ctx, int64_t rhs, const double* points, const int32_t* domain_of_point, int64_t n_points,
               bem_z* out, int on_device);
 

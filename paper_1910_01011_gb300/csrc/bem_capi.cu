@@ -520,6 +520,7 @@ int bem_ctx::check_device_error() {
     CK(cudaStreamSynchronize(stream));
     if (h) {
         CK(cudaMemsetAsync(dev.err, 0, sizeof(int), stream));
+        if (h & 4) return fail(BEM_ERR_INVALID_ARG, "a device-side input index was out of range (checked by a kernel)");
         return fail(BEM_ERR_TIMEOUT, "a device-side wait timed out (error flag set by a kernel)");
     }
     return BEM_OK;

@@ -118,8 +118,9 @@ struct FarArgs32 {
     int tgt_begin;          // first target tile (grid.x offset)
     int chunk_tiles;        // source tiles per grid.y index
     int slot1;              // 1: interior wavenumber on own-domain sources
-    int64_t n_pts;
-    float* partial;         // [grid.y][2][NCOMP][n_pts]
+    int64_t n_pts;          // points per (chunk, slot, component) row of partial
+    int64_t p_off;          // point number stored at column 0 of partial (0 unless a caller batches targets)
+    float* partial;         // [grid.y][2][NCOMP][n_pts], column p - p_off for point p
     int* err;               // device error flag (bounded waits)
     const int2* work;       // null: grid (target tiles, chunks); else [n_work] (target tile offset, chunk)
                             // in launch order, heaviest first, on a 1-D grid
@@ -169,6 +170,7 @@ struct ProjectArgs {
     int tgt_begin, tgt_end;     // target tiles
     int n_chunks;
     int64_t n_pts;
+    int64_t p_off;              // point number at column 0 of the partials (as FarArgs32::p_off)
     const float* partial32;     // one of the two is non-null
     const double* partial64;
     // touching-pair correction (may be empty)

@@ -411,11 +411,11 @@ __device__ __forceinline__ void far32_item(const FarArgs32& A, int tx, int cy) {
         }
     }
 
-    float* out = A.partial + (int64_t)cy * 2 * NCOMP * A.n_pts;
+    float* out = A.partial + (int64_t)cy * 2 * NCOMP * A.n_pts + (p - A.p_off);
 #pragma unroll
     for (int c = 0; c < NCOMP; c++) {
-        out[(int64_t)c * A.n_pts + p] = a0.v[c];
-        out[(int64_t)(NCOMP + c) * A.n_pts + p] = a1.v[c];
+        out[(int64_t)c * A.n_pts] = a0.v[c];
+        out[(int64_t)(NCOMP + c) * A.n_pts] = a1.v[c];
     }
 }
 
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(TP) project_kernel(ProjectArgs a) {
             const int64_t step = 2 * NCOMP * a.n_pts;  // one chunk
             if (a.partial32) {
                 // all components at once: NCOMP independent loads per chunk
-                const float* src = a.partial32 + (int64_t)sl * NCOMP * a.n_pts + p;
+                const float* src = a.partial32 + (int64_t)sl * NCOMP * a.n_pts + (p - a.p_off);
                 float hi[NCOMP], lo[NCOMP];
 #pragma unroll
                 for (int c = 0; c < NCOMP; c++) hi[c] = lo[c] = 0.f;
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(TP) project_kernel(ProjectArgs a) {
                 for (int c = 0; c < NCOMP; c++) Ps[sl][c][tid] = (double)hi[c] + (double)lo[c];
             } else {
                 for (int c = 0; c < NCOMP; c++) {
-                    const double* src = a.partial64 + ((int64_t)sl * NCOMP + c) * a.n_pts + p;
+                    const double* src = a.partial64 + ((int64_t)sl * NCOMP + c) * a.n_pts + (p - a.p_off);
                     double sum = 0.0;
                     for (int ch = 0; ch < a.n_chunks; ch++) sum += src[ch * step];
                     Ps[sl][c][tid] = sum;

@@ -33,6 +33,8 @@ struct FieldArgs {
     const int* tdom;
     const double2* kdom;
     const double* rho_ratio; // [n_dom]
+    int n_dom;
+    int* err;                // device error flag: value 4 or-ed in for a domain id out of range
     double2 k0;
     int n_tiles;
     int inc_kind;            // 1 plane wave, 2 pistons
@@ -127,6 +129,9 @@ __global__ void __launch_bounds__(TP) field_partial_kernel(FieldArgs a) {
         z = a.pts[3 * i + 2];
         dom = a.dom[i];
     }
+    const bool bad = live && (dom < -1 || dom >= a.n_dom);  // device-side ids are checked here
+    const bool use = live && !bad;
+    if (bad) dom = -1;
     const double2 k = dom < 0 ? a.k0 : a.kdom[dom];
     const bool lossy = k.y != 0.0;
     const f2 kr2 = bc2((float)k.x), nkr2 = bc2((float)-k.x), ki2 = bc2((float)k.y);
@@ -140,7 +145,7 @@ __global__ void __launch_bounds__(TP) field_partial_kernel(FieldArgs a) {
         s_pd[threadIdx.x] = a.pd[pb + threadIdx.x];
         if (threadIdx.x < TT) s_tg[threadIdx.x] = a.tg[(int64_t)s * TT + threadIdx.x];
         __syncthreads();
-        if (!live || (dom >= 0 && a.tdom[s] != dom)) continue;
+        if (!use || (dom >= 0 && a.tdom[s] != dom)) continue;
         const double4 c = a.tc[s];
         const double Dx = x - c.x, Dy = y - c.y, Dz = z - c.z;  // x - c_source
         const double R = sqrt(Dx * Dx + Dy * Dy + Dz * Dz);
@@ -155,6 +160,7 @@ __global__ void __launch_bounds__(TP) field_partial_kernel(FieldArgs a) {
                               slr, sli, dlr, dli);
     }
     if (live) a.partial[(int64_t)blockIdx.y * a.n + i] = make_float4(slr, sli, dlr, dli);
+    if (bad && blockIdx.y == 0) atomicOr(a.err, 4);
 }
 
 // Pass 2, one thread per point: the chunks summed in chunk order (compensated
@@ -165,6 +171,10 @@ __global__ void field_finish_kernel(FieldArgs a) {
     if (i >= a.n) return;
     const double x = a.pts[3 * i], y = a.pts[3 * i + 1], z = a.pts[3 * i + 2];
     const int dom = a.dom[i];
+    if (dom < -1 || dom >= a.n_dom) {  // reported through the error flag by the partial kernel
+        a.out[i] = make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
+        return;
+    }
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
     for (int ch = 0; ch < a.n_chunks; ch++) {
         const float4 v = a.partial[(int64_t)ch * a.n + i];
@@ -266,7 +276,7 @@ extern "C" int bem_field(bem_ctx* ctx, int64_t rhs, const double* points, const 
     int rc = solve_field_inputs(ctx, rhs, &u, &disc, &wts, &n_elem, &nq);
     if (rc) return rc;
     const Geometry& g = ctx->geo;
-    // check the domain ids on the host copy (device ids are checked by the caller's contract)
+    // check the domain ids of a host array here; the kernels check device arrays
     if (!on_device)
         for (int64_t i = 0; i < n_points; i++)
             if (domain_of_point[i] < -1 || domain_of_point[i] >= g.n_dom)
@@ -323,6 +333,7 @@ extern "C" int bem_field(bem_ctx* ctx, int64_t rhs, const double* points, const 
     a.pts = dp; a.dom = dd; a.n = n_points;
     a.pg = ctx->dev.pgp32; a.pd = ctx->dev.pd32; a.tg = ctx->dev.tg32; a.tc = ctx->dev.tc; a.tntri = ctx->dev.tntri;
     a.tdom = ctx->dev.tdom; a.kdom = ctx->dev.kdom; a.rho_ratio = drr; a.k0 = make_double2(ctx->k0re, ctx->k0im);
+    a.n_dom = g.n_dom; a.err = ctx->dev.err;
     a.n_tiles = g.n_tiles; a.inc_kind = ctx->field_kind;
     for (int c = 0; c < 3; c++) a.pw_d[c] = ctx->pw_dir[c];
     a.pw_amp = make_double2(ctx->pw_amp[0], ctx->pw_amp[1]);

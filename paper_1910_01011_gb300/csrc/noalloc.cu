@@ -89,23 +89,21 @@ extern "C" int bem_apply_noalloc(bem_ctx* ctx, const bem_z* x, bem_z* y) {
     for (int tb = 0; tb < n_tiles; tb += batch) {
         const int te = std::min(n_tiles, tb + batch);
         const int64_t stride = (int64_t)(te - tb) * TP;
-        // The kernels index the partial buffer by absolute point number p as
-        // base[(chunk, slot, component) * stride + p]; shifting the base by
-        // the batch's first point keeps every access inside the scratch.
-        float* base = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(scratch) -
-                                               (uintptr_t)((int64_t)tb * TP * (int64_t)sizeof(float)));
+        // The scratch holds the batch's points only: point p of the batch is
+        // column p - p_off of each (chunk, slot, component) row of length stride.
+        const int64_t p_off = (int64_t)tb * TP;
         FarArgs32 fa{};
         fa.pg = ctx->dev.pg32; fa.pgp = ctx->dev.pgp32; fa.tg = ctx->dev.tg32; fa.tc = ctx->dev.tc; fa.tdom = ctx->dev.tdom;
         fa.tntri = ctx->dev.tntri; fa.pd = ctx->dev.pd32; fa.tcurl = ctx->dev.tcurl32;
         fa.dom_tiles = ctx->dev.dom_tiles; fa.kdom = ctx->dev.kdom;
         fa.k0 = make_double2(ctx->k0re, ctx->k0im);
         fa.src_begin = 0; fa.src_end = n_tiles; fa.tgt_begin = tb; fa.chunk_tiles = chunk_tiles; fa.slot1 = 1;
-        fa.n_pts = stride; fa.partial = base; fa.err = ctx->dev.err;
+        fa.n_pts = stride; fa.p_off = p_off; fa.partial = scratch; fa.err = ctx->dev.err;
         CK(launch_far32(fa, te - tb, n_chunks, ctx->stream));
         ProjectArgs pa{};
         pa.slot_v = ctx->dev.slot_v; pa.pt_w = ctx->dev.pt_w; pa.slot_curl = ctx->dev.slot_curl;
         pa.tntri = ctx->dev.tntri; pa.tdom = ctx->dev.tdom; pa.coef = ctx->dev.coef;
-        pa.tgt_begin = tb; pa.tgt_end = te; pa.n_chunks = n_chunks; pa.n_pts = stride; pa.partial32 = base;
+        pa.tgt_begin = tb; pa.tgt_end = te; pa.n_chunks = n_chunks; pa.n_pts = stride; pa.p_off = p_off; pa.partial32 = scratch;
         if (ctx->pmchwt_near.n_pairs > 0) {
             pa.np_ptr = ctx->dev.np_ptr; pa.np_src = ctx->dev.np_src; pa.nb32 = ctx->pmchwt_near.nb32;
         }

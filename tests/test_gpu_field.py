@@ -94,3 +94,35 @@ def test_field_many_points_against_oracle_sample():
     alone = c.field(pts[pick], dom[pick])
     assert rel(got[pick], alone) < 1e-6
     c.close()
+
+
+def test_field_device_domain_ids_checked_by_the_kernels():
+    """Domain ids in a device array are range-checked by the field kernels:
+    an id beyond the domain count gives INVALID_ARG (and NaN at that point)
+    instead of an out-of-range read, and the context stays usable."""
+    import ctypes
+
+    import torch
+
+    from paper_1910_01011_gb300 import api
+    s = scenes.sphere_scene(1)
+    c = api.Context.from_scene(s)
+    c.set_plane_wave((0, 0, 1))
+    assert c.solve(precision=0, tol=1e-10)["converged"]
+    pts, dom = grid(9)
+    good = c.field(pts, dom)
+    dom_bad = dom.copy()
+    dom_bad[3] = 5  # one domain only
+    dp = torch.from_numpy(pts).cuda()
+    dd = torch.from_numpy(dom_bad).cuda()
+    out = torch.zeros(pts.shape[0], dtype=torch.complex128, device="cuda")
+    rc = c.lib.bem_field(c.h, 0, ctypes.c_void_p(dp.data_ptr()), ctypes.c_void_p(dd.data_ptr()), pts.shape[0],
+                         ctypes.c_void_p(out.data_ptr()), 1)
+    assert rc == -1  # BEM_ERR_INVALID_ARG
+    o = out.cpu().numpy()
+    assert np.isnan(o[3])
+    keep = np.arange(pts.shape[0]) != 3
+    assert rel(o[keep], good[keep]) < 1e-12
+    again = c.field(pts, dom)  # the flag was cleared
+    assert rel(again, good) < 1e-14
+    c.close()
