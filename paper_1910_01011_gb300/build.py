@@ -1,5 +1,6 @@
 """Build the CUDA library in-tree: every translation unit of csrc/ compiled
-for sm_103a in parallel, then linked into _build/libgbem.so."""
+for sm_103a in parallel, then linked into _build/libgbem.so (CUDA runtime
+only; no vendor math library)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -52,7 +53,7 @@ def build(verbose: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     if not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        r = subprocess.run(["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas"], capture_output=True,
+        r = subprocess.run(["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True,
                            text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stderr)

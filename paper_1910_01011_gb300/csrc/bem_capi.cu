@@ -2,7 +2,6 @@
 // operator application pipeline
 //   gather (trial densities) -> far field (FP32 or FP64) -> projection onto
 //   P1 test functions with the touching-pair correction -> vertex reduction.
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -124,6 +123,9 @@ static void release_device(bem_ctx* ctx) {
     ctx->asm_ready = false;
     ctx->asm64_ready = false;
     ctx->asm64 = nullptr;
+    ctx->df_exp = nullptr;
+    ctx->df_work = nullptr;
+    ctx->df_work_bytes = 0;
     ctx->asm_planes = nullptr;
     ctx->asm_work = nullptr;
     ctx->asm_work_bytes = 0;
@@ -571,7 +573,6 @@ int bem_destroy(bem_ctx* ctx) {
     if (!ctx) return BEM_OK;
     release_device(ctx);
     release_group(ctx);
-    if (ctx->cublas) cublasDestroy(ctx->cublas);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return BEM_OK;

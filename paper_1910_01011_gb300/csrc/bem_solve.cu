@@ -680,12 +680,20 @@ int bem_solve_basis(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* 
                 S->n_basis = 0;
             }
         }
+        if (!rc && !ctx->df_exp) {
+            ctx->df_exp = (int*)ctx->dalloc(2 * sizeof(int), &rc);
+            if (rc) ctx->df_exp = nullptr;
+        }
         if (!rc) {
+            // kept in the split form of k_df64.cu for bem_superpose
             CK(cudaMemcpyAsync(S->basis, S->u, (size_t)ne * N * sizeof(double2), cudaMemcpyDeviceToDevice,
                                ctx->stream));
-            CK(cudaStreamSynchronize(ctx->stream));
-            S->n_basis = ne;
-            rc = solve_rc;
+            rc = df_prepare_inplace(ctx, S->basis, ne * N, ctx->df_exp + 1);
+            if (!rc) CK(cudaStreamSynchronize(ctx->stream));
+            if (!rc) {
+                S->n_basis = ne;
+                rc = solve_rc;
+            }
         }
     }
     ctx->tr_w = saved_w;
@@ -721,18 +729,8 @@ int bem_superpose(bem_ctx* ctx, const bem_z* w, int64_t n_exc, bem_z* u, int on_
         wd = S->wstage;
         ud = S->wstage + n_exc * ne;
     }
-    if (!ctx->cublas) {
-        if (cublasCreate(&ctx->cublas) != CUBLAS_STATUS_SUCCESS) return ctx->fail(BEM_ERR_CUDA, "cublasCreate failed");
-    }
-    if (cublasSetStream(ctx->cublas, ctx->stream) != CUBLAS_STATUS_SUCCESS)
-        return ctx->fail(BEM_ERR_CUDA, "cublasSetStream failed");
-    // column-major view: U^T (N x n_exc) = B^T (N x ne) W^T (ne x n_exc)
-    const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
-    if (cublasZgemm(ctx->cublas, CUBLAS_OP_N, CUBLAS_OP_N, (int)N, (int)n_exc, (int)ne, &one,
-                    (const cuDoubleComplex*)S->basis, (int)N, (const cuDoubleComplex*)wd, (int)ne, &zero,
-                    (cuDoubleComplex*)ud, (int)N) != CUBLAS_STATUS_SUCCESS)
-        return ctx->fail(BEM_ERR_CUDA, "cuBLAS superposition product failed");
-    ctx->launches += 1;
+    // U = W B with the basis in the split form of k_df64.cu (FP64 accuracy)
+    if ((rc = df_combine(ctx, (const float4*)S->basis, ctx->df_exp + 1, ne, N, wd, n_exc, ud))) return rc;
     if (!on_device) {
         CK(cudaMemcpyAsync(u, ud, (size_t)n_exc * N * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));

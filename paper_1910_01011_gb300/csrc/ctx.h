@@ -1,7 +1,6 @@
 // ctx.h -- the opaque bem_ctx behind the C ABI.
 #pragma once
 
-#include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -127,10 +126,13 @@ struct bem_ctx {
     int64_t asm_mpad = 0, asm_kpad = 0;
     void* asm_work = nullptr;
     size_t asm_work_bytes = 0;
-    // assembled operator in complex128 (FP64 refinement residuals)
+    // assembled operator for FP64 refinement residuals: complex128 entries stored as
+    // scaled FP32 (hi, lo) pairs, 16 bytes each (k_df64.cu)
     bool asm64_ready = false;
     double2* asm64 = nullptr;
-    cublasHandle_t cublas = nullptr;
+    int* df_exp = nullptr;          // device [2]: exponents of asm64 and of the superposition basis
+    void* df_work = nullptr;        // split vectors of the FP64-accurate products (grow-only)
+    size_t df_work_bytes = 0;
     gbem::OsrcState* osrc = nullptr;
     double osrc_tol = 1e-11;  // relative residual of the preconditioner's sparse solves
     bool osrc_strict = true;  // a sparse solve that stops short of osrc_tol is an error (false: keep its iterate)
@@ -167,3 +169,12 @@ struct bem_ctx {
     int ensure_assembled64();
     int apply_assembled64(const double2* x, double2* y, int64_t n_rhs);
 };
+
+namespace gbem {
+// FP64-accurate complex products in FP32 arithmetic (k_df64.cu).
+int df_prepare_inplace(bem_ctx* ctx, double2* v, int64_t n, int* e);
+int df_gemv(bem_ctx* ctx, const float4* A, const int* eA, int64_t m, int64_t k, int64_t lda, const double2* X,
+            int64_t R, double2* Y, int64_t ldy);
+int df_combine(bem_ctx* ctx, const float4* B, const int* eB, int64_t K, int64_t n, const double2* W, int64_t R,
+               double2* U);
+}  // namespace gbem

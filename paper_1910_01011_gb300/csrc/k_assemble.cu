@@ -13,7 +13,6 @@
 // Sauter-Schwab correction block (k_near.cu).  Local blocks are added into
 // the matrix with FP32 atomics (set-up only; the order of additions varies
 // between runs at the level of FP32 rounding).
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -386,7 +385,9 @@ int bem_ctx::ensure_assembled() {
 
 // A_hat assembled in complex128 (FP64 arithmetic), kept for the FP64
 // residual of the refinement: one pass of FP64 interactions at set-up, then
-// every residual is a memory-bound complex GEMM / GEMV (cuBLAS).
+// the matrix is stored as scaled FP32 (hi, lo) pairs in the same 16 bytes per
+// entry, and every residual is a product to FP64 accuracy in FP32 arithmetic
+// that streams it at the HBM rate (k_df64.cu).
 int bem_ctx::ensure_assembled64() {
     bem_ctx* const ctx = this;
     if (asm64_ready) return BEM_OK;
@@ -417,34 +418,25 @@ int bem_ctx::ensure_assembled64() {
                                                                            n, asm64);
         CK(cudaGetLastError());
     }
-    if (!cublas) {
-        if (cublasCreate(&cublas) != CUBLAS_STATUS_SUCCESS) return fail(BEM_ERR_CUDA, "cublasCreate failed");
+    CK(cudaGetLastError());
+    if (!df_exp) {
+        df_exp = (int*)dalloc(2 * sizeof(int), &rc);
+        if (rc) { df_exp = nullptr; return rc; }
     }
-    if (cublasSetStream(cublas, stream) != CUBLAS_STATUS_SUCCESS) return fail(BEM_ERR_CUDA, "cublasSetStream failed");
+    if ((rc = df_prepare_inplace(this, asm64, n * n, df_exp))) return rc;
     CK(cudaStreamSynchronize(stream));
     launches += 3;
     asm64_ready = true;
     return BEM_OK;
 }
 
-// Y = A_hat X (FP64, assembled) for n_rhs system-order vectors.  A is
-// row-major, i.e. column-major A^T for cuBLAS: Y = (A^T)^T X.
+// Y = A_hat X (FP64 accuracy, assembled) for n_rhs system-order vectors;
+// A_hat is row-major in the split form of k_df64.cu.
 int bem_ctx::apply_assembled64(const double2* x, double2* y, int64_t n_rhs) {
     int rc = ensure_assembled64();
     if (rc) return rc;
     const int64_t n = geo.n_dof;
-    const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
-    cublasStatus_t st;
-    if (n_rhs == 1)
-        st = cublasZgemv(cublas, CUBLAS_OP_T, (int)n, (int)n, &one, (const cuDoubleComplex*)asm64, (int)n,
-                         (const cuDoubleComplex*)x, 1, &zero, (cuDoubleComplex*)y, 1);
-    else
-        st = cublasZgemm(cublas, CUBLAS_OP_T, CUBLAS_OP_N, (int)n, (int)n_rhs, (int)n, &one,
-                         (const cuDoubleComplex*)asm64, (int)n, (const cuDoubleComplex*)x, (int)n, &zero,
-                         (cuDoubleComplex*)y, (int)n);
-    if (st != CUBLAS_STATUS_SUCCESS) return fail(BEM_ERR_CUDA, "cuBLAS complex product failed");
-    launches += 1;
-    return BEM_OK;
+    return df_gemv(this, (const float4*)asm64, df_exp, n, n, n, x, n_rhs, y, n);
 }
 
 // Y = A_hat X for n_rhs system-order vectors (complex128, device), through

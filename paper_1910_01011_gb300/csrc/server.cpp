@@ -331,7 +331,6 @@ int bem_server_add_scene(bem_server* s, bem_ctx* ctx, int32_t* scene_id) {
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) {
             ctx->stream = st;
             ctx->own_stream = true;
-            if (ctx->cublas) cublasSetStream(ctx->cublas, st);
         }
     }
     auto sc = std::make_unique<Scene>();

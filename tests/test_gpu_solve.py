@@ -196,8 +196,10 @@ def test_superposition_matches_direct_solves(api):
         c.superpose(np.ones((1, tr["radii"].size)))       # no basis yet
     rep = c.solve_basis(precision=1, tol=1e-12, batch_rhs=6)
     assert rep["converged"], rep
+    basis = np.stack([c.solution(m) for m in range(tr["radii"].size)])  # the unit-excitation solutions
     W = np.exp(2j * np.pi * np.random.default_rng(4).random((3, tr["radii"].size)))
     U = c.superpose(W)
+    assert rel(U, W @ basis) < 1e-12  # the product itself, to FP64 accuracy
     c.set_excitations(W)
     B = c.rhs(3)
     assert c.solve(precision=1, tol=1e-10)["converged"]
