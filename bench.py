@@ -38,8 +38,21 @@ UNIT = "Ginteractions/s"
 FL_SHARED = 21.0 + 11.0 / 6.0
 FL_SLOT_LOSSLESS = 52.0 + 32.0 / 6.0
 FL_SLOT_LOSSY = 54.0 + 32.0 / 6.0
+# Of a slot's flops, the part that does not depend on the densities: the phase,
+# G, the gradient factor F and the sum of G w (14 + 4 flops; +2 for Im k != 0).
+# With R right-hand sides sharing a pair's G and F (far32m_kernel) the work of
+# R interactions is R x the one-vector count minus (R - 1) x this part and the
+# shared geometry.
+FL_SLOT_SHARED_LOSSLESS = 18.0
+FL_SLOT_SHARED_LOSSY = 20.0
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def measured_fp32_peak(stream=None):
+    """Packed-FFMA rate measured on this GPU now (bem_peak_probe), TFLOP/s."""
+    from paper_1910_01011_gb300 import api
+    return max(api.peak_probe(0, 20000, stream) for _ in range(2)) / 1e12
 
 
 def _measured_bf16():
@@ -72,6 +85,19 @@ def workload(name):
     else:
         raise SystemExit(f"unknown workload {name}")
     return s, desc
+
+
+def algorithmic_flops_multi(s, R):
+    """FP32 flops of one far-field launch on scene s for R right-hand sides
+    that share each pair's geometry, G and F (see the constants above)."""
+    slot0 = (FL_SLOT_SHARED_LOSSY if complex(s.k0).imag != 0 else FL_SLOT_SHARED_LOSSLESS)
+    P = [6 * d.tris.shape[0] for d in s.domains]
+    tot = sum(P)
+    shared = 0.0
+    for d, p in zip(s.domains, P):
+        slot1 = FL_SLOT_SHARED_LOSSY if complex(d.k).imag != 0 else FL_SLOT_SHARED_LOSSLESS
+        shared += p * (tot - p) * (FL_SHARED + slot0) + p * p * (FL_SHARED + slot0 + slot1)
+    return R * algorithmic_flops(s) - (R - 1) * shared
 
 
 def pair_counts(s):
@@ -194,10 +220,12 @@ def traffic_from_profile():
     return float(m.group(1))
 
 
-def kidney_apply_metrics(local, steps=3):
+def kidney_apply_metrics(local, steps=3, n_rhs=16, peak=FP32_PEAK_TFLOPS):
     """The same operator application on the kidney + perinephric fat scene
     (61,996 triangles, 1 MHz), autotuned launch shape, L2 flushed between
-    steps."""
+    steps; then the kidney workload of 16 right-hand sides in ONE matrix-free
+    FP32 far-field launch (far32m_kernel, the pair's G and F shared by groups
+    of four vectors), as interaction-RHS per second."""
     import torch
 
     from paper_1910_01011_gb300.api import Context
@@ -226,14 +254,41 @@ def kidney_apply_metrics(local, steps=3):
         torch.cuda.synchronize()
         ms += a.elapsed_time(b)
     prof = c.profile_read(reset=True)
-    c.close()
     far_ms = prof["far_ms"] / max(1, prof["far_launches"])
     achieved = algorithmic_flops(s) / (far_ms / 1e3) / 1e12
     n_int = pair_counts(s)[2]
-    return {"workload": desc, "value": n_int * steps / (ms / 1e3) / 1e9, "unit": UNIT,
-            "far_field_chunk_tiles": tuned["chunk_tiles"],
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "kernel_ms": far_ms}}
+    single = {"workload": desc, "value": n_int * steps / (ms / 1e3) / 1e9, "unit": UNIT,
+              "far_field_chunk_tiles": tuned["chunk_tiles"],
+              "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                           "frac": achieved / peak, "kernel_ms": far_ms}}
+    # 16 right-hand sides in one launch
+    X = torch.complex(torch.randn(n_rhs, N, dtype=torch.float64, device="cuda", generator=g),
+                      torch.randn(n_rhs, N, dtype=torch.float64, device="cuda", generator=g))
+    Y = torch.empty_like(X)
+    c.apply(X, precision=1, out=Y)
+    c.profile_read(reset=True)
+    ms_m = []
+    for _ in range(2):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c.apply(X, precision=1, out=Y)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_m.append(a.elapsed_time(b))
+    prof = c.profile_read(reset=True)
+    c.close()
+    far_m = prof["far_ms"] / max(1, prof["far_launches"])
+    ach_m = algorithmic_flops_multi(s, n_rhs) / (far_m / 1e3) / 1e12
+    ms_med = sorted(ms_m)[len(ms_m) // 2]
+    single["multi_rhs"] = {
+        "workload": f"kidney scene, {n_rhs} right-hand sides in one FP32 far-field launch (far32m_kernel)",
+        "value": n_int * n_rhs / (ms_med / 1e3) / 1e9, "unit": "Ginteraction-RHS/s", "ms_per_apply": ms_med,
+        "speedup_vs_single_rhs_applies": (ms * n_rhs / steps) / ms_med,
+        "roofline": {"bound": "alu", "achieved": ach_m, "peak": peak, "unit": "TFLOP/s", "frac": ach_m / peak,
+                     "kernel": "far32m_kernel", "kernel_ms": far_m,
+                     "work": "R x the one-vector flops minus (R-1) x the density-independent geometry, G and F"}}
+    return single
 
 
 def sphere_solve_metrics(local, reps=12):
@@ -552,10 +607,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the solve and assembled-GEMM measurements")
     ap.add_argument("--quick", action="store_true", help="skip the rib-scene solve and the serving trace")
+    ap.add_argument("--extra", action="append", default=None,
+                    choices=["assembled", "solve_sphere", "apply_kidney", "solve", "serving"],
+                    help="run only these extras (repeatable); default: all that the other flags allow")
     ap.add_argument("--step", default="apply", choices=["apply", "prec"],
                     help="apply: the operator application (the headline metric); prec: one OSRC preconditioner "
                          "application to --prec-rhs right-hand sides (for profiling the sparse solves)")
     ap.add_argument("--prec-rhs", type=int, default=8)
+    ap.add_argument("--rhs", type=int, default=1,
+                    help="right-hand sides per apply step; > 1 applies them in one matrix-free far-field launch "
+                         "(far32m_kernel) and reports interaction-RHS per second (profiling of the multi-RHS path)")
     ap.add_argument("--clocks-log", default=None, help="keep the raw nvidia-smi clock samples in this CSV file")
     ap.add_argument("--osrc-solver", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="sparse solver of the preconditioner step: 0 automatic, 1 one CTA per system, 2 grid-wide, "
@@ -587,16 +648,18 @@ def main():
     N = ctx.n_dofs
     single, fused, n_int = pair_counts(s)
     assert n_int == ctx.interactions
-    flops = algorithmic_flops(s)
+    R = max(1, args.rhs)
+    flops = algorithmic_flops(s) if R == 1 else algorithmic_flops_multi(s, R)
 
     gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
-    x = torch.complex(torch.randn(N, dtype=torch.float64, device="cuda", generator=gen),
-                      torch.randn(N, dtype=torch.float64, device="cuda", generator=gen))
+    shape = (N,) if R == 1 else (R, N)
+    x = torch.complex(torch.randn(shape, dtype=torch.float64, device="cuda", generator=gen),
+                      torch.randn(shape, dtype=torch.float64, device="cuda", generator=gen))
     y = torch.empty_like(x)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ctx.apply(x, precision=1, out=y)          # set-up (geometry, near field) outside timing
     torch.cuda.synchronize()
-    tuned = None if args.no_autotune else ctx.autotune(1)   # launch shape picked by timing (bem_autotune)
+    tuned = None if (args.no_autotune or R > 1) else ctx.autotune(1)   # launch shape picked by timing (bem_autotune)
     for _ in range(max(3, args.warmup)):
         ctx.apply(x, precision=1, out=y)
     torch.cuda.synchronize()
@@ -621,11 +684,13 @@ def main():
     ctx.profile(False)
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, ends)), world)
     ms_per_step = ms / args.steps
-    value = job_rate(n_int * args.steps, world, ms / 1e3) / 1e9
+    value = job_rate(n_int * R * args.steps, world, ms / 1e3) / 1e9
+    # the FP32 FFMA rate measured on this GPU right after the timed region
+    peak_meas = measured_fp32_peak(stream.cuda_stream)
 
     # e2e: the public call with host buffers (pinned), copies inside the timing
-    xh = torch.empty(N, dtype=torch.complex128).pin_memory()
-    yh = torch.empty(N, dtype=torch.complex128).pin_memory()
+    xh = torch.empty(shape, dtype=torch.complex128).pin_memory()
+    yh = torch.empty(shape, dtype=torch.complex128).pin_memory()
     xh.copy_(x.cpu())
     xa, ya = xh.numpy(), yh.numpy()
     ctx.apply(xa, precision=1, out=ya)
@@ -637,27 +702,34 @@ def main():
         ctx.apply(xa, precision=1, out=ya)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_value = job_rate(n_int * args.steps, world, e2e_s) / 1e9
+    e2e_value = job_rate(n_int * R * args.steps, world, e2e_s) / 1e9
 
     far_ms = prof["far_ms"] / max(1, prof["far_launches"])
     achieved = flops / (far_ms / 1e3) / 1e12
     traffic = traffic_from_profile()
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC if R == 1 else f"BEM operator-apply Ginteraction-RHS/s ({R} RHS in one launch)",
+            "value": value, "unit": UNIT if R == 1 else "Ginteraction-RHS/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "n_triangles": s.n_triangles, "n_dofs": N,
-                       "interactions_per_step": n_int, "precision": "FP32 far field, FP64 near field/output",
+                       "interactions_per_step": n_int * R, "rhs_per_step": R,
+                       "precision": "FP32 far field, FP64 near field/output",
                        "l2": "flushed between timed steps (256 MB write)", "replicas": world,
                        "far_field_chunk_tiles": (tuned or {}).get("chunk_tiles", "built-in")},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                         "kernel": "far32_kernel", "kernel_ms": far_ms,
-                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FFMA) x 2070 MHz max clock"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * N, "d2h_bytes_per_step": 16 * N},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_meas, "unit": "TFLOP/s",
+                         "frac": achieved / peak_meas, "traffic": traffic if R == 1 else None,
+                         "kernel": "far32_kernel" if R == 1 else "far32m_kernel", "kernel_ms": far_ms,
+                         "peak_basis": "measured: packed FFMA2 chains on every SM (bem_peak_probe), in this run",
+                         "peak_derived": FP32_PEAK_TFLOPS, "frac_of_derived": achieved / FP32_PEAK_TFLOPS,
+                         "peak_derived_basis": "152 SMs x 128 FP32 lanes x 2 (FFMA) x 2070 MHz max clock"},
+            "e2e": {"value": e2e_value, "unit": UNIT if R == 1 else "Ginteraction-RHS/s",
+                    "h2d_bytes_per_step": 16 * N * R, "d2h_bytes_per_step": 16 * N * R},
             "gpu_launches": prof["kernel_launches"],
             "clocks": clk.summary()}
     if not args.no_extras:
         def extra(name, fn, *a):
+            if args.extra and name not in args.extra:
+                return
             try:
                 line[name] = fn(*a)
             except Exception as e:  # the line still prints; the failure is part of it
@@ -665,7 +737,7 @@ def main():
         extra("assembled", assembled_metrics, ctx, s, n_int, local)
         extra("solve_sphere", sphere_solve_metrics, local)
         if not args.quick and world == 1:
-            extra("apply_kidney", kidney_apply_metrics, local)
+            extra("apply_kidney", kidney_apply_metrics, local, 3, 16, peak_meas)
             # the minutes-long solve and serving measurements run on one GPU; replicas
             # of them on more GPUs would only repeat the same numbers
             extra("solve", rib_solve_metrics, local)

@@ -83,6 +83,10 @@ typedef struct {
                                   kernels, 3 one 8-CTA thread-block cluster per system and domain, 4 as 3
                                   with the Pade shifts of one right-hand side in one cluster; same results
                                   within osrc_tol */
+    int32_t osrc_wavenumber;   /* wavenumber each domain's OSRC block is built at (Sec. 2.3 eq. OSRC_prec_blocks
+                                  writes the blocks with a "+" superscript and leaves this open): 0 (default)
+                                  the domain's own k_j, 1 the exterior k0.  Only the GMRES iteration count
+                                  depends on it; k_j needed 1.3-2.1x fewer iterations on every scene measured */
 } bem_opts;
 
 /* Fill opts with the defaults above. */
@@ -303,6 +307,16 @@ int bem_autotune(bem_ctx* ctx, int precision, int32_t* chunk_tiles, double* best
  * the kernels for device arrays (those points are skipped and written as NaN). */
 int bem_field(bem_ctx* ctx, int64_t rhs, const double* points, const int32_t* domain_of_point, int64_t n_points,
               bem_z* out, int on_device);
+
+/* Arithmetic-rate probe for roofline denominators (no counterpart in the
+ * paper): runs independent dependency chains of one operation on every SM of
+ * the current device, on cuda_stream (a cudaStream_t, NULL = legacy default
+ * stream), and returns the measured rate of one timed launch after a
+ * warm-up.  which = 0: packed FP32 FMA (flops/s, FMA = 2 flops); 1: MUFU
+ * sine (operations/s); 2: FP64 FMA (flops/s).  iters scales the work (each of
+ * 16 x SMs x 256 threads issues iters x 128 operations).  Allocates and frees
+ * 4 bytes of device memory.  Errors: INVALID_ARG, CUDA. */
+int bem_peak_probe(int which, int iters, void* cuda_stream, double* ops_per_s);
 
 /* Message of the last error on ctx (never NULL). */
 const char* bem_last_error(const bem_ctx* ctx);

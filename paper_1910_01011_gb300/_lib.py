@@ -28,7 +28,7 @@ class bem_opts(ctypes.Structure):
     _fields_ = [("n_gauss_singular", ctypes.c_int32), ("chunk_tiles", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_int64), ("n_pade", ctypes.c_int32), ("pade_theta", ctypes.c_double),
                 ("r_eps", ctypes.c_double), ("eps_exponent", ctypes.c_double), ("osrc_tol", ctypes.c_double),
-                ("osrc_solver", ctypes.c_int32)]
+                ("osrc_solver", ctypes.c_int32), ("osrc_wavenumber", ctypes.c_int32)]
 
 
 class bem_solve_opts(ctypes.Structure):
@@ -116,6 +116,7 @@ _SIGS = {
     "bem_profile_enable": [_P, ctypes.c_int],
     "bem_profile_read": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
+    "bem_peak_probe": [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)],
     "bem_quadrature_table": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_int)],
 }

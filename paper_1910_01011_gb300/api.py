@@ -244,6 +244,15 @@ class Context:
         return {"far_ms": ms.value, "far_launches": nf.value, "kernel_launches": nk.value}
 
 
+def peak_probe(which, iters, stream=None):
+    """Measured arithmetic rate (bem_peak_probe): which 0 packed FP32 FMA
+    (flops/s), 1 MUFU sine (ops/s), 2 FP64 FMA (flops/s)."""
+    lib = _lib.load()
+    r = ctypes.c_double()
+    check(lib.bem_peak_probe(int(which), int(iters), ctypes.c_void_p(stream or 0), ctypes.byref(r)))
+    return r.value
+
+
 def quadrature_table(which, n=6):
     lib = _lib.load()
     buf = (ctypes.c_double * 256)()

@@ -135,6 +135,11 @@ static void release_device(bem_ctx* ctx) {
     ctx->field_buf_bytes = 0;
     ctx->far_work = nullptr;
     for (int& k : ctx->far_work_key) k = -1;
+    ctx->multi_buf = nullptr;
+    ctx->multi_buf_bytes = 0;
+    ctx->multi_work = nullptr;
+    ctx->multi_n_work = 0;
+    for (int& k : ctx->multi_key) k = -1;
     ctx->pmchwt_near = NearSet();
     destroy_solver_state(ctx);
 }
@@ -147,6 +152,19 @@ void invalidate_basis(bem_ctx* ctx);
 // the host description (meshes, materials, transducer) stays and the device
 // state is rebuilt on next use.
 void release_device_memory(bem_ctx* ctx) { release_device(ctx); }
+
+void multi_chunking(int n_tiles, int64_t n_pts, int64_t R, int* n_chunks, int* chunk_tiles) {
+    const int groups = (int)((R + MRG - 1) / MRG);
+    int nc = std::max(1, (152 * 2 * 8 + n_tiles * groups - 1) / std::max(1, n_tiles * groups));
+    nc = std::max(nc, (n_tiles + CHUNK_MAX - 1) / CHUNK_MAX);
+    const size_t per_chunk = (size_t)R * 2 * NCOMP * n_pts * sizeof(float);
+    const int nc_mem = (int)std::max<size_t>(1, ((size_t)2 << 30) / std::max<size_t>(1, per_chunk));
+    if (nc > nc_mem) nc = std::max(nc_mem, (n_tiles + CHUNK_MAX - 1) / CHUNK_MAX);
+    nc = std::max(1, std::min(nc, n_tiles));
+    const int ct = (n_tiles + nc - 1) / nc;
+    *chunk_tiles = ct;
+    *n_chunks = (n_tiles + ct - 1) / ct;
+}
 
 // Device bytes a solve of n_exc excitations with options o may need at its
 // peak, from the mesh sizes alone (no device state is needed); every term
@@ -177,10 +195,19 @@ int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_
     if (o.precondition && o.flexible) b += (int64_t)o.restart * R * N * 16;  // flexible basis
     b += 4 * R * N * 16;
     if (o.precondition) {
-        const int64_t L = ctx->opts.n_pade, nnz = 8 * nv, ms = 2 * L * R;
-        b += nnz * 20 + (nv + 1) * 8 + 2 * nv * 8;
-        b += 6 * ms * nv * 16 + ms * (16 + 128 * 4 * 8 + 64) + 4 * R * nv * 16;
+        const int64_t L = ctx->opts.n_pade, nnz = 8 * nv, ms = 2 * L * R, nd = (int64_t)ctx->doms.size();
+        b += nnz * 20 + (nv + 1) * 8 + 2 * nv * 8 + nv * 4 + nd * (L + 4) * 16;
+        b += 6 * ms * nv * 16 + ms * (16 * nd + 128 * 4 * 8 + 64) + 4 * R * nv * 16;
     }
+    // several right-hand sides in one matrix-free FP32 far-field launch
+    if (o.operator_mode == 0 && o.precision == BEM_PREC_FP32 && R > 1) {
+        int ncm = 1, ctm = 1;
+        multi_chunking((int)tiles, pts, R, &ncm, &ctm);
+        b += R * (pts * 16 + 2 * slots * 16 + (int64_t)ncm * 2 * NCOMP * pts * 4) +
+             tiles * ncm * 2 * ((R + MRG - 1) / MRG) * 16;
+    }
+    // split vectors of the FP64-accurate residual product
+    b += R * N * 16 + 4096;
     if (o.operator_mode == 1) {
         const int64_t mp = (N + 127) / 128 * 128, kp = (N + 31) / 32 * 32;
         const int64_t planes = 6 * mp * kp * 2;
@@ -506,6 +533,120 @@ int bem_ctx::run_apply(const double2* x, double2* y, int precision, const ApplyM
     return BEM_OK;
 }
 
+// A_hat applied to n_rhs vectors x [n_rhs][N] -> y [n_rhs][N] at FP32 with
+// one far-field launch for all of them (far32m_kernel: the Green's function
+// and gradient factor of a pair are evaluated once per group of MRG vectors),
+// then the projection (with the near-field correction) and the reduction of
+// each vector.  Same arithmetic per vector as apply_ahat at FP32 except the
+// chunk boundaries of the source sums.
+int bem_ctx::apply_ahat_multi(const double2* x, double2* y, int64_t n_rhs) {
+    bem_ctx* const ctx = this;
+    int rc = ensure_near();
+    if (rc) return rc;
+    const Geometry& g = geo;
+    const int n_tiles = g.n_tiles;
+    const int groups = (int)((n_rhs + MRG - 1) / MRG);
+    int n_chunks, chunk_tiles;
+    multi_chunking(n_tiles, g.n_pts, n_rhs, &n_chunks, &chunk_tiles);
+    const int64_t rstride = (int64_t)n_chunks * 2 * NCOMP * g.n_pts;
+    const size_t b_pd = (size_t)n_rhs * g.n_pts * sizeof(float4);
+    const size_t b_tc = (size_t)n_rhs * 2 * g.n_slots * sizeof(float4);
+    const size_t b_part = (size_t)n_rhs * rstride * sizeof(float);
+    const size_t need = b_pd + b_tc + b_part;
+    if (need > multi_buf_bytes) {
+        dfree(multi_buf);
+        multi_buf = dalloc(need, &rc);
+        if (rc) { multi_buf = nullptr; multi_buf_bytes = 0; return rc; }
+        multi_buf_bytes = need;
+    }
+    float4* pdm = (float4*)multi_buf;
+    float4* tcm = (float4*)((char*)multi_buf + b_pd);
+    float* part = (float*)((char*)multi_buf + b_pd + b_tc);
+    // work list: (target tile, chunk, slot, group), heaviest first
+    const int key[3] = {n_chunks, chunk_tiles, groups};
+    if (!multi_work || !std::equal(key, key + 3, multi_key)) {
+        std::vector<std::pair<int64_t, int4>> items;
+        items.reserve((size_t)n_tiles * n_chunks * 2 * groups);
+        for (int t = 0; t < n_tiles; t++) {
+            const int d = g.tile_dom[t];
+            const int own_b = g.dom_tile_begin[d], own_e = g.dom_tile_end[d];
+            for (int c = 0; c < n_chunks; c++) {
+                const int sb = c * chunk_tiles, se = std::min(sb + chunk_tiles, n_tiles);
+                int64_t w0 = 0, w1 = 0;
+                for (int s = sb; s < se; s++) {
+                    w0 += g.tile_ntri[s];
+                    if (s >= own_b && s < own_e) w1 += g.tile_ntri[s];
+                }
+                for (int gr = 0; gr < groups; gr++) {
+                    items.push_back({-w0, make_int4(t, c, 0, gr)});
+                    items.push_back({-w1, make_int4(t, c, 1, gr)});  // empty ranges write zeros
+                }
+            }
+        }
+        std::stable_sort(items.begin(), items.end(),
+                         [](const std::pair<int64_t, int4>& a, const std::pair<int64_t, int4>& b) { return a.first < b.first; });
+        std::vector<int4> work(items.size());
+        for (size_t i = 0; i < items.size(); i++) work[i] = items[i].second;
+        dfree(multi_work);
+        multi_work = nullptr;
+        multi_work = (int4*)dalloc(work.size() * sizeof(int4), &rc);
+        if (rc) { multi_work = nullptr; return rc; }
+        CK(cudaMemcpyAsync(multi_work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
+        CK(cudaStreamSynchronize(stream));
+        multi_n_work = (int64_t)work.size();
+        std::copy(key, key + 3, multi_key);
+    }
+    const int64_t N = g.n_dof;
+    // 1. trial densities of every vector
+    for (int64_t r = 0; r < n_rhs; r++) {
+        GatherArgs ga{};
+        ga.slot_v = dev.slot_v; ga.v_dof1 = dev.v_dof1; ga.v_dof2 = dev.v_dof2; ga.pt_w = dev.pt_w;
+        ga.slot_curl = dev.slot_curl; ga.x = x + r * N; ga.s_begin = 0; ga.s_end = g.n_slots;
+        for (int q = 0; q < QP; q++)
+            for (int k = 0; k < 3; k++) ga.lam[q][k] = quad.lam[q][k];
+        ga.pd32 = pdm + r * g.n_pts;
+        ga.tcurl32 = tcm + r * 2 * g.n_slots;
+        CK(launch_gather(ga, stream));
+    }
+    // 2. far field of all vectors in one launch
+    FarArgs32M fa{};
+    fa.pg = dev.pg32; fa.pgp = dev.pgp32; fa.tg = dev.tg32; fa.tc = dev.tc; fa.tdom = dev.tdom; fa.tntri = dev.tntri;
+    fa.pd = pdm; fa.tcurl = tcm; fa.dom_tiles = dev.dom_tiles; fa.kdom = dev.kdom;
+    fa.k0 = make_double2(k0re, k0im);
+    fa.src_begin = 0; fa.src_end = n_tiles; fa.tgt_begin = 0; fa.chunk_tiles = chunk_tiles;
+    fa.R = (int)n_rhs; fa.n_pts = g.n_pts; fa.n_slots = g.n_slots; fa.rstride = rstride; fa.partial = part;
+    fa.err = dev.err; fa.work = multi_work;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (profiling) {
+        CK(cudaEventCreate(&ev0));
+        CK(cudaEventCreate(&ev1));
+        CK(cudaEventRecord(ev0, stream));
+    }
+    CK(launch_far32_multi(fa, multi_n_work, stream));
+    if (profiling) {
+        CK(cudaEventRecord(ev1, stream));
+        far_events.push_back({ev0, ev1});
+    }
+    // 3. projection and reduction of each vector
+    for (int64_t r = 0; r < n_rhs; r++) {
+        ProjectArgs pa{};
+        pa.slot_v = dev.slot_v; pa.pt_w = dev.pt_w; pa.slot_curl = dev.slot_curl; pa.tntri = dev.tntri; pa.tdom = dev.tdom;
+        pa.coef = dev.coef; pa.tgt_begin = 0; pa.tgt_end = n_tiles; pa.n_chunks = n_chunks; pa.n_pts = g.n_pts;
+        pa.partial32 = part + r * rstride;
+        if (pmchwt_near.n_pairs > 0) { pa.np_ptr = dev.np_ptr; pa.np_src = dev.np_src; pa.nb32 = pmchwt_near.nb32; }
+        pa.v_dof1 = dev.v_dof1; pa.v_dof2 = dev.v_dof2; pa.x = x + r * N; pa.tri_out = dev.tri_out;
+        for (int q = 0; q < QP; q++)
+            for (int k = 0; k < 3; k++) pa.lam[q][k] = quad.lam[q][k];
+        CK(launch_project(pa, stream));
+        ReduceArgs ra{};
+        ra.vc_ptr = dev.vc_ptr; ra.vc_idx = dev.vc_idx; ra.v_dof1 = dev.v_dof1; ra.v_dof2 = dev.v_dof2;
+        ra.tri_out = dev.tri_out; ra.y = y + r * N; ra.v_begin = 0; ra.v_end = g.n_vert;
+        CK(launch_reduce(ra, stream));
+    }
+    launches += 3 * n_rhs + 1;
+    return BEM_OK;
+}
+
 int bem_ctx::apply_ahat(const double2* x, double2* y, int precision) {
     int rc = ensure_near();
     if (rc) return rc;
@@ -544,6 +685,7 @@ int bem_default_opts(bem_opts* o) {
     o->eps_exponent = 1.0 / 3.0;
     o->osrc_tol = 1e-11;
     o->osrc_solver = 0;
+    o->osrc_wavenumber = 0;
     return BEM_OK;
 }
 
@@ -560,7 +702,8 @@ int bem_create(bem_ctx** out, int device, void* cuda_stream, const bem_opts* opt
     bem_default_opts(&c->opts);
     if (opts) c->opts = *opts;
     if (c->opts.n_gauss_singular < 2 || c->opts.n_gauss_singular > 20 || !(c->opts.osrc_tol > 0) ||
-        !(c->opts.osrc_tol < 1) || c->opts.osrc_solver < 0 || c->opts.osrc_solver > 4) {
+        !(c->opts.osrc_tol < 1) || c->opts.osrc_solver < 0 || c->opts.osrc_solver > 4 ||
+        c->opts.osrc_wavenumber < 0 || c->opts.osrc_wavenumber > 1) {
         delete c;
         return BEM_ERR_INVALID_ARG;
     }
@@ -682,8 +825,10 @@ int bem_apply(bem_ctx* ctx, int op, const bem_z* x, bem_z* y, int64_t n_rhs, int
     int rc = ctx->finalize();
     if (rc) return rc;
     const int64_t N = ctx->geo.n_dof;
-    if ((precision == BEM_PREC_BF16X3 || precision == BEM_PREC_FP64_ASSEMBLED) && op != BEM_OP_PREC) {
-        // all right-hand sides in one tensor-core GEMM on the assembled operator
+    const bool multi32 = precision == BEM_PREC_FP32 && n_rhs > 1;
+    if ((precision == BEM_PREC_BF16X3 || precision == BEM_PREC_FP64_ASSEMBLED || multi32) && op != BEM_OP_PREC) {
+        // all right-hand sides at once: one product on the assembled operator, or
+        // one matrix-free far-field launch for all of them at FP32
         const double2* xd = (const double2*)x;
         double2* yd = (double2*)y;
         double2* stage = nullptr;
@@ -700,7 +845,9 @@ int bem_apply(bem_ctx* ctx, int op, const bem_z* x, bem_z* y, int64_t n_rhs, int
             if (rc) return rc;
         }
         double2* dst = tmp ? tmp : yd;
-        rc = precision == BEM_PREC_BF16X3 ? ctx->apply_assembled(xd, dst, n_rhs) : ctx->apply_assembled64(xd, dst, n_rhs);
+        rc = precision == BEM_PREC_BF16X3         ? ctx->apply_assembled(xd, dst, n_rhs)
+             : precision == BEM_PREC_FP64_ASSEMBLED ? ctx->apply_assembled64(xd, dst, n_rhs)
+                                                    : ctx->apply_ahat_multi(xd, dst, n_rhs);
         if (!rc && tmp) rc = ctx->apply_prec_batch(tmp, yd, n_rhs);
         if (tmp) {
             cudaStreamSynchronize(ctx->stream);

@@ -427,6 +427,7 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
     auto plain = [ctx, &o, N](const double2* X, double2* Y, int prec, int64_t nr) -> int {
         if (o.operator_mode == 1)
             return prec == BEM_PREC_FP64 ? ctx->apply_assembled64(X, Y, nr) : ctx->apply_assembled(X, Y, nr);
+        if (prec == BEM_PREC_FP32 && nr > 1) return ctx->apply_ahat_multi(X, Y, nr);
         for (int64_t r = 0; r < nr; r++) {
             int e = ctx->apply_ahat(X + r * N, Y + r * N, prec);
             if (e) return e;

@@ -107,6 +107,12 @@ struct bem_ctx {
     // far-field work list (heaviest (target tile, chunk) first) and the launch it was built for
     int2* far_work = nullptr;
     int far_work_key[6] = {-1, -1, -1, -1, -1, -1};
+    // several right-hand sides in one far-field launch: densities, partials and the work list
+    void* multi_buf = nullptr;
+    size_t multi_buf_bytes = 0;
+    int4* multi_work = nullptr;
+    int64_t multi_n_work = 0;
+    int multi_key[3] = {-1, -1, -1};  // (n_chunks, chunk_tiles, groups) the list was built for
     std::vector<std::pair<void*, size_t>> allocs;
     size_t used_bytes = 0;
     size_t peak_bytes = 0;                     // largest used_bytes seen
@@ -160,6 +166,7 @@ struct bem_ctx {
                    int fill_tiles = 0);
     int run_apply(const double2* x, double2* y, int precision, const gbem::ApplyMode& m);
     int apply_ahat(const double2* x, double2* y, int precision);
+    int apply_ahat_multi(const double2* x, double2* y, int64_t n_rhs);
     int apply_prec(const double2* x, double2* y);
     int apply_prec_batch(const double2* x, double2* y, int64_t n_rhs);
     int apply_prec_ahat(const double2* x, double2* y, int precision);
@@ -171,6 +178,10 @@ struct bem_ctx {
 };
 
 namespace gbem {
+// Source chunks of the several-right-hand-side far field (bem_capi.cu): enough
+// work items to fill the GPU, at most CHUNK_MAX tiles, and the partial
+// potentials of all R vectors within 2 GiB where possible.
+void multi_chunking(int n_tiles, int64_t n_pts, int64_t R, int* n_chunks, int* chunk_tiles);
 // FP64-accurate complex products in FP32 arithmetic (k_df64.cu).
 int df_prepare_inplace(bem_ctx* ctx, double2* v, int64_t n, int* e);
 int df_gemv(bem_ctx* ctx, const float4* A, const int* eA, int64_t m, int64_t k, int64_t lda, const double2* X,

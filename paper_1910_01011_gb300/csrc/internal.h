@@ -126,6 +126,33 @@ struct FarArgs32 {
                             // in launch order, heaviest first, on a 1-D grid
 };
 
+// Several right-hand sides in one far-field launch: work item
+// (target tile offset, source chunk, wavenumber slot, group of MRG right-hand
+// sides).  Right-hand side r has its own densities (pd + r * n_pts,
+// tcurl + r * 2 * n_slots) and its own partial buffer (partial + r * rstride,
+// laid out as for one right-hand side).
+constexpr int MRG = 4;
+struct FarArgs32M {
+    const float4* pg;       // target points
+    const float4* pgp;      // source points, pair-interleaved
+    const float4* tg;
+    const double4* tc;
+    const int* tdom;
+    const int* tntri;
+    const float4* pd;       // [R][n_pts] densities, pair-interleaved
+    const float4* tcurl;    // [R][2 * n_slots]
+    const int2* dom_tiles;
+    const double2* kdom;
+    double2 k0;
+    int src_begin, src_end, tgt_begin, chunk_tiles;
+    int R;
+    int64_t n_pts, n_slots;
+    int64_t rstride;        // floats between the partial buffers of consecutive right-hand sides
+    float* partial;         // [R][n_chunks][2][NCOMP][n_pts]
+    int* err;
+    const int4* work;       // [n_work] (target tile offset, chunk, slot, group), heaviest first
+};
+
 struct FarArgs64 {
     const double4* pg;      // (dx, dy, dz, w)
     const double4* tg;      // (nx, ny, nz, h)
@@ -232,6 +259,7 @@ struct NearCombineArgs {
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
 cudaError_t launch_far32(const FarArgs32& a, int n_tgt_tiles, int n_chunks, cudaStream_t s);
 cudaError_t launch_far32_group(const FarArgs32* group, const int4* gwork, int64_t n_work, cudaStream_t s);
+cudaError_t launch_far32_multi(const FarArgs32M& a, int64_t n_work, cudaStream_t s);
 cudaError_t launch_far64(const FarArgs64& a, int n_tgt_tiles, int n_chunks, cudaStream_t s);
 cudaError_t launch_project(const ProjectArgs& a, cudaStream_t s);
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t s);

@@ -461,6 +461,258 @@ cudaError_t launch_far32_group(const FarArgs32* group, const int4* gwork, int64_
     return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------- FP32 far field, several right-hand sides
+//
+// The Green's function G and the gradient factor F of a (target point,
+// source point) pair do not depend on the densities, so a work item that
+// serves MRG right-hand sides evaluates the geometry, the phase and the MUFU
+// functions once and accumulates MRG sets of potentials.  One wavenumber
+// slot per work item keeps the per-thread state (14 potentials and eight
+// packed triangle sums per right-hand side) within the register budget of
+// the one-vector kernel; own-domain sources are visited once per slot.
+
+constexpr int NSTAGE_M = 3;
+
+struct __align__(16) StageM {
+    float4 pg[TP];           // source points (dx, dy, dz, w), pair-interleaved
+    float4 tg[TT];           // triangles (n, h)
+    float4 pd[MRG][TP];      // densities of each right-hand side, pair-interleaved
+    float4 tc[MRG][2 * TT];  // curl densities of each right-hand side
+};
+constexpr uint32_t STAGE_M_BYTES = sizeof(StageM);
+static_assert(STAGE_M_BYTES == 3584 + MRG * 4096, "multi stage layout");
+
+struct FarSmemM {
+    StageM st[NSTAGE_M];
+    float4 tab[2 * CHUNK_MAX];
+    uint64_t full[NSTAGE_M];
+    int cnt[NSTAGE_M];
+};
+
+// Per right-hand side: the V and K' sums run packed over the whole item
+// (no per-triangle factor; folded once at the end), the K and W terms need
+// per-triangle sums (K' and K kept with the sign of -F, as in the one-vector
+// kernel).
+struct AccM {
+    f2 Vr, Vi, nKpr, nKpi;
+    float K[2], Wm[2], Wc[6];
+};
+struct PairTriM {
+    f2 nS1r, nS1i, S3r, S3i;
+};
+
+template <bool LOSSY>
+__device__ __forceinline__ void tile_body_m(const StageM& st, int ntri, int skip_tl, const PairTgt& X, float4 c0,
+                                            float Rcf, PairK k, AccM (&acc)[MRG]) {
+    const float D2x = c0.x, D2y = c0.y, D2z = c0.z;
+    const f2 m2x = bc2(-fmaf(2.f, X.dx, D2x)), m2y = bc2(-fmaf(2.f, X.dy, D2y)), m2z = bc2(-fmaf(2.f, X.dz, D2z));
+    const f2 cb = bc2(fmaf(D2x, X.dx, fmaf(D2y, X.dy, fmaf(D2z, X.dz, X.dd))));
+    const f2 cn = bc2(fmaf(0.5f, X.nx * D2x + X.ny * D2y + X.nz * D2z, X.nd));
+    const f2 Rc2 = bc2(c0.w), Rc = bc2(Rcf);
+    const float Xx = fmaf(0.5f, D2x, X.dx), Xy = fmaf(0.5f, D2y, X.dy), Xz = fmaf(0.5f, D2z, X.dz);  // x - c_source
+    const f2 z2 = make_float2(0.f, 0.f);
+    for (int tl = 0; tl < ntri; tl++) {
+        if (tl == skip_tl) continue;  // identical triangle: near-field correction only
+        PairTriM S[MRG];
+#pragma unroll
+        for (int q = 0; q < MRG; q++) S[q] = PairTriM{z2, z2, z2, z2};
+        f2 S2r = z2, S2i = z2;
+#pragma unroll
+        for (int j = 0; j < QP / 2; j++) {
+            const float4 GA = st.pg[tl * QP + 2 * j], GB = st.pg[tl * QP + 2 * j + 1];
+            const f2 gx = lo2(GA), gy = hi2(GA), gz = lo2(GB), w = hi2(GB);
+            const f2 s = fma2(gx, add2(gx, m2x), fma2(gy, add2(gy, m2y), fma2(gz, add2(gz, m2z), cb)));
+            const f2 r2 = add2(s, Rc2);
+            const f2 rinv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+            const f2 rinv2 = mul2(rinv, rinv);
+            const f2 den = fma2(r2, rinv, Rc);  // r + R_c
+            const f2 rho = mul2(s, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+            const f2 ndot = fma2(X.nnx, gx, fma2(X.nny, gy, fma2(X.nnz, gz, cn)));
+            const f2 arg = fma2(k.kr, rho, k.th);
+            f2 sn, cs;
+            sincos_approx(arg.x, &sn.x, &cs.x);
+            sincos_approx(arg.y, &sn.y, &cs.y);
+            f2 a = rinv;
+            if constexpr (LOSSY) {
+                const f2 e = mul2(k.nkil2, mul2(r2, rinv));
+                a = mul2(make_float2(ex2_approx(e.x), ex2_approx(e.y)), rinv);
+            }
+            const f2 Gr = mul2(a, cs), Gi = mul2(a, sn);
+            const f2 B = mul2(k.kr, rinv), nB = mul2(k.nkr, rinv);
+            const f2 P = LOSSY ? fma2(k.ki, rinv, rinv2) : rinv2;
+            const f2 nFr = fma2(P, Gr, mul2(B, Gi));
+            const f2 nFi = fma2(P, Gi, mul2(nB, Gr));
+            const f2 nFnr = mul2(ndot, nFr), nFni = mul2(ndot, nFi);
+            S2r = fma2(Gr, w, S2r);
+            S2i = fma2(Gi, w, S2i);
+#pragma unroll
+            for (int q = 0; q < MRG; q++) {
+                const float4 DA = st.pd[q][tl * QP + 2 * j], DB = st.pd[q][tl * QP + 2 * j + 1];
+                const f2 d1r = lo2(DA), d1i = hi2(DA), d2r = lo2(DB), d2i = hi2(DB);
+                const f2 nd1i = neg2(d1i), nd2i = neg2(d2i);  // folded into the packed FMAs' operands
+                PairTriM& T = S[q];
+                AccM& U = acc[q];
+                U.Vr = fma2(Gr, d1r, fma2(Gi, nd1i, U.Vr));
+                U.Vi = fma2(Gr, d1i, fma2(Gi, d1r, U.Vi));
+                U.nKpr = fma2(nFnr, d1r, fma2(nFni, nd1i, U.nKpr));
+                U.nKpi = fma2(nFnr, d1i, fma2(nFni, d1r, U.nKpi));
+                T.nS1r = fma2(nFr, d2r, fma2(nFi, nd2i, T.nS1r));
+                T.nS1i = fma2(nFr, d2i, fma2(nFi, d2r, T.nS1i));
+                T.S3r = fma2(Gr, d2r, fma2(Gi, nd2i, T.S3r));
+                T.S3i = fma2(Gr, d2i, fma2(Gi, d2r, T.S3i));
+            }
+        }
+        const float4 tg = st.tg[tl];
+        const float fK = tg.w - (tg.x * Xx + tg.y * Xy + tg.z * Xz);  // n_t.(y - x)
+        const float nn = X.nx * tg.x + X.ny * tg.y + X.nz * tg.z;      // n_x.n_t
+        const float s2r = S2r.x + S2r.y, s2i = S2i.x + S2i.y;
+#pragma unroll
+        for (int q = 0; q < MRG; q++) {
+            const PairTriM& T = S[q];
+            AccM& t = acc[q];
+            const float4 cre = st.tc[q][2 * tl], cim = st.tc[q][2 * tl + 1];
+            t.K[0] = fmaf(-fK, T.nS1r.x + T.nS1r.y, t.K[0]);
+            t.K[1] = fmaf(-fK, T.nS1i.x + T.nS1i.y, t.K[1]);
+            t.Wm[0] = fmaf(nn, T.S3r.x + T.S3r.y, t.Wm[0]);
+            t.Wm[1] = fmaf(nn, T.S3i.x + T.S3i.y, t.Wm[1]);
+            t.Wc[0] = fmaf(s2r, cre.x, fmaf(-s2i, cim.x, t.Wc[0]));
+            t.Wc[1] = fmaf(s2r, cre.y, fmaf(-s2i, cim.y, t.Wc[1]));
+            t.Wc[2] = fmaf(s2r, cre.z, fmaf(-s2i, cim.z, t.Wc[2]));
+            t.Wc[3] = fmaf(s2r, cim.x, fmaf(s2i, cre.x, t.Wc[3]));
+            t.Wc[4] = fmaf(s2r, cim.y, fmaf(s2i, cre.y, t.Wc[4]));
+            t.Wc[5] = fmaf(s2r, cim.z, fmaf(s2i, cre.z, t.Wc[5]));
+        }
+    }
+}
+
+// Work item: target tile tx (offset from A.tgt_begin) against source chunk
+// cy at wavenumber slot `slot` (0: k0 on every source tile; 1: the target
+// domain's k_j on its own tiles), right-hand sides grp * MRG ... + MRG - 1.
+template <bool LOSSY>
+__device__ __forceinline__ void far32m_item(const FarArgs32M& A, int tx, int cy, int slot, int grp) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FarSmemM& sm = *reinterpret_cast<FarSmemM*>(smem_raw);
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int tt = A.tgt_begin + tx;
+    const int mydom = A.tdom[tt];
+    const int2 dr = A.dom_tiles[mydom];
+    int sb = A.src_begin + cy * A.chunk_tiles;
+    int se = min(sb + A.chunk_tiles, A.src_end);
+    if (slot) {
+        sb = max(sb, dr.x);
+        se = min(se, dr.y);
+    }
+    const int nsrc = max(0, se - sb);
+    const int r0 = grp * MRG;
+    const int nq = min(MRG, A.R - r0);
+
+    const int64_t p = (int64_t)tt * TP + tid;
+    const float4 g = A.pg[p];
+    const int mt = tid / QP;
+    const float4 ng = A.tg[(int64_t)tt * TT + mt];
+    const double4 ct = A.tc[tt];
+    const double2 kk = slot ? A.kdom[mydom] : A.k0;
+    const PairK k{bc2((float)kk.x), bc2((float)-kk.x), bc2(0.f), bc2((float)kk.y),
+                  bc2((float)(-kk.y * 1.4426950408889634))};
+    const PairTgt X{g.x, g.y, g.z, ng.x, ng.y, ng.z, g.x * g.x + g.y * g.y + g.z * g.z,
+                    ng.x * g.x + ng.y * g.y + ng.z * g.z, bc2(-ng.x), bc2(-ng.y), bc2(-ng.z)};
+
+    // tile-pair table: 2D, R_c^2, R_c and the FP64-reduced phase
+    for (int i = tid; i < nsrc; i += TP) {
+        const double4 cs = A.tc[sb + i];
+        const double Dx = ct.x - cs.x, Dy = ct.y - cs.y, Dz = ct.z - cs.z;
+        const double R = sqrt(Dx * Dx + Dy * Dy + Dz * Dz);
+        sm.tab[2 * i] = make_float4((float)(2 * Dx), (float)(2 * Dy), (float)(2 * Dz), (float)(R * R));
+        sm.tab[2 * i + 1] = make_float4((float)R, reduce_phase(kk.x * R), 0.f, 0.f);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE_M; s++) {
+            mbar_init(&sm.full[s], 1);
+            sm.cnt[s] = 0;
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    auto issue = [&](int i, int st) {
+        const int s = sb + i;
+        StageM& S = sm.st[st];
+        mbar_arrive_expect_tx(&sm.full[st], STAGE_M_BYTES);
+        bulk_g2s(S.pg, A.pgp + (int64_t)s * TP, TP * 16, &sm.full[st]);
+        bulk_g2s(S.tg, A.tg + (int64_t)s * TT, TT * 16, &sm.full[st]);
+#pragma unroll
+        for (int q = 0; q < MRG; q++) {
+            const int64_t r = min(r0 + q, A.R - 1);  // a short last group repeats the last vector (not written)
+            bulk_g2s(S.pd[q], A.pd + r * A.n_pts + (int64_t)s * TP, TP * 16, &sm.full[st]);
+            bulk_g2s(S.tc[q], A.tcurl + r * 2 * A.n_slots + (int64_t)s * 2 * TT, 2 * TT * 16, &sm.full[st]);
+        }
+    };
+    if (tid == 0)
+        for (int i = 0; i < min(NSTAGE_M, nsrc); i++) issue(i, i);
+
+    AccM acc[MRG];
+#pragma unroll
+    for (int q = 0; q < MRG; q++) {
+        const f2 z2 = make_float2(0.f, 0.f);
+        acc[q].Vr = acc[q].Vi = acc[q].nKpr = acc[q].nKpi = z2;
+        acc[q].K[0] = acc[q].K[1] = acc[q].Wm[0] = acc[q].Wm[1] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 6; c++) acc[q].Wc[c] = 0.f;
+    }
+    for (int i = 0; i < nsrc; i++) {
+        const int st = i % NSTAGE_M;
+        mbar_wait_bounded(&sm.full[st], (uint32_t)((i / NSTAGE_M) & 1), A.err);
+        const int s = sb + i;
+        const int ntri = A.tntri[s];
+        const int skip = (s == tt) ? mt : -1;
+        const float4 c0 = sm.tab[2 * i], c1 = sm.tab[2 * i + 1];
+        PairK kt = k;
+        kt.th = bc2(c1.y);
+        tile_body_m<LOSSY>(sm.st[st], ntri, skip, X, c0, c1.x, kt, acc);
+        // leave the stage; the last warp out refills it with the tile NSTAGE_M ahead
+        __syncwarp();
+        if (lane == 0) {
+            const int old = atomicAdd(&sm.cnt[st], 1);
+            if (old == NWARP - 1) {
+                sm.cnt[st] = 0;
+                if (i + NSTAGE_M < nsrc) issue(i + NSTAGE_M, st);
+            }
+        }
+    }
+
+#pragma unroll
+    for (int q = 0; q < MRG; q++) {
+        if (q >= nq) break;
+        const AccM& t = acc[q];
+        // the 14 potentials in the order of the one-vector kernel: PV, PK, PK', PWm, PWc
+        const float v[NCOMP] = {t.Vr.x + t.Vr.y, t.Vi.x + t.Vi.y, t.K[0], t.K[1], -(t.nKpr.x + t.nKpr.y),
+                                -(t.nKpi.x + t.nKpi.y), t.Wm[0], t.Wm[1], t.Wc[0], t.Wc[1], t.Wc[2], t.Wc[3],
+                                t.Wc[4], t.Wc[5]};
+        float* out = A.partial + (int64_t)(r0 + q) * A.rstride + ((int64_t)cy * 2 + slot) * NCOMP * A.n_pts + p;
+#pragma unroll
+        for (int c = 0; c < NCOMP; c++) out[(int64_t)c * A.n_pts] = v[c];
+    }
+}
+
+__global__ void __launch_bounds__(TP, 2) far32m_kernel(FarArgs32M A) {
+    const int4 w = A.work[blockIdx.x];
+    const int mydom = A.tdom[A.tgt_begin + w.x];
+    const double ki = w.z ? A.kdom[mydom].y : A.k0.y;
+    if (ki != 0.0) far32m_item<true>(A, w.x, w.y, w.z, w.w);
+    else far32m_item<false>(A, w.x, w.y, w.z, w.w);
+}
+
+cudaError_t launch_far32_multi(const FarArgs32M& a, int64_t n_work, cudaStream_t s) {
+    const size_t smem = sizeof(FarSmemM);
+    static const cudaError_t attr_e =
+        cudaFuncSetAttribute(far32m_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr_e != cudaSuccess) return attr_e;
+    if (n_work <= 0) return cudaSuccess;
+    far32m_kernel<<<(unsigned)n_work, TP, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------- FP64 far field
 
 __global__ void __launch_bounds__(TP) far64_kernel(FarArgs64 A) {

@@ -43,15 +43,21 @@ struct OsrcState {
     double* dm = nullptr;              // diag(M)
     double* ds = nullptr;              // diag(S)
     int n_pade = 0;
-    double2 C0{}, ikk{};               // C0 and i k
-    std::vector<double2> A, B;         // A_l / k_eps^2, B_l / k_eps^2
-    double2 inv_keps2{};               // 1 / k_eps^2
+    // per domain d (the block's wavenumber k_d, bem_opts.osrc_wavenumber):
+    double2 C0{};                      // C0 (the same for every domain)
+    std::vector<double2> ikk;          // [n_dom] i k_d
+    std::vector<double2> A, B;         // [n_dom][n_pade] A_l / k_eps,d^2, B_l / k_eps,d^2
+    std::vector<double2> inv_keps2;    // [n_dom] 1 / k_eps,d^2
+    double2* dA = nullptr;             // device [n_dom][n_pade] copy of A
+    double2* post_b = nullptr;         // device [n_dom][2]: (i k_d, 1), the bracket rows' factors
+    double2* post_c = nullptr;         // device [n_dom][2]: (1, 1 / (i k_d)), the closing factors
+    int32_t* vdom = nullptr;           // device [n] domain of each vertex
     int max_sys = 0;
     int64_t max_rhs = 0;               // right-hand sides the batched buffers hold
     int nblk = 0;
     // batched COCG state, [max_sys][n] complex; max_sys = 2 n_pade max_rhs
     double2 *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *b = nullptr;
-    double2* beta = nullptr;           // [max_sys] shifts
+    double2* beta = nullptr;           // [max_sys][n_dom] shifts (per system and domain)
     double* part = nullptr;            // [max_sys][nblk][4] partial sums
     double* scal = nullptr;            // [max_sys][8]: rho(2 parities) re/im, bnorm2, rnorm2, active
     // stage vectors, [max_rhs][2][n]
@@ -129,7 +135,9 @@ struct CocgArgs {
     const int64_t* rp;
     const int32_t* ci;
     const double *vm, *vs, *dm, *ds;
-    const double2* beta;
+    const double2* beta;   // [n_sys][nd]
+    const int32_t* vdom;   // [n] domain of each row
+    int nd;
     double2 *x, *r, *z, *p, *q, *b;
     double* part;
     double* scal;
@@ -146,12 +154,12 @@ __device__ __forceinline__ double2 diag_inv(const CocgArgs& a, int64_t i, double
 // init: x = 0, r = b, z = D^-1 b, p = z; partials of b^T z and |b|^2
 __global__ void cocg_init(CocgArgs a) {
     const int s = blockIdx.y;
-    const double2 be = a.beta[s];
+    const double2* bes = a.beta + (int64_t)s * a.nd;
     const int64_t off = (int64_t)s * a.n;
     double v[4] = {0, 0, 0, 0};
     for (int64_t i = (int64_t)blockIdx.x * SP_THREADS + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * SP_THREADS) {
         const double2 bi = a.b[off + i];
-        const double2 zi = cmul(diag_inv(a, i, be), bi);
+        const double2 zi = cmul(diag_inv(a, i, bes[a.vdom[i]]), bi);
         a.x[off + i] = make_double2(0, 0);
         a.r[off + i] = bi;
         a.z[off + i] = zi;
@@ -181,12 +189,13 @@ __global__ void cocg_init_scalars(CocgArgs a) {
 // q = (M - beta S) p ; partials of p^T q
 __global__ void cocg_spmv(CocgArgs a) {
     const int s = blockIdx.y;
-    const double2 be = a.beta[s];
+    const double2* bes = a.beta + (int64_t)s * a.nd;
     const int64_t off = (int64_t)s * a.n;
     double v[4] = {0, 0, 0, 0};
     const bool active = a.scal[(int64_t)s * 8 + 6] != 0.0;
     if (active)
         for (int64_t i = (int64_t)blockIdx.x * SP_THREADS + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * SP_THREADS) {
+            const double2 be = bes[a.vdom[i]];  // the matrix is block diagonal over domains
             double qr = 0, qi = 0;
             for (int64_t e = a.rp[i]; e < a.rp[i + 1]; e++) {
                 const double2 pj = a.p[off + a.ci[e]];
@@ -223,7 +232,7 @@ __global__ void cocg_update(CocgArgs a) {
         const int par = a.it & 1;
         const double2 rho = make_double2(sc[2 * par], sc[2 * par + 1]);
         const double2 alpha = cdiv(rho, make_double2(pqr, pqi));
-        const double2 be = a.beta[s];
+        const double2* bes = a.beta + (int64_t)s * a.nd;
         const int64_t off = (int64_t)s * a.n;
         for (int64_t i = (int64_t)blockIdx.x * SP_THREADS + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * SP_THREADS) {
             const double2 pi = a.p[off + i], qi = a.q[off + i];
@@ -233,7 +242,7 @@ __global__ void cocg_update(CocgArgs a) {
             ri.x -= aq.x; ri.y -= aq.y;
             a.x[off + i] = xi;
             a.r[off + i] = ri;
-            const double2 zi = cmul(diag_inv(a, i, be), ri);
+            const double2 zi = cmul(diag_inv(a, i, bes[a.vdom[i]]), ri);
             a.z[off + i] = zi;
             const double2 rz = cmul(ri, zi);
             v[0] += rz.x;
@@ -300,7 +309,7 @@ struct CocgCtaArgs {
     const int32_t* eci;        // ELL [W][n]
     const double *em, *es;     // ELL [W][n]
     const double *dm, *ds;
-    const double2* beta;       // [n_sys]
+    const double2* beta;       // [n_sys][n_dom]
     const double2* b;          // [n_sys][n]
     double2 *x, *r, *z, *p, *q;
     const int64_t* dom_v0;     // [n_dom + 1]
@@ -343,7 +352,7 @@ __global__ void __launch_bounds__(NT) cocg_cta_kernel(CocgCtaArgs a) {
     const int s = blockIdx.x / a.n_dom, j = blockIdx.x % a.n_dom;
     const int64_t v0 = a.dom_v0[j], v1 = a.dom_v0[j + 1];
     const int64_t n = a.n, off = (int64_t)s * n;
-    const double2 be = a.beta[s];
+    const double2 be = a.beta[(int64_t)s * a.n_dom + j];
     const double2* b = a.b + off;
     double2 *x = a.x + off, *r = a.r + off, *z = a.z + off, *p = a.p + off, *q = a.q + off;
     auto dinv = [&](int64_t i) {
@@ -505,7 +514,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) cocg_cluster_ke
     const int64_t per = (d1 - d0 + CL - 1) / CL;
     const int64_t v0 = min(d1, d0 + rank * per), v1 = min(d1, v0 + per);
     const int64_t n = a.n, off = (int64_t)s * n;
-    const double2 be = a.beta[s];
+    const double2 be = a.beta[(int64_t)s * a.n_dom + j];
     const double2* b = a.b + off;
     double2 *x = a.x + off, *r = a.r + off, *z = a.z + off, *p = a.p + off, *q = a.q + off;
     auto dinv = [&](int64_t i) {
@@ -663,7 +672,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) cocg_cluster_sh
     const int64_t n = a.n, off0 = (int64_t)grp * L * n;  // system grp*L + l at off0 + l*n
     const double2* b = a.b + off0;                       // the shared right-hand side (first shift's copy)
     if (threadIdx.x < L) {
-        be[threadIdx.x] = a.beta[grp * L + threadIdx.x];
+        be[threadIdx.x] = a.beta[((int64_t)grp * L + threadIdx.x) * a.n_dom + j];
         brk[threadIdx.x] = 0;
     }
     __syncthreads();
@@ -835,8 +844,9 @@ struct BracketArgs {
     const double2* w;
     int L;
     double2 C0;
-    double2 A[16];
-    double2 post[2];   // factor applied to row 0 / row 1 of the result
+    const double2* A;      // [n_dom][L] (vertex i uses the row of its domain)
+    const double2* post;   // [n_dom][2] factor applied to row 0 / row 1 of the result
+    const int32_t* vdom;   // [n]
     double2* out;
 };
 
@@ -846,6 +856,7 @@ __global__ void bracket_kernel(BracketArgs a) {
     const int row = blockIdx.y;
     const int64_t rr = (int64_t)blockIdx.z * 2 + row;  // (rhs, row)
     if (i >= a.n) return;
+    const int d = a.vdom[i];
     double2 acc = cmul(a.C0, a.g[rr * a.n + i]);
     for (int l = 0; l < a.L; l++) {
         const double2* wl = a.w + (rr * a.L + l) * a.n;
@@ -855,11 +866,11 @@ __global__ void bracket_kernel(BracketArgs a) {
             sr += a.vs[e] * wj.x;
             si += a.vs[e] * wj.y;
         }
-        const double2 t = cmul(a.A[l], make_double2(sr, si));
+        const double2 t = cmul(a.A[d * a.L + l], make_double2(sr, si));
         acc.x -= t.x;
         acc.y -= t.y;
     }
-    a.out[rr * a.n + i] = cmul(a.post[row], acc);
+    a.out[rr * a.n + i] = cmul(a.post[2 * d + row], acc);
 }
 
 // gather system-order rows (right-hand side blockIdx.y, N = 2n dofs each) into
@@ -935,7 +946,7 @@ static int ensure_osrc_batch(bem_ctx* ctx, OsrcState* o, int64_t R) {
     o->p = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
     o->q = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
     o->b = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
-    o->beta = (double2*)ctx->dalloc(ms * sizeof(double2), &rc); if (rc) return rc;
+    o->beta = (double2*)ctx->dalloc((size_t)ms * o->n_dom * sizeof(double2), &rc); if (rc) return rc;
     o->part = (double*)ctx->dalloc((size_t)ms * o->nblk * 4 * sizeof(double), &rc); if (rc) return rc;
     o->scal = (double*)ctx->dalloc((size_t)ms * 8 * sizeof(double), &rc); if (rc) return rc;
     o->u = (double2*)ctx->dalloc((size_t)2 * R * n * sizeof(double2), &rc); if (rc) return rc;
@@ -958,7 +969,8 @@ static int osrc_build(bem_ctx* ctx) {
         for (void* p : {(void*)o->rp, (void*)o->ci, (void*)o->vm, (void*)o->vs, (void*)o->dm, (void*)o->ds,
                         (void*)o->x, (void*)o->r, (void*)o->z, (void*)o->p, (void*)o->q, (void*)o->b,
                         (void*)o->beta, (void*)o->part, (void*)o->scal, (void*)o->u, (void*)o->g,
-                        (void*)o->dom_v0, (void*)o->stat, (void*)o->ell_ci, (void*)o->ell_m, (void*)o->ell_s})
+                        (void*)o->dom_v0, (void*)o->stat, (void*)o->ell_ci, (void*)o->ell_m, (void*)o->ell_s,
+                        (void*)o->dA, (void*)o->post_b, (void*)o->post_c, (void*)o->vdom})
             ctx->dfree(p);
         for (auto& g : o->graphs) cudaGraphExecDestroy(g.exec);
         if (o->cap) cudaStreamDestroy(o->cap);
@@ -1047,7 +1059,12 @@ static int osrc_build(bem_ctx* ctx) {
         (rc = up(&o->dm, dm)) || (rc = up(&o->ds, ds)) || (rc = up(&o->dom_v0, dv0)) || (rc = up(&o->stat, st0)))
         return rc;
     if (ell_w && ((rc = up(&o->ell_ci, eci)) || (rc = up(&o->ell_m, em)) || (rc = up(&o->ell_s, es)))) return rc;
-    // Pade coefficients and the damped wavenumber (exterior k0, Sec. 2.3)
+    std::vector<int32_t> vd(n);
+    for (int d = 0; d < g.n_dom; d++)
+        for (int64_t v = dv0[d]; v < dv0[d + 1]; v++) vd[v] = d;
+    if ((rc = up(&o->vdom, vd))) return rc;
+    // Pade coefficients and, per domain, the damped wavenumber of its block
+    // (Sec. 2.3): the domain's own k_d, or the exterior k0 for every block
     const int N = ctx->opts.n_pade;
     if (N < 1 || N > 16) return ctx->fail(BEM_ERR_INVALID_ARG, "n_pade must be in 1..16");
     const double th = ctx->opts.pade_theta;
@@ -1063,24 +1080,36 @@ static int osrc_build(bem_ctx* ctx) {
     }
     const cd C0 = std::exp(cd(0, 0.5 * th)) * R;
     double reps = ctx->opts.r_eps > 0 ? ctx->opts.r_eps : 0.1 * g.max_diameter;
-    const cd k0(ctx->k0re, ctx->k0im);
-    const double eps = 0.4 * std::pow(ctx->k0re, ctx->opts.eps_exponent) * std::pow(reps, -2.0 / 3.0);
-    const cd keps = k0 + cd(0, eps);
-    const cd ik2 = 1.0 / (keps * keps);
+    const int nd = g.n_dom;
     o->n_pade = N;
     o->C0 = make_double2(C0.real(), C0.imag());
-    const cd ik = cd(0, 1) * k0;
-    o->ikk = make_double2(ik.real(), ik.imag());
-    o->inv_keps2 = make_double2(ik2.real(), ik2.imag());
-    o->A.resize(N);
-    o->B.resize(N);
-    for (int l = 0; l < N; l++) {
-        const cd den = 1.0 + bl[l] * (e - 1.0);
-        const cd Al = std::exp(cd(0, -0.5 * th)) * al[l] / (den * den) * ik2;
-        const cd Bl = e * bl[l] / den * ik2;
-        o->A[l] = make_double2(Al.real(), Al.imag());
-        o->B[l] = make_double2(Bl.real(), Bl.imag());
+    o->ikk.resize(nd);
+    o->inv_keps2.resize(nd);
+    o->A.resize((size_t)nd * N);
+    o->B.resize((size_t)nd * N);
+    std::vector<double2> pb((size_t)2 * nd), pc((size_t)2 * nd);
+    for (int d = 0; d < nd; d++) {
+        const cd kd = ctx->opts.osrc_wavenumber == 1 ? cd(ctx->k0re, ctx->k0im) : cd(ctx->doms[d].kre, ctx->doms[d].kim);
+        const double eps = 0.4 * std::pow(kd.real(), ctx->opts.eps_exponent) * std::pow(reps, -2.0 / 3.0);
+        const cd keps = kd + cd(0, eps);
+        const cd ik2 = 1.0 / (keps * keps);
+        const cd ik = cd(0, 1) * kd;
+        o->ikk[d] = make_double2(ik.real(), ik.imag());
+        o->inv_keps2[d] = make_double2(ik2.real(), ik2.imag());
+        for (int l = 0; l < N; l++) {
+            const cd den = 1.0 + bl[l] * (e - 1.0);
+            const cd Al = std::exp(cd(0, -0.5 * th)) * al[l] / (den * den) * ik2;
+            const cd Bl = e * bl[l] / den * ik2;
+            o->A[(size_t)d * N + l] = make_double2(Al.real(), Al.imag());
+            o->B[(size_t)d * N + l] = make_double2(Bl.real(), Bl.imag());
+        }
+        const cd inv = 1.0 / ik;
+        pb[2 * d] = o->ikk[d];
+        pb[2 * d + 1] = make_double2(1.0, 0.0);
+        pc[2 * d] = make_double2(1.0, 0.0);
+        pc[2 * d + 1] = make_double2(inv.real(), inv.imag());
     }
+    if ((rc = up(&o->dA, o->A)) || (rc = up(&o->post_b, pb)) || (rc = up(&o->post_c, pc))) return rc;
     o->nblk = (int)std::min<int64_t>(128, (n + SP_THREADS - 1) / SP_THREADS);
     if ((rc = ensure_osrc_batch(ctx, o, 1))) return rc;
     o->tol = ctx->osrc_tol;
@@ -1186,6 +1215,7 @@ static int cocg_solve_grid(bem_ctx* ctx, int n_sys) {
     CocgArgs a{};
     a.n = o->n; a.rp = o->rp; a.ci = o->ci; a.vm = o->vm; a.vs = o->vs; a.dm = o->dm; a.ds = o->ds;
     a.beta = o->beta; a.x = o->x; a.r = o->r; a.z = o->z; a.p = o->p; a.q = o->q; a.b = o->b;
+    a.vdom = o->vdom; a.nd = o->n_dom;
     a.part = o->part; a.scal = o->scal; a.nblk = o->nblk; a.tol2 = o->tol * o->tol;
     const dim3 grid(o->nblk, n_sys);
     cocg_init<<<grid, SP_THREADS, 0, ctx->stream>>>(a);
@@ -1251,33 +1281,33 @@ int bem_ctx::apply_prec_batch(const double2* xin, double2* yout, int64_t R) {
     const int ns = (int)(2 * L * R);
     // rows in vertex order: g[rb][0] = row1, g[rb][1] = row2
     rows_to_vertex<<<dim3(nb, (unsigned)R), SP_THREADS, 0, stream>>>(n, dev.v_dof1, dev.v_dof2, xin, o->g);
-    // Pade solves w_{rb,i,l} = (M - B_l S)^-1 row_i, systems ordered [rb][row][l]
+    // Pade solves w_{rb,i,l} = (M - B_l S)^-1 row_i, systems ordered [rb][row][l],
+    // the shift of system s on domain d at be[s][d]
     replicate_rows<<<dim3(nb, (unsigned)ns), SP_THREADS, 0, stream>>>(n, L, o->g, o->b);
-    std::vector<double2> be(ns);
-    for (int s = 0; s < ns; s++) be[s] = o->B[s % L];
-    CK(cudaMemcpyAsync(o->beta, be.data(), ns * sizeof(double2), cudaMemcpyHostToDevice, stream));
+    const int nd = o->n_dom;
+    std::vector<double2> be((size_t)ns * nd);
+    for (int s = 0; s < ns; s++)
+        for (int d = 0; d < nd; d++) be[(size_t)s * nd + d] = o->B[(size_t)d * L + s % L];
+    CK(cudaMemcpyAsync(o->beta, be.data(), be.size() * sizeof(double2), cudaMemcpyHostToDevice, stream));
     if ((rc = cocg_solve(this, ns, L))) return rc;
     // brackets; row 1 scaled by i k (the DtN weak form)
     BracketArgs ba{};
     ba.n = n; ba.rp = o->rp; ba.ci = o->ci; ba.vs = o->vs; ba.g = o->g; ba.w = o->x; ba.L = L; ba.C0 = o->C0;
-    for (int l = 0; l < L; l++) ba.A[l] = o->A[l];
-    ba.post[0] = o->ikk;
-    ba.post[1] = make_double2(1.0, 0.0);
+    ba.A = o->dA; ba.post = o->post_b; ba.vdom = o->vdom;
     ba.out = o->b;
     bracket_kernel<<<dim3(nb, 2, (unsigned)R), SP_THREADS, 0, stream>>>(ba);
     // out1 = M^-1 (i k bracket_1);  out2 = (M - S/k_eps^2)^-1 bracket_2, then / (i k)
-    for (int64_t rb = 0; rb < R; rb++) {
-        be[2 * rb] = make_double2(0, 0);
-        be[2 * rb + 1] = o->inv_keps2;
-    }
-    CK(cudaMemcpyAsync(o->beta, be.data(), 2 * R * sizeof(double2), cudaMemcpyHostToDevice, stream));
+    for (int64_t rb = 0; rb < R; rb++)
+        for (int d = 0; d < nd; d++) {
+            be[(size_t)(2 * rb) * nd + d] = make_double2(0, 0);
+            be[(size_t)(2 * rb + 1) * nd + d] = o->inv_keps2[d];
+        }
+    CK(cudaMemcpyAsync(o->beta, be.data(), (size_t)2 * R * nd * sizeof(double2), cudaMemcpyHostToDevice, stream));
     if ((rc = cocg_solve(this, (int)(2 * R)))) return rc;
-    const std::complex<double> inv = 1.0 / std::complex<double>(o->ikk.x, o->ikk.y);
     BracketArgs cp{};  // scaled copy (no Pade terms): u_row = post_row * x_row
     cp.n = n; cp.rp = o->rp; cp.ci = o->ci; cp.vs = o->vs; cp.g = o->x; cp.w = nullptr; cp.L = 0;
     cp.C0 = make_double2(1.0, 0.0);
-    cp.post[0] = make_double2(1.0, 0.0);
-    cp.post[1] = make_double2(inv.real(), inv.imag());
+    cp.post = o->post_c; cp.vdom = o->vdom;
     cp.out = o->u;
     bracket_kernel<<<dim3(nb, 2, (unsigned)R), SP_THREADS, 0, stream>>>(cp);
     vertex_to_rows<<<dim3(nb, (unsigned)R), SP_THREADS, 0, stream>>>(n, dev.v_dof1, dev.v_dof2, o->u, yout);

@@ -51,6 +51,27 @@ def test_kidney_scene_sampled_rows(kidney, prec, tol):
     c.close()
 
 
+def test_kidney_scene_16_rhs_one_launch(kidney):
+    """The kidney workload with 16 right-hand sides in one matrix-free FP32
+    far-field launch: sampled rows of every column against the oracle."""
+    from paper_1910_01011_gb300 import api
+    s, rows, x, _ = kidney
+    X = np.stack([x * np.exp(0.37j * r) + 0.2 * scenes.random_complex(s.n_dofs, 60 + r) for r in range(16)])
+    c = api.Context.from_scene(s)
+    Y = c.apply(X, precision=1)
+    off = pmchwt.offsets(s)
+    errs = []
+    for r in (0, 7, 15):
+        ref = pmchwt.apply_rows(s, X[r], rows)
+        for j, d in enumerate(s.domains):
+            nv = d.verts.shape[0]
+            got = np.concatenate([Y[r][off[j] + rows[j]], Y[r][off[j] + nv + rows[j]]])
+            errs.append(rel(got, np.concatenate(ref[j])))
+    print(errs)
+    assert max(errs) < 2e-5
+    c.close()
+
+
 RIB_SMALL_H = 6e-3
 RIB_SMALL_FREQ = 0.1e6 * 2.65 / 6.0  # k h as for the 41k-triangle scene at 0.1 MHz
 
