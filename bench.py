@@ -341,6 +341,8 @@ def sphere_solve_metrics(local, reps=12):
             "speedup_vs_fp64": float(np.median(t64) / np.median(t32)),
             "trace_rel_diff_mixed_vs_fp64": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
             "iterations": {"fp64": r64["iterations"], "mixed": r32["iterations"], "refinements": r32["refinements"]},
+            "ms_per_iteration": {"fp64": 1e3 * float(np.median(t64)) / max(1, r64["iterations"]),
+                                 "mixed": 1e3 * float(np.median(t32)) / max(1, r32["iterations"])},
             "field": field}
 
 

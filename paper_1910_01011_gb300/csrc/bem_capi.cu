@@ -192,6 +192,7 @@ int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_
     // GMRES basis and work (per lockstep column)
     const int64_t R = o.batch_rhs > 1 ? std::min<int64_t>(o.batch_rhs, n_exc) : 1;
     b += (int64_t)(o.restart + 1) * R * N * 16 + 2 * R * N * 16 + (int64_t)(o.restart + 2) * 120 * R * 16 * 3 + 8 * R;
+    b += (int64_t)R * ((o.restart + 1) * o.restart + 3 * o.restart + 1) * 16 + 32 * R + 16;  // device least squares
     if (o.precondition && o.flexible) b += (int64_t)o.restart * R * N * 16;  // flexible basis
     b += 4 * R * N * 16;
     if (o.precondition) {

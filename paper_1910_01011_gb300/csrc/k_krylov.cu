@@ -1,8 +1,12 @@
 // k_krylov.cu -- restarted GMRES with FP64 device vectors (the paper's
 // solver: GMRES, restart 100, Sec. 3).  Arnoldi by classical Gram-Schmidt
 // applied twice (one batched dot-product kernel and one batched update per
-// pass), deterministic fixed-order reductions, Givens rotations on the host
-// (the Hessenberg column is j+2 numbers per iteration).
+// pass), deterministic fixed-order reductions.  The Hessenberg columns, the
+// Givens rotations, the residual estimates and the triangular solve of each
+// restart cycle stay on the device in FP64 (one small kernel per step), so an
+// Arnoldi step does not wait for the host: the host reads how many columns
+// are still running a few steps late (POLL_LAG) and stops launching steps
+// once none is.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -180,6 +184,94 @@ __global__ void kvb_scale(double2* W, int64_t n, const double* s) {
     W[(int64_t)r * n + i] = v;
 }
 
+// ---- least squares on the device
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+struct GivensArgs {
+    const double2* part;   // [R][nbk] partial sums of |v_{j+1}|^2 (real parts)
+    int nbk;
+    const double2* h1;     // [R][ldh] first Gram-Schmidt pass
+    const double2* h2;     // [R][ldh] second pass
+    int ldh, j, m;
+    double2 *H, *cs, *sn, *g;
+    const double* bn;
+    double* res;
+    int *run, *jr, *its;
+    double* scale;         // [R] 1 / h_{j+1,j} for running columns, else 0
+    double tol;
+    int* n_run;            // running columns after this step (zeroed before the launch)
+};
+
+// Step j of every column: Hessenberg column j = h1 + h2 and |v_{j+1}|, the
+// earlier rotations applied to it, the new rotation that zeroes h_{j+1,j},
+// the rotated right-hand side g and the residual estimate |g_{j+1}| / |b|.
+__global__ void givens_step_kernel(GivensArgs a) {
+    const int r = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    a.scale[r] = 0.0;
+    if (!a.run[r]) return;
+    const int m = a.m, j = a.j;
+    double s = 0;
+    for (int q = 0; q < a.nbk; q++) s += a.part[(int64_t)r * a.nbk + q].x;
+    const double hn = sqrt(fmax(0.0, s));
+    double2* H = a.H + (int64_t)r * (m + 1) * m;
+    double2* cs = a.cs + (int64_t)r * m;
+    double2* sn = a.sn + (int64_t)r * m;
+    double2* g = a.g + (int64_t)r * (m + 1);
+    for (int i = 0; i <= j; i++) H[i * m + j] = zadd(a.h1[(int64_t)r * a.ldh + i], a.h2[(int64_t)r * a.ldh + i]);
+    H[(j + 1) * m + j] = make_double2(hn, 0.0);
+    for (int i = 0; i < j; i++) {
+        const double2 x = H[i * m + j], y = H[(i + 1) * m + j];
+        H[i * m + j] = zadd(zmul(zconj(cs[i]), x), zmul(zconj(sn[i]), y));
+        H[(i + 1) * m + j] = zsub(zmul(cs[i], y), zmul(sn[i], x));
+    }
+    const double2 x = H[j * m + j], y = H[(j + 1) * m + j];
+    const double den = sqrt(x.x * x.x + x.y * x.y + y.x * y.x + y.y * y.y);
+    cs[j] = den > 0 ? make_double2(x.x / den, x.y / den) : make_double2(1.0, 0.0);
+    sn[j] = den > 0 ? make_double2(y.x / den, y.y / den) : make_double2(0.0, 0.0);
+    H[j * m + j] = make_double2(den, 0.0);
+    H[(j + 1) * m + j] = make_double2(0.0, 0.0);
+    const double2 gj = g[j];
+    g[j + 1] = zmul(make_double2(-sn[j].x, -sn[j].y), gj);
+    g[j] = zmul(zconj(cs[j]), gj);
+    a.its[r] += 1;
+    a.jr[r] = j + 1;
+    const double rr = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y) / a.bn[r];
+    a.res[r] = rr;
+    if (rr <= a.tol || hn == 0) {
+        a.run[r] = 0;
+    } else {
+        a.scale[r] = 1.0 / hn;
+        atomicAdd(a.n_run, 1);
+    }
+}
+
+// y = H^-1 g over each column's own jr steps (zeros beyond), FP64.
+__global__ void backsolve_kernel(const double2* H, const double2* g, const int* jr, int m, double2* y, int ldh) {
+    const int r = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    const double2* Hr = H + (int64_t)r * (m + 1) * m;
+    const double2* gr = g + (int64_t)r * (m + 1);
+    double2* yr = y + (int64_t)r * ldh;
+    const int jj = jr[r];
+    for (int i = jj; i < ldh; i++) yr[i] = make_double2(0.0, 0.0);
+    for (int i = jj - 1; i >= 0; i--) {
+        double2 s = gr[i];
+        for (int k = i + 1; k < jj; k++) s = zsub(s, zmul(Hr[i * m + k], yr[k]));
+        yr[i] = zdiv(s, Hr[i * m + i]);
+    }
+}
+
 }  // namespace gbem
 
 using namespace gbem;
@@ -206,6 +298,23 @@ int Krylov::ensure(bem_ctx* ctx, int64_t n_, int m_, int64_t R_) {
     h = (double2*)ctx->dalloc((m + 2) * R * sizeof(double2), &rc); if (rc) return rc;
     y = (double2*)ctx->dalloc((m + 2) * R * sizeof(double2), &rc); if (rc) return rc;
     sc = (double*)ctx->dalloc(R * sizeof(double), &rc); if (rc) return rc;
+    H = (double2*)ctx->dalloc((size_t)R * (m + 1) * m * sizeof(double2), &rc); if (rc) return rc;
+    cs = (double2*)ctx->dalloc((size_t)R * m * sizeof(double2), &rc); if (rc) return rc;
+    sn = (double2*)ctx->dalloc((size_t)R * m * sizeof(double2), &rc); if (rc) return rc;
+    g = (double2*)ctx->dalloc((size_t)R * (m + 1) * sizeof(double2), &rc); if (rc) return rc;
+    bn = (double*)ctx->dalloc(R * sizeof(double), &rc); if (rc) return rc;
+    res = (double*)ctx->dalloc(R * sizeof(double), &rc); if (rc) return rc;
+    run = (int*)ctx->dalloc(R * sizeof(int), &rc); if (rc) return rc;
+    jr = (int*)ctx->dalloc(R * sizeof(int), &rc); if (rc) return rc;
+    its = (int*)ctx->dalloc(R * sizeof(int), &rc); if (rc) return rc;
+    n_run = (int*)ctx->dalloc(4 * sizeof(int), &rc); if (rc) return rc;
+    if (!n_run_host && cudaMallocHost(&n_run_host, 4 * sizeof(int)) != cudaSuccess) {
+        n_run_host = nullptr;
+        return ctx->fail(BEM_ERR_CUDA, "cudaMallocHost (GMRES poll)");
+    }
+    for (auto& e : poll_ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return ctx->fail(BEM_ERR_CUDA, "cudaEventCreate (GMRES poll)");
     return BEM_OK;
 }
 
@@ -217,9 +326,13 @@ int Krylov::ensure_flexible(bem_ctx* ctx) {
 }
 
 void Krylov::release(bem_ctx* ctx) {
-    for (void* p : {(void*)V, (void*)w, (void*)t, (void*)part, (void*)h, (void*)y, (void*)sc, (void*)Z}) ctx->dfree(p);
-    V = w = t = part = h = y = Z = nullptr;
-    sc = nullptr;
+    for (void* p : {(void*)V, (void*)w, (void*)t, (void*)part, (void*)h, (void*)y, (void*)sc, (void*)Z, (void*)H,
+                    (void*)cs, (void*)sn, (void*)g, (void*)bn, (void*)res, (void*)run, (void*)jr, (void*)its,
+                    (void*)n_run})
+        ctx->dfree(p);
+    V = w = t = part = h = y = Z = H = cs = sn = g = nullptr;
+    sc = bn = res = nullptr;
+    run = jr = its = n_run = nullptr;
     n = 0;
     m = 0;
     R = 0;
@@ -256,117 +369,10 @@ int Krylov::axpby(bem_ctx* ctx, std::complex<double> a, const double2* x, std::c
 }
 
 // Solve op(x) = b to ||b - op(x)|| <= tol ||b|| (residual of the system it is
-// given), x holds the initial guess on entry.
+// given), x holds the initial guess on entry: the batched solver with one column.
 int Krylov::gmres(bem_ctx* ctx, const Op& op, const double2* b, double2* x, int restart, double tol, int max_iter,
                   int* iters, double* relres, bool zero_guess, const Op* prec) {
-    using cd = std::complex<double>;
-    int rc = ensure(ctx, n, restart);
-    if (rc) return rc;
-    if (prec && (rc = ensure_flexible(ctx))) return rc;
-    const int64_t ldz = R * n;  // stride of the flexible basis (column 0 of each block)
-    const unsigned nb = (unsigned)((n + KV_THREADS - 1) / KV_THREADS);
-    double bnorm;
-    if ((rc = norm(ctx, b, &bnorm))) return rc;
-    *iters = 0;
-    if (bnorm == 0) {
-        CK(cudaMemsetAsync(x, 0, n * sizeof(double2), ctx->stream));
-        *relres = 0;
-        return BEM_OK;
-    }
-    std::vector<cd> H((size_t)(restart + 1) * restart), cs(restart), sn(restart), g(restart + 1);
-    std::vector<double2> hcol(restart + 2);
-    double res = 1.0;
-    bool first = true;
-    while (*iters < max_iter) {
-        // r = b - op(x) into V_0
-        if (first && zero_guess) {
-            CK(cudaMemcpyAsync(V, b, n * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
-            CK(cudaMemsetAsync(x, 0, n * sizeof(double2), ctx->stream));
-        } else {
-            if ((rc = op(x, t))) return rc;
-            if ((rc = axpby(ctx, 1.0, b, -1.0, t, V))) return rc;
-        }
-        first = false;
-        double beta;
-        if ((rc = norm(ctx, V, &beta))) return rc;
-        res = beta / bnorm;
-        if (res <= tol) break;
-        if ((rc = axpby(ctx, 1.0 / beta, V, 0.0, nullptr, V))) return rc;
-        std::fill(g.begin(), g.end(), cd(0));
-        g[0] = beta;
-        int j = 0;
-        for (; j < restart && *iters < max_iter; j++) {
-            double2* vj1 = V + (int64_t)(j + 1) * n;
-            if (prec) {
-                double2* zj = Z + (int64_t)j * ldz;
-                if ((rc = (*prec)(V + (int64_t)j * n, zj))) return rc;
-                if ((rc = op(zj, vj1))) return rc;
-            } else if ((rc = op(V + (int64_t)j * n, vj1))) {
-                return rc;
-            }
-            // CGS2: two passes of h = V^H w; w -= V h
-            for (int pass = 0; pass < 2; pass++) {
-                kv_dots<<<dim3(KV_BLOCKS, j + 1), KV_THREADS, 0, ctx->stream>>>(V, n, j + 1, vj1, n, part);
-                kv_reduce<<<j + 1, 32, 0, ctx->stream>>>(part, KV_BLOCKS, pass == 0 ? h : y, 0);
-                kv_subtract<<<nb, KV_THREADS, 0, ctx->stream>>>(V, n, j + 1, pass == 0 ? h : y, vj1, n);
-                ctx->launches += 3;
-            }
-            CK(cudaGetLastError());
-            double hn;
-            if ((rc = norm(ctx, vj1, &hn))) return rc;
-            CK(cudaMemcpyAsync(hcol.data(), h, (j + 1) * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
-            std::vector<double2> h2(j + 1);
-            CK(cudaMemcpyAsync(h2.data(), y, (j + 1) * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
-            CK(cudaStreamSynchronize(ctx->stream));
-            for (int i = 0; i <= j; i++) H[(size_t)i * restart + j] = cd(hcol[i].x + h2[i].x, hcol[i].y + h2[i].y);
-            H[(size_t)(j + 1) * restart + j] = hn;
-            if (hn > 0) {
-                if ((rc = axpby(ctx, 1.0 / hn, vj1, 0.0, nullptr, vj1))) return rc;
-            }
-            // apply previous rotations, then the new one
-            for (int i = 0; i < j; i++) {
-                cd a = H[(size_t)i * restart + j], c = H[(size_t)(i + 1) * restart + j];
-                H[(size_t)i * restart + j] = std::conj(cs[i]) * a + std::conj(sn[i]) * c;
-                H[(size_t)(i + 1) * restart + j] = -sn[i] * a + cs[i] * c;
-            }
-            cd a = H[(size_t)j * restart + j], c = H[(size_t)(j + 1) * restart + j];
-            double den = std::sqrt(std::norm(a) + std::norm(c));
-            cs[j] = den > 0 ? a / den : 1.0;
-            sn[j] = den > 0 ? c / den : 0.0;
-            H[(size_t)j * restart + j] = den;
-            H[(size_t)(j + 1) * restart + j] = 0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = std::conj(cs[j]) * g[j];
-            (*iters)++;
-            res = std::abs(g[j + 1]) / bnorm;
-            if (res <= tol || hn == 0) {
-                j++;
-                break;
-            }
-        }
-        // back substitution and x += V y
-        std::vector<cd> yv(j);
-        for (int i = j - 1; i >= 0; i--) {
-            cd s = g[i];
-            for (int k = i + 1; k < j; k++) s -= H[(size_t)i * restart + k] * yv[k];
-            yv[i] = s / H[(size_t)i * restart + i];
-        }
-        std::vector<double2> yd(j);
-        for (int i = 0; i < j; i++) yd[i] = make_double2(yv[i].real(), yv[i].imag());
-        CK(cudaMemcpyAsync(y, yd.data(), j * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
-        if (prec) kv_combine<<<nb, KV_THREADS, 0, ctx->stream>>>(Z, ldz, j, y, x, n);
-        else kv_combine<<<nb, KV_THREADS, 0, ctx->stream>>>(V, n, j, y, x, n);
-        ctx->launches += 1;
-        CK(cudaGetLastError());
-        if (res <= tol) break;
-    }
-    // true residual of the given system
-    if ((rc = op(x, t))) return rc;
-    if ((rc = axpby(ctx, 1.0, b, -1.0, t, t))) return rc;
-    double rn;
-    if ((rc = norm(ctx, t, &rn))) return rc;
-    *relres = rn / bnorm;
-    return BEM_OK;
+    return gmres_batch(ctx, op, b, x, 1, restart, tol, max_iter, iters, relres, zero_guess, prec);
 }
 
 // ---------------------------------------------------------------- batched GMRES
@@ -393,32 +399,27 @@ int Krylov::norms(bem_ctx* ctx, const double2* a, int64_t Rn, double* out) {
 
 int Krylov::gmres_batch(bem_ctx* ctx, const Op& op, const double2* B, double2* X, int64_t Rn, int restart,
                         double tol, int max_iter, int* iters, double* relres, bool zero_guess, const Op* prec) {
-    using cd = std::complex<double>;
     int rc = ensure(ctx, n, restart, Rn);
     if (rc) return rc;
     if (prec && (rc = ensure_flexible(ctx))) return rc;
+    constexpr int POLL_LAG = 2;  // steps the host may run ahead of the last running-count it has seen
     const int64_t ldk = Rn * n;  // stride between basis blocks
     const int ldh = m + 2;
     const unsigned nb = (unsigned)((n + KV_THREADS - 1) / KV_THREADS);
     const dim3 gcol(nb, (unsigned)Rn);
-    std::vector<double> bnorm(Rn), beta(Rn), hn(Rn), scale(Rn), res(Rn, 0.0);
+    std::vector<double> bnorm(Rn), beta(Rn), scale(Rn), resv(Rn, 0.0);
     if ((rc = norms(ctx, B, Rn, bnorm.data()))) return rc;
     std::vector<char> live(Rn);
     for (int64_t r = 0; r < Rn; r++) {
         iters[r] = 0;
         live[r] = bnorm[r] > 0;
     }
-    const size_t hs = (size_t)(restart + 1) * restart;
-    std::vector<cd> H(hs * Rn), cs((size_t)restart * Rn), sn((size_t)restart * Rn), g((size_t)(restart + 1) * Rn);
-    std::vector<int> jr(Rn);
-    std::vector<char> run(Rn);
-    std::vector<double2> hc((size_t)ldh * Rn), hc2((size_t)ldh * Rn), yd((size_t)ldh * Rn);
+    CK(cudaMemcpyAsync(bn, bnorm.data(), Rn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(its, 0, Rn * sizeof(int), ctx->stream));
+    std::vector<double2> g0((size_t)(m + 1) * Rn);
+    std::vector<int> run0(Rn), itv(Rn);
     int total = 0;
     bool first = true;
-    auto upload_scale = [&]() -> int {
-        CK(cudaMemcpyAsync(sc, scale.data(), Rn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-        return BEM_OK;
-    };
     while (total < max_iter) {
         // residual block into V_0
         if (first && zero_guess) {
@@ -431,23 +432,26 @@ int Krylov::gmres_batch(bem_ctx* ctx, const Op& op, const double2* B, double2* X
             ctx->launches += 1;
         }
         first = false;
-        if ((rc = norms(ctx, V, Rn, beta.data()))) return rc;
+        if ((rc = norms(ctx, V, Rn, beta.data()))) return rc;  // synchronises (once per restart cycle)
         bool any = false;
+        std::fill(g0.begin(), g0.end(), make_double2(0, 0));
         for (int64_t r = 0; r < Rn; r++) {
-            if (live[r]) res[r] = beta[r] / bnorm[r];
-            run[r] = live[r] && res[r] > tol;
-            live[r] = run[r];
-            any |= run[r];
-            scale[r] = run[r] ? 1.0 / beta[r] : 0.0;  // finished columns carry zeros
-            jr[r] = 0;
-            std::fill(g.begin() + (size_t)r * (restart + 1), g.begin() + (size_t)(r + 1) * (restart + 1), cd(0));
-            g[(size_t)r * (restart + 1)] = run[r] ? beta[r] : 0.0;
+            if (live[r]) resv[r] = beta[r] / bnorm[r];
+            const bool go = live[r] && resv[r] > tol;
+            live[r] = go;
+            any |= go;
+            run0[r] = go;
+            scale[r] = go ? 1.0 / beta[r] : 0.0;  // finished columns carry zeros
+            g0[(size_t)r * (m + 1)] = make_double2(go ? beta[r] : 0.0, 0.0);
         }
         if (!any) break;
-        if ((rc = upload_scale())) return rc;
+        CK(cudaMemcpyAsync(sc, scale.data(), Rn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(g, g0.data(), g0.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(run, run0.data(), Rn * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemsetAsync(jr, 0, Rn * sizeof(int), ctx->stream));
         kvb_scale<<<gcol, KV_THREADS, 0, ctx->stream>>>(V, n, sc);
         ctx->launches += 1;
-        int j = 0;
+        int j = 0, polled = 0;
         for (; j < restart && total < max_iter; j++) {
             double2* vj1 = V + (int64_t)(j + 1) * ldk;
             if (prec) {
@@ -465,77 +469,53 @@ int Krylov::gmres_batch(bem_ctx* ctx, const Op& op, const double2* B, double2* X
                 kvb_update<<<gcol, KV_THREADS, 0, ctx->stream>>>(V, ldk, j + 1, hp, ldh, vj1, n, -1.0);
                 ctx->launches += 3;
             }
-            CK(cudaGetLastError());
-            CK(cudaMemcpyAsync(hc.data(), h, hc.size() * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
-            CK(cudaMemcpyAsync(hc2.data(), y, hc2.size() * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
-            if ((rc = norms(ctx, vj1, Rn, hn.data()))) return rc;  // synchronises
-            total++;
-            bool still = false;
-            for (int64_t r = 0; r < Rn; r++) {
-                scale[r] = 0.0;
-                if (!run[r]) continue;
-                cd* Hr = H.data() + hs * r;
-                cd* csr = cs.data() + (size_t)restart * r;
-                cd* snr = sn.data() + (size_t)restart * r;
-                cd* gr = g.data() + (size_t)(restart + 1) * r;
-                for (int i = 0; i <= j; i++) {
-                    const double2 a = hc[(size_t)r * ldh + i], b2 = hc2[(size_t)r * ldh + i];
-                    Hr[(size_t)i * restart + j] = cd(a.x + b2.x, a.y + b2.y);
-                }
-                Hr[(size_t)(j + 1) * restart + j] = hn[r];
-                for (int i = 0; i < j; i++) {
-                    const cd a = Hr[(size_t)i * restart + j], c = Hr[(size_t)(i + 1) * restart + j];
-                    Hr[(size_t)i * restart + j] = std::conj(csr[i]) * a + std::conj(snr[i]) * c;
-                    Hr[(size_t)(i + 1) * restart + j] = -snr[i] * a + csr[i] * c;
-                }
-                const cd a = Hr[(size_t)j * restart + j], c = Hr[(size_t)(j + 1) * restart + j];
-                const double den = std::sqrt(std::norm(a) + std::norm(c));
-                csr[j] = den > 0 ? a / den : 1.0;
-                snr[j] = den > 0 ? c / den : 0.0;
-                Hr[(size_t)j * restart + j] = den;
-                Hr[(size_t)(j + 1) * restart + j] = 0;
-                gr[j + 1] = -snr[j] * gr[j];
-                gr[j] = std::conj(csr[j]) * gr[j];
-                iters[r]++;
-                jr[r] = j + 1;
-                res[r] = std::abs(gr[j + 1]) / bnorm[r];
-                if (res[r] <= tol || hn[r] == 0) {
-                    run[r] = 0;
-                } else {
-                    scale[r] = 1.0 / hn[r];
-                    still = true;
-                }
-            }
-            if ((rc = upload_scale())) return rc;
+            // |v_{j+1}|^2 partials, then the least-squares step of every column
+            const int nb1 = batch_blocks(n, Rn);
+            kvb_dots<<<dim3(nb1, 1, (unsigned)Rn), KV_THREADS, 0, ctx->stream>>>(vj1, 0, 1, vj1, n, nb1, part);
+            const int slot = j % 4;
+            CK(cudaMemsetAsync(n_run + slot, 0, sizeof(int), ctx->stream));
+            GivensArgs ga{part, nb1, h, y, ldh, j, m, H, cs, sn, g, bn, res, run, jr, its, sc, tol, n_run + slot};
+            givens_step_kernel<<<(unsigned)Rn, 32, 0, ctx->stream>>>(ga);
             kvb_scale<<<gcol, KV_THREADS, 0, ctx->stream>>>(vj1, n, sc);
-            ctx->launches += 1;
-            if (!still) {
+            CK(cudaMemcpyAsync(n_run_host + slot, n_run + slot, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaEventRecord(poll_ev[slot], ctx->stream));
+            ctx->launches += 3;
+            CK(cudaGetLastError());
+            total++;
+            // read the running counts of finished steps; wait only for the one POLL_LAG steps back
+            bool done = false;
+            while (polled <= j) {
+                const cudaError_t q = polled <= j - POLL_LAG ? cudaEventSynchronize(poll_ev[polled % 4])
+                                                             : cudaEventQuery(poll_ev[polled % 4]);
+                if (q == cudaErrorNotReady) break;
+                if (q != cudaSuccess) return ctx->fail(BEM_ERR_CUDA, std::string("GMRES poll: ") + cudaGetErrorString(q));
+                if (n_run_host[polled % 4] == 0) {
+                    done = true;
+                    break;
+                }
+                polled++;
+            }
+            if (done) {
                 j++;
                 break;
             }
         }
         // back substitution per column (its own length) and X += V y
-        std::fill(yd.begin(), yd.end(), make_double2(0, 0));
-        for (int64_t r = 0; r < Rn; r++) {
-            const int jj = jr[r];
-            const cd* Hr = H.data() + hs * r;
-            const cd* gr = g.data() + (size_t)(restart + 1) * r;
-            std::vector<cd> yv(jj);
-            for (int i = jj - 1; i >= 0; i--) {
-                cd s2 = gr[i];
-                for (int k = i + 1; k < jj; k++) s2 -= Hr[(size_t)i * restart + k] * yv[k];
-                yv[i] = s2 / Hr[(size_t)i * restart + i];
-            }
-            for (int i = 0; i < jj; i++) yd[(size_t)r * ldh + i] = make_double2(yv[i].real(), yv[i].imag());
-        }
-        CK(cudaMemcpyAsync(y, yd.data(), yd.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+        backsolve_kernel<<<(unsigned)Rn, 32, 0, ctx->stream>>>(H, g, jr, m, y, ldh);
+        ctx->launches += 1;
         if (j > 0) {
             kvb_update<<<gcol, KV_THREADS, 0, ctx->stream>>>(prec ? Z : V, ldk, j, y, ldh, X, n, 1.0);
             ctx->launches += 1;
         }
         CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(resv.data(), res, Rn * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(itv.data(), its, Rn * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
         bool open = false;
-        for (int64_t r = 0; r < Rn; r++) open |= live[r] && res[r] > tol;
+        for (int64_t r = 0; r < Rn; r++) {
+            iters[r] = itv[r];
+            open |= live[r] && resv[r] > tol;
+        }
         if (!open) break;
     }
     // true residuals of the given systems

@@ -15,6 +15,22 @@ struct Krylov {
     double2 *V = nullptr, *w = nullptr, *t = nullptr, *part = nullptr, *h = nullptr, *y = nullptr;
     double2* Z = nullptr;  // preconditioned basis of flexible GMRES, [m][R][n] (allocated on first use)
     double* sc = nullptr;
+    // least-squares state of every column on the device (Givens rotations applied there)
+    double2 *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr;  // [R][(m+1) m], [R][m], [R][m], [R][m+1]
+    double *bn = nullptr, *res = nullptr;                               // [R] |b|, |residual| / |b|
+    int *run = nullptr, *jr = nullptr, *its = nullptr;                  // [R]
+    int* n_run = nullptr;                                               // [POLL] running-column counts
+    int* n_run_host = nullptr;                                          // pinned copy of n_run
+    cudaEvent_t poll_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+    Krylov() = default;
+    Krylov(const Krylov&) = delete;
+    Krylov& operator=(const Krylov&) = delete;
+    ~Krylov() {  // device buffers belong to the context's allocations; the host-side poll objects are ours
+        if (n_run_host) cudaFreeHost(n_run_host);
+        for (auto& e : poll_ev)
+            if (e) cudaEventDestroy(e);
+    }
 
     int ensure(bem_ctx* ctx, int64_t n, int m, int64_t R = 1);
     void release(bem_ctx* ctx);
