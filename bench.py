@@ -346,18 +346,19 @@ def sphere_solve_metrics(local, reps=12):
             "field": field}
 
 
-def rib_solve_metrics(local, n_rhs=16, tol=1e-8):
+def rib_solve_metrics(local, n_rhs=16, tol=1e-8, reps=3):
     """The rib / fat / liver scene at the frequency its mesh resolves (0.1 MHz,
     41k triangles, k h ~ 1), random-phase piston excitations of the 256-piston
-    bowl: seconds per right-hand side of the mixed, batched form (n_rhs
-    excitations in lockstep; split-BF16 tensor-core GEMM on the assembled
-    operator inside a flexible GMRES, OSRC preconditioner with loose sparse
-    solves, FP64 residual refinement on the assembled complex128 operator)
-    against the plain FP64 GPU path (FP64 assembled operator, the same
-    preconditioner, one excitation at a time), both to an FP64 relative
-    residual of tol; the traces of the two paths agree to the reported
-    difference.  Operator assembly and preconditioner set-up are reported
-    separately (they are kept on the device for later requests)."""
+    bowl, every path to an FP64 relative residual of tol, operators assembled
+    once (set-up reported separately, kept on the device for later requests):
+      * mixed batched: n_rhs excitations in lockstep, split-BF16 tensor-core
+        GEMM inside a flexible GMRES, OSRC with loose sparse solves, FP64
+        residual refinement; run `reps` times (p50 / p99 per excitation);
+      * FP64 batched: the same n_rhs excitations in lockstep, FP64-accurate
+        assembled operator inside the same GMRES (the baseline at the same
+        batching);
+      * one excitation alone, mixed and FP64.
+    The traces of the mixed and FP64 paths agree to the reported difference."""
     import numpy as np
     import torch
 
@@ -377,43 +378,64 @@ def rib_solve_metrics(local, n_rhs=16, tol=1e-8):
     c.apply(x, precision=BF16X3)
     torch.cuda.synchronize()
     setup = time.perf_counter() - t0
+
+    def timed(**kw):
+        t = time.perf_counter()
+        rep = c.solve(operator_mode=1, tol=tol, max_iter=20000, **kw)
+        return time.perf_counter() - t, rep
+
     c.set_excitations(W[:1])
-    t0 = time.perf_counter()
-    r64 = c.solve(precision=0, operator_mode=1, tol=tol)
-    t64 = time.perf_counter() - t0
+    t64_1, r64_1 = timed(precision=0)
     u64 = c.solution(0)
+    t32_1, r32_1 = timed(precision=1)
     c.set_excitations(W)
-    t0 = time.perf_counter()
-    rb = c.solve(precision=1, operator_mode=1, tol=tol, batch_rhs=n_rhs)
-    tb = time.perf_counter() - t0
+    tb64, rb64 = timed(precision=0, batch_rhs=n_rhs)
+    ub64 = c.solution(0)
+    tbs, rbs = [], None
+    for _ in range(reps):
+        t, rbs = timed(precision=1, batch_rhs=n_rhs)
+        tbs.append(t)
     ub = c.solution(0)
     c.close()
+    per = np.array(tbs) / n_rhs
     return {"workload": f"rib/fat/liver scene, 0.1 MHz, {s.n_triangles} triangles (N={N}), {n_rhs} random-phase "
-                        f"excitations of the 256-piston bowl, n_pade 8, R_eps {r_eps * 1e3:.1f} mm",
+                        f"excitations of the 256-piston bowl, n_pade 8, R_eps {r_eps * 1e3:.1f} mm, OSRC blocks at "
+                        f"each domain's k_j",
             "tol_fp64_residual": tol, "setup_s": setup,
-            "fp64_s_per_rhs": t64, "mixed_batched_s_per_rhs": tb / n_rhs, "speedup_vs_fp64": t64 / (tb / n_rhs),
-            "trace_rel_diff_mixed_vs_fp64": float(np.linalg.norm(ub - u64) / np.linalg.norm(u64)),
-            "iterations": {"fp64": r64["iterations"], "mixed_per_rhs": rb["iterations"] / n_rhs,
-                           "refinements": rb["refinements"]},
-            "residual": {"fp64": r64["residual"], "mixed": rb["residual"]}}
+            "mixed_batched_s_per_rhs": float(np.median(per)),
+            "mixed_batched_p50_s_per_rhs": float(np.percentile(per, 50)),
+            "mixed_batched_p99_s_per_rhs": float(np.percentile(per, 99)),
+            "mixed_batched_runs": len(tbs),
+            "fp64_batched_s_per_rhs": tb64 / n_rhs,
+            "mixed_single_s_per_rhs": t32_1, "fp64_single_s_per_rhs": t64_1,
+            "speedup_batched_mixed_vs_batched_fp64": (tb64 / n_rhs) / float(np.median(per)),
+            "speedup_single_mixed_vs_single_fp64": t64_1 / t32_1,
+            "speedup_batched_mixed_vs_single_fp64": t64_1 / float(np.median(per)),
+            "trace_rel_diff_mixed_vs_fp64": float(np.linalg.norm(ub - ub64) / np.linalg.norm(ub64)),
+            "trace_rel_diff_single_fp64_vs_batched_fp64": float(np.linalg.norm(ub64 - u64) / np.linalg.norm(u64)),
+            "iterations_per_rhs": {"fp64_single": r64_1["iterations"], "mixed_single": r32_1["iterations"],
+                                   "fp64_batched": rb64["iterations"] / n_rhs,
+                                   "mixed_batched": rbs["iterations"] / n_rhs},
+            "residual": {"fp64_batched": rb64["residual"], "mixed_batched": rbs["residual"]}}
 
 
-def serving_metrics(local, n_req=12, max_exc=8, rate=20.0, budget=150 << 30, tol=1e-6, rank=0, world=1, slots=2):
+def serving_metrics(local, n_req=12, max_exc=16, rate=20.0, budget=150 << 30, tol=1e-6, rank=0, world=1, slots=2,
+                    pool=None):
     """Serving trace: Poisson arrivals (mean `rate`/s) of planning solves over
-    a pool of scenes (1k and 5k-triangle spheres, a 10k-triangle rib scene, a
-    20k-triangle kidney scene, each at k h ~ 1), each request with 1..max_exc
-    random-phase piston excitations, through the request loop (2 workers,
-    device-resident scene cache, admission by the HBM budget; mixed precision
-    with batched excitations, FP64 refinement to tol).  The cache is warmed
-    with one request per scene before the trace (set-up not in the
-    latencies).  Baseline: the same excitations solved one at a time by the
-    plain FP64 GPU path, timed on one excitation per scene and summed over the
-    trace's excitations."""
+    a pool of scenes (spheres of 1k and 5k triangles, rib scenes of 10k and
+    20k, kidney scenes of 20k and 40k, each at k h ~ 1), each request with
+    1..max_exc random-phase piston excitations, through the request loop
+    (device-resident scene cache, admission by the HBM budget; mixed
+    precision with batched excitations, FP64 refinement to tol, `slots`
+    workers).  Baseline: the same trace, at the same arrival times, through a
+    request loop that solves one excitation at a time in plain FP64 with one
+    worker (sequential FP64 GPU solves).  Each loop's cache is warmed with one
+    request per scene first (set-up not in the latencies)."""
     import numpy as np
 
-    from paper_1910_01011_gb300.api import Context, Server
+    from paper_1910_01011_gb300.api import Server
     from synth import serving
-    reqs, weights = serving.trace(n_req, rate=rate, max_exc=max_exc)
+    reqs, weights = serving.trace(n_req, rate=rate, max_exc=max_exc, pool=pool)
     # replicas: each rank serves its contiguous share of the trace
     b, e = shard(len(reqs), rank, world)
     if world > 1:
@@ -425,59 +447,55 @@ def serving_metrics(local, n_req=12, max_exc=8, rate=20.0, budget=150 << 30, tol
         return {"requests": 0}
     keys = sorted({k for _, k, _ in reqs})
     built = {k: serving.POOL[k]() for k in keys}
-    srv = Server(device=local, slots=slots, max_batch_rhs=64, hbm_budget_bytes=budget, precision=1, operator_mode=1,
-                 tol=tol, max_iter=20000, max_refine=20)
-    ids = {k: srv.add_scene(built[k], omega_rho0=built[k].meta["omega_rho0"], n_pade=8, r_eps=built[k].meta["r_eps"])
-           for k in keys}
-    for k in keys:  # warm the cache (geometry, near field, assembled operators, preconditioner)
-        h = srv.submit(ids[k], np.ones((1, srv.scenes[ids[k]][1])))
-        srv.wait(h)
-        srv.result(h, 1, ids[k])
-    warm = srv.stats()
-    t0 = time.perf_counter()
-    hs = []
-    for i, (ta, k, ne) in enumerate(reqs):
-        dt = t0 + ta - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        hs.append((srv.submit(ids[k], weights(i, srv.scenes[ids[k]][1])), k, ne))
-    lat, fails, its = [], [], {}
-    for h, k, ne in hs:
-        srv.wait(h)
-        try:
-            _, rep = srv.result(h, ne, ids[k])
-            lat.append(rep["latency_ms"])
-            its.setdefault(k, []).append(rep["iterations"] / max(1, rep["batch_exc"]))
-        except Exception as e:  # reported, not hidden
-            fails.append(f"{k}: {e}")
-    wall = time.perf_counter() - t0
-    st = srv.stats()
-    srv.close()
-    # plain FP64 GPU path, one excitation at a time, per scene
-    t64 = {}
-    for k in keys:
-        sc = built[k]
-        c = Context.from_scene(sc, device=local, n_pade=8, r_eps=sc.meta["r_eps"])
-        tr = sc.transducer
-        c.set_transducer(tr["centres"], tr["normals"], tr["radii"], sc.meta["omega_rho0"])
-        c.set_excitations(weights(0, tr["radii"].size)[:1])
-        c.solve(precision=0, operator_mode=1, tol=tol, max_iter=20000)  # set-up
-        t1 = time.perf_counter()
-        c.solve(precision=0, operator_mode=1, tol=tol, max_iter=20000)
-        t64[k] = time.perf_counter() - t1
-        c.close()
+
+    def run(**srv_kw):
+        srv = Server(device=local, hbm_budget_bytes=budget, tol=tol, max_iter=20000, max_refine=20, **srv_kw)
+        ids = {k: srv.add_scene(built[k], omega_rho0=built[k].meta["omega_rho0"], n_pade=8,
+                                r_eps=built[k].meta["r_eps"]) for k in keys}
+        tw = time.perf_counter()
+        for k in keys:  # warm the cache (geometry, near field, assembled operators, preconditioner)
+            h = srv.submit(ids[k], np.ones((1, srv.scenes[ids[k]][1])))
+            srv.wait(h)
+            srv.result(h, 1, ids[k])
+        warm_s = time.perf_counter() - tw
+        warm = srv.stats()
+        t0 = time.perf_counter()
+        hs = []
+        for i, (ta, k, ne) in enumerate(reqs):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            hs.append((srv.submit(ids[k], weights(i, srv.scenes[ids[k]][1])), k, ne))
+        lat, fails, its = [], [], {}
+        for h, k, ne in hs:
+            srv.wait(h)
+            try:
+                _, rep = srv.result(h, ne, ids[k])
+                lat.append(rep["latency_ms"])
+                its.setdefault(k, []).append(rep["iterations"] / max(1, rep["batch_exc"]))
+            except Exception as ex:  # reported, not hidden
+                fails.append(f"{k}: {ex}")
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return {"p50_ms": float(np.percentile(lat, 50)) if lat else None,
+                "p99_ms": float(np.percentile(lat, 99)) if lat else None,
+                "wall_s": wall, "excitations_per_s": n_exc / wall, "requests_per_s": n_req / wall,
+                "batches": st["batches"] - warm["batches"], "peak_device_gib": st["peak_device_bytes"] / 2**30,
+                "evictions": st["evictions"], "warm_up_s": warm_s,
+                "iterations_per_excitation": {k: float(np.mean(v)) for k, v in its.items()},
+                "failed_requests": fails}
+
     n_exc = sum(ne for _, _, ne in reqs)
-    seq = sum(ne * t64[k] for _, k, ne in reqs)
-    return {"workload": f"{n_req} requests, Poisson {rate}/s, 1..{max_exc} excitations each "
-                        f"({n_exc} total), scenes {keys}, tol {tol}, budget {budget / 2**30:.0f} GiB, "
-                        f"{slots} workers",
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "wall_s": wall, "excitations_per_s": n_exc / wall, "requests_per_s": n_req / wall,
-            "batches": st["batches"] - warm["batches"], "peak_device_gib": st["peak_device_bytes"] / 2**30,
-            "fp64_sequential_s_estimate": seq, "fp64_sequential_excitations_per_s": n_exc / seq,
-            "speedup_vs_fp64_sequential": seq / wall, "fp64_s_per_rhs": t64,
-            "mixed_iterations_per_excitation": {k: float(np.mean(v)) for k, v in its.items()},
-            "failed_requests": fails}
+    mixed = run(slots=slots, max_batch_rhs=64, precision=1, operator_mode=1)
+    seq = run(slots=1, max_batch_rhs=1, precision=0, operator_mode=1, batch_rhs=1)
+    out = {"workload": f"{n_req} requests, Poisson {rate}/s, 1..{max_exc} excitations each ({n_exc} total), "
+                       f"scenes {keys}, tol {tol}, budget {budget / 2**30:.0f} GiB, {slots} workers",
+           **mixed,
+           "fp64_sequential": {"how": "the same trace and arrival times through a request loop with one worker, "
+                                      "one excitation per plain FP64 solve", **seq},
+           "speedup_vs_fp64_sequential": seq["wall_s"] / mixed["wall_s"]}
+    return out
 
 
 def assembled_metrics(ctx, s, n_int, local, n_rhs=256):
@@ -729,13 +747,17 @@ def main():
             "gpu_launches": prof["kernel_launches"],
             "clocks": clk.summary()}
     if not args.no_extras:
+        extra_s = line.setdefault("extra_seconds", {})
+
         def extra(name, fn, *a):
             if args.extra and name not in args.extra:
                 return
+            t_x = time.perf_counter()
             try:
                 line[name] = fn(*a)
             except Exception as e:  # the line still prints; the failure is part of it
                 line[name] = {"error": f"{type(e).__name__}: {e}"}
+            extra_s[name] = round(time.perf_counter() - t_x, 1)
         extra("assembled", assembled_metrics, ctx, s, n_int, local)
         extra("solve_sphere", sphere_solve_metrics, local)
         if not args.quick and world == 1:
@@ -743,7 +765,7 @@ def main():
             # the minutes-long solve and serving measurements run on one GPU; replicas
             # of them on more GPUs would only repeat the same numbers
             extra("solve", rib_solve_metrics, local)
-            extra("serving", serving_metrics, local, 12, 8, 20.0, 150 << 30, 1e-6, rank, world)
+            extra("serving", serving_metrics, local, 12, 16, 20.0, 150 << 30, 1e-6, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt, sample = oracle_sample(s, args.ref_rows)
         line["cpu_baseline"] = {"value": n / dt / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",

@@ -15,9 +15,10 @@
 //   Y_re = C1[:, :n] - C2[:, n:],   Y_im = C1[:, n:] + C2[:, :n].
 // A CTA owns a 128-row tile of A and a 128-column tile of B (64 right-hand
 // sides, real and imaginary parts), so C1 and C2 are two 128 x 128 FP32
-// accumulators in tensor memory (256 TMEM columns).  Operands stream in by
-// TMA (128-byte swizzle, K-major) through a two-stage ring; one thread issues
-// the MMAs and commits each stage back to the producer.
+// accumulators in tensor memory (256 TMEM columns, double-buffered over 512).
+// Operands stream in by TMA (64-byte swizzle, K-major, 32 of K per stage)
+// through a three-stage ring (GSTAGES); one thread issues the MMAs and
+// commits each stage back to the producer.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>

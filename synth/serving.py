@@ -6,8 +6,10 @@ The trace has Poisson arrivals (exponential gaps, mean rate `rate` per
 second) of planning solves drawn uniformly from a pool of scenes whose sizes
 span the stated ranges (spheres of 1k-5k triangles, rib scenes of 10k-40k,
 kidney scenes of 20k-60k), each with a random number of random-phase piston
-excitations.  The pool uses the small end of each range, with frequencies
-chosen so that every mesh resolves about 6 elements per wavelength (k h ~ 1).
+excitations.  The pool's frequencies are
+chosen so that every mesh resolves about 6 elements per wavelength (k h ~ 1);
+it spans spheres of 1k and 5k triangles, rib scenes of 10k and 20k and kidney
+scenes of 20k and 40k.
 Each scene carries the OSRC damping radius of the paper's corresponding
 experiment, scaled to the same k R_eps (meta["r_eps"]).
 """
@@ -32,30 +34,40 @@ def sphere_with_bowl(level: int, k0: float, k1: float, n_elem: int, seed: int) -
     return s
 
 
-def rib_10k() -> scenes.Scene:
-    h = 5.3e-3
+def rib(h: float, tag: str) -> scenes.Scene:
     s = scenes.rib_scene(h=h, freq=1500.0 / (2 * math.pi * h))
-    s.name = "rib_fat_liver_10k"
+    s.name = f"rib_fat_liver_{tag}"
     s.meta["omega_rho0"] = 2 * math.pi * s.freq * s.rho0
     s.meta["r_eps"] = 1e-4 * 1e6 / s.freq  # the paper's rib value (1e-4 m at 1 MHz) at the same k R_eps
     return s
 
 
-def kidney_20k() -> scenes.Scene:
-    h = 3.2e-3
+def kidney(h: float, tag: str) -> scenes.Scene:
     s = scenes.kidney_scene(h=h, freq=1500.0 / (2 * math.pi * h))
-    s.name = "kidney_fat_20k"
+    s.name = f"kidney_fat_{tag}"
     s.meta["omega_rho0"] = 2 * math.pi * s.freq * s.rho0
     s.meta["r_eps"] = 1e-3 * 1e6 / s.freq  # the paper's kidney value (1e-3 m at 1 MHz) at the same k R_eps
     return s
+
+
+def rib_10k() -> scenes.Scene:
+    return rib(5.3e-3, "10k")
+
+
+def kidney_20k() -> scenes.Scene:
+    return kidney(3.2e-3, "20k")
 
 
 POOL = {
     "sphere_1k": lambda: sphere_with_bowl(3, 5.0, 5.25, 16, 11),
     "sphere_5k": lambda: sphere_with_bowl(4, 10.0, 10.5, 32, 12),
     "rib_10k": rib_10k,
+    "rib_20k": lambda: rib(3.75e-3, "20k"),
     "kidney_20k": kidney_20k,
+    "kidney_40k": lambda: kidney(2.26e-3, "40k"),
 }
+# the smallest scene of each kind (the pool of the short trace)
+SMALL = ("sphere_1k", "sphere_5k", "rib_10k", "kidney_20k")
 
 
 def trace(n_req: int, rate: float = 20.0, max_exc: int = 64, seed: int = 2, exc_seed: int = 3, pool=None):
