@@ -73,6 +73,9 @@ def workload(name):
     elif name == "rib_small":
         s = scenes.rib_scene(h=6e-3)
         desc = "rib/fat/liver scene at 6 mm element size (~8k triangles; profiling case)"
+    elif name == "rib_small_resolved":
+        s = scenes.rib_scene(h=6e-3, freq=0.1e6 * 2.65 / 6.0)
+        desc = "rib/fat/liver scene at 6 mm element size and the frequency it resolves (k h ~ 1; ~8k triangles)"
     elif name == "rib_resolved":
         s = scenes.rib_scene_resolved()
         desc = "rib/fat/liver scene, 0.1 MHz (k h ~ 1), ~41k triangles (the solve-time workload)"
@@ -592,6 +595,40 @@ def prec_step(args, s, desc, local, world):
                       "gpu_launches": prof["kernel_launches"]}))
 
 
+def solve_step(args, s, desc, local, world):
+    """Mixed batched solves (split-BF16 assembled operator, flexible GMRES,
+    OSRC with loose FP32 sparse solves, FP64 refinement to 1e-8) of
+    --prec-rhs random-phase piston excitations, --steps times after --warmup
+    untimed solves; seconds per excitation."""
+    import numpy as np
+
+    from paper_1910_01011_gb300.api import Context
+    tr = s.transducer
+    ctx = Context.from_scene(s, device=local, n_pade=8, r_eps=1e-4 * 1e6 / s.freq, osrc_solver=args.osrc_solver)
+    ctx.set_transducer(tr["centres"], tr["normals"], tr["radii"], 2 * np.pi * s.freq * s.rho0)
+    R = args.prec_rhs
+    ctx.set_excitations(np.exp(2j * np.pi * np.random.default_rng(3).random((R, tr["radii"].size))))
+    kw = dict(precision=1, operator_mode=1, tol=1e-8, batch_rhs=R, max_iter=20000)
+    for _ in range(max(1, args.warmup)):
+        ctx.solve(**kw)
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    t0 = time.perf_counter()
+    rep = None
+    for _ in range(args.steps):
+        rep = ctx.solve(**kw)
+    dt = time.perf_counter() - t0
+    prof = ctx.profile_read(reset=True)
+    ctx.close()
+    print(json.dumps({"metric": "mixed batched solve, seconds per excitation", "value": dt / args.steps / R,
+                      "unit": "s/RHS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": False,
+                      "config": {"workload": desc, "n_rhs": R, "n_pade": 8, "tol": 1e-8,
+                                 "osrc_solver": ["automatic", "one CTA per system", "grid-wide", "cluster per system",
+                                                 "cluster per group of shifts"][args.osrc_solver]},
+                      "iterations_per_rhs": rep["iterations"] / R, "gpu_launches": prof["kernel_launches"]}))
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -622,7 +659,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rib", choices=["rib", "rib_small", "rib_resolved", "kidney", "sphere"])
+    ap.add_argument("--workload", default="rib",
+                    choices=["rib", "rib_small", "rib_small_resolved", "rib_resolved", "kidney", "sphere"])
     ap.add_argument("--ref-rows", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the solve and assembled-GEMM measurements")
@@ -630,9 +668,11 @@ def main():
     ap.add_argument("--extra", action="append", default=None,
                     choices=["assembled", "solve_sphere", "apply_kidney", "solve", "serving"],
                     help="run only these extras (repeatable); default: all that the other flags allow")
-    ap.add_argument("--step", default="apply", choices=["apply", "prec"],
+    ap.add_argument("--step", default="apply", choices=["apply", "prec", "solve"],
                     help="apply: the operator application (the headline metric); prec: one OSRC preconditioner "
-                         "application to --prec-rhs right-hand sides (for profiling the sparse solves)")
+                         "application to --prec-rhs right-hand sides (for profiling the sparse solves); solve: one "
+                         "mixed batched solve of --prec-rhs piston excitations with assembled operators (for "
+                         "profiling the loose sparse solves inside the flexible GMRES)")
     ap.add_argument("--prec-rhs", type=int, default=8)
     ap.add_argument("--rhs", type=int, default=1,
                     help="right-hand sides per apply step; > 1 applies them in one matrix-free far-field launch "
@@ -664,6 +704,8 @@ def main():
     stream = torch.cuda.current_stream()
     if args.step == "prec":
         return prec_step(args, s, desc, local, world)
+    if args.step == "solve":
+        return solve_step(args, s, desc, local, world)
     ctx = Context.from_scene(s, device=local, stream=stream.cuda_stream)
     N = ctx.n_dofs
     single, fused, n_int = pair_counts(s)

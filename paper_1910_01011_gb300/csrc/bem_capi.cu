@@ -199,6 +199,7 @@ int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_
         const int64_t L = ctx->opts.n_pade, nnz = 8 * nv, ms = 2 * L * R, nd = (int64_t)ctx->doms.size();
         b += nnz * 20 + (nv + 1) * 8 + 2 * nv * 8 + nv * 4 + nd * (L + 4) * 16;
         b += 6 * ms * nv * 16 + ms * (16 * nd + 128 * 4 * 8 + 64) + 4 * R * nv * 16;
+        b += 5 * ms * nv * 8 + 16 * nv * 8 + 2 * nv * 4;  // FP32 vectors and matrix copies of the loose solves
     }
     // several right-hand sides in one matrix-free FP32 far-field launch
     if (o.operator_mode == 0 && o.precision == BEM_PREC_FP32 && R > 1) {

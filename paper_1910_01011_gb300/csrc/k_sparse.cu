@@ -71,6 +71,10 @@ struct OsrcState {
     int ell_w = 0;                     // ELL width (max nonzeros per row), 0 if too wide
     int32_t* ell_ci = nullptr;         // [ell_w][n] column indices (padding: the row itself)
     double *ell_m = nullptr, *ell_s = nullptr;  // [ell_w][n] mass / stiffness values (padding: 0)
+    // FP32 copies for the loose solves inside a flexible GMRES (GB300's FP64 rate
+    // is ~1/64 of its FP32 rate, and a 10-30 % residual needs no FP64)
+    float *ell_m32 = nullptr, *ell_s32 = nullptr, *dm32 = nullptr, *ds32 = nullptr;
+    float2 *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // [max_sys][n]
     int64_t* dom_v0 = nullptr;         // [n_dom + 1] vertex offsets
     unsigned long long* stat = nullptr;  // [0]: iterations (sum over CTAs), [1]: CTAs that did not converge
     // CUDA graphs of GRAPH_ITERS COCG iterations, per (number of systems, tolerance)
@@ -613,6 +617,240 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) cocg_cluster_ke
     }
 }
 
+// ---- the same two solvers in FP32, for loose tolerances
+//
+// Inside the flexible GMRES the sparse solves stop at a 10-30 % relative
+// residual.  In FP64 the cluster solver is bound by GB300's FP64 pipe (68 %
+// of its cycles busy on the 41k-triangle rib scene at 16 right-hand sides,
+// ncu), so these variants keep the vectors, matrix values and arithmetic in
+// FP32: b is read once in FP64, x is written back once in FP64.  The
+// iteration, its stopping test and its breakdown guards are those of the FP64
+// solvers.
+
+__device__ __forceinline__ float2 fcmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 fcdiv(float2 a, float2 b) {
+    const float d = b.x * b.x + b.y * b.y;
+    return make_float2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+struct CocgArgs32 {
+    int64_t n;
+    const int32_t* eci;       // ELL [W][n]
+    const float *em, *es;     // ELL [W][n]
+    const float *dm, *ds;
+    const double2* beta;      // [n_sys][n_dom]
+    const double2* b;         // [n_sys][n]
+    double2* xout;            // [n_sys][n]
+    float2 *x, *r, *z, *p, *q;
+    const int64_t* dom_v0;
+    int n_dom;
+    float tol2;
+    int max_iter;
+    unsigned long long* stat;
+};
+
+template <int NT, int NV>
+__device__ __forceinline__ void cta_sum32(float (&v)[NV]) {
+    __shared__ float sh[NT / 32][NV];
+    __shared__ float tot[NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        float t = v[k];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[warp][k] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        float t = 0;
+        for (int w = 0; w < NT / 32; w++) t += sh[w][threadIdx.x];
+        tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = tot[k];
+    __syncthreads();
+}
+
+template <int NT>
+struct CtaRed32 {
+    template <int NV>
+    __device__ __forceinline__ void sum(float (&v)[NV]) { cta_sum32<NT, NV>(v); }
+    __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+
+// Rows [v0, v1) of domain j of system s; `red` sums over the rows of all the
+// CTAs that share the system (one CTA, or the CTAs of a cluster).
+template <int NT, int W, class Red>
+__device__ __forceinline__ void cocg32_body(const CocgArgs32& a, int s, int j, int64_t v0, int64_t v1, Red& red,
+                                            bool leader) {
+    const int64_t n = a.n, off = (int64_t)s * n;
+    const double2 be64 = a.beta[(int64_t)s * a.n_dom + j];
+    const float2 be = make_float2((float)be64.x, (float)be64.y);
+    const double2* b = a.b + off;
+    float2 *x = a.x + off, *r = a.r + off, *z = a.z + off, *p = a.p + off, *q = a.q + off;
+    auto dinv = [&](int64_t i) {
+        return fcdiv(make_float2(1.f, 0.f), make_float2(a.dm[i] - be.x * a.ds[i], -be.y * a.ds[i]));
+    };
+    float v3[3] = {0, 0, 0};
+    for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+        const double2 b64 = b[i];
+        const float2 bi = make_float2((float)b64.x, (float)b64.y);
+        const float2 zi = fcmul(dinv(i), bi);
+        x[i] = make_float2(0.f, 0.f);
+        r[i] = bi;
+        z[i] = zi;
+        p[i] = zi;
+        const float2 rz = fcmul(bi, zi);
+        v3[0] += rz.x;
+        v3[1] += rz.y;
+        v3[2] += bi.x * bi.x + bi.y * bi.y;
+    }
+    red.template sum<3>(v3);  // also publishes the initial p
+    float2 rho = make_float2(v3[0], v3[1]);
+    const float lim = a.tol2 * v3[2];
+    int it = 0;
+    bool ok = !(v3[2] > 0);  // zero right-hand side: x = 0 is exact
+    while (!ok && it < a.max_iter) {
+        it++;
+        float v2[2] = {0, 0};
+        for (int64_t i0 = v0 + threadIdx.x; i0 < v1; i0 += CTA_U * NT) {
+            float qr[CTA_U], qi[CTA_U];
+#pragma unroll
+            for (int u = 0; u < CTA_U; u++) {
+                qr[u] = 0;
+                qi[u] = 0;
+                const int64_t i = i0 + (int64_t)u * NT;
+                if (i < v1) {
+#pragma unroll
+                    for (int k = 0; k < W; k++) {
+                        const int64_t e = (int64_t)k * n + i;
+                        const float2 pj = __ldcg(p + a.eci[e]);  // other CTAs' rows: read through L2
+                        const float mr = a.em[e] - be.x * a.es[e], mi = -be.y * a.es[e];
+                        qr[u] += mr * pj.x - mi * pj.y;
+                        qi[u] += mr * pj.y + mi * pj.x;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CTA_U; u++) {
+                const int64_t i = i0 + (int64_t)u * NT;
+                if (i < v1) {
+                    q[i] = make_float2(qr[u], qi[u]);
+                    const float2 pi = p[i];
+                    v2[0] += pi.x * qr[u] - pi.y * qi[u];
+                    v2[1] += pi.x * qi[u] + pi.y * qr[u];
+                }
+            }
+        }
+        red.template sum<2>(v2);
+        const float2 alpha = fcdiv(rho, make_float2(v2[0], v2[1]));
+        if (!isfinite(alpha.x) || !isfinite(alpha.y)) break;  // breakdown, identical for every CTA: keep x
+        float w3[3] = {0, 0, 0};
+        for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+            const float2 pi = p[i], qi = q[i];
+            float2 xi = x[i], ri = r[i];
+            const float2 ap = fcmul(alpha, pi), aq = fcmul(alpha, qi);
+            xi.x += ap.x; xi.y += ap.y;
+            ri.x -= aq.x; ri.y -= aq.y;
+            x[i] = xi;
+            r[i] = ri;
+            const float2 zi = fcmul(dinv(i), ri);
+            z[i] = zi;
+            const float2 rz = fcmul(ri, zi);
+            w3[0] += rz.x;
+            w3[1] += rz.y;
+            w3[2] += ri.x * ri.x + ri.y * ri.y;
+        }
+        red.template sum<3>(w3);
+        if (w3[2] <= lim) {
+            ok = true;
+            break;
+        }
+        const float2 rn = make_float2(w3[0], w3[1]);
+        const float2 bt = fcdiv(rn, rho);
+        if (!isfinite(bt.x) || !isfinite(bt.y)) break;
+        rho = rn;
+        for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) {
+            const float2 zi = z[i], pi = p[i];
+            const float2 bp = fcmul(bt, pi);
+            p[i] = make_float2(zi.x + bp.x, zi.y + bp.y);
+        }
+        red.sync();  // the new p, read across rows (and CTAs) by the next product
+    }
+    double2* xo = a.xout + off;
+    for (int64_t i = v0 + threadIdx.x; i < v1; i += NT) xo[i] = make_double2((double)x[i].x, (double)x[i].y);
+    if (leader) {
+        atomicAdd(&a.stat[0], (unsigned long long)it);
+        if (!ok) atomicAdd(&a.stat[1], 1ull);
+    }
+}
+
+// At most 64 registers (1024 / NT CTAs of NT threads per SM): the FP32 state
+// is small, and the solve's time is the iteration latency of many systems.
+template <int NT, int W>
+__global__ void __launch_bounds__(NT, 1024 / NT) cocg_cta32_kernel(CocgArgs32 a) {
+    const int s = blockIdx.x / a.n_dom, j = blockIdx.x % a.n_dom;
+    CtaRed32<NT> red;
+    cocg32_body<NT, W>(a, s, j, a.dom_v0[j], a.dom_v0[j + 1], red, threadIdx.x == 0);
+}
+
+template <int NT, int NV>
+__device__ __forceinline__ void cluster_sum32(cg::cluster_group& cl, float (&v)[NV], float (*buf)[NV], int& phase) {
+    __shared__ float sh[NT / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        float t = v[k];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[warp][k] = t;
+    }
+    __syncthreads();
+    float* mine = buf[phase];
+    if (threadIdx.x < NV) {
+        float t = 0;
+        for (int w = 0; w < NT / 32; w++) t += sh[w][threadIdx.x];
+        mine[threadIdx.x] = t;
+    }
+    cl.sync();  // publishes every CTA's partial sums
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        float t = 0;
+        for (int r = 0; r < CL; r++) t += cl.map_shared_rank(mine, r)[k];
+        v[k] = t;
+    }
+    phase ^= 1;  // the next sum writes the other buffer
+}
+
+template <int NT>
+struct ClusterRed32 {
+    cg::cluster_group cl;
+    float (*buf2)[2];
+    float (*buf3)[3];
+    int ph2 = 0, ph3 = 0;
+    template <int NV>
+    __device__ __forceinline__ void sum(float (&v)[NV]) {
+        if constexpr (NV == 2) cluster_sum32<NT, 2>(cl, v, buf2, ph2);
+        else cluster_sum32<NT, 3>(cl, v, buf3, ph3);
+    }
+    __device__ __forceinline__ void sync() { cl.sync(); }
+};
+
+template <int NT, int W>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 1024 / NT) cocg_cluster32_kernel(CocgArgs32 a) {
+    __shared__ float buf2[2][2], buf3[2][3];
+    ClusterRed32<NT> red{cg::this_cluster(), buf2, buf3};
+    const int item = blockIdx.x / CL, rank = (int)red.cl.block_rank();
+    const int s = item / a.n_dom, j = item % a.n_dom;
+    const int64_t d0 = a.dom_v0[j], d1 = a.dom_v0[j + 1];
+    const int64_t per = (d1 - d0 + CL - 1) / CL;
+    const int64_t v0 = min(d1, d0 + rank * per), v1 = min(d1, v0 + per);
+    cocg32_body<NT, W>(a, s, j, v0, v1, red, rank == 0 && threadIdx.x == 0);
+    red.sync();  // no CTA may leave while another still reads its shared memory
+}
+
 // ---- the Pade shifts of one right-hand side together: one cluster per (group, domain)
 //
 // The 2 N_pade Pade systems of a right-hand side come in groups of N_pade
@@ -927,9 +1165,11 @@ static int ensure_osrc_batch(bem_ctx* ctx, OsrcState* o, int64_t R) {
     if (R <= o->max_rhs) return BEM_OK;
     CK(cudaStreamSynchronize(ctx->stream));
     for (void* p : {(void*)o->x, (void*)o->r, (void*)o->z, (void*)o->p, (void*)o->q, (void*)o->b, (void*)o->beta,
-                    (void*)o->part, (void*)o->scal, (void*)o->u, (void*)o->g})
+                    (void*)o->part, (void*)o->scal, (void*)o->u, (void*)o->g, (void*)o->x32, (void*)o->r32,
+                    (void*)o->z32, (void*)o->p32, (void*)o->q32})
         ctx->dfree(p);
     o->x = o->r = o->z = o->p = o->q = o->b = o->beta = o->u = o->g = nullptr;
+    o->x32 = o->r32 = o->z32 = o->p32 = o->q32 = nullptr;
     o->part = o->scal = nullptr;
     for (auto& gr : o->graphs) cudaGraphExecDestroy(gr.exec);
     o->graphs.clear();
@@ -951,6 +1191,11 @@ static int ensure_osrc_batch(bem_ctx* ctx, OsrcState* o, int64_t R) {
     o->scal = (double*)ctx->dalloc((size_t)ms * 8 * sizeof(double), &rc); if (rc) return rc;
     o->u = (double2*)ctx->dalloc((size_t)2 * R * n * sizeof(double2), &rc); if (rc) return rc;
     o->g = (double2*)ctx->dalloc((size_t)2 * R * n * sizeof(double2), &rc); if (rc) return rc;
+    const size_t vec32 = (size_t)ms * n * sizeof(float2);
+    for (float2** v : {&o->x32, &o->r32, &o->z32, &o->p32, &o->q32}) {
+        *v = (float2*)ctx->dalloc(vec32, &rc);
+        if (rc) return rc;
+    }
     o->max_sys = (int)ms;
     o->max_rhs = R;
     return BEM_OK;
@@ -970,7 +1215,9 @@ static int osrc_build(bem_ctx* ctx) {
                         (void*)o->x, (void*)o->r, (void*)o->z, (void*)o->p, (void*)o->q, (void*)o->b,
                         (void*)o->beta, (void*)o->part, (void*)o->scal, (void*)o->u, (void*)o->g,
                         (void*)o->dom_v0, (void*)o->stat, (void*)o->ell_ci, (void*)o->ell_m, (void*)o->ell_s,
-                        (void*)o->dA, (void*)o->post_b, (void*)o->post_c, (void*)o->vdom})
+                        (void*)o->dA, (void*)o->post_b, (void*)o->post_c, (void*)o->vdom, (void*)o->ell_m32,
+                        (void*)o->ell_s32, (void*)o->dm32, (void*)o->ds32, (void*)o->x32, (void*)o->r32,
+                        (void*)o->z32, (void*)o->p32, (void*)o->q32})
             ctx->dfree(p);
         for (auto& g : o->graphs) cudaGraphExecDestroy(g.exec);
         if (o->cap) cudaStreamDestroy(o->cap);
@@ -1059,6 +1306,12 @@ static int osrc_build(bem_ctx* ctx) {
         (rc = up(&o->dm, dm)) || (rc = up(&o->ds, ds)) || (rc = up(&o->dom_v0, dv0)) || (rc = up(&o->stat, st0)))
         return rc;
     if (ell_w && ((rc = up(&o->ell_ci, eci)) || (rc = up(&o->ell_m, em)) || (rc = up(&o->ell_s, es)))) return rc;
+    {
+        const std::vector<float> em32(em.begin(), em.end()), es32(es.begin(), es.end());
+        const std::vector<float> dm32(dm.begin(), dm.end()), ds32(ds.begin(), ds.end());
+        if (ell_w && ((rc = up(&o->ell_m32, em32)) || (rc = up(&o->ell_s32, es32)))) return rc;
+        if ((rc = up(&o->dm32, dm32)) || (rc = up(&o->ds32, ds32))) return rc;
+    }
     std::vector<int32_t> vd(n);
     for (int d = 0; d < g.n_dom; d++)
         for (int64_t v = dv0[d]; v < dv0[d + 1]; v++) vd[v] = d;
@@ -1173,6 +1426,33 @@ static int cocg_solve(bem_ctx* ctx, int n_sys, int shifts = 1) {
     CK(cudaMemsetAsync(o->stat, 0, 2 * sizeof(unsigned long long), ctx->stream));
     if ((mode == 1 || mode == 3 || mode == 4) && o->ell_w == 0)
         return ctx->fail(BEM_ERR_INVALID_ARG, "mesh rows too wide for the CTA solvers");
+    // loose solves (inside a flexible GMRES) run in FP32: the same iteration on
+    // FP32 vectors, with the same choice between clusters and single CTAs
+    if (!ctx->osrc_strict && o->tol >= 1e-4 && !grouped && o->ell_w) {
+        CocgArgs32 b{};
+        b.n = o->n; b.eci = o->ell_ci; b.em = o->ell_m32; b.es = o->ell_s32; b.dm = o->dm32; b.ds = o->ds32;
+        b.beta = o->beta; b.b = o->b; b.xout = o->x;
+        b.x = o->x32; b.r = o->r32; b.z = o->z32; b.p = o->p32; b.q = o->q32;
+        b.dom_v0 = o->dom_v0; b.n_dom = o->n_dom; b.tol2 = (float)(o->tol * o->tol); b.max_iter = a.max_iter;
+        b.stat = o->stat;
+        if (clustered) {
+            const unsigned grid = ctas * CL;
+            if (o->ell_w == 8) cocg_cluster32_kernel<256, 8><<<grid, 256, 0, ctx->stream>>>(b);
+            else if (o->ell_w == 12) cocg_cluster32_kernel<256, 12><<<grid, 256, 0, ctx->stream>>>(b);
+            else cocg_cluster32_kernel<256, 16><<<grid, 256, 0, ctx->stream>>>(b);
+        } else if (ctas <= 152) {
+            if (o->ell_w == 8) cocg_cta32_kernel<1024, 8><<<ctas, 1024, 0, ctx->stream>>>(b);
+            else if (o->ell_w == 12) cocg_cta32_kernel<1024, 12><<<ctas, 1024, 0, ctx->stream>>>(b);
+            else cocg_cta32_kernel<1024, 16><<<ctas, 1024, 0, ctx->stream>>>(b);
+        } else {
+            if (o->ell_w == 8) cocg_cta32_kernel<256, 8><<<ctas, 256, 0, ctx->stream>>>(b);
+            else if (o->ell_w == 12) cocg_cta32_kernel<256, 12><<<ctas, 256, 0, ctx->stream>>>(b);
+            else cocg_cta32_kernel<256, 16><<<ctas, 256, 0, ctx->stream>>>(b);
+        }
+        ctx->launches += 1;
+        CK(cudaGetLastError());
+        return BEM_OK;  // loose: the counters are not read back
+    }
     // up to one wave: 1024 threads per CTA (one CTA per SM, shortest iterations);
     // beyond: 256 threads, three CTAs per SM
     if (grouped) {
