@@ -26,6 +26,11 @@
  * the design notes and shared with the CUDA path as a *rule*, not as code):
  *   - pairs of triangles with no common vertex: a symmetric triangle rule
  *     (the 6-point degree-4 rule, passed in) on both triangles;
+ *   - of those, the near pairs, whose centroids are closer than twice the
+ *     longer of the two triangles' longest edges: a collapsed Gauss-Legendre
+ *     rule on each triangle (the n Gauss-Legendre nodes passed in, in both
+ *     directions of the unit square, mapped by s1 = u, s2 = u v with
+ *     Jacobian u onto the reference triangle below);
  *   - pairs sharing a vertex, an edge, or identical: the Sauter-Schwab
  *     regularising transformations (Sauter & Schwab, Boundary Element
  *     Methods, Sec. 5.2) with an n-point Gauss-Legendre rule in each of the
@@ -48,6 +53,7 @@ typedef double complex zc;
 #define REL_VERTEX 1
 #define REL_EDGE 2
 #define REL_SAME 3
+#define REL_NEAR 4 /* reported by orc_pair only: no common vertex, but near */
 
 typedef struct {
     double P[3][3];    /* vertex coordinates, local order */
@@ -213,6 +219,47 @@ static void pair_singular(pairmat *M, const tri_t *X, const tri_t *Y, int rel, z
                 }
 }
 
+/* Near pair: centroids closer than twice the longest edge of either triangle
+ * (squared distances, vertex coordinates in their original order). */
+static int is_near(const double *VX[3], const double *VY[3]) {
+    double cx[3], cy[3], h2 = 0.0;
+    for (int d = 0; d < 3; d++) {
+        cx[d] = (VX[0][d] + VX[1][d] + VX[2][d]) / 3.0;
+        cy[d] = (VY[0][d] + VY[1][d] + VY[2][d]) / 3.0;
+    }
+    for (int i = 0; i < 3; i++) {
+        double e[3];
+        sub3(VX[(i + 1) % 3], VX[i], e);
+        if (dot3(e, e) > h2) h2 = dot3(e, e);
+        sub3(VY[(i + 1) % 3], VY[i], e);
+        if (dot3(e, e) > h2) h2 = dot3(e, e);
+    }
+    double c[3];
+    sub3(cx, cy, c);
+    return dot3(c, c) < 4.0 * h2;
+}
+
+/* Near pair: the collapsed Gauss-Legendre rule on both triangles, in the
+ * reference parametrisation of the singular rules (Jacobian 2|T| u each). */
+static void pair_near(pairmat *M, const tri_t *X, const tri_t *Y, zc k, int ng, const double *gl) {
+    const double scale = (2.0 * X->area) * (2.0 * Y->area);
+    for (int a = 0; a < ng; a++)
+        for (int b = 0; b < ng; b++) {
+            const double u = gl[2 * a], s[2] = {u, u * gl[2 * b]};
+            const double wx = gl[2 * a + 1] * gl[2 * b + 1] * u;
+            double x[3], px[3];
+            ref_point(X, s, x, px);
+            for (int c = 0; c < ng; c++)
+                for (int e = 0; e < ng; e++) {
+                    const double v = gl[2 * c], t[2] = {v, v * gl[2 * e]};
+                    const double wy = gl[2 * c + 1] * gl[2 * e + 1] * v;
+                    double y[3], py[3];
+                    ref_point(Y, t, y, py);
+                    accumulate(M, X, Y, x, y, px, py, wx * wy * scale, k);
+                }
+        }
+}
+
 /* Relation of two triangles of the same surface from their vertex ids, and
  * local orders that put the shared vertices first (in matching order). */
 static int classify(const int *a, const int *b, int pa[3], int pb[3]) {
@@ -246,7 +293,8 @@ static void pair_local(pairmat *out, const double *VX[3], const int *ix, const d
     tri_setup(&Y, VY, pb);
     pairmat M;
     memset(&M, 0, sizeof M);
-    if (rel == REL_NONE) pair_regular(&M, &X, &Y, k, nq, qr);
+    if (rel == REL_NONE && is_near(VX, VY)) pair_near(&M, &X, &Y, k, ng, gl);
+    else if (rel == REL_NONE) pair_regular(&M, &X, &Y, k, nq, qr);
     else pair_singular(&M, &X, &Y, rel, k, ng, gl);
     memset(out, 0, sizeof *out);
     for (int i = 0; i < 3; i++)
@@ -265,6 +313,7 @@ int orc_pair(const double *vx, const int *ix, const double *vy, const int *iy, i
     const double *VX[3] = {vx, vx + 3, vx + 6}, *VY[3] = {vy, vy + 3, vy + 6};
     int pa[3], pb[3];
     *rel_out = same_surface ? classify(ix, iy, pa, pb) : REL_NONE;
+    if (*rel_out == REL_NONE && is_near(VX, VY)) *rel_out = REL_NEAR;
     pairmat M;
     pair_local(&M, VX, ix, VY, iy, same_surface, kre + I * kim, nq, qr, ng, gl);
     zc *o = (zc *)out;

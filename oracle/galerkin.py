@@ -18,14 +18,16 @@ _SRC = os.path.join(_HERE, "bem_oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liborc.so")
 _lib = None
 
-REL_NONE, REL_VERTEX, REL_EDGE, REL_SAME = 0, 1, 2, 3
+REL_NONE, REL_VERTEX, REL_EDGE, REL_SAME, REL_NEAR = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         tmp = _OUT + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", _SRC, "-o", tmp, "-lm"])
+        # no fused multiply-adds: the near-pair test must round exactly as written
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", _SRC,
+                               "-o", tmp, "-lm"])
         os.replace(tmp, _OUT)
     return _OUT
 

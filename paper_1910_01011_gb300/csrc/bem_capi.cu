@@ -176,7 +176,10 @@ int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_
         nv += d.nv;
         tiles += (d.nt + TT - 1) / TT;
     }
-    const int64_t N = 2 * nv, pts = tiles * TP, slots = tiles * TT, pairs = 16 * T;
+    // correction pairs: touching (about 13 per triangle) and near (20-80 per
+    // triangle on the meshes measured): the exact count once the geometry exists
+    const int64_t pairs = ctx->ready ? (int64_t)ctx->geo.np_src.size() : 96 * T;
+    const int64_t N = 2 * nv, pts = tiles * TP, slots = tiles * TT;
     const int64_t ne = (int64_t)ctx->tr_r.size();
     int64_t b = 0;
     // geometry, densities, staging vectors
@@ -279,7 +282,7 @@ int bem_ctx::finalize() {
     for (int64_t s = 0; s < g.n_slots; s++)
         for (int64_t i = g.np_ptr[s]; i < g.np_ptr[s + 1]; i++) ptgt[i] = (int32_t)s;
     if ((rc = upload(this, &d.np_tgt, ptgt))) return rc;
-    for (int r = 1; r <= 3; r++)
+    for (int r = 0; r <= 3; r++)  // 0: the near-pair rule, 1-3: Sauter-Schwab
         if ((rc = upload(this, &d.ss_tab[r], quad.ss[r]))) return rc;
     // working buffers
     d.pd32 = (float4*)dalloc(g.n_pts * sizeof(float4), &rc); if (rc) return rc;
@@ -339,12 +342,10 @@ int bem_ctx::build_near(NearSet& ns, int n_slot_k, double kre, double kim, const
         a.slot_n = dev.slot_n;
         a.slot_area = dev.slot_area;
         a.slot_curl = dev.slot_curl;
-        for (int r = 1; r <= 3; r++) {
+        for (int r = 0; r <= 3; r++) {
             a.ss_tab[r] = dev.ss_tab[r];
             a.ss_n[r] = (int)(quad.ss[r].size() / 5);
         }
-        a.ss_tab[0] = nullptr;
-        a.ss_n[0] = 0;
         for (int q = 0; q < QP; q++) {
             a.rule[3 * q] = quad.l1[q];
             a.rule[3 * q + 1] = quad.l2[q];
@@ -947,7 +948,9 @@ int bem_apply_block(bem_ctx* ctx, int32_t j, int32_t i, bem_z k, const bem_z* x,
     ApplyMode m;
     m.tgt_dom_lo = j; m.tgt_dom_hi = j + 1; m.src_dom_lo = i; m.src_dom_hi = i + 1;
     m.kre = k.re; m.kim = k.im; m.slot1 = 0; m.coef = bc->coef;
-    m.near = (i == j) ? &bc->near : nullptr;
+    // touching pairs within domain i and near pairs from domain j to domain i
+    // (the other pairs of the set meet zeros of x outside domain i)
+    m.near = &bc->near;
     if ((rc = ctx->run_apply(ctx->dev.xs, ctx->dev.ys, precision, m))) return rc;
     const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     CK(cudaMemcpyAsync(y, ctx->dev.ys + off_j, nvj * sizeof(double2), kout, ctx->stream));            // row1

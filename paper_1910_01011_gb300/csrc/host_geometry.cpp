@@ -154,6 +154,20 @@ bool build_quadrature(Quadrature& q, int n_gauss) {
     q.ng = n_gauss;
     std::vector<double> gx, gw;
     gauss_legendre01(n_gauss, gx, gw);
+    // near pairs (no common vertex): the collapsed Gauss-Legendre rule on each
+    // triangle, s = (u, u v) with Jacobian u, in the reference parametrisation
+    // of the singular tables
+    {
+        auto& tab = q.ss[0];
+        tab.clear();
+        for (int a = 0; a < n_gauss; a++)
+            for (int b = 0; b < n_gauss; b++)
+                for (int c = 0; c < n_gauss; c++)
+                    for (int d = 0; d < n_gauss; d++) {
+                        const double wt = gw[a] * gw[b] * gx[a] * gw[c] * gw[d] * gx[c];
+                        tab.insert(tab.end(), {gx[a], gx[a] * gx[b], gx[c], gx[c] * gx[d], wt});
+                    }
+    }
     for (int rel = 1; rel <= 3; rel++) {
         int nreg = rel == 3 ? 6 : rel == 2 ? 5 : 2;
         auto& tab = q.ss[rel];
@@ -391,6 +405,79 @@ std::string build_geometry(const std::vector<HostDomain>& doms, const Quadrature
                 int32_t code = rel | (pa[0] << 4) | (pa[1] << 6) | (pa[2] << 8) | (pb[0] << 10) | (pb[1] << 12) | (pb[2] << 14);
                 lists[dom_slot[d][a]].push_back({(int32_t)dom_slot[d][b], code});
             }
+        }
+    }
+    // ---- near pairs: no common vertex, centroids closer than twice the longer
+    // of the two triangles' longest edges, within a domain or across domains.
+    // The test is evaluated exactly as written (squared lengths, no fused
+    // multiply-adds), so the library and an independent evaluation of the same
+    // rule take the same decision.
+    {
+        struct Cen {
+            double c[3], h2;
+            int d;
+            int32_t t;
+        };
+        std::vector<Cen> cs;
+        cs.reserve((size_t)n_tri);
+        double hmax2 = 0.0;
+        for (int d = 0; d < g.n_dom; d++) {
+            const HostDomain& D = doms[d];
+            for (int64_t t = 0; t < D.nt; t++) {
+                const double* P[3] = {&D.verts[3 * D.tris[3 * t]], &D.verts[3 * D.tris[3 * t + 1]],
+                                      &D.verts[3 * D.tris[3 * t + 2]]};
+                Cen e{};
+                for (int k = 0; k < 3; k++) e.c[k] = (P[0][k] + P[1][k] + P[2][k]) / 3.0;
+                for (int i = 0; i < 3; i++) {
+                    const double* A = P[i];
+                    const double* B = P[(i + 1) % 3];
+                    const double x = B[0] - A[0], y = B[1] - A[1], z = B[2] - A[2];
+                    const double l2 = x * x + y * y + z * z;
+                    if (l2 > e.h2) e.h2 = l2;
+                }
+                e.d = d;
+                e.t = (int32_t)t;
+                hmax2 = std::max(hmax2, e.h2);
+                cs.push_back(e);
+            }
+        }
+        // uniform grid of cell 2 hmax: every near partner lies in the 27 neighbouring cells
+        const double cell = 2.0 * std::sqrt(hmax2) * (1.0 + 1e-9);
+        double lo[3] = {1e300, 1e300, 1e300};
+        for (const Cen& e : cs)
+            for (int k = 0; k < 3; k++) lo[k] = std::min(lo[k], e.c[k]);
+        auto cell_of = [&](const double* c, int k) { return (int64_t)std::floor((c[k] - lo[k]) / cell); };
+        auto key = [](int64_t i, int64_t j, int64_t k) { return (i * 1048576 + j) * 1048576 + k; };
+        std::vector<std::pair<int64_t, int32_t>> keyed(cs.size());
+        for (size_t i = 0; i < cs.size(); i++)
+            keyed[i] = {key(cell_of(cs[i].c, 0), cell_of(cs[i].c, 1), cell_of(cs[i].c, 2)), (int32_t)i};
+        std::sort(keyed.begin(), keyed.end());
+        const int32_t near_code = 0 | (0 << 4) | (1 << 6) | (2 << 8) | (0 << 10) | (1 << 12) | (2 << 14);
+        for (size_t ia = 0; ia < cs.size(); ia++) {
+            const Cen& A = cs[ia];
+            const int64_t ci = cell_of(A.c, 0), cj = cell_of(A.c, 1), ck = cell_of(A.c, 2);
+            const int32_t* TA = &doms[A.d].tris[3 * (int64_t)A.t];
+            for (int64_t di = -1; di <= 1; di++)
+                for (int64_t dj = -1; dj <= 1; dj++)
+                    for (int64_t dk = -1; dk <= 1; dk++) {
+                        const int64_t kk = key(ci + di, cj + dj, ck + dk);
+                        auto it = std::lower_bound(keyed.begin(), keyed.end(), std::make_pair(kk, (int32_t)INT32_MIN));
+                        for (; it != keyed.end() && it->first == kk; ++it) {
+                            const Cen& B = cs[it->second];
+                            if (it->second == (int32_t)ia) continue;
+                            if (B.d == A.d) {  // touching pairs have their own rules
+                                const int32_t* TB = &doms[B.d].tris[3 * (int64_t)B.t];
+                                bool share = false;
+                                for (int u = 0; u < 3; u++)
+                                    for (int v = 0; v < 3; v++) share |= TA[u] == TB[v];
+                                if (share) continue;
+                            }
+                            const double x = A.c[0] - B.c[0], y = A.c[1] - B.c[1], z = A.c[2] - B.c[2];
+                            const double h2 = std::max(A.h2, B.h2);
+                            if (x * x + y * y + z * z < 4.0 * h2)
+                                lists[dom_slot[A.d][A.t]].push_back({(int32_t)dom_slot[B.d][B.t], near_code});
+                        }
+                    }
         }
     }
     g.n_tri = n_tri;

@@ -31,7 +31,8 @@ struct Quadrature {
     double l1[QP], l2[QP], w[QP];  // regular rule (weights sum to 1)
     double lam[QP][3];             // P1 values at the rule points
     int ng = 6;                    // Gauss points per singular direction
-    // Sauter-Schwab point tables per relation (1 vertex, 2 edge, 3 identical):
+    // point tables per relation (0 near pair: collapsed Gauss-Legendre on each
+    // triangle; 1 vertex, 2 edge, 3 identical: Sauter-Schwab):
     // rows (s1, s2, t1, t2, weight * jacobian)
     std::vector<double> ss[4];
 };

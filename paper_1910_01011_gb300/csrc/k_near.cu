@@ -1,11 +1,15 @@
-// k_near.cu -- near-field correction for touching triangle pairs (FP64).
+// k_near.cu -- near-field correction for touching and near triangle pairs (FP64).
 //
 // For every pair of triangles of one surface that shares a vertex, an edge
 // or is identical, the far-field kernel's regular 6-point x 6-point rule is
 // wrong (or, for the identical pair, skipped).  This file integrates the
 // pair with the Sauter-Schwab regularising maps (Sauter & Schwab, Boundary
 // Element Methods, Sec. 5.2; the paper leaves quadrature to its BEM library,
-// Sec. 3) and subtracts exactly what the far-field kernel adds, giving
+// Sec. 3).  Pairs without a common vertex whose centroids are closer than
+// twice the longer of their longest edges (within a surface or across
+// domains) are integrated with a collapsed Gauss-Legendre rule on each
+// triangle (table 0).  Either way the kernel subtracts exactly what the
+// far-field kernel adds, giving
 // per-pair 3x3 corrections of V, K, K' (paper App. A); W follows from V by
 // its integration-by-parts form: W_ab = curl_a.curl_b sum(V) - k^2 (n_x.n_y) V_ab.
 // The corrections of both wavenumbers of a domain are combined with the
@@ -59,6 +63,8 @@ __global__ void __launch_bounds__(NEAR_THREADS) near_build_kernel(NearArgs A) {
     }
     const int dom = A.slot_dom[4 * tgt + 3];
     const double2 k = sl == 0 ? A.k[0] : A.kdom[dom];
+    // the own-domain wavenumber applies only to pairs within the target's domain
+    const bool live = sl == 0 || A.slot_dom[4 * src + 3] == dom;
     // reordered vertices: shared ones first, in matching order
     double PX[3][3], PY[3][3], OX[3][3], OY[3][3], nx[3], ny[3];
     for (int i = 0; i < 3; i++)
@@ -77,7 +83,7 @@ __global__ void __launch_bounds__(NEAR_THREADS) near_build_kernel(NearArgs A) {
     for (int i = 0; i < NACC; i++) acc[i][0] = acc[i][1] = 0.0;
     // Sauter-Schwab part, accumulated in the ORIGINAL local order
     const double* tab = A.ss_tab[rel];
-    const int n = A.ss_n[rel];
+    const int n = live ? A.ss_n[rel] : 0;
     const double scale = 4.0 * ax * ay;
     for (int idx = threadIdx.x; idx < n; idx += NEAR_THREADS) {
         const double s1 = tab[5 * idx], s2 = tab[5 * idx + 1], t1 = tab[5 * idx + 2], t2 = tab[5 * idx + 3];
@@ -94,7 +100,7 @@ __global__ void __launch_bounds__(NEAR_THREADS) near_build_kernel(NearArgs A) {
         kernel_eval(x, y, nx, ny, k.x, k.y, w, lx, ly, acc);
     }
     // minus the regular rule the far-field kernel applied (not for identical pairs)
-    if (rel != 3) {
+    if (rel != 3 && live) {
         for (int idx = threadIdx.x; idx < QP * QP; idx += NEAR_THREADS) {
             const int qa = idx / QP, qb = idx % QP;
             const double l1 = A.rule[3 * qa], l2 = A.rule[3 * qa + 1], wa = A.rule[3 * qa + 2];
