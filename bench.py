@@ -360,7 +360,9 @@ def rib_solve_metrics(local, n_rhs=16, tol=1e-8, reps=3):
       * FP64 batched: the same n_rhs excitations in lockstep, FP64-accurate
         assembled operator inside the same GMRES (the baseline at the same
         batching);
-      * one excitation alone, mixed and FP64.
+      * one excitation alone, mixed and FP64;
+      * block GMRES (one Krylov space per block of the n_rhs excitations,
+        grown by n_rhs vectors per step), mixed (`reps` runs) and FP64.
     The traces of the mixed and FP64 paths agree to the reported difference."""
     import numpy as np
     import torch
@@ -399,8 +401,16 @@ def rib_solve_metrics(local, n_rhs=16, tol=1e-8, reps=3):
         t, rbs = timed(precision=1, batch_rhs=n_rhs)
         tbs.append(t)
     ub = c.solution(0)
+    tks, rks = [], None
+    for _ in range(reps):
+        t, rks = timed(precision=1, batch_rhs=n_rhs, block_gmres=1)
+        tks.append(t)
+    ubk = c.solution(0)
+    tk64, rk64 = timed(precision=0, batch_rhs=n_rhs, block_gmres=1)
+    ubk64 = c.solution(0)
     c.close()
     per = np.array(tbs) / n_rhs
+    perk = np.array(tks) / n_rhs
     return {"workload": f"rib/fat/liver scene, 0.1 MHz, {s.n_triangles} triangles (N={N}), {n_rhs} random-phase "
                         f"excitations of the 256-piston bowl, n_pade 8, R_eps {r_eps * 1e3:.1f} mm, OSRC blocks at "
                         f"each domain's k_j",
@@ -410,6 +420,14 @@ def rib_solve_metrics(local, n_rhs=16, tol=1e-8, reps=3):
             "mixed_batched_p99_s_per_rhs": float(np.percentile(per, 99)),
             "mixed_batched_runs": len(tbs),
             "fp64_batched_s_per_rhs": tb64 / n_rhs,
+            "mixed_block_s_per_rhs": float(np.median(perk)),
+            "mixed_block_p50_s_per_rhs": float(np.percentile(perk, 50)),
+            "mixed_block_p99_s_per_rhs": float(np.percentile(perk, 99)),
+            "fp64_block_s_per_rhs": tk64 / n_rhs,
+            "speedup_block_mixed_vs_block_fp64": (tk64 / n_rhs) / float(np.median(perk)),
+            "speedup_block_mixed_vs_batched_fp64": (tb64 / n_rhs) / float(np.median(perk)),
+            "trace_rel_diff_block_mixed_vs_fp64": float(np.linalg.norm(ubk - ub64) / np.linalg.norm(ub64)),
+            "trace_rel_diff_block_fp64_vs_fp64": float(np.linalg.norm(ubk64 - ub64) / np.linalg.norm(ub64)),
             "mixed_single_s_per_rhs": t32_1, "fp64_single_s_per_rhs": t64_1,
             "speedup_batched_mixed_vs_batched_fp64": (tb64 / n_rhs) / float(np.median(per)),
             "speedup_single_mixed_vs_single_fp64": t64_1 / t32_1,
@@ -418,8 +436,11 @@ def rib_solve_metrics(local, n_rhs=16, tol=1e-8, reps=3):
             "trace_rel_diff_single_fp64_vs_batched_fp64": float(np.linalg.norm(ub64 - u64) / np.linalg.norm(u64)),
             "iterations_per_rhs": {"fp64_single": r64_1["iterations"], "mixed_single": r32_1["iterations"],
                                    "fp64_batched": rb64["iterations"] / n_rhs,
-                                   "mixed_batched": rbs["iterations"] / n_rhs},
-            "residual": {"fp64_batched": rb64["residual"], "mixed_batched": rbs["residual"]}}
+                                   "mixed_batched": rbs["iterations"] / n_rhs,
+                                   "mixed_block_steps": rks["iterations"] / n_rhs,
+                                   "fp64_block_steps": rk64["iterations"] / n_rhs},
+            "residual": {"fp64_batched": rb64["residual"], "mixed_batched": rbs["residual"],
+                         "mixed_block": rks["residual"], "fp64_block": rk64["residual"]}}
 
 
 def serving_metrics(local, n_req=12, max_exc=16, rate=20.0, budget=150 << 30, tol=1e-6, rank=0, world=1, slots=2,
@@ -429,8 +450,8 @@ def serving_metrics(local, n_req=12, max_exc=16, rate=20.0, budget=150 << 30, to
     20k, kidney scenes of 20k and 40k, each at k h ~ 1), each request with
     1..max_exc random-phase piston excitations, through the request loop
     (device-resident scene cache, admission by the HBM budget; mixed
-    precision with batched excitations, FP64 refinement to tol, `slots`
-    workers).  Baseline: the same trace, at the same arrival times, through a
+    precision with batched excitations solved by block GMRES, FP64
+    refinement to tol, `slots` workers).  Baseline: the same trace, at the same arrival times, through a
     request loop that solves one excitation at a time in plain FP64 with one
     worker (sequential FP64 GPU solves).  Each loop's cache is warmed with one
     request per scene first (set-up not in the latencies)."""
@@ -491,7 +512,7 @@ def serving_metrics(local, n_req=12, max_exc=16, rate=20.0, budget=150 << 30, to
 
     n_exc = sum(ne for _, _, ne in reqs)
     mixed = run(slots=slots, max_batch_rhs=64, precision=1, operator_mode=1)
-    seq = run(slots=1, max_batch_rhs=1, precision=0, operator_mode=1, batch_rhs=1)
+    seq = run(slots=1, max_batch_rhs=1, precision=0, operator_mode=1, batch_rhs=1, block_gmres=0)
     out = {"workload": f"{n_req} requests, Poisson {rate}/s, 1..{max_exc} excitations each ({n_exc} total), "
                        f"scenes {keys}, tol {tol}, budget {budget / 2**30:.0f} GiB, {slots} workers",
            **mixed,
@@ -608,7 +629,7 @@ def solve_step(args, s, desc, local, world):
     ctx.set_transducer(tr["centres"], tr["normals"], tr["radii"], 2 * np.pi * s.freq * s.rho0)
     R = args.prec_rhs
     ctx.set_excitations(np.exp(2j * np.pi * np.random.default_rng(3).random((R, tr["radii"].size))))
-    kw = dict(precision=1, operator_mode=1, tol=1e-8, batch_rhs=R, max_iter=20000)
+    kw = dict(precision=1, operator_mode=1, tol=1e-8, batch_rhs=R, max_iter=20000, block_gmres=1 if args.block else 0)
     for _ in range(max(1, args.warmup)):
         ctx.solve(**kw)
     ctx.profile(True)
@@ -624,6 +645,7 @@ def solve_step(args, s, desc, local, world):
                       "unit": "s/RHS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                       "higher_is_better": False,
                       "config": {"workload": desc, "n_rhs": R, "n_pade": 8, "tol": 1e-8,
+                                 "gmres": "block" if args.block else "lockstep",
                                  "osrc_solver": ["automatic", "one CTA per system", "grid-wide", "cluster per system",
                                                  "cluster per group of shifts"][args.osrc_solver]},
                       "iterations_per_rhs": rep["iterations"] / R, "gpu_launches": prof["kernel_launches"]}))
@@ -674,6 +696,7 @@ def main():
                          "mixed batched solve of --prec-rhs piston excitations with assembled operators (for "
                          "profiling the loose sparse solves inside the flexible GMRES)")
     ap.add_argument("--prec-rhs", type=int, default=8)
+    ap.add_argument("--block", action="store_true", help="--step solve: block GMRES instead of lockstep GMRES")
     ap.add_argument("--rhs", type=int, default=1,
                     help="right-hand sides per apply step; > 1 applies them in one matrix-free far-field launch "
                          "(far32m_kernel) and reports interaction-RHS per second (profiling of the multi-RHS path)")

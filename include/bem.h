@@ -208,6 +208,12 @@ typedef struct {
                               GMRES (sparse solves to 1/100 of the GMRES tolerance).  Same solution. */
     double prec_tol;       /* relative residual of the preconditioner's sparse solves inside the solve;
                               0 = automatic (0.3 flexible, 1/100 of the GMRES tolerance otherwise) */
+    int32_t block_gmres;   /* with batch_rhs > 1: 0 (default) R independent GMRES runs in lockstep; 1 block
+                              GMRES, one Krylov space shared by the block's R columns and grown by R vectors per
+                              step (restart then counts steps of R vectors; report.iterations counts steps per
+                              column, each one application of the operator and preconditioner to R vectors);
+                              blocks are at most 16 columns wide, a larger batch is split evenly.  Same
+                              solution. */
 } bem_solve_opts;
 
 typedef struct {
@@ -354,7 +360,8 @@ typedef struct {
     int32_t slots;            /* concurrent solves (worker threads; default 2) */
     int32_t max_batch_rhs;    /* excitations merged into one solve (default 64) */
     int64_t hbm_budget_bytes; /* device bytes all scenes may hold together (default 150 GiB; 0 = no limit) */
-    bem_solve_opts solve;     /* options of every solve (default: mixed precision, batch_rhs = max_batch_rhs) */
+    bem_solve_opts solve;     /* options of every solve (default: mixed precision, batch_rhs = max_batch_rhs,
+                                 block_gmres = 1) */
 } bem_server_opts;
 
 typedef struct {

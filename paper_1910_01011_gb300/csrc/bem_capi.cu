@@ -193,10 +193,16 @@ int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_
     // right-hand sides, solutions, piston data
     b += n_exc * (2 * N * 16 + slots * 6 * 16 + ne * 16) + ne * 32 * 32 + 3 * N * 16;
     // GMRES basis and work (per lockstep column)
-    const int64_t R = o.batch_rhs > 1 ? std::min<int64_t>(o.batch_rhs, n_exc) : 1;
+    const int64_t R = o.batch_rhs > 1 ? solve_batch_width(o, n_exc) : 1;
     b += (int64_t)(o.restart + 1) * R * N * 16 + 2 * R * N * 16 + (int64_t)(o.restart + 2) * 120 * R * 16 * 3 + 8 * R;
     b += (int64_t)R * ((o.restart + 1) * o.restart + 3 * o.restart + 1) * 16 + 32 * R + 16;  // device least squares
     if (o.precondition && o.flexible) b += (int64_t)o.restart * R * N * 16;  // flexible basis
+    if (o.block_gmres) {  // FP32 basis and work blocks, dot partials, coefficient blocks
+        const int64_t gx = ((int64_t)(o.restart + 1) * R + 63) / 64;
+        b += (int64_t)(o.restart + 3) * R * N * 8 +
+             16 * std::max<int64_t>((int64_t)(o.restart + 1) * R * R * 8, R * 64 * std::max<int64_t>(gx, 608)) +
+             16 * (2 * (int64_t)(o.restart + 1) * R * R + R * R);
+    }
     b += 4 * R * N * 16;
     if (o.precondition) {
         const int64_t L = ctx->opts.n_pade, nnz = 8 * nv, ms = 2 * L * R, nd = (int64_t)ctx->doms.size();

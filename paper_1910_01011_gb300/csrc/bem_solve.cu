@@ -89,62 +89,119 @@ struct PistonArgs {
     double2* tri_out;    // [n_rhs][n_slots*3][2]
 };
 
+// Excitations per block row of piston_kernel (its accumulators live in
+// registers: 4 doubles per excitation and thread).
+constexpr int PK_RC = 16;
+constexpr int PK_SLOTS = 16;  // slots per block; one thread per (slot, rule point)
+
+// Rayleigh field of piston m (its disc points, weights folded in) at x and
+// its normal derivative along n: e = sum_j w_j exp(ik R_j)/R_j,
+// f = sum_j w_j exp(ik R_j)/R_j (ik - 1/R_j) (x - y_j).n / R_j.
+template <bool ATTEN>
+__device__ __forceinline__ void piston_field(const double4* __restrict__ disc, int nq, double2 k0, double x, double y,
+                                             double z, double nx, double ny, double nz, double& er, double& ei,
+                                             double& fr, double& fi) {
+    er = ei = fr = fi = 0;
+    for (int j = 0; j < nq; j++) {
+        const double4 d = disc[j];
+        const double ex = x - d.x, ey = y - d.y, ez = z - d.z;
+        const double R = sqrt(ex * ex + ey * ey + ez * ez);
+        const double Ri = 1.0 / R;
+        double sn, cs;
+        sincos(k0.x * R, &sn, &cs);
+        const double amp = (ATTEN ? exp(-k0.y * R) : 1.0) * Ri * d.w;
+        const double gr = amp * cs, gi = amp * sn;  // w exp(ikR)/R
+        er += gr;
+        ei += gi;
+        const double ur = -k0.y - Ri, ui = k0.x;
+        const double dn = (ex * nx + ey * ny + ez * nz) * Ri;
+        fr += (gr * ur - gi * ui) * dn;
+        fi += (gr * ui + gi * ur) * dn;
+    }
+}
+
 // Per slot and excitation: <p_inc, phi_k> and <dp_inc/dn, phi_k> with the
 // Rayleigh sum over piston discs (baffled-piston reading of the transducer
-// field; the paper defers it to its ref. elwin2015, Sec. 3.2).
-__global__ void piston_kernel(PistonArgs a) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int rhs = blockIdx.y;
-    if (s >= a.n_slots) return;
-    if (a.slot_v[s].x < 0) return;
-    const double4 c = a.tc[s / TT];
-    const double nx = a.slot_n[3 * s], ny = a.slot_n[3 * s + 1], nz = a.slot_n[3 * s + 2];
-    const double2* wr = a.w + (int64_t)rhs * a.n_elem;
-    double r[3][2][2] = {};
-    for (int q = 0; q < QP; q++) {
+// field; the paper defers it to its ref. elwin2015, Sec. 3.2).  The Green's
+// function sums do not depend on the weights, so each thread evaluates every
+// piston's field once at its rule point and accumulates it into the PK_RC
+// excitations of its block row; a piston whose weight is zero in all of them
+// is skipped (a block-uniform test), so the unit excitations of a
+// superposition basis cost one evaluation per piston.  The rule points of a
+// slot are summed against the P1 values in shared memory.
+__global__ void __launch_bounds__(PK_SLOTS * QP) piston_kernel(PistonArgs a) {
+    const int sl = threadIdx.x / QP, q = threadIdx.x % QP;
+    const int64_t s = (int64_t)blockIdx.x * PK_SLOTS + sl;
+    const int r0 = blockIdx.y * PK_RC, nrc = min(PK_RC, a.n_rhs - r0);
+    const bool live = s < a.n_slots && a.slot_v[s].x >= 0;
+    double acc[PK_RC][4];
+#pragma unroll
+    for (int c = 0; c < PK_RC; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0;
+    double gw = 0;
+    if (live) {
+        const double4 c0 = a.tc[s / TT];
+        const double nx = a.slot_n[3 * s], ny = a.slot_n[3 * s + 1], nz = a.slot_n[3 * s + 2];
         const double4 g = a.pg[s * QP + q];
-        const double x = c.x + g.x, y = c.y + g.y, z = c.z + g.z;
-        double pr = 0, pi = 0, dr = 0, di = 0;
+        gw = g.w;
+        const double x = c0.x + g.x, y = c0.y + g.y, z = c0.z + g.z;
+        const double2* wr = a.w + (int64_t)r0 * a.n_elem;
         for (int m = 0; m < a.n_elem; m++) {
-            double er = 0, ei = 0, fr = 0, fi = 0;
-            for (int j = 0; j < a.nq; j++) {
-                const double4 d = a.disc[(int64_t)m * a.nq + j];
-                const double ex = x - d.x, ey = y - d.y, ez = z - d.z;
-                const double R = sqrt(ex * ex + ey * ey + ez * ez);
-                const double Ri = 1.0 / R;
-                double sn, cs;
-                sincos(a.k0.x * R, &sn, &cs);
-                const double amp = exp(-a.k0.y * R) * Ri * d.w;
-                const double gr = amp * cs, gi = amp * sn;          // w exp(ikR)/R
-                er += gr;
-                ei += gi;
-                // d/dn: exp(ikR)/R (ik - 1/R) (x-y).n / R
-                const double ur = -a.k0.y - Ri, ui = a.k0.x;
-                const double dn = (ex * nx + ey * ny + ez * nz) * Ri;
-                fr += (gr * ur - gi * ui) * dn;
-                fi += (gr * ui + gi * ur) * dn;
+            bool any = false;
+            for (int c = 0; c < nrc && !any; c++) {
+                const double2 wm = wr[(int64_t)c * a.n_elem + m];
+                any = wm.x != 0.0 || wm.y != 0.0;
             }
-            const double2 wm = wr[m];
-            pr += wm.x * er - wm.y * ei;
-            pi += wm.x * ei + wm.y * er;
-            dr += wm.x * fr - wm.y * fi;
-            di += wm.x * fi + wm.y * fr;
-        }
-        const double Pr = a.pref.x * pr - a.pref.y * pi, Pi = a.pref.x * pi + a.pref.y * pr;
-        const double Dr = a.pref.x * dr - a.pref.y * di, Di = a.pref.x * di + a.pref.y * dr;
-        for (int k = 0; k < 3; k++) {
-            const double wl = g.w * a.lam[q][k];
-            r[k][0][0] += wl * Pr;
-            r[k][0][1] += wl * Pi;
-            r[k][1][0] += wl * Dr;
-            r[k][1][1] += wl * Di;
+            if (!any) continue;
+            double er, ei, fr, fi;
+            if (a.k0.y != 0.0)
+                piston_field<true>(a.disc + (int64_t)m * a.nq, a.nq, a.k0, x, y, z, nx, ny, nz, er, ei, fr, fi);
+            else
+                piston_field<false>(a.disc + (int64_t)m * a.nq, a.nq, a.k0, x, y, z, nx, ny, nz, er, ei, fr, fi);
+#pragma unroll
+            for (int c = 0; c < PK_RC; c++)
+                if (c < nrc) {
+                    const double2 wm = wr[(int64_t)c * a.n_elem + m];
+                    acc[c][0] += wm.x * er - wm.y * ei;
+                    acc[c][1] += wm.x * ei + wm.y * er;
+                    acc[c][2] += wm.x * fr - wm.y * fi;
+                    acc[c][3] += wm.x * fi + wm.y * fr;
+                }
         }
     }
-    double2* out = a.tri_out + (int64_t)rhs * a.n_slots * 6;
-    for (int k = 0; k < 3; k++) {
-        out[(s * 3 + k) * 2] = make_double2(r[k][0][0], r[k][0][1]);
-        out[(s * 3 + k) * 2 + 1] = make_double2(r[k][1][0], r[k][1][1]);
+    // Galerkin moments out_k = sum_q w_q lam_qk (pref x) in rule order; after
+    // the exchange, thread (sl, q) writes trace q & 1 of P1 function q >> 1
+    __shared__ double sh[PK_SLOTS][QP][5];
+    static_assert(QP == 6, "one output (3 P1 functions x 2 traces) per rule point");
+    const int k = q >> 1, tr = q & 1;
+#pragma unroll
+    for (int c = 0; c < PK_RC; c++) {
+        if (c >= nrc) break;
+        sh[sl][q][0] = a.pref.x * acc[c][0] - a.pref.y * acc[c][1];
+        sh[sl][q][1] = a.pref.x * acc[c][1] + a.pref.y * acc[c][0];
+        sh[sl][q][2] = a.pref.x * acc[c][2] - a.pref.y * acc[c][3];
+        sh[sl][q][3] = a.pref.x * acc[c][3] + a.pref.y * acc[c][2];
+        sh[sl][q][4] = gw;
+        __syncthreads();
+        if (live) {
+            double vr = 0, vi = 0;
+            for (int qq = 0; qq < QP; qq++) {
+                const double wl = sh[sl][qq][4] * a.lam[qq][k];
+                vr += wl * sh[sl][qq][2 * tr];
+                vi += wl * sh[sl][qq][2 * tr + 1];
+            }
+            a.tri_out[(int64_t)(r0 + c) * a.n_slots * 6 + (s * 3 + k) * 2 + tr] = make_double2(vr, vi);
+        }
+        __syncthreads();
     }
+}
+
+constexpr int64_t BLOCK_COLS = 16;  // widest block of block GMRES
+
+int64_t solve_batch_width(const bem_solve_opts& o, int64_t n_exc) {
+    const int64_t lead = std::max<int64_t>(1, std::min<int64_t>(o.batch_rhs, n_exc));
+    if (!o.block_gmres) return lead;
+    const int64_t groups = (lead + BLOCK_COLS - 1) / BLOCK_COLS;
+    return (lead + groups - 1) / groups;
 }
 
 struct SolveState {
@@ -240,7 +297,8 @@ static int build_rhs(bem_ctx* ctx) {
             for (int k = 0; k < 3; k++) a.lam[q][k] = ctx->quad.lam[q][k];
         a.tri_out = S->tri_rhs;
         CK(cudaMemsetAsync(S->tri_rhs, 0, nr * g.n_slots * 6 * sizeof(double2), ctx->stream));
-        piston_kernel<<<dim3((unsigned)((g.n_slots + 63) / 64), (unsigned)nr), 64, 0, ctx->stream>>>(a);
+        piston_kernel<<<dim3((unsigned)((g.n_slots + PK_SLOTS - 1) / PK_SLOTS), (unsigned)((nr + PK_RC - 1) / PK_RC)),
+                        PK_SLOTS * QP, 0, ctx->stream>>>(a);
         ctx->launches++;
     } else {
         return ctx->fail(BEM_ERR_STATE, "no incident field set");
@@ -386,6 +444,7 @@ int bem_default_solve_opts(bem_solve_opts* o) {
     o->batch_rhs = 0;
     o->flexible = 1;
     o->prec_tol = 0.0;
+    o->block_gmres = 0;
     return BEM_OK;
 }
 
@@ -465,14 +524,25 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
     CK(cudaMemsetAsync(u, 0, R * N * sizeof(double2), ctx->stream));
     int it = 0;
     double worst = 0;
+    // block GMRES, or R GMRES runs in lockstep (also where the block's
+    // starting residuals are dependent columns)
+    auto inner_solve = [&](const Krylov::Op& op, const double2* rhs, double2* x, double tol_in, bool zero_guess,
+                           bool fp32_basis) -> int {
+        if (o.block_gmres) {
+            bool deficient = false;
+            const int e = S->kry.gmres_block(ctx, op, rhs, x, R, o.restart, tol_in, o.max_iter - it, its.data(),
+                                             irel.data(), zero_guess, rp, fp32_basis, &deficient);
+            if (e || !deficient) return e;
+        }
+        return S->kry.gmres_batch(ctx, op, rhs, x, R, o.restart, tol_in, o.max_iter - it, its.data(), irel.data(),
+                                  zero_guess, rp);
+    };
     if (o.precision == BEM_PREC_FP64) {
         const double2* sb = rhs_of(b);
         if (rc) return rc;
         double inner = o.tol;
         for (int attempt = 0; attempt < 4; attempt++) {
-            if ((rc = S->kry.gmres_batch(ctx, op_for(BEM_PREC_FP64), sb, u, R, o.restart, inner, o.max_iter - it,
-                                         its.data(), irel.data(), attempt == 0, rp)))
-                return rc;
+            if ((rc = inner_solve(op_for(BEM_PREC_FP64), sb, u, inner, attempt == 0, false))) return rc;
             it += *std::max_element(its.begin(), its.end());
             for (int64_t r = 0; r < R; r++) rep->iterations += its[r];
             if ((rc = residual(rel, bn))) return rc;
@@ -494,9 +564,8 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
             prev = worst;
             const double2* sr = rhs_of(S->br);
             if (rc) return rc;
-            if ((rc = S->kry.gmres_batch(ctx, op_for(inner_prec), sr, S->bd, R, o.restart,
-                                         inner_tolerance(o, worst), o.max_iter - it, its.data(), irel.data(), true,
-                                         rp)))
+            if ((rc = inner_solve(op_for(inner_prec), sr, S->bd, inner_tolerance(o, worst), true,
+                                  inner_prec != BEM_PREC_FP64)))
                 return rc;
             it += *std::max_element(its.begin(), its.end());
             for (int64_t r = 0; r < R; r++) rep->iterations += its[r];
@@ -517,7 +586,7 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     if (opts) o = *opts;
     if (o.restart < 1 || o.max_iter < 1 || !(o.tol > 0) || (o.precision != BEM_PREC_FP64 && o.precision != BEM_PREC_FP32) ||
         (o.operator_mode != 0 && o.operator_mode != 1) || o.batch_rhs < 0 || o.flexible < 0 || o.flexible > 1 ||
-        !(o.prec_tol >= 0) || o.prec_tol >= 1)
+        !(o.prec_tol >= 0) || o.prec_tol >= 1 || o.block_gmres < 0 || o.block_gmres > 1)
         return ctx->fail(BEM_ERR_INVALID_ARG, "bad solve options");
     CK(cudaSetDevice(ctx->device));
     const auto t0 = std::chrono::steady_clock::now();
@@ -564,9 +633,12 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     const Krylov::Op right = [ctx](const double2* x, double2* y) -> int { return ctx->apply_prec(x, y); };
     const Krylov::Op* rp = (o.precondition && o.flexible) ? &right : nullptr;
     if (o.batch_rhs > 1 && nr > 1) {
-        // blocks of up to batch_rhs excitations, GMRES in lockstep
-        for (int64_t r0 = 0; r0 < nr; r0 += o.batch_rhs) {
-            const int64_t Rb = std::min<int64_t>(o.batch_rhs, nr - r0);
+        // blocks of up to batch_rhs excitations, GMRES in lockstep; block GMRES
+        // takes at most BLOCK_COLS columns per block (its host-side band QR
+        // update costs O(step x P^3)), the batch split evenly
+        const int64_t width = solve_batch_width(o, nr);
+        for (int64_t r0 = 0; r0 < nr; r0 += width) {
+            const int64_t Rb = std::min<int64_t>(width, nr - r0);
             if ((rc = solve_block(ctx, o, S->b + r0 * N, S->u + r0 * N, Rb, &R, &converged))) return rc;
         }
     }

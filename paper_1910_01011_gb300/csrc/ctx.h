@@ -182,6 +182,9 @@ namespace gbem {
 // work items to fill the GPU, at most CHUNK_MAX tiles, and the partial
 // potentials of all R vectors within 2 GiB where possible.
 void multi_chunking(int n_tiles, int64_t n_pts, int64_t R, int* n_chunks, int* chunk_tiles);
+// excitations per batched solve: batch_rhs (at most n_exc), or for block GMRES
+// the batch split evenly into blocks of at most 16 columns
+int64_t solve_batch_width(const bem_solve_opts& o, int64_t n_exc);
 // FP64-accurate complex products in FP32 arithmetic (k_df64.cu).
 int df_prepare_inplace(bem_ctx* ctx, double2* v, int64_t n, int* e);
 int df_gemv(bem_ctx* ctx, const float4* A, const int* eA, int64_t m, int64_t k, int64_t lda, const double2* X,

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <complex>
 #include <functional>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.h"
@@ -184,6 +185,234 @@ __global__ void kvb_scale(double2* W, int64_t n, const double* s) {
     W[(int64_t)r * n + i] = v;
 }
 
+// ---- block GMRES: products between a basis of K vectors and P columns
+
+constexpr int KB_COLS = 16;  // columns handled per pass of the block kernels
+
+// part[(k P + c) nsplit + blk] = sum_{i in blk} conj(V_k[i]) W_c[i] for the
+// KB_COLS columns c0 .. c0 + KB_COLS - 1 (those below P); grid (K, nsplit).
+__global__ void __launch_bounds__(KV_THREADS) kbd_dots(int64_t n, int K, int P, const double2* __restrict__ V,
+                                                       const double2* __restrict__ W, int c0, int nsplit,
+                                                       double2* __restrict__ part) {
+    const int k = blockIdx.x, blk = blockIdx.y;
+    const int nc = min(KB_COLS, P - c0);
+    double ar[KB_COLS], ai[KB_COLS];
+#pragma unroll
+    for (int c = 0; c < KB_COLS; c++) ar[c] = ai[c] = 0.0;
+    const double2* v = V + (int64_t)k * n;
+    for (int64_t i = (int64_t)blk * KV_THREADS + threadIdx.x; i < n; i += (int64_t)nsplit * KV_THREADS) {
+        const double2 a = v[i];
+#pragma unroll
+        for (int c = 0; c < KB_COLS; c++)
+            if (c < nc) {
+                const double2 b = W[(int64_t)(c0 + c) * n + i];
+                ar[c] += a.x * b.x + a.y * b.y;
+                ai[c] += a.x * b.y - a.y * b.x;
+            }
+    }
+    __shared__ double sh[KV_THREADS / 32][KB_COLS][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < KB_COLS; c++) {
+        double x = ar[c], y = ai[c];
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+        if (lane == 0) {
+            sh[warp][c][0] = x;
+            sh[warp][c][1] = y;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        double x = 0, y = 0;
+        for (int w = 0; w < KV_THREADS / 32; w++) {
+            x += sh[w][threadIdx.x][0];
+            y += sh[w][threadIdx.x][1];
+        }
+        part[((int64_t)k * P + c0 + threadIdx.x) * nsplit + blk] = make_double2(x, y);
+    }
+}
+
+// C[k P + c] = sum_blk part[(k P + c) nsplit + blk]  (fixed order)
+__global__ void kbd_reduce(int KP, int nsplit, const double2* __restrict__ part, double2* __restrict__ C) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= KP) return;
+    double x = 0, y = 0;
+    for (int q = 0; q < nsplit; q++) {
+        x += part[(int64_t)e * nsplit + q].x;
+        y += part[(int64_t)e * nsplit + q].y;
+    }
+    C[e] = make_double2(x, y);
+}
+
+// out_c[i] = beta base_c[i] + alpha sum_k V_k[i] C[k P + c] for the columns
+// c0 .. c0 + KB_COLS - 1 below P (base may be null; out may equal base, not V).
+__global__ void __launch_bounds__(KV_THREADS) kbd_combine(int64_t n, int K, int P, const double2* __restrict__ V,
+                                                          const double2* __restrict__ C, double alpha,
+                                                          const double2* base, double beta, double2* out, int c0) {
+    __shared__ double2 cs[64][KB_COLS];
+    const int64_t i = (int64_t)blockIdx.x * KV_THREADS + threadIdx.x;
+    const int nc = min(KB_COLS, P - c0);
+    double ar[KB_COLS], ai[KB_COLS];
+#pragma unroll
+    for (int c = 0; c < KB_COLS; c++) {
+        ar[c] = ai[c] = 0.0;
+        if (base && c < nc && i < n) {
+            const double2 b = base[(int64_t)(c0 + c) * n + i];
+            ar[c] = beta * b.x;
+            ai[c] = beta * b.y;
+        }
+    }
+    for (int k0 = 0; k0 < K; k0 += 64) {
+        const int kn = min(64, K - k0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kn * KB_COLS; e += KV_THREADS) {
+            const int kk = e / KB_COLS, c = e % KB_COLS;
+            const double2 v = c < nc ? C[(int64_t)(k0 + kk) * P + c0 + c] : make_double2(0, 0);
+            cs[kk][c] = make_double2(alpha * v.x, alpha * v.y);
+        }
+        __syncthreads();
+        if (i < n)
+            for (int kk = 0; kk < kn; kk++) {
+                const double2 v = V[(int64_t)(k0 + kk) * n + i];
+#pragma unroll
+                for (int c = 0; c < KB_COLS; c++) {
+                    const double2 cc = cs[kk][c];
+                    ar[c] += v.x * cc.x - v.y * cc.y;
+                    ai[c] += v.x * cc.y + v.y * cc.x;
+                }
+            }
+    }
+    if (i < n)
+#pragma unroll
+        for (int c = 0; c < KB_COLS; c++)
+            if (c < nc) out[(int64_t)(c0 + c) * n + i] = make_double2(ar[c], ai[c]);
+}
+
+// FP32 forms of the two block kernels (the inner solves of the mixed path,
+// whose tolerance (1e-4) needs no FP64 orthogonalisation): FP32 vectors and
+// arithmetic, per-block partial sums returned in FP64.
+// FP32 block dots as a tiled contraction: CTA (x, y) forms the 64 x KB_COLS
+// tile of C = V^H W for rows 64 x .. 64 x + 63 and the columns c0 .. over the
+// y-th slice of n, staging 32 entries of each row and column in shared memory
+// per step (V read once from memory, W once per row tile).  Thread (ty, tx)
+// accumulates rows ty + 16 r (r < 4) of column tx; each 32-entry chunk is
+// summed in FP32 and folded into a compensated (Kahan) FP32 total, which is
+// written as FP64 partials part[(k P + c) nsplit + y].
+constexpr int KD_ROWS = 64, KD_CHUNK = 32;
+__global__ void __launch_bounds__(KV_THREADS) kbd_dots32(int64_t n, int K, int P, const float2* __restrict__ V,
+                                                         const float2* __restrict__ W, int c0, int nsplit,
+                                                         int64_t slice, double2* __restrict__ part) {
+    __shared__ float2 vs[KD_ROWS][KD_CHUNK + 1];
+    __shared__ float2 ws[KB_COLS][KD_CHUNK + 1];
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int k0 = blockIdx.x * KD_ROWS, blk = blockIdx.y;
+    const int nc = min(KB_COLS, P - c0);
+    const int64_t i_begin = (int64_t)blk * slice, i_end = min(n, i_begin + slice);
+    float tr[4], ti[4], cr[4], ci[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) tr[r] = ti[r] = cr[r] = ci[r] = 0.f;
+    for (int64_t i0 = i_begin; i0 < i_end; i0 += KD_CHUNK) {
+#pragma unroll
+        for (int l = 0; l < KD_ROWS * KD_CHUNK / KV_THREADS; l++) {
+            const int idx = l * KV_THREADS + t, row = idx / KD_CHUNK, e = idx % KD_CHUNK;
+            const int64_t i = i0 + e;
+            vs[row][e] = (k0 + row < K && i < i_end) ? V[(int64_t)(k0 + row) * n + i] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int l = 0; l < KB_COLS * KD_CHUNK / KV_THREADS; l++) {
+            const int idx = l * KV_THREADS + t, col = idx / KD_CHUNK, e = idx % KD_CHUNK;
+            const int64_t i = i0 + e;
+            ws[col][e] = (col < nc && i < i_end) ? W[(int64_t)(c0 + col) * n + i] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int e = 0; e < KD_CHUNK; e++) {
+            const float2 b = ws[tx][e];
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const float2 a = vs[ty + 16 * r][e];
+                ar[r] = fmaf(a.x, b.x, fmaf(a.y, b.y, ar[r]));
+                ai[r] = fmaf(a.x, b.y, fmaf(-a.y, b.x, ai[r]));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            float y = ar[r] - cr[r], u = tr[r] + y;
+            cr[r] = (u - tr[r]) - y;
+            tr[r] = u;
+            y = ai[r] - ci[r];
+            u = ti[r] + y;
+            ci[r] = (u - ti[r]) - y;
+            ti[r] = u;
+        }
+        __syncthreads();
+    }
+    if (tx >= nc) return;
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int k = k0 + ty + 16 * r;
+        if (k < K)
+            part[((int64_t)k * P + c0 + tx) * nsplit + blk] =
+                make_double2((double)tr[r] - (double)cr[r], (double)ti[r] - (double)ci[r]);
+    }
+}
+
+__global__ void __launch_bounds__(KV_THREADS) kbd_combine32(int64_t n, int K, int P, const float2* __restrict__ V,
+                                                            const double2* __restrict__ C, float alpha,
+                                                            const float2* base, float beta, float2* out, int c0) {
+    __shared__ float2 cs[64][KB_COLS];
+    const int64_t i = (int64_t)blockIdx.x * KV_THREADS + threadIdx.x;
+    const int nc = min(KB_COLS, P - c0);
+    float ar[KB_COLS], ai[KB_COLS];
+#pragma unroll
+    for (int c = 0; c < KB_COLS; c++) {
+        ar[c] = ai[c] = 0.f;
+        if (base && c < nc && i < n) {
+            const float2 b = base[(int64_t)(c0 + c) * n + i];
+            ar[c] = beta * b.x;
+            ai[c] = beta * b.y;
+        }
+    }
+    for (int k0 = 0; k0 < K; k0 += 64) {
+        const int kn = min(64, K - k0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kn * KB_COLS; e += KV_THREADS) {
+            const int kk = e / KB_COLS, c = e % KB_COLS;
+            const double2 v = c < nc ? C[(int64_t)(k0 + kk) * P + c0 + c] : make_double2(0, 0);
+            cs[kk][c] = make_float2(alpha * (float)v.x, alpha * (float)v.y);
+        }
+        __syncthreads();
+        if (i < n)
+#pragma unroll 4
+            for (int kk = 0; kk < kn; kk++) {
+                const float2 v = V[(int64_t)(k0 + kk) * n + i];
+#pragma unroll
+                for (int c = 0; c < KB_COLS; c++) {
+                    const float2 cc = cs[kk][c];
+                    ar[c] = fmaf(v.x, cc.x, fmaf(-v.y, cc.y, ar[c]));
+                    ai[c] = fmaf(v.x, cc.y, fmaf(v.y, cc.x, ai[c]));
+                }
+            }
+    }
+    if (i < n)
+#pragma unroll
+        for (int c = 0; c < KB_COLS; c++)
+            if (c < nc) out[(int64_t)(c0 + c) * n + i] = make_float2(ar[c], ai[c]);
+}
+
+__global__ void kv_to32(int64_t len, const double2* __restrict__ a, float2* __restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * KV_THREADS + threadIdx.x;
+    if (i < len) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+__global__ void kv_to64(int64_t len, const float2* __restrict__ a, double2* __restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * KV_THREADS + threadIdx.x;
+    if (i < len) b[i] = make_double2((double)a[i].x, (double)a[i].y);
+}
+
 // ---- least squares on the device
 
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
@@ -318,6 +547,11 @@ int Krylov::ensure(bem_ctx* ctx, int64_t n_, int m_, int64_t R_) {
     return BEM_OK;
 }
 
+void Krylov::dfree_buf(bem_ctx* ctx, void** p) {
+    ctx->dfree(*p);
+    *p = nullptr;
+}
+
 int Krylov::ensure_flexible(bem_ctx* ctx) {
     if (Z) return BEM_OK;
     int rc;
@@ -328,9 +562,11 @@ int Krylov::ensure_flexible(bem_ctx* ctx) {
 void Krylov::release(bem_ctx* ctx) {
     for (void* p : {(void*)V, (void*)w, (void*)t, (void*)part, (void*)h, (void*)y, (void*)sc, (void*)Z, (void*)H,
                     (void*)cs, (void*)sn, (void*)g, (void*)bn, (void*)res, (void*)run, (void*)jr, (void*)its,
-                    (void*)n_run})
+                    (void*)n_run, (void*)bpart, (void*)bC, (void*)b32})
         ctx->dfree(p);
-    V = w = t = part = h = y = Z = H = cs = sn = g = nullptr;
+    V = w = t = part = h = y = Z = H = cs = sn = g = bpart = bC = nullptr;
+    b32 = nullptr;
+    bpart_n = bC_n = b32_n = 0;
     sc = bn = res = nullptr;
     run = jr = its = n_run = nullptr;
     n = 0;
@@ -527,4 +763,375 @@ int Krylov::gmres_batch(bem_ctx* ctx, const Op& op, const double2* B, double2* X
     if ((rc = norms(ctx, t, Rn, rn.data()))) return rc;
     for (int64_t r = 0; r < Rn; r++) relres[r] = bnorm[r] > 0 ? rn[r] / bnorm[r] : 0.0;
     return BEM_OK;
+}
+
+// ---------------------------------------------------------------- block GMRES
+
+namespace {
+
+using zd = std::complex<double>;
+
+// slices of n for the tiled FP32 dots: about 4 x 152 CTAs in all, slices of
+// at least 8 chunks; nsplit x gx <= max(gx, 608)
+int nsplit_tiled(int64_t n, int gx) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 8 * KD_CHUNK - 1) / (8 * KD_CHUNK), 4 * 152 / gx));
+}
+
+int nsplit_for(int64_t n, int K) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>({8, (n + KV_THREADS - 1) / KV_THREADS,
+                                                         (4 * 152 + K - 1) / std::max(1, K)}));
+}
+
+// C [K][P] (device, FP64) = V[0:K]^H W for P columns of n, FP64 or FP32 vectors.
+template <class T>
+int block_dots(bem_ctx* ctx, Krylov& k, const T* V, int K, const T* W, int P, double2* C) {
+    const int64_t n = k.n;
+    constexpr bool F32 = std::is_same<T, float2>::value;
+    // FP32: row tiles of KD_ROWS, slices of whole chunks, about 4 CTAs per SM
+    const int gx = F32 ? (K + KD_ROWS - 1) / KD_ROWS : K;
+    const int nsplit = F32 ? nsplit_tiled(n, gx) : nsplit_for(n, K);
+    const int64_t slice = F32 ? ((n + nsplit - 1) / nsplit + KD_CHUNK - 1) / KD_CHUNK * KD_CHUNK : 0;
+    for (int c0 = 0; c0 < P; c0 += KB_COLS) {
+        if constexpr (std::is_same<T, double2>::value)
+            kbd_dots<<<dim3((unsigned)K, (unsigned)nsplit), KV_THREADS, 0, ctx->stream>>>(n, K, P, V, W, c0, nsplit,
+                                                                                         k.bpart);
+        else
+            kbd_dots32<<<dim3((unsigned)gx, (unsigned)nsplit), KV_THREADS, 0, ctx->stream>>>(n, K, P, V, W, c0, nsplit,
+                                                                                            slice, k.bpart);
+    }
+    kbd_reduce<<<(unsigned)((K * P + 127) / 128), 128, 0, ctx->stream>>>(K * P, nsplit, k.bpart, C);
+    ctx->launches += (P + KB_COLS - 1) / KB_COLS + 1;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BEM_OK : ctx->fail(BEM_ERR_CUDA, std::string("block dots: ") + cudaGetErrorString(e));
+}
+
+// out = beta base + alpha V[0:K] C (C [K][P] device FP64), column groups of KB_COLS.
+template <class T>
+int block_combine(bem_ctx* ctx, int64_t n, const T* V, int K, int P, const double2* C, double alpha, const T* base,
+                  double beta, T* out) {
+    const unsigned nb = (unsigned)((n + KV_THREADS - 1) / KV_THREADS);
+    for (int c0 = 0; c0 < P; c0 += KB_COLS) {
+        if constexpr (std::is_same<T, double2>::value)
+            kbd_combine<<<nb, KV_THREADS, 0, ctx->stream>>>(n, K, P, V, C, alpha, base, beta, out, c0);
+        else
+            kbd_combine32<<<nb, KV_THREADS, 0, ctx->stream>>>(n, K, P, V, C, (float)alpha, base, (float)beta, out, c0);
+    }
+    ctx->launches += (P + KB_COLS - 1) / KB_COLS;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BEM_OK : ctx->fail(BEM_ERR_CUDA, std::string("block combine: ") + cudaGetErrorString(e));
+}
+
+// In place: lower-triangular L with G = L L^H (G Hermitian P x P, row-major).
+// Returns false if G is not numerically positive definite.
+bool cholesky(std::vector<zd>& G, int P) {
+    for (int j = 0; j < P; j++) {
+        double d = G[(size_t)j * P + j].real();
+        for (int k2 = 0; k2 < j; k2++) d -= std::norm(G[(size_t)j * P + k2]);
+        if (!(d > 0)) return false;
+        const double l = std::sqrt(d);
+        G[(size_t)j * P + j] = l;
+        for (int i = j + 1; i < P; i++) {
+            zd s = G[(size_t)i * P + j];
+            for (int k2 = 0; k2 < j; k2++) s -= G[(size_t)i * P + k2] * std::conj(G[(size_t)j * P + k2]);
+            G[(size_t)i * P + j] = s / l;
+        }
+        for (int i = 0; i < j; i++) G[(size_t)i * P + j] = 0.0;
+    }
+    return true;
+}
+
+// U^-1 for U = L^H (L lower triangular, row-major), row-major.
+std::vector<zd> upper_inverse(const std::vector<zd>& L, int P) {
+    std::vector<zd> Ui((size_t)P * P, zd(0));
+    for (int c = 0; c < P; c++)
+        for (int i = c; i >= 0; i--) {
+            zd s = i == c ? 1.0 : 0.0;
+            for (int k2 = i + 1; k2 <= c; k2++) s -= std::conj(L[(size_t)k2 * P + i]) * Ui[(size_t)k2 * P + c];
+            Ui[(size_t)i * P + c] = s / std::conj(L[(size_t)i * P + i]);
+        }
+    return Ui;
+}
+
+// The block GMRES iteration with its orthogonalisation on T vectors: the
+// Krylov basis Vt [(m+1) P][n], work columns Wt, Tt [P][n]; V (FP64) holds the
+// blocks that the preconditioner and operator read, Z their preconditioned
+// images.  With T = float2 every new block is converted to FP64 into V.
+template <class T>
+int gmres_block_impl(Krylov& k, bem_ctx* ctx, const Krylov::Op& op, const double2* B, double2* X, int P, int m,
+                     double tol, int max_iter, int* iters, double* relres, bool zero_guess, const Krylov::Op* prec,
+                     bool* deficient, T* Vt, T* Wt, T* Tt) {
+    constexpr bool F32 = std::is_same<T, float2>::value;
+    const int64_t n = k.n, ldk = (int64_t)P * n;
+    const unsigned nbl = (unsigned)((ldk + KV_THREADS - 1) / KV_THREADS);
+    int rc;
+    std::vector<double> bnorm(P), rres(P, 1.0);
+    if ((rc = k.norms(ctx, B, P, bnorm.data()))) return rc;
+    for (int c = 0; c < P; c++) iters[c] = 0;
+    std::vector<double2> tmp((size_t)P * P);
+    std::vector<zd> Gh((size_t)P * P);
+    // orthonormalise the P columns of Wc in place (column scaling folded into
+    // the first of two Cholesky QR passes); Rout: W_in = Q Rout, upper P x P
+    auto orth = [&](T* Wc, std::vector<zd>& Rout) -> int {
+        std::vector<double> D(P, 1.0);
+        std::fill(Rout.begin(), Rout.end(), zd(0));
+        for (int c = 0; c < P; c++) Rout[(size_t)c * P + c] = 1.0;
+        for (int pass = 0; pass < 2; pass++) {
+            const T* src = pass == 0 ? Wc : Tt;
+            T* dst = pass == 0 ? Tt : Wc;
+            int e = block_dots(ctx, k, src, P, src, P, k.bC);
+            if (e) return e;
+            CK(cudaMemcpyAsync(tmp.data(), k.bC, tmp.size() * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            for (int c = 0; c < P; c++) {
+                const double g = tmp[(size_t)c * P + c].x;
+                D[c] = pass == 0 && g > 0 ? std::sqrt(g) : 1.0;
+            }
+            for (int i = 0; i < P; i++)
+                for (int j = 0; j < P; j++)
+                    Gh[(size_t)i * P + j] = zd(tmp[(size_t)i * P + j].x, tmp[(size_t)i * P + j].y) / (D[i] * D[j]);
+            if (!cholesky(Gh, P)) return BEM_ERR_NOT_CONVERGED;  // dependent columns: the block space is exhausted
+            const std::vector<zd> Ui = upper_inverse(Gh, P);
+            for (int i = 0; i < P; i++)
+                for (int j = 0; j < P; j++) {
+                    const zd v = Ui[(size_t)i * P + j] / D[i];
+                    tmp[(size_t)i * P + j] = make_double2(v.real(), v.imag());
+                }
+            CK(cudaMemcpyAsync(k.bC, tmp.data(), tmp.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+            if ((e = block_combine(ctx, n, src, P, P, k.bC, 1.0, (const T*)nullptr, 0.0, dst))) return e;
+            // Rout <- U D Rout
+            std::vector<zd> Rt((size_t)P * P);
+            for (int i = 0; i < P; i++)
+                for (int j = 0; j < P; j++) {
+                    zd s = 0;
+                    for (int k2 = i; k2 < P; k2++) s += std::conj(Gh[(size_t)k2 * P + i]) * D[k2] * Rout[(size_t)k2 * P + j];
+                    Rt[(size_t)i * P + j] = s;
+                }
+            Rout = Rt;
+        }
+        return BEM_OK;
+    };
+    const int KM = (m + 1) * P;
+    std::vector<double2> Hs((size_t)KM * m * P);     // rotated block Hessenberg (upper triangle), Hs[col * KM + row]
+    std::vector<double2> Gr((size_t)KM * P);         // rotated right-hand sides, row-major Gr[row * P + c]
+    std::vector<double2> rcs((size_t)m * P * P), rsn((size_t)m * P * P);  // P Givens rotations per basis column
+    std::vector<double2> hcs;
+    int total = 0;
+    bool first = true;
+    while (total < max_iter) {
+        // block residual into V_0 (and its T copy)
+        if (first && zero_guess) {
+            CK(cudaMemcpyAsync(k.V, B, (size_t)ldk * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaMemsetAsync(X, 0, (size_t)ldk * sizeof(double2), ctx->stream));
+        } else {
+            if ((rc = op(X, k.t))) return rc;
+            kv_axpby<<<nbl, KV_THREADS, 0, ctx->stream>>>(ldk, make_double2(1, 0), B, make_double2(-1, 0), k.t, k.V);
+            ctx->launches += 1;
+        }
+        first = false;
+        std::vector<double> rn(P);
+        if ((rc = k.norms(ctx, k.V, P, rn.data()))) return rc;
+        bool open = false;
+        for (int c = 0; c < P; c++) {
+            rres[c] = bnorm[c] > 0 ? rn[c] / bnorm[c] : 0.0;
+            open |= rres[c] > tol;
+        }
+        if (!open) break;
+        if constexpr (F32) kv_to32<<<nbl, KV_THREADS, 0, ctx->stream>>>(ldk, k.V, Vt);
+        std::vector<zd> S((size_t)P * P);
+        if ((rc = orth(Vt, S))) {
+            if (rc != BEM_ERR_NOT_CONVERGED) return rc;
+            // dependent residual columns: nothing to build on; if this call has
+            // made no step yet the caller solves the block another way
+            if (total == 0 && deficient) {
+                *deficient = true;
+                return BEM_OK;
+            }
+            break;
+        }
+        if constexpr (F32) kv_to64<<<nbl, KV_THREADS, 0, ctx->stream>>>(ldk, Vt, k.V);
+        std::fill(Gr.begin(), Gr.end(), make_double2(0, 0));
+        for (int r = 0; r < P; r++)
+            for (int c = 0; c < P; c++) Gr[(size_t)r * P + c] = make_double2(S[(size_t)r * P + c].real(), S[(size_t)r * P + c].imag());
+        int j = 0;
+        bool breakdown = false;
+        for (; j < m && total < max_iter; j++) {
+            double2* Vj = k.V + (size_t)j * ldk;
+            if (prec) {
+                double2* Zj = k.Z + (size_t)j * ldk;
+                if ((rc = (*prec)(Vj, Zj))) return rc;
+                if ((rc = op(Zj, k.w))) return rc;
+            } else if ((rc = op(Vj, k.w))) {
+                return rc;
+            }
+            if constexpr (F32) kv_to32<<<nbl, KV_THREADS, 0, ctx->stream>>>(ldk, k.w, Wt);
+            const int K = (j + 1) * P;
+            // CGS2 against every basis vector so far; both coefficient sets read back at once
+            for (int pass = 0; pass < 2; pass++) {
+                double2* Cp = k.bC + (size_t)pass * K * P;
+                if ((rc = block_dots(ctx, k, (const T*)Vt, K, (const T*)Wt, P, Cp))) return rc;
+                if ((rc = block_combine(ctx, n, (const T*)Vt, K, P, Cp, -1.0, (const T*)Wt, 1.0, Wt))) return rc;
+            }
+            hcs.resize((size_t)2 * K * P);
+            CK(cudaMemcpyAsync(hcs.data(), k.bC, hcs.size() * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            std::vector<zd> Rn((size_t)P * P);
+            rc = orth(Wt, Rn);
+            if (rc == BEM_ERR_NOT_CONVERGED) {  // the block space is exhausted: solve with what there is
+                breakdown = true;
+                rc = BEM_OK;
+                std::fill(Rn.begin(), Rn.end(), zd(0));
+            } else if (rc) {
+                return rc;
+            } else {
+                T* Vn = Vt + (size_t)(j + 1) * ldk;
+                CK(cudaMemcpyAsync(Vn, Wt, (size_t)ldk * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
+                if constexpr (F32) kv_to64<<<nbl, KV_THREADS, 0, ctx->stream>>>(ldk, Wt, k.V + (size_t)(j + 1) * ldk);
+            }
+            // the new block column of the Hessenberg matrix, row-major over its P
+            // columns (Hb[row * P + c]), plain double arithmetic
+            std::vector<double2> Hb((size_t)(K + P) * P);
+            for (int kk = 0; kk < K; kk++)
+                for (int c = 0; c < P; c++) {
+                    const double2 a = hcs[(size_t)kk * P + c], b = hcs[(size_t)K * P + (size_t)kk * P + c];
+                    Hb[(size_t)kk * P + c] = make_double2(a.x + b.x, a.y + b.y);
+                }
+            for (int r = 0; r < P; r++)
+                for (int c = 0; c < P; c++)
+                    Hb[(size_t)(K + r) * P + c] = make_double2(Rn[(size_t)r * P + c].real(), Rn[(size_t)r * P + c].imag());
+            // (a, b) <- (conj(cs) a + conj(sn) b, -sn a + cs b) on rows (row, row + 1) of columns c0..P-1
+            auto rot = [&](double2* M, int ld, int row, int c0, int c1, double2 cs, double2 sn) {
+                double2* A = M + (size_t)row * ld;
+                double2* Bq = M + (size_t)(row + 1) * ld;
+                for (int c = c0; c < c1; c++) {
+                    const double2 a = A[c], b = Bq[c];
+                    A[c] = make_double2(cs.x * a.x + cs.y * a.y + sn.x * b.x + sn.y * b.y,
+                                        cs.x * a.y - cs.y * a.x + sn.x * b.y - sn.y * b.x);
+                    Bq[c] = make_double2(-(sn.x * a.x - sn.y * a.y) + cs.x * b.x - cs.y * b.y,
+                                         -(sn.x * a.y + sn.y * a.x) + cs.x * b.y + cs.y * b.x);
+                }
+            };
+            // earlier rotations (in the order they were made) on all P new columns
+            for (int qq = 0; qq < j * P; qq++)
+                for (int l = 0; l < P; l++)
+                    rot(Hb.data(), P, qq + P - 1 - l, 0, P, rcs[(size_t)qq * P + l], rsn[(size_t)qq * P + l]);
+            // P new rotations per column, applied to the later columns of the block and to G
+            for (int c = 0; c < P; c++) {
+                const int q = j * P + c;
+                for (int l = 0; l < P; l++) {
+                    const int row = q + P - 1 - l;
+                    const double2 a = Hb[(size_t)row * P + c], b = Hb[(size_t)(row + 1) * P + c];
+                    const double den = std::sqrt(a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y);
+                    const double2 cs = den > 0 ? make_double2(a.x / den, a.y / den) : make_double2(1, 0);
+                    const double2 sn = den > 0 ? make_double2(b.x / den, b.y / den) : make_double2(0, 0);
+                    rcs[(size_t)q * P + l] = cs;
+                    rsn[(size_t)q * P + l] = sn;
+                    Hb[(size_t)row * P + c] = make_double2(den, 0);
+                    Hb[(size_t)(row + 1) * P + c] = make_double2(0, 0);
+                    rot(Hb.data(), P, row, c + 1, P, cs, sn);
+                    rot(Gr.data(), P, row, 0, P, cs, sn);
+                }
+            }
+            // keep the rotated columns (upper triangle) for the back substitution
+            for (int c = 0; c < P; c++) {
+                const int q = j * P + c;
+                double2* col = &Hs[(size_t)q * KM];
+                for (int r = 0; r <= q; r++) col[r] = Hb[(size_t)r * P + c];
+            }
+            total++;
+            // residual of each column: the last P rows of its rotated right-hand side
+            bool all = true;
+            for (int c = 0; c < P; c++) {
+                double s2 = 0;
+                for (int r = K; r < K + P; r++) s2 += Gr[(size_t)r * P + c].x * Gr[(size_t)r * P + c].x +
+                                                      Gr[(size_t)r * P + c].y * Gr[(size_t)r * P + c].y;
+                rres[c] = bnorm[c] > 0 ? std::sqrt(s2) / bnorm[c] : 0.0;
+                if (rres[c] > tol) {
+                    all = false;
+                    iters[c]++;
+                }
+            }
+            if (all || breakdown) {
+                j++;
+                break;
+            }
+        }
+        // Y = H^-1 G (upper triangular, J unknowns per column), X += Z Y (FP64)
+        const int J = j * P;
+        if (J > 0) {
+            std::vector<double2> Yd((size_t)J * P);  // row-major [unknown][column]
+            for (int i = J - 1; i >= 0; i--) {
+                const double2 d = Hs[(size_t)i * KM + i];
+                const double dd = d.x * d.x + d.y * d.y;
+                for (int c = 0; c < P; c++) {
+                    double sr = Gr[(size_t)i * P + c].x, si = Gr[(size_t)i * P + c].y;
+                    for (int kk = i + 1; kk < J; kk++) {
+                        const double2 h = Hs[(size_t)kk * KM + i], y = Yd[(size_t)kk * P + c];
+                        sr -= h.x * y.x - h.y * y.y;
+                        si -= h.x * y.y + h.y * y.x;
+                    }
+                    Yd[(size_t)i * P + c] = dd > 0 ? make_double2((sr * d.x + si * d.y) / dd, (si * d.x - sr * d.y) / dd)
+                                                   : make_double2(0, 0);
+                }
+            }
+            CK(cudaMemcpyAsync(k.bC, Yd.data(), Yd.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+            if ((rc = block_combine(ctx, n, (const double2*)(prec ? k.Z : k.V), J, P, k.bC, 1.0, (const double2*)X, 1.0, X)))
+                return rc;
+        }
+        bool open2 = false;
+        for (int c = 0; c < P; c++) open2 |= rres[c] > tol;
+        if (!open2 || breakdown) break;
+    }
+    // true residuals of the given systems
+    if ((rc = op(X, k.t))) return rc;
+    kv_axpby<<<nbl, KV_THREADS, 0, ctx->stream>>>(ldk, make_double2(1, 0), B, make_double2(-1, 0), k.t, k.t);
+    ctx->launches += 1;
+    std::vector<double> rn(P);
+    if ((rc = k.norms(ctx, k.t, P, rn.data()))) return rc;
+    for (int c = 0; c < P; c++) relres[c] = bnorm[c] > 0 ? rn[c] / bnorm[c] : 0.0;
+    return BEM_OK;
+}
+
+}  // namespace
+
+int Krylov::gmres_block(bem_ctx* ctx, const Op& op, const double2* B, double2* X, int64_t Rn, int restart,
+                        double tol, int max_iter, int* iters, double* relres, bool zero_guess, const Op* prec,
+                        bool fp32_basis, bool* deficient) {
+    const int P = (int)Rn;
+    if (deficient) *deficient = false;
+    int rc = ensure(ctx, n, restart, Rn);
+    if (rc) return rc;
+    if (prec && (rc = ensure_flexible(ctx))) return rc;
+    const int m = restart;
+    // scratch: partials of K x P dots (K <= (m+1) P) and two sets of K x P coefficients
+    // (FP64: K x P x nsplit <= 8 K P; tiled FP32: K x nsplit <= 64 max(row tiles, 608))
+    const size_t gx_max = ((size_t)(m + 1) * P + KD_ROWS - 1) / KD_ROWS;
+    const size_t need_part = std::max((size_t)(m + 1) * P * P * 8, (size_t)P * KD_ROWS * std::max<size_t>(gx_max, 608)),
+                 need_c = (size_t)2 * (m + 1) * P * P + (size_t)P * P;
+    if (bpart_n < need_part) {
+        dfree_buf(ctx, (void**)&bpart);
+        bpart = (double2*)ctx->dalloc(need_part * sizeof(double2), &rc);
+        if (rc) { bpart = nullptr; bpart_n = 0; return rc; }
+        bpart_n = need_part;
+    }
+    if (bC_n < need_c) {
+        dfree_buf(ctx, (void**)&bC);
+        bC = (double2*)ctx->dalloc(need_c * sizeof(double2), &rc);
+        if (rc) { bC = nullptr; bC_n = 0; return rc; }
+        bC_n = need_c;
+    }
+    if (!fp32_basis)
+        return gmres_block_impl<double2>(*this, ctx, op, B, X, P, m, tol, max_iter, iters, relres, zero_guess, prec,
+                                         deficient, V, w, t);
+    const size_t need32 = (size_t)(m + 3) * P * n;  // basis, then two work blocks
+    if (b32_n < need32) {
+        dfree_buf(ctx, (void**)&b32);
+        b32 = (float2*)ctx->dalloc(need32 * sizeof(float2), &rc);
+        if (rc) { b32 = nullptr; b32_n = 0; return rc; }
+        b32_n = need32;
+    }
+    float2* V32 = b32;
+    float2* W32 = b32 + (size_t)(m + 1) * P * n;
+    float2* T32 = W32 + (size_t)P * n;
+    return gmres_block_impl<float2>(*this, ctx, op, B, X, P, m, tol, max_iter, iters, relres, zero_guess, prec,
+                                    deficient, V32, W32, T32);
 }

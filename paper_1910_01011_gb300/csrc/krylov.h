@@ -53,6 +53,25 @@ struct Krylov {
     // by column; column r stops once its own residual meets tol.
     int gmres_batch(bem_ctx* ctx, const Op& op, const double2* B, double2* X, int64_t R, int restart, double tol,
                     int max_iter, int* iters, double* relres, bool zero_guess, const Op* prec = nullptr);
+    // Block GMRES over the R columns: one Krylov space shared by all columns,
+    // grown by R vectors per step (op and prec applied to the R newest basis
+    // vectors at once), restarted after `restart` steps; flexible (right
+    // preconditioned) when prec is given.  iters[r] counts the steps.
+    // fp32_basis: the basis is kept and orthogonalised in FP32 (an inner solve
+    // of the mixed path, whose tolerance needs no FP64 orthogonalisation); the
+    // vectors handed to op and prec and the solution update stay FP64.
+    // deficient (optional): set when the block of starting residuals has
+    // dependent columns (e.g. more excitations than pistons, or a zero one),
+    // so that not one step could be taken; X is then as on entry (zero with
+    // zero_guess) and the caller solves the columns another way.
+    int gmres_block(bem_ctx* ctx, const Op& op, const double2* B, double2* X, int64_t R, int restart, double tol,
+                    int max_iter, int* iters, double* relres, bool zero_guess, const Op* prec = nullptr,
+                    bool fp32_basis = false, bool* deficient = nullptr);
+    double2 *bpart = nullptr, *bC = nullptr;  // block GMRES scratch (allocated on first use)
+    size_t bpart_n = 0, bC_n = 0;
+    float2* b32 = nullptr;                    // FP32 basis and work blocks of the block GMRES
+    size_t b32_n = 0;
+    static void dfree_buf(bem_ctx* ctx, void** p);
 };
 
 }  // namespace gbem

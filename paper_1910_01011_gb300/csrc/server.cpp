@@ -6,8 +6,8 @@
 // and are admitted to one of `slots` worker threads as soon as a worker and
 // enough of the device-memory budget are free.  Requests for the same scene
 // that are queued when a worker picks that scene are merged into one solve
-// of up to max_batch_rhs excitations (GMRES in lockstep, one GEMM per
-// operator application); requests for different scenes run on different
+// of up to max_batch_rhs excitations (by default block GMRES over blocks of
+// at most 16 excitations, one GEMM per operator application); requests for different scenes run on different
 // workers, each scene on its own CUDA stream, so their kernels overlap on the
 // GPU.  The budget is a hard limit: every device allocation of every scene
 // draws on one shared counter and fails (BEM_ERR_OUT_OF_BUDGET) past it;
@@ -273,6 +273,7 @@ int bem_server_default_opts(bem_server_opts* o) {
     bem_default_solve_opts(&o->solve);
     o->solve.precision = BEM_PREC_FP32;
     o->solve.batch_rhs = 64;
+    o->solve.block_gmres = 1;
     return BEM_OK;
 }
 

@@ -145,3 +145,39 @@ def test_request_that_can_never_fit_is_refused(api):
         srv.result(h, 1, ids["sphere"])
     assert srv.stats()["failed"] == 1
     srv.close()
+
+
+def test_two_scenes_overlap_on_the_device(api):
+    """Requests for two scenes submitted together run at the same time, each
+    on its scene's own stream: the server reports two solves on the GPU at
+    once, and the pair finishes clearly sooner than the same two requests run
+    one after the other (the kernels of the two solves overlap)."""
+    import time
+    srv = api.Server(precision=1, tol=TOL, slots=2, max_batch_rhs=8, hbm_budget_bytes=8 << 30)
+    ids = [srv.add_scene(scenes.sphere_scene(3), transducer=transducer(i), omega_rho0=OMEGA_RHO0, r_eps=0.2)
+           for i in range(2)]
+    W = [np.exp(2j * np.pi * np.random.default_rng(30 + i).random((8, 6))) for i in range(2)]
+    for i in ids:  # set-up (near field, preconditioner) outside the timings
+        h = srv.submit(i, W[0][:1])
+        srv.wait(h)
+        srv.result(h, 1, i)
+    solo = []
+    for k, i in enumerate(ids):
+        t0 = time.perf_counter()
+        h = srv.submit(i, W[k])
+        srv.wait(h)
+        solo.append(time.perf_counter() - t0)
+        srv.result(h, 8, i)
+    t0 = time.perf_counter()
+    hs = [srv.submit(i, W[k]) for k, i in enumerate(ids)]
+    most = 0
+    while any(srv.poll(h) in (0, 1) for h in hs):  # queued or running
+        most = max(most, srv.stats()["running"])
+        time.sleep(0.001)
+    both = time.perf_counter() - t0
+    for k, (h, i) in enumerate(zip(hs, ids)):
+        srv.result(h, 8, i)
+    srv.close()
+    print("solo", solo, "together", both, "most running", most)
+    assert most == 2
+    assert both < 0.85 * sum(solo)

@@ -140,6 +140,34 @@ def test_transducer_rhs_and_multi_rhs_solve(api):
         assert rel(got, u) < 1e-6
 
 
+def test_transducer_rhs_excitation_groups(api):
+    """Right-hand sides of 37 excitations (the piston kernel's groups of 16
+    excitations: two full, one ragged) mixing unit, sparse, dense random-phase
+    and all-zero weight rows, so that pistons skipped for a whole group and
+    pistons shared by several excitations both occur: every row against the
+    oracle's Rayleigh field (a zero row gives an exactly zero right-hand side)."""
+    s = scenes.two_sphere_scene(1)
+    tr = small_transducer()
+    ne = tr["radii"].size
+    rng = np.random.default_rng(17)
+    W = np.exp(2j * np.pi * rng.random((37, ne)))
+    W[:ne] = np.eye(ne)                       # group 0: unit excitations, then dense rows
+    W[16:32] *= rng.random((16, ne)) < 0.4    # group 1: sparse rows (some pistons unused by all)
+    W[16:32, 2] = 0.0
+    W[20] = 0.0                               # an all-zero row
+    omega, rho0 = 2.0, 1.3
+    c = ctx_for(api, s)
+    c.set_transducer(tr["centres"], tr["normals"], tr["radii"], omega * rho0)
+    c.set_excitations(W)
+    B = c.rhs(W.shape[0])
+    for r in range(W.shape[0]):
+        if not W[r].any():
+            assert not B[r].any(), r
+            continue
+        ref = pmchwt.rhs(s, rayleigh.field(tr, W[r], s.k0, omega, rho0))
+        assert rel(B[r], ref) < 1e-12, r
+
+
 def test_solve_reports_not_converged(api):
     s = scenes.sphere_scene(2)
     c = ctx_for(api, s)
@@ -161,11 +189,14 @@ def test_batched_preconditioner_matches_single(api, solver):
         assert rel(Y[r], osrc.apply(s, pre, X[r])) < 1e-9
 
 
-@pytest.mark.parametrize("precision,operator_mode,flexible", [(0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1), (1, 0, 0)])
-def test_batched_solve_matches_oracle(api, precision, operator_mode, flexible):
-    """Excitations solved in lockstep blocks (batch_rhs = 3 over 7 excitations,
-    so one ragged block): every column within 1e-6 of the oracle's dense
-    solve, as the one-at-a-time path."""
+@pytest.mark.parametrize("precision,operator_mode,flexible,block", [(0, 0, 1, 0), (1, 0, 1, 0), (1, 1, 1, 0), (0, 1, 1, 0),
+                                                                    (1, 0, 0, 0), (1, 1, 1, 1), (0, 1, 1, 1),
+                                                                    (1, 0, 1, 1), (1, 0, 0, 1)])
+def test_batched_solve_matches_oracle(api, precision, operator_mode, flexible, block):
+    """Excitations solved in blocks of batch_rhs = 3 over 7 excitations (so
+    one ragged block), either as independent GMRES runs in lockstep or by block
+    GMRES (one Krylov space per block): every column within 1e-6 of the
+    oracle's dense solve, as the one-at-a-time path."""
     s = scenes.two_sphere_scene(1)
     tr = small_transducer()
     W = np.vstack([np.eye(tr["radii"].size), scenes.focusing_weights(tr, s.k0)[None, :]]).astype(complex)
@@ -174,12 +205,41 @@ def test_batched_solve_matches_oracle(api, precision, operator_mode, flexible):
     c.set_excitations(W)
     B = c.rhs(W.shape[0])
     A = pmchwt.assemble(s)
-    rep = c.solve(precision=precision, tol=1e-10, batch_rhs=3, operator_mode=operator_mode, flexible=flexible)
+    rep = c.solve(precision=precision, tol=1e-10, batch_rhs=3, operator_mode=operator_mode, flexible=flexible,
+                  block_gmres=block)
     assert rep["converged"], rep
     for r in range(W.shape[0]):
         u = np.linalg.solve(A, B[r])
         got = np.concatenate([np.concatenate([c.traces(j, r)[1], c.traces(j, r)[0]]) for j in range(2)])
         assert rel(got, u) < 1e-6, r
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_block_gmres_dependent_excitations(api, precision):
+    """Block GMRES on a block whose right-hand sides are dependent: nine
+    excitations of a six-piston array (one repeated, one all zero) in one
+    block.  The block of starting residuals has rank six, so the solve takes
+    the lockstep path for it; every column still meets the oracle's dense
+    solve (the zero excitation gives a zero solution)."""
+    s = scenes.two_sphere_scene(1)
+    tr = small_transducer()
+    rng = np.random.default_rng(23)
+    W = np.exp(2j * np.pi * rng.random((9, tr["radii"].size)))
+    W[4] = W[1]
+    W[6] = 0.0
+    c = ctx_for(api, s)
+    c.set_transducer(tr["centres"], tr["normals"], tr["radii"], 2.6)
+    c.set_excitations(W)
+    B = c.rhs(W.shape[0])
+    A = pmchwt.assemble(s)
+    rep = c.solve(precision=precision, tol=1e-10, batch_rhs=9, operator_mode=1, block_gmres=1)
+    assert rep["converged"], rep
+    for r in range(W.shape[0]):
+        got = np.concatenate([np.concatenate([c.traces(j, r)[1], c.traces(j, r)[0]]) for j in range(2)])
+        if r == 6:
+            assert np.linalg.norm(got) < 1e-12
+            continue
+        assert rel(got, np.linalg.solve(A, B[r])) < 1e-6, r
 
 
 def test_superposition_matches_direct_solves(api):
@@ -209,3 +269,23 @@ def test_superposition_matches_direct_solves(api):
     c.set_transducer(tr["centres"], tr["normals"], tr["radii"], 2.6)  # a new transducer drops the basis
     with pytest.raises(Exception):
         c.superpose(W)
+
+
+def test_superposition_512_element_array(api):
+    """A 512-element array (the size of the full-matrix-capture arrays the
+    paper's introduction cites): every piston solved alone in lockstep
+    batches of 64 (bem_solve_basis), then two random-phase patterns formed
+    from the basis by one product, against the oracle's dense solves."""
+    s = scenes.sphere_scene(2)
+    tr = scenes.bowl_transducer(seed=5, n_elem=512, R=4.0, aperture=6.0, piston_radius=0.06, gap=0.02)
+    A = pmchwt.assemble(s)
+    c = ctx_for(api, s)
+    c.set_transducer(tr["centres"], tr["normals"], tr["radii"], 2.6)
+    rep = c.solve_basis(precision=1, tol=1e-10, batch_rhs=64)
+    assert rep["converged"], rep
+    W = np.exp(2j * np.pi * np.random.default_rng(12).random((2, 512)))
+    U = c.superpose(W)
+    for r in range(2):
+        b = pmchwt.rhs(s, rayleigh.field(tr, W[r], s.k0, 2.6, 1.0))
+        assert rel(U[r], np.linalg.solve(A, b)) < 1e-6
+    c.close()
