@@ -195,7 +195,9 @@ typedef struct {
     int32_t max_refine;    /* outer refinement cap (default 10) */
     int32_t operator_mode; /* 0: matrix-free operators; 1: assembled operators (BF16-split tensor-core
                               GEMM inside GMRES, complex128 GEMV for FP64 residuals), set up once and
-                              kept on the device for later solves */
+                              kept on the device for later solves; 2: automatic, assembled where those
+                              operators take at most 4 GiB (36 N^2 bytes, N <= 10,922), else
+                              matrix-free */
     int32_t batch_rhs;     /* >1: excitations are solved in blocks of up to batch_rhs right-hand sides,
                               R independent GMRES runs in lockstep whose operator and preconditioner
                               applications act on all R columns at once (one GEMM per application with
@@ -361,7 +363,7 @@ typedef struct {
     int32_t max_batch_rhs;    /* excitations merged into one solve (default 64) */
     int64_t hbm_budget_bytes; /* device bytes all scenes may hold together (default 150 GiB; 0 = no limit) */
     bem_solve_opts solve;     /* options of every solve (default: mixed precision, batch_rhs = max_batch_rhs,
-                                 block_gmres = 1) */
+                                 block_gmres = 1, operator_mode = 2) */
 } bem_server_opts;
 
 typedef struct {

@@ -137,6 +137,8 @@ static void release_device(bem_ctx* ctx) {
     for (int& k : ctx->far_work_key) k = -1;
     ctx->multi_buf = nullptr;
     ctx->multi_buf_bytes = 0;
+    ctx->multi64_buf = nullptr;
+    ctx->multi64_buf_bytes = 0;
     ctx->multi_work = nullptr;
     ctx->multi_n_work = 0;
     for (int& k : ctx->multi_key) k = -1;
@@ -166,16 +168,30 @@ void multi_chunking(int n_tiles, int64_t n_pts, int64_t R, int* n_chunks, int* c
     *n_chunks = (n_tiles + ct - 1) / ct;
 }
 
+// Chunks of the FP64 multi-vector far field: about 8 CTAs per SM over
+// (target tile, chunk, slot, group), no more (each chunk adds R x 2 x NCOMP
+// x n_pts doubles of partial potentials).
+void multi64_chunking(int n_tiles, int64_t R, int* n_chunks, int* chunk_tiles) {
+    const int64_t groups = (R + RG64 - 1) / RG64;
+    int64_t nc = (152 * 8 + 2 * groups * n_tiles - 1) / std::max<int64_t>(1, 2 * groups * n_tiles);
+    nc = std::max<int64_t>(1, std::min<int64_t>(nc, n_tiles));
+    const int ct = (int)((n_tiles + nc - 1) / nc);
+    *chunk_tiles = ct;
+    *n_chunks = (n_tiles + ct - 1) / ct;
+}
+
 // Device bytes a solve of n_exc excitations with options o may need at its
 // peak, from the mesh sizes alone (no device state is needed); every term
 // follows one allocation of the solver, rounded up, with a 10 % margin.
-int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_opts& o) {
+int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_opts& o_in) {
     int64_t T = 0, nv = 0, tiles = 0;
     for (auto& d : ctx->doms) {
         T += d.nt;
         nv += d.nv;
         tiles += (d.nt + TT - 1) / TT;
     }
+    bem_solve_opts o = o_in;
+    o.operator_mode = resolved_operator_mode(o.operator_mode, 2 * nv);
     // correction pairs: touching (about 13 per triangle) and near (20-80 per
     // triangle on the meshes measured): the exact count once the geometry exists
     const int64_t pairs = ctx->ready ? (int64_t)ctx->geo.np_src.size() : 96 * T;
@@ -216,6 +232,12 @@ int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_
         multi_chunking((int)tiles, pts, R, &ncm, &ctm);
         b += R * (pts * 16 + 2 * slots * 16 + (int64_t)ncm * 2 * NCOMP * pts * 4) +
              tiles * ncm * 2 * ((R + MRG - 1) / MRG) * 16;
+    }
+    // FP64 residuals of several vectors in one matrix-free launch
+    if (o.operator_mode == 0 && R > 1) {
+        int nc64 = 1, ct64 = 1;
+        multi64_chunking((int)tiles, R, &nc64, &ct64);
+        b += R * (pts * 32 + 2 * slots * 32 + (int64_t)nc64 * 2 * NCOMP * pts * 8);
     }
     // split vectors of the FP64-accurate residual product
     b += R * N * 16 + 4096;
@@ -656,6 +678,79 @@ int bem_ctx::apply_ahat_multi(const double2* x, double2* y, int64_t n_rhs) {
     return BEM_OK;
 }
 
+// A_hat applied to n_rhs vectors at FP64 with one far-field launch for all of
+// them (far64m_kernel: the kernel values of a pair evaluated once per group of
+// RG64 vectors), then the projection (with the FP64 near-field correction) and
+// the reduction of each vector.
+int bem_ctx::apply_ahat64_multi(const double2* x, double2* y, int64_t n_rhs) {
+    bem_ctx* const ctx = this;
+    int rc = ensure_near();
+    if (rc) return rc;
+    const Geometry& g = geo;
+    const int n_tiles = g.n_tiles;
+    int n_chunks, chunk_tiles;
+    multi64_chunking(n_tiles, n_rhs, &n_chunks, &chunk_tiles);
+    const int64_t rstride = (int64_t)n_chunks * 2 * NCOMP * g.n_pts;
+    const size_t b_pd = (size_t)n_rhs * g.n_pts * sizeof(double4);
+    const size_t b_tc = (size_t)n_rhs * 2 * g.n_slots * sizeof(double4);
+    const size_t need = b_pd + b_tc + (size_t)n_rhs * rstride * sizeof(double);
+    if (need > multi64_buf_bytes) {
+        dfree(multi64_buf);
+        multi64_buf = dalloc(need, &rc);
+        if (rc) { multi64_buf = nullptr; multi64_buf_bytes = 0; return rc; }
+        multi64_buf_bytes = need;
+    }
+    double4* pdm = (double4*)multi64_buf;
+    double4* tcm = (double4*)((char*)multi64_buf + b_pd);
+    double* part = (double*)((char*)multi64_buf + b_pd + b_tc);
+    const int64_t N = g.n_dof;
+    for (int64_t r = 0; r < n_rhs; r++) {
+        GatherArgs ga{};
+        ga.slot_v = dev.slot_v; ga.v_dof1 = dev.v_dof1; ga.v_dof2 = dev.v_dof2; ga.pt_w = dev.pt_w;
+        ga.slot_curl = dev.slot_curl; ga.x = x + r * N; ga.s_begin = 0; ga.s_end = g.n_slots;
+        for (int q = 0; q < QP; q++)
+            for (int k = 0; k < 3; k++) ga.lam[q][k] = quad.lam[q][k];
+        ga.pd64 = pdm + r * g.n_pts;
+        ga.tcurl64 = tcm + r * 2 * g.n_slots;
+        CK(launch_gather(ga, stream));
+    }
+    FarArgs64M fa{};
+    fa.pg = dev.pg64; fa.tg = dev.tg64; fa.tc = dev.tc; fa.tdom = dev.tdom; fa.tntri = dev.tntri;
+    fa.pd = pdm; fa.tcurl = tcm; fa.dom_tiles = dev.dom_tiles; fa.kdom = dev.kdom;
+    fa.k0 = make_double2(k0re, k0im);
+    fa.src_begin = 0; fa.src_end = n_tiles; fa.tgt_begin = 0; fa.chunk_tiles = chunk_tiles; fa.slot1 = 1;
+    fa.groups = (int)((n_rhs + RG64 - 1) / RG64); fa.R = (int)n_rhs;
+    fa.n_pts = g.n_pts; fa.n_slots = g.n_slots; fa.rstride = rstride; fa.partial = part;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (profiling) {
+        CK(cudaEventCreate(&ev0));
+        CK(cudaEventCreate(&ev1));
+        CK(cudaEventRecord(ev0, stream));
+    }
+    CK(launch_far64_multi(fa, n_tiles, n_chunks, stream));
+    if (profiling) {
+        CK(cudaEventRecord(ev1, stream));
+        far_events.push_back({ev0, ev1});
+    }
+    for (int64_t r = 0; r < n_rhs; r++) {
+        ProjectArgs pa{};
+        pa.slot_v = dev.slot_v; pa.pt_w = dev.pt_w; pa.slot_curl = dev.slot_curl; pa.tntri = dev.tntri; pa.tdom = dev.tdom;
+        pa.coef = dev.coef; pa.tgt_begin = 0; pa.tgt_end = n_tiles; pa.n_chunks = n_chunks; pa.n_pts = g.n_pts;
+        pa.partial64 = part + r * rstride;
+        if (pmchwt_near.n_pairs > 0) { pa.np_ptr = dev.np_ptr; pa.np_src = dev.np_src; pa.nb64 = pmchwt_near.nb64; }
+        pa.v_dof1 = dev.v_dof1; pa.v_dof2 = dev.v_dof2; pa.x = x + r * N; pa.tri_out = dev.tri_out;
+        for (int q = 0; q < QP; q++)
+            for (int k = 0; k < 3; k++) pa.lam[q][k] = quad.lam[q][k];
+        CK(launch_project(pa, stream));
+        ReduceArgs ra{};
+        ra.vc_ptr = dev.vc_ptr; ra.vc_idx = dev.vc_idx; ra.v_dof1 = dev.v_dof1; ra.v_dof2 = dev.v_dof2;
+        ra.tri_out = dev.tri_out; ra.y = y + r * N; ra.v_begin = 0; ra.v_end = g.n_vert;
+        CK(launch_reduce(ra, stream));
+    }
+    launches += 3 * n_rhs + 1;
+    return BEM_OK;
+}
+
 int bem_ctx::apply_ahat(const double2* x, double2* y, int precision) {
     int rc = ensure_near();
     if (rc) return rc;
@@ -834,10 +929,10 @@ int bem_apply(bem_ctx* ctx, int op, const bem_z* x, bem_z* y, int64_t n_rhs, int
     int rc = ctx->finalize();
     if (rc) return rc;
     const int64_t N = ctx->geo.n_dof;
-    const bool multi32 = precision == BEM_PREC_FP32 && n_rhs > 1;
-    if ((precision == BEM_PREC_BF16X3 || precision == BEM_PREC_FP64_ASSEMBLED || multi32) && op != BEM_OP_PREC) {
+    const bool multi = (precision == BEM_PREC_FP32 || precision == BEM_PREC_FP64) && n_rhs > 1;
+    if ((precision == BEM_PREC_BF16X3 || precision == BEM_PREC_FP64_ASSEMBLED || multi) && op != BEM_OP_PREC) {
         // all right-hand sides at once: one product on the assembled operator, or
-        // one matrix-free far-field launch for all of them at FP32
+        // one matrix-free far-field launch for all of them
         const double2* xd = (const double2*)x;
         double2* yd = (double2*)y;
         double2* stage = nullptr;
@@ -856,6 +951,7 @@ int bem_apply(bem_ctx* ctx, int op, const bem_z* x, bem_z* y, int64_t n_rhs, int
         double2* dst = tmp ? tmp : yd;
         rc = precision == BEM_PREC_BF16X3         ? ctx->apply_assembled(xd, dst, n_rhs)
              : precision == BEM_PREC_FP64_ASSEMBLED ? ctx->apply_assembled64(xd, dst, n_rhs)
+             : precision == BEM_PREC_FP64           ? ctx->apply_ahat64_multi(xd, dst, n_rhs)
                                                     : ctx->apply_ahat_multi(xd, dst, n_rhs);
         if (!rc && tmp) rc = ctx->apply_prec_batch(tmp, yd, n_rhs);
         if (tmp) {

@@ -486,7 +486,7 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
     auto plain = [ctx, &o, N](const double2* X, double2* Y, int prec, int64_t nr) -> int {
         if (o.operator_mode == 1)
             return prec == BEM_PREC_FP64 ? ctx->apply_assembled64(X, Y, nr) : ctx->apply_assembled(X, Y, nr);
-        if (prec == BEM_PREC_FP32 && nr > 1) return ctx->apply_ahat_multi(X, Y, nr);
+        if (nr > 1) return prec == BEM_PREC_FP32 ? ctx->apply_ahat_multi(X, Y, nr) : ctx->apply_ahat64_multi(X, Y, nr);
         for (int64_t r = 0; r < nr; r++) {
             int e = ctx->apply_ahat(X + r * N, Y + r * N, prec);
             if (e) return e;
@@ -585,7 +585,7 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     bem_default_solve_opts(&o);
     if (opts) o = *opts;
     if (o.restart < 1 || o.max_iter < 1 || !(o.tol > 0) || (o.precision != BEM_PREC_FP64 && o.precision != BEM_PREC_FP32) ||
-        (o.operator_mode != 0 && o.operator_mode != 1) || o.batch_rhs < 0 || o.flexible < 0 || o.flexible > 1 ||
+        o.operator_mode < 0 || o.operator_mode > 2 || o.batch_rhs < 0 || o.flexible < 0 || o.flexible > 1 ||
         !(o.prec_tol >= 0) || o.prec_tol >= 1 || o.block_gmres < 0 || o.block_gmres > 1)
         return ctx->fail(BEM_ERR_INVALID_ARG, "bad solve options");
     CK(cudaSetDevice(ctx->device));
@@ -597,6 +597,7 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     if ((rc = build_rhs(ctx))) return rc;
     SolveState* S = ctx->solve;
     const int64_t N = ctx->geo.n_dof, nr = ctx->field_kind == 2 ? ctx->n_rhs : 1;
+    o.operator_mode = resolved_operator_mode(o.operator_mode, N);
     if ((rc = S->kry.ensure(ctx, N, o.restart))) return rc;
     // the preconditioner only has to be a fixed linear map to the accuracy the
     // GMRES it sits in needs: two orders below that GMRES's tolerance

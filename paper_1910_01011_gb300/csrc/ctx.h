@@ -110,6 +110,8 @@ struct bem_ctx {
     // several right-hand sides in one far-field launch: densities, partials and the work list
     void* multi_buf = nullptr;
     size_t multi_buf_bytes = 0;
+    void* multi64_buf = nullptr;  // FP64 multi-vector far field: densities, curls, partial potentials
+    size_t multi64_buf_bytes = 0;
     int4* multi_work = nullptr;
     int64_t multi_n_work = 0;
     int multi_key[3] = {-1, -1, -1};  // (n_chunks, chunk_tiles, groups) the list was built for
@@ -167,6 +169,7 @@ struct bem_ctx {
     int run_apply(const double2* x, double2* y, int precision, const gbem::ApplyMode& m);
     int apply_ahat(const double2* x, double2* y, int precision);
     int apply_ahat_multi(const double2* x, double2* y, int64_t n_rhs);
+    int apply_ahat64_multi(const double2* x, double2* y, int64_t n_rhs);
     int apply_prec(const double2* x, double2* y);
     int apply_prec_batch(const double2* x, double2* y, int64_t n_rhs);
     int apply_prec_ahat(const double2* x, double2* y, int precision);
@@ -182,9 +185,15 @@ namespace gbem {
 // work items to fill the GPU, at most CHUNK_MAX tiles, and the partial
 // potentials of all R vectors within 2 GiB where possible.
 void multi_chunking(int n_tiles, int64_t n_pts, int64_t R, int* n_chunks, int* chunk_tiles);
+void multi64_chunking(int n_tiles, int64_t R, int* n_chunks, int* chunk_tiles);
 // excitations per batched solve: batch_rhs (at most n_exc), or for block GMRES
 // the batch split evenly into blocks of at most 16 columns
 int64_t solve_batch_width(const bem_solve_opts& o, int64_t n_exc);
+// operator_mode 2 (automatic) resolved for n_dof unknowns: 1 (assembled) where
+// the assembled operators take at most 4 GiB, else 0 (matrix-free)
+inline int resolved_operator_mode(int mode, int64_t n_dof) {
+    return mode != 2 ? mode : (36.0 * (double)n_dof * (double)n_dof <= 4.0 * 1073741824.0 ? 1 : 0);
+}
 // FP64-accurate complex products in FP32 arithmetic (k_df64.cu).
 int df_prepare_inplace(bem_ctx* ctx, double2* v, int64_t n, int* e);
 int df_gemv(bem_ctx* ctx, const float4* A, const int* eA, int64_t m, int64_t k, int64_t lda, const double2* X,

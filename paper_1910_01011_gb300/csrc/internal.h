@@ -170,6 +170,28 @@ struct FarArgs64 {
     double* partial;
 };
 
+// Several vectors in one FP64 far-field launch (far64m_kernel): CTA (x, y, z)
+// = (target tile, source chunk, slot x group); slot 0 sums every source tile
+// of the chunk at k0, slot 1 the target domain's own tiles at k_j (PMCHWT),
+// a group is RG64 consecutive vectors.
+constexpr int RG64 = 4;
+struct FarArgs64M {
+    const double4* pg;      // (dx, dy, dz, w)
+    const double4* tg;      // (nx, ny, nz, h)
+    const double4* tc;
+    const int* tdom;
+    const int* tntri;
+    const double4* pd;      // [R][n_pts] (sigN re, im, sigD re, im) * w
+    const double4* tcurl;   // [R][2 n_slots]
+    const int2* dom_tiles;
+    const double2* kdom;
+    double2 k0;
+    int src_begin, src_end, tgt_begin, chunk_tiles, slot1, groups, R;
+    int64_t n_pts, n_slots, rstride;  // rstride: doubles between consecutive vectors' partials
+    double* partial;        // [R][n_chunks][2][NCOMP][n_pts]
+};
+cudaError_t launch_far64_multi(const FarArgs64M& a, int n_tgt_tiles, int n_chunks, cudaStream_t s);
+
 struct GatherArgs {
     const int4* slot_v;         // [n_slots] vertex ids (-1 pad), .w = domain
     const int64_t* v_dof1;      // per global vertex

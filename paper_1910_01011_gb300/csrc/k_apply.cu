@@ -795,6 +795,117 @@ cudaError_t launch_far64(const FarArgs64& a, int n_tgt_tiles, int n_chunks, cuda
     return cudaGetLastError();
 }
 
+// Several vectors per FP64 far-field CTA.  The Green's function G, its radial
+// factor F and the geometric weights of a (target point, source point) pair
+// are computed once and applied to each of the group's vectors, with the
+// target-normal and source-edge factors folded into the point terms:
+// 16 FP64 FMAs per vector and pair beside the shared evaluation (sqrt, the
+// reciprocal, sincos and, for a complex wavenumber, exp).  Sums per vector
+// and component in source order, so results do not depend on the group.
+template <int RG, bool ATTEN>
+__device__ __forceinline__ void far64m_body(const FarArgs64M& A, int sl, int grp) {
+    const int tid = threadIdx.x;
+    const int tt = A.tgt_begin + blockIdx.x;
+    const int chunk = blockIdx.y;
+    int sb = A.src_begin + chunk * A.chunk_tiles;
+    int se = min(sb + A.chunk_tiles, A.src_end);
+    const int64_t p = (int64_t)tt * TP + tid;
+    const double4 g = A.pg[p];
+    const int mt = tid / QP;
+    const double4 ng = A.tg[(int64_t)tt * TT + mt];
+    const double4 ct = A.tc[tt];
+    const int mydom = A.tdom[tt];
+    if (sl == 1) {
+        const int2 dr = A.dom_tiles[mydom];
+        sb = max(sb, dr.x);
+        se = min(se, dr.y);
+    }
+    const double2 kk = sl ? A.kdom[mydom] : A.k0;
+    const double kr = kk.x, ki = kk.y;
+    const int r0 = grp * RG, nv = min(RG, A.R - r0);
+    double acc[RG][NCOMP];
+#pragma unroll
+    for (int v = 0; v < RG; v++)
+#pragma unroll
+        for (int c = 0; c < NCOMP; c++) acc[v][c] = 0.0;
+    for (int s = sb; s < se; s++) {
+        const double4 cs = A.tc[s];
+        const double Xx = g.x + (ct.x - cs.x), Xy = g.y + (ct.y - cs.y), Xz = g.z + (ct.z - cs.z);  // x - c_source
+        const int ntri = A.tntri[s];
+        for (int tl = 0; tl < ntri; tl++) {
+            if (s == tt && tl == mt) continue;
+            const int64_t ts = (int64_t)s * TT + tl;
+            const double4 tg = A.tg[ts];
+            const double fK = tg.w - (tg.x * Xx + tg.y * Xy + tg.z * Xz);
+            const double nn = ng.x * tg.x + ng.y * tg.y + ng.z * tg.z;
+            double S2r = 0, S2i = 0;
+            for (int q = 0; q < QP; q++) {
+                const double4 y = A.pg[ts * QP + q];
+                const double ex = Xx - y.x, ey = Xy - y.y, ez = Xz - y.z;  // x - y
+                const double r = sqrt(ex * ex + ey * ey + ez * ez);
+                const double rinv = 1.0 / r;
+                double sn, cs2;
+                sincos(kr * r, &sn, &cs2);
+                const double a = (ATTEN ? exp(-ki * r) : 1.0) * rinv;
+                const double Gr = a * cs2, Gi = a * sn;
+                const double u = -ki - rinv;
+                const double Fr = (Gr * u - Gi * kr) * rinv, Fi = (Gr * kr + Gi * u) * rinv;
+                const double ndot = ng.x * ex + ng.y * ey + ng.z * ez;
+                const double nFr = ndot * Fr, nFi = ndot * Fi;  // K' point factor
+                const double kFr = fK * Fr, kFi = fK * Fi;      // K point factor
+                const double wGr = nn * Gr, wGi = nn * Gi;      // W (normal-normal) point factor
+                S2r += Gr * y.w;
+                S2i += Gi * y.w;
+#pragma unroll
+                for (int v = 0; v < RG; v++) {
+                    if (v >= nv) break;
+                    const double4 d = A.pd[(int64_t)(r0 + v) * A.n_pts + ts * QP + q];
+                    acc[v][0] += Gr * d.x - Gi * d.y;
+                    acc[v][1] += Gr * d.y + Gi * d.x;
+                    acc[v][2] += kFr * d.z - kFi * d.w;
+                    acc[v][3] += kFr * d.w + kFi * d.z;
+                    acc[v][4] += nFr * d.x - nFi * d.y;
+                    acc[v][5] += nFr * d.y + nFi * d.x;
+                    acc[v][6] += wGr * d.z - wGi * d.w;
+                    acc[v][7] += wGr * d.w + wGi * d.z;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < RG; v++) {
+                if (v >= nv) break;
+                const double4* tcv = A.tcurl + (int64_t)(r0 + v) * 2 * A.n_slots;
+                const double4 cre = tcv[2 * ts], cim = tcv[2 * ts + 1];
+                acc[v][8] += S2r * cre.x - S2i * cim.x;
+                acc[v][9] += S2r * cre.y - S2i * cim.y;
+                acc[v][10] += S2r * cre.z - S2i * cim.z;
+                acc[v][11] += S2r * cim.x + S2i * cre.x;
+                acc[v][12] += S2r * cim.y + S2i * cre.y;
+                acc[v][13] += S2r * cim.z + S2i * cre.z;
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < RG; v++) {
+        if (v >= nv) break;
+        double* out = A.partial + (int64_t)(r0 + v) * A.rstride + ((int64_t)chunk * 2 + sl) * NCOMP * A.n_pts + p;
+#pragma unroll
+        for (int c = 0; c < NCOMP; c++) out[(int64_t)c * A.n_pts] = acc[v][c];
+    }
+}
+
+__global__ void __launch_bounds__(TP, 1) far64m_kernel(FarArgs64M A) {
+    const int sl = blockIdx.z / A.groups, grp = blockIdx.z % A.groups;
+    const double ki = sl ? A.kdom[A.tdom[A.tgt_begin + blockIdx.x]].y : A.k0.y;
+    if (ki != 0.0) far64m_body<RG64, true>(A, sl, grp);
+    else far64m_body<RG64, false>(A, sl, grp);
+}
+
+cudaError_t launch_far64_multi(const FarArgs64M& a, int n_tgt_tiles, int n_chunks, cudaStream_t s) {
+    if (n_tgt_tiles <= 0 || n_chunks <= 0 || a.groups <= 0) return cudaSuccess;
+    far64m_kernel<<<dim3(n_tgt_tiles, n_chunks, (a.slot1 ? 2 : 1) * a.groups), TP, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------- projection onto P1 test functions
 
 // One CTA per target tile.  Its TP threads first sum, each for its own
@@ -847,71 +958,128 @@ __global__ void __launch_bounds__(TP) project_kernel(ProjectArgs a) {
         }
     }
     __syncthreads();
-    if (tid >= TT) return;
+    // far part: thread tid < TT owns slot tile * TT + tid
     const int64_t s = (int64_t)tile * TT + tid;
-    const int4 v = a.slot_v[s];
-    if (v.x < 0) return;
-    const int dom = tdom;  // a tile holds triangles of one domain
-    const double inv4pi = 0.07957747154594767;
+    const bool own = tid < TT && a.slot_v[s].x >= 0;
     double r1[3][2] = {{0, 0}, {0, 0}, {0, 0}}, r2[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-    for (int sl = 0; sl < 2; sl++) {
-        const SlotCoef cf = a.coef[dom * 2 + sl];
-        if (cf.cV == 0 && cf.cK == 0 && cf.cKp == 0 && cf.cW == 0) continue;
-        double wc[6] = {0, 0, 0, 0, 0, 0};
-        for (int q = 0; q < QP; q++) {
-            const int64_t p = s * QP + q;
-            double P[NCOMP];
-            for (int c = 0; c < NCOMP; c++) P[c] = Ps[sl][c][tid * QP + q];
-            const double w = a.pt_w[p] * inv4pi;
-            // row1 potential: cV PV - cK PK ; row2 (pointwise part): cKp PKp - cW k^2 PWm
-            const double t1r = cf.cV * P[0] - cf.cK * P[2], t1i = cf.cV * P[1] - cf.cK * P[3];
-            const double kwr = cf.k2re * P[6] - cf.k2im * P[7], kwi = cf.k2re * P[7] + cf.k2im * P[6];
-            const double t2r = cf.cKp * P[4] - cf.cW * kwr, t2i = cf.cKp * P[5] - cf.cW * kwi;
+    if (own) {
+        const int dom = tdom;  // a tile holds triangles of one domain
+        const double inv4pi = 0.07957747154594767;
+        for (int sl = 0; sl < 2; sl++) {
+            const SlotCoef cf = a.coef[dom * 2 + sl];
+            if (cf.cV == 0 && cf.cK == 0 && cf.cKp == 0 && cf.cW == 0) continue;
+            double wc[6] = {0, 0, 0, 0, 0, 0};
+            for (int q = 0; q < QP; q++) {
+                const int64_t p = s * QP + q;
+                double P[NCOMP];
+                for (int c = 0; c < NCOMP; c++) P[c] = Ps[sl][c][tid * QP + q];
+                const double w = a.pt_w[p] * inv4pi;
+                // row1 potential: cV PV - cK PK ; row2 (pointwise part): cKp PKp - cW k^2 PWm
+                const double t1r = cf.cV * P[0] - cf.cK * P[2], t1i = cf.cV * P[1] - cf.cK * P[3];
+                const double kwr = cf.k2re * P[6] - cf.k2im * P[7], kwi = cf.k2re * P[7] + cf.k2im * P[6];
+                const double t2r = cf.cKp * P[4] - cf.cW * kwr, t2i = cf.cKp * P[5] - cf.cW * kwi;
+                for (int k = 0; k < 3; k++) {
+                    const double wl = w * a.lam[q][k];
+                    r1[k][0] += wl * t1r;
+                    r1[k][1] += wl * t1i;
+                    r2[k][0] += wl * t2r;
+                    r2[k][1] += wl * t2i;
+                }
+                for (int c = 0; c < 6; c++) wc[c] += w * P[8 + c];
+            }
             for (int k = 0; k < 3; k++) {
-                const double wl = w * a.lam[q][k];
-                r1[k][0] += wl * t1r;
-                r1[k][1] += wl * t1i;
-                r2[k][0] += wl * t2r;
-                r2[k][1] += wl * t2i;
+                const double* cu = &a.slot_curl[s * 9 + 3 * k];
+                r2[k][0] += cf.cW * (cu[0] * wc[0] + cu[1] * wc[1] + cu[2] * wc[2]);
+                r2[k][1] += cf.cW * (cu[0] * wc[3] + cu[1] * wc[4] + cu[2] * wc[5]);
             }
-            for (int c = 0; c < 6; c++) wc[c] += w * P[8 + c];
-        }
-        for (int k = 0; k < 3; k++) {
-            const double* cu = &a.slot_curl[s * 9 + 3 * k];
-            r2[k][0] += cf.cW * (cu[0] * wc[0] + cu[1] * wc[1] + cu[2] * wc[2]);
-            r2[k][1] += cf.cW * (cu[0] * wc[3] + cu[1] * wc[4] + cu[2] * wc[5]);
         }
     }
-    // touching pairs: combined 3x3 sub-blocks (row1<-psi, row1<-phi, row2<-psi, row2<-phi)
+    // near pairs (touching and near band): combined 3x3 sub-blocks (row1<-psi,
+    // row1<-phi, row2<-psi, row2<-phi).  Every thread takes part: thread
+    // (j, sub) = (tid / NSUB, tid % NSUB) sums every NSUB-th pair of slot
+    // tile * TT + j; the NSUB partial sums meet in shared memory (Ps is free
+    // again) and are added in a fixed order, so results are deterministic.
+    // FP32 blocks (the FP32 operator) take FP32 products and sums.
     if (a.np_ptr) {
-        for (int64_t pi = a.np_ptr[s]; pi < a.np_ptr[s + 1]; pi++) {
-            const int4 vt = a.slot_v[a.np_src[pi]];
-            const int vid[3] = {vt.x, vt.y, vt.z};
-            double2 xs[3], xf[3];
-            for (int b = 0; b < 3; b++) {
-                xs[b] = a.x[a.v_dof1[vid[b]]];
-                xf[b] = a.x[a.v_dof2[vid[b]]];
-            }
-            for (int blk = 0; blk < 4; blk++)
-                for (int k = 0; k < 3; k++)
+        constexpr int NSUB = TP / TT;
+        double* red = &Ps[0][0][0];  // [TT][NSUB][12]
+        static_assert(TT * NSUB * 12 <= 2 * NCOMP * TP, "near partial sums fit in the potential buffer");
+        __syncthreads();
+        const int j = tid / NSUB, sub = tid % NSUB;
+        const int64_t sj = (int64_t)tile * TT + j;
+        double acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; c++) acc[c] = 0;
+        if (a.slot_v[sj].x >= 0) {
+            const int64_t pe = a.np_ptr[sj + 1];
+            if (a.nb32) {
+                float f[12];
+#pragma unroll
+                for (int c = 0; c < 12; c++) f[c] = 0.f;
+                for (int64_t pi = a.np_ptr[sj] + sub; pi < pe; pi += NSUB) {
+                    const int4 vt = a.slot_v[a.np_src[pi]];
+                    const int vid[3] = {vt.x, vt.y, vt.z};
+                    float2 xv[2][3];
+#pragma unroll
                     for (int b = 0; b < 3; b++) {
-                        double br, bi;
-                        if (a.nb32) {
-                            const float2 B = a.nb32[(pi * 4 + blk) * 9 + 3 * k + b];
-                            br = B.x;
-                            bi = B.y;
-                        } else {
-                            const double2 B = a.nb64[(pi * 4 + blk) * 9 + 3 * k + b];
-                            br = B.x;
-                            bi = B.y;
-                        }
-                        const double2 xv = (blk & 1) ? xf[b] : xs[b];
-                        double* dst = blk < 2 ? r1[k] : r2[k];
-                        dst[0] += br * xv.x - bi * xv.y;
-                        dst[1] += br * xv.y + bi * xv.x;
+                        const double2 x1 = a.x[a.v_dof1[vid[b]]], x2 = a.x[a.v_dof2[vid[b]]];
+                        xv[0][b] = make_float2((float)x1.x, (float)x1.y);
+                        xv[1][b] = make_float2((float)x2.x, (float)x2.y);
                     }
+                    // 36 complex entries as 18 aligned float4 (pair stride 288 bytes)
+                    const float4* B4 = reinterpret_cast<const float4*>(a.nb32 + pi * 36);
+#pragma unroll
+                    for (int e2 = 0; e2 < 18; e2++) {
+                        const float4 B = B4[e2];
+#pragma unroll
+                        for (int h = 0; h < 2; h++) {
+                            const int e = 2 * e2 + h, blk = e / 9, k = (e % 9) / 3, b = e % 3;
+                            const float br = h ? B.z : B.x, bi = h ? B.w : B.y;
+                            const float2 x = xv[blk & 1][b];
+                            const int o = (blk < 2 ? 0 : 6) + 2 * k;
+                            f[o] = fmaf(br, x.x, fmaf(-bi, x.y, f[o]));
+                            f[o + 1] = fmaf(br, x.y, fmaf(bi, x.x, f[o + 1]));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 12; c++) acc[c] = f[c];
+            } else {
+                for (int64_t pi = a.np_ptr[sj] + sub; pi < pe; pi += NSUB) {
+                    const int4 vt = a.slot_v[a.np_src[pi]];
+                    const int vid[3] = {vt.x, vt.y, vt.z};
+                    double2 xv[2][3];
+                    for (int b = 0; b < 3; b++) {
+                        xv[0][b] = a.x[a.v_dof1[vid[b]]];
+                        xv[1][b] = a.x[a.v_dof2[vid[b]]];
+                    }
+#pragma unroll
+                    for (int e = 0; e < 36; e++) {
+                        const int blk = e / 9, k = (e % 9) / 3, b = e % 3;
+                        const double2 B = a.nb64[pi * 36 + e];
+                        const double2 x = xv[blk & 1][b];
+                        const int o = (blk < 2 ? 0 : 6) + 2 * k;
+                        acc[o] += B.x * x.x - B.y * x.y;
+                        acc[o + 1] += B.x * x.y + B.y * x.x;
+                    }
+                }
+            }
         }
+#pragma unroll
+        for (int c = 0; c < 12; c++) red[(j * NSUB + sub) * 12 + c] = acc[c];
+        __syncthreads();
+        if (own)
+            for (int u = 0; u < NSUB; u++) {
+                const double* q = red + (tid * NSUB + u) * 12;
+                for (int k = 0; k < 3; k++) {
+                    r1[k][0] += q[2 * k];
+                    r1[k][1] += q[2 * k + 1];
+                    r2[k][0] += q[6 + 2 * k];
+                    r2[k][1] += q[6 + 2 * k + 1];
+                }
+            }
     }
+    if (!own) return;
     for (int k = 0; k < 3; k++) {
         a.tri_out[(s * 3 + k) * 2] = make_double2(r1[k][0], r1[k][1]);
         a.tri_out[(s * 3 + k) * 2 + 1] = make_double2(r2[k][0], r2[k][1]);

@@ -821,13 +821,14 @@ int block_combine(bem_ctx* ctx, int64_t n, const T* V, int K, int P, const doubl
     return e == cudaSuccess ? BEM_OK : ctx->fail(BEM_ERR_CUDA, std::string("block combine: ") + cudaGetErrorString(e));
 }
 
-// In place: lower-triangular L with G = L L^H (G Hermitian P x P, row-major).
-// Returns false if G is not numerically positive definite.
-bool cholesky(std::vector<zd>& G, int P) {
+// In place: lower-triangular L with G = L L^H (G Hermitian P x P, row-major,
+// unit diagonal up to rounding).  Returns false if a pivot falls to piv_min
+// or below: the columns are dependent to within the vectors' precision.
+bool cholesky(std::vector<zd>& G, int P, double piv_min) {
     for (int j = 0; j < P; j++) {
         double d = G[(size_t)j * P + j].real();
         for (int k2 = 0; k2 < j; k2++) d -= std::norm(G[(size_t)j * P + k2]);
-        if (!(d > 0)) return false;
+        if (!(d > piv_min)) return false;
         const double l = std::sqrt(d);
         G[(size_t)j * P + j] = l;
         for (int i = j + 1; i < P; i++) {
@@ -889,7 +890,12 @@ int gmres_block_impl(Krylov& k, bem_ctx* ctx, const Krylov::Op& op, const double
             for (int i = 0; i < P; i++)
                 for (int j = 0; j < P; j++)
                     Gh[(size_t)i * P + j] = zd(tmp[(size_t)i * P + j].x, tmp[(size_t)i * P + j].y) / (D[i] * D[j]);
-            if (!cholesky(Gh, P)) return BEM_ERR_NOT_CONVERGED;  // dependent columns: the block space is exhausted
+            // dependent columns (the block space is exhausted): a pivot of the
+            // column-scaled Gram matrix below 1e-6 (FP32 vectors, whose Gram
+            // entries carry errors near 1e-7; singular values below 1e-3 of
+            // the largest) or 1e-12 (FP64), where Cholesky QR stops being
+            // reliable anyway
+            if (!cholesky(Gh, P, F32 ? 1e-6 : 1e-12)) return BEM_ERR_NOT_CONVERGED;
             const std::vector<zd> Ui = upper_inverse(Gh, P);
             for (int i = 0; i < P; i++)
                 for (int j = 0; j < P; j++) {

@@ -274,6 +274,7 @@ int bem_server_default_opts(bem_server_opts* o) {
     o->solve.precision = BEM_PREC_FP32;
     o->solve.batch_rhs = 64;
     o->solve.block_gmres = 1;
+    o->solve.operator_mode = 2;
     return BEM_OK;
 }
 

@@ -131,6 +131,26 @@ def test_multi_rhs_far_field_matches_oracle(api, name):
             assert rel(Y[r], c.apply(X[r], precision=1)) < 2e-6, (R, r)
 
 
+@pytest.mark.parametrize("name", ["ragged", "shell", "phase"])
+def test_multi_rhs_fp64_far_field_matches_oracle(api, name):
+    """Several vectors in one FP64 far-field launch (kernel values of a pair
+    shared by a group of four, one launch per slot and group): every column
+    against the oracle's dense A_hat (FP64 bar) and against the one-vector
+    FP64 path; group counts 2, 4, 5 (a short last group) and 9, on a
+    complex interior wavenumber (the attenuated branch) and real ones."""
+    s = {"ragged": ragged_scene, "shell": lambda: scenes.shell_scene(1),
+         "phase": lambda: scenes.sphere_scene(2, k0=60.0, k1=66.0 + 0.5j)}[name]()
+    A = pmchwt.assemble(s)
+    c = ctx_for(api, s)
+    for R in (2, 4, 5, 9):
+        X = np.stack([scenes.random_complex(A.shape[0], 60 + r) for r in range(R - 1)] +
+                     [scenes.smooth_trace_vector(s, 3)])
+        Y = c.apply(X, precision=0)
+        for r in range(R):
+            assert rel(Y[r], A @ X[r]) < TOL[0], (R, r)
+            assert rel(Y[r], c.apply(X[r], precision=0)) < 1e-13, (R, r)
+
+
 def test_large_phase_accuracy_fp32(api):
     """k|x-y| up to ~120 rad on a unit sphere: the FP32 path keeps the
     phase through the tile-local offsets (a plain FP32 distance would lose

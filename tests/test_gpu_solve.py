@@ -168,6 +168,33 @@ def test_transducer_rhs_excitation_groups(api):
         assert rel(B[r], ref) < 1e-12, r
 
 
+def test_automatic_operator_mode(api):
+    """operator_mode 2 resolves to the assembled operators on a small scene
+    (36 N^2 bytes far below 4 GiB): the same solution and memory estimate
+    as operator_mode 1; an out-of-range mode is refused."""
+    from paper_1910_01011_gb300._lib import BemError
+    s = scenes.two_sphere_scene(1)
+    tr = small_transducer()
+    W = np.exp(2j * np.pi * np.random.default_rng(4).random((3, tr["radii"].size)))
+    sols, reps = [], []
+    for mode in (1, 2):
+        c = ctx_for(api, s)
+        c.set_transducer(tr["centres"], tr["normals"], tr["radii"], 2.6)
+        c.set_excitations(W)
+        reps.append(c.solve(precision=1, tol=1e-10, batch_rhs=3, operator_mode=mode))
+        sols.append(np.stack([c.solution(r) for r in range(3)]))
+        if mode == 2:
+            assert c.estimate_solve_bytes(3, batch_rhs=3, operator_mode=2) == \
+                c.estimate_solve_bytes(3, batch_rhs=3, operator_mode=1)
+            with pytest.raises(BemError):
+                c.solve(operator_mode=3)
+        c.close()
+    # the near-field corrections enter the assembled matrices through atomic
+    # additions, so two contexts agree to rounding, not bit for bit
+    assert abs(reps[0]["iterations"] - reps[1]["iterations"]) <= 3
+    assert rel(sols[1].ravel(), sols[0].ravel()) < 1e-8
+
+
 def test_solve_reports_not_converged(api):
     s = scenes.sphere_scene(2)
     c = ctx_for(api, s)
