@@ -920,7 +920,6 @@ int gmres_block_impl(Krylov& k, bem_ctx* ctx, const Krylov::Op& op, const double
     std::vector<double2> Hs((size_t)KM * m * P);     // rotated block Hessenberg (upper triangle), Hs[col * KM + row]
     std::vector<double2> Gr((size_t)KM * P);         // rotated right-hand sides, row-major Gr[row * P + c]
     std::vector<double2> rcs((size_t)m * P * P), rsn((size_t)m * P * P);  // P Givens rotations per basis column
-    std::vector<double2> hcs;
     int total = 0;
     bool first = true;
     while (total < max_iter) {
@@ -958,71 +957,48 @@ int gmres_block_impl(Krylov& k, bem_ctx* ctx, const Krylov::Op& op, const double
         std::fill(Gr.begin(), Gr.end(), make_double2(0, 0));
         for (int r = 0; r < P; r++)
             for (int c = 0; c < P; c++) Gr[(size_t)r * P + c] = make_double2(S[(size_t)r * P + c].real(), S[(size_t)r * P + c].imag());
-        int j = 0;
-        bool breakdown = false;
-        for (; j < m && total < max_iter; j++) {
-            double2* Vj = k.V + (size_t)j * ldk;
-            if (prec) {
-                double2* Zj = k.Z + (size_t)j * ldk;
-                if ((rc = (*prec)(Vj, Zj))) return rc;
-                if ((rc = op(Zj, k.w))) return rc;
-            } else if ((rc = op(Vj, k.w))) {
-                return rc;
+        // Step j's device work (preconditioner, operator, CGS2, its coefficients
+        // copied to pinned memory) is issued before the host folds step j - 1
+        // into the least squares (band Givens, O(j P^3) on the host), so the two
+        // overlap; the stopping test therefore lags one step, and a step issued
+        // after the last one needed is discarded.
+        int folded = 0;        // steps in the least squares
+        int issued = 0;        // steps whose device work was issued
+        bool breakdown = false, converged = false, pending = false;
+        std::vector<zd> Rn_pend((size_t)P * P);
+        // the new block column of the Hessenberg matrix, row-major over its P
+        // columns (Hb[row * P + c]), plain double arithmetic
+        // (a, b) <- (conj(cs) a + conj(sn) b, -sn a + cs b) on rows (row, row + 1) of columns c0..P-1
+        auto rot = [&](double2* M, int ld, int row, int c0, int c1, double2 cs, double2 sn) {
+            double2* A = M + (size_t)row * ld;
+            double2* Bq = M + (size_t)(row + 1) * ld;
+            for (int c = c0; c < c1; c++) {
+                const double2 a = A[c], b = Bq[c];
+                A[c] = make_double2(cs.x * a.x + cs.y * a.y + sn.x * b.x + sn.y * b.y,
+                                    cs.x * a.y - cs.y * a.x + sn.x * b.y - sn.y * b.x);
+                Bq[c] = make_double2(-(sn.x * a.x - sn.y * a.y) + cs.x * b.x - cs.y * b.y,
+                                     -(sn.x * a.y + sn.y * a.x) + cs.x * b.y + cs.y * b.x);
             }
-            if constexpr (F32) kv_to32<<<nbl, KV_THREADS, 0, ctx->stream>>>(ldk, k.w, Wt);
-            const int K = (j + 1) * P;
-            // CGS2 against every basis vector so far; both coefficient sets read back at once
-            for (int pass = 0; pass < 2; pass++) {
-                double2* Cp = k.bC + (size_t)pass * K * P;
-                if ((rc = block_dots(ctx, k, (const T*)Vt, K, (const T*)Wt, P, Cp))) return rc;
-                if ((rc = block_combine(ctx, n, (const T*)Vt, K, P, Cp, -1.0, (const T*)Wt, 1.0, Wt))) return rc;
-            }
-            hcs.resize((size_t)2 * K * P);
-            CK(cudaMemcpyAsync(hcs.data(), k.bC, hcs.size() * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
-            CK(cudaStreamSynchronize(ctx->stream));
-            std::vector<zd> Rn((size_t)P * P);
-            rc = orth(Wt, Rn);
-            if (rc == BEM_ERR_NOT_CONVERGED) {  // the block space is exhausted: solve with what there is
-                breakdown = true;
-                rc = BEM_OK;
-                std::fill(Rn.begin(), Rn.end(), zd(0));
-            } else if (rc) {
-                return rc;
-            } else {
-                T* Vn = Vt + (size_t)(j + 1) * ldk;
-                CK(cudaMemcpyAsync(Vn, Wt, (size_t)ldk * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
-                if constexpr (F32) kv_to64<<<nbl, KV_THREADS, 0, ctx->stream>>>(ldk, Wt, k.V + (size_t)(j + 1) * ldk);
-            }
-            // the new block column of the Hessenberg matrix, row-major over its P
-            // columns (Hb[row * P + c]), plain double arithmetic
+        };
+        // fold step jj (coefficients hc, new-block factor Rn); true once every column meets tol
+        auto fold = [&](int jj, const double2* hc, const std::vector<zd>& Rn) -> bool {
+            const int K = (jj + 1) * P;
             std::vector<double2> Hb((size_t)(K + P) * P);
             for (int kk = 0; kk < K; kk++)
                 for (int c = 0; c < P; c++) {
-                    const double2 a = hcs[(size_t)kk * P + c], b = hcs[(size_t)K * P + (size_t)kk * P + c];
+                    const double2 a = hc[(size_t)kk * P + c], b = hc[(size_t)K * P + (size_t)kk * P + c];
                     Hb[(size_t)kk * P + c] = make_double2(a.x + b.x, a.y + b.y);
                 }
             for (int r = 0; r < P; r++)
                 for (int c = 0; c < P; c++)
                     Hb[(size_t)(K + r) * P + c] = make_double2(Rn[(size_t)r * P + c].real(), Rn[(size_t)r * P + c].imag());
-            // (a, b) <- (conj(cs) a + conj(sn) b, -sn a + cs b) on rows (row, row + 1) of columns c0..P-1
-            auto rot = [&](double2* M, int ld, int row, int c0, int c1, double2 cs, double2 sn) {
-                double2* A = M + (size_t)row * ld;
-                double2* Bq = M + (size_t)(row + 1) * ld;
-                for (int c = c0; c < c1; c++) {
-                    const double2 a = A[c], b = Bq[c];
-                    A[c] = make_double2(cs.x * a.x + cs.y * a.y + sn.x * b.x + sn.y * b.y,
-                                        cs.x * a.y - cs.y * a.x + sn.x * b.y - sn.y * b.x);
-                    Bq[c] = make_double2(-(sn.x * a.x - sn.y * a.y) + cs.x * b.x - cs.y * b.y,
-                                         -(sn.x * a.y + sn.y * a.x) + cs.x * b.y + cs.y * b.x);
-                }
-            };
             // earlier rotations (in the order they were made) on all P new columns
-            for (int qq = 0; qq < j * P; qq++)
+            for (int qq = 0; qq < jj * P; qq++)
                 for (int l = 0; l < P; l++)
                     rot(Hb.data(), P, qq + P - 1 - l, 0, P, rcs[(size_t)qq * P + l], rsn[(size_t)qq * P + l]);
             // P new rotations per column, applied to the later columns of the block and to G
             for (int c = 0; c < P; c++) {
-                const int q = j * P + c;
+                const int q = jj * P + c;
                 for (int l = 0; l < P; l++) {
                     const int row = q + P - 1 - l;
                     const double2 a = Hb[(size_t)row * P + c], b = Hb[(size_t)(row + 1) * P + c];
@@ -1039,11 +1015,10 @@ int gmres_block_impl(Krylov& k, bem_ctx* ctx, const Krylov::Op& op, const double
             }
             // keep the rotated columns (upper triangle) for the back substitution
             for (int c = 0; c < P; c++) {
-                const int q = j * P + c;
+                const int q = jj * P + c;
                 double2* col = &Hs[(size_t)q * KM];
                 for (int r = 0; r <= q; r++) col[r] = Hb[(size_t)r * P + c];
             }
-            total++;
             // residual of each column: the last P rows of its rotated right-hand side
             bool all = true;
             for (int c = 0; c < P; c++) {
@@ -1056,11 +1031,56 @@ int gmres_block_impl(Krylov& k, bem_ctx* ctx, const Krylov::Op& op, const double
                     iters[c]++;
                 }
             }
-            if (all || breakdown) {
-                j++;
-                break;
+            return all;
+        };
+        while (true) {
+            const int j = issued;
+            const bool issue = !breakdown && !converged && j < m && total + (pending ? 1 : 0) < max_iter;
+            double2* hc = k.hpin + (size_t)(j & 1) * 2 * KM * P;
+            if (issue) {
+                double2* Vj = k.V + (size_t)j * ldk;
+                if (prec) {
+                    double2* Zj = k.Z + (size_t)j * ldk;
+                    if ((rc = (*prec)(Vj, Zj))) return rc;
+                    if ((rc = op(Zj, k.w))) return rc;
+                } else if ((rc = op(Vj, k.w))) {
+                    return rc;
+                }
+                if constexpr (F32) kv_to32<<<nbl, KV_THREADS, 0, ctx->stream>>>(ldk, k.w, Wt);
+                const int K = (j + 1) * P;
+                // CGS2 against every basis vector so far; both coefficient sets read back at once
+                for (int pass = 0; pass < 2; pass++) {
+                    double2* Cp = k.bC + (size_t)pass * K * P;
+                    if ((rc = block_dots(ctx, k, (const T*)Vt, K, (const T*)Wt, P, Cp))) return rc;
+                    if ((rc = block_combine(ctx, n, (const T*)Vt, K, P, Cp, -1.0, (const T*)Wt, 1.0, Wt))) return rc;
+                }
+                CK(cudaMemcpyAsync(hc, k.bC, (size_t)2 * K * P * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+                issued++;
             }
+            if (pending) {  // while the GPU works on step j
+                pending = false;
+                converged = fold(folded, k.hpin + (size_t)(folded & 1) * 2 * KM * P, Rn_pend);
+                folded++;
+                total++;
+                if (converged) break;
+            }
+            if (!issue) break;
+            CK(cudaStreamSynchronize(ctx->stream));
+            rc = orth(Wt, Rn_pend);
+            if (rc == BEM_ERR_NOT_CONVERGED) {  // the block space is exhausted: solve with what there is
+                breakdown = true;
+                rc = BEM_OK;
+                std::fill(Rn_pend.begin(), Rn_pend.end(), zd(0));
+            } else if (rc) {
+                return rc;
+            } else {
+                T* Vn = Vt + (size_t)(j + 1) * ldk;
+                CK(cudaMemcpyAsync(Vn, Wt, (size_t)ldk * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
+                if constexpr (F32) kv_to64<<<nbl, KV_THREADS, 0, ctx->stream>>>(ldk, Wt, k.V + (size_t)(j + 1) * ldk);
+            }
+            pending = true;
         }
+        const int j = folded;
         // Y = H^-1 G (upper triangular, J unknowns per column), X += Z Y (FP64)
         const int J = j * P;
         if (J > 0) {
@@ -1118,6 +1138,17 @@ int Krylov::gmres_block(bem_ctx* ctx, const Op& op, const double2* B, double2* X
         bpart = (double2*)ctx->dalloc(need_part * sizeof(double2), &rc);
         if (rc) { bpart = nullptr; bpart_n = 0; return rc; }
         bpart_n = need_part;
+    }
+    const size_t need_h = (size_t)2 * 2 * (m + 1) * P * P;  // two steps of two K x P coefficient sets
+    if (hpin_n < need_h) {
+        if (hpin) cudaFreeHost(hpin);
+        hpin = nullptr;
+        hpin_n = 0;
+        if (cudaHostAlloc((void**)&hpin, need_h * sizeof(double2), cudaHostAllocDefault) != cudaSuccess) {
+            hpin = nullptr;
+            return ctx->fail(BEM_ERR_CUDA, "block GMRES: pinned host buffer");
+        }
+        hpin_n = need_h;
     }
     if (bC_n < need_c) {
         dfree_buf(ctx, (void**)&bC);

@@ -28,6 +28,7 @@ struct Krylov {
     Krylov& operator=(const Krylov&) = delete;
     ~Krylov() {  // device buffers belong to the context's allocations; the host-side poll objects are ours
         if (n_run_host) cudaFreeHost(n_run_host);
+        if (hpin) cudaFreeHost(hpin);
         for (auto& e : poll_ev)
             if (e) cudaEventDestroy(e);
     }
@@ -71,6 +72,8 @@ struct Krylov {
     size_t bpart_n = 0, bC_n = 0;
     float2* b32 = nullptr;                    // FP32 basis and work blocks of the block GMRES
     size_t b32_n = 0;
+    double2* hpin = nullptr;                  // pinned Hessenberg coefficients of two consecutive steps
+    size_t hpin_n = 0;
     static void dfree_buf(bem_ctx* ctx, void** p);
 };
 
