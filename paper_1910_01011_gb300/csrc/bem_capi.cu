@@ -460,6 +460,11 @@ void bem_ctx::chunking(int n_tgt, int n_src, int* n_chunks, int* chunk_tiles) co
     int want = std::max(1, (152 * 2 * 8 + n_tgt - 1) / std::max(1, n_tgt));
     int nc = std::max(want, (n_src + CHUNK_MAX - 1) / CHUNK_MAX);
     if (opts.chunk_tiles > 0) nc = (n_src + opts.chunk_tiles - 1) / opts.chunk_tiles;
+    // the partial potentials grow as chunks x points: at most 8 GiB of them at
+    // FP64 (4 GiB at FP32), unless CHUNK_MAX forces more chunks
+    const int64_t per_chunk = (int64_t)2 * NCOMP * n_tgt * TP * sizeof(double);
+    const int nc_mem = (int)std::max<int64_t>(1, ((int64_t)8 << 30) / std::max<int64_t>(1, per_chunk));
+    nc = std::min(nc, std::max(nc_mem, (n_src + CHUNK_MAX - 1) / CHUNK_MAX));
     nc = std::max(1, std::min(nc, n_src));
     int ct = (n_src + nc - 1) / nc;
     ct = std::min(ct, CHUNK_MAX);

@@ -9,8 +9,9 @@ test_gpu_fullsize.py.
   excitation per piston) on the rib / fat / liver scene at 6 mm elements
   (8,172 triangles, N = 8,200) at the frequency its mesh resolves (k h ~ 1):
   8 seeded pistons, each alone, solved by the oracle's dense LU and on the
-  GPU by the mixed batched path and the plain FP64 path (bar 1e-6 on the
-  traces, eq. Galerkin_disc_lhs/_rhs1 with the Rayleigh incident field)."""
+  GPU by the mixed and the plain FP64 paths, each with the 8 excitations in
+  lockstep and as one block GMRES (bar 1e-6 on the traces, eq.
+  Galerkin_disc_lhs/_rhs1 with the Rayleigh incident field)."""
 import numpy as np
 import pytest
 
@@ -92,8 +93,8 @@ def rib_small():
     return s, pistons, B, U
 
 
-@pytest.mark.parametrize("precision,batch", [(1, 8), (0, 8)])
-def test_rib_scene_piston_solves_match_oracle(rib_small, precision, batch):
+@pytest.mark.parametrize("precision,batch,block", [(1, 8, 0), (0, 8, 0), (1, 8, 1), (0, 8, 1)])
+def test_rib_scene_piston_solves_match_oracle(rib_small, precision, batch, block):
     from paper_1910_01011_gb300 import api
     s, pistons, B, U = rib_small
     tr = s.transducer
@@ -105,7 +106,8 @@ def test_rib_scene_piston_solves_match_oracle(rib_small, precision, batch):
     c.set_excitations(W)
     b = c.rhs(len(pistons))
     assert rel(b.reshape(len(pistons), -1).T, B) < 1e-12
-    rep = c.solve(precision=precision, operator_mode=1, tol=1e-9, batch_rhs=batch, max_iter=20000, max_refine=20)
+    rep = c.solve(precision=precision, operator_mode=1, tol=1e-9, batch_rhs=batch, max_iter=20000, max_refine=20,
+                  block_gmres=block)
     assert rep["converged"], rep
     errs = [rel(c.solution(r), U[:, r]) for r in range(len(pistons))]
     print(precision, rep, errs)
