@@ -28,7 +28,8 @@ class bem_opts(ctypes.Structure):
     _fields_ = [("n_gauss_singular", ctypes.c_int32), ("chunk_tiles", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_int64), ("n_pade", ctypes.c_int32), ("pade_theta", ctypes.c_double),
                 ("r_eps", ctypes.c_double), ("eps_exponent", ctypes.c_double), ("osrc_tol", ctypes.c_double),
-                ("osrc_solver", ctypes.c_int32), ("osrc_wavenumber", ctypes.c_int32)]
+                ("osrc_solver", ctypes.c_int32), ("osrc_wavenumber", ctypes.c_int32),
+                ("fp64_far", ctypes.c_int32)]
 
 
 class bem_solve_opts(ctypes.Structure):

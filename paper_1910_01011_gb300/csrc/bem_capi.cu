@@ -139,6 +139,9 @@ static void release_device(bem_ctx* ctx) {
     ctx->multi_buf_bytes = 0;
     ctx->multi64_buf = nullptr;
     ctx->multi64_buf_bytes = 0;
+    ctx->dfg = bem_ctx::DfGeom();
+    ctx->dfv_buf = nullptr;
+    ctx->dfv_bytes = 0;
     ctx->multi_work = nullptr;
     ctx->multi_n_work = 0;
     for (int& k : ctx->multi_key) k = -1;
@@ -239,6 +242,9 @@ int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_
         multi64_chunking((int)tiles, R, &nc64, &ct64);
         b += R * (pts * 32 + 2 * slots * 32 + (int64_t)nc64 * 2 * NCOMP * pts * 8);
     }
+    // double-float far field: split geometry and tables; split densities of R vectors
+    if (o.operator_mode == 0 && ctx->opts.fp64_far == 0)
+        b += 32 * (pts + slots + tiles) + 4096 + R * (pts * 32 + 2 * slots * 32 + 16);
     // split vectors of the FP64-accurate residual product
     b += R * N * 16 + 4096;
     if (o.operator_mode == 1) {
@@ -557,8 +563,16 @@ int bem_ctx::run_apply(const double2* x, double2* y, int precision, const ApplyM
         CK(cudaEventCreate(&ev1));
         CK(cudaEventRecord(ev0, stream));
     }
-    if (P.fp64) CK(launch_far64(P.fa64, P.n_tgt, P.n_chunks, stream));
-    else CK(launch_far32(P.fa32, P.n_tgt, P.n_chunks, stream));
+    if (P.fp64 && opts.fp64_far == 0) {
+        const FarArgs64& f = P.fa64;
+        if ((rc = far_df(dev.pd64, dev.tcurl64, 1, f.tgt_begin, f.tgt_begin + P.n_tgt, f.src_begin, f.src_end,
+                         f.chunk_tiles, P.n_chunks, f.slot1, f.k0.x, f.k0.y, f.partial, 0)))
+            return rc;
+    } else if (P.fp64) {
+        CK(launch_far64(P.fa64, P.n_tgt, P.n_chunks, stream));
+    } else {
+        CK(launch_far32(P.fa32, P.n_tgt, P.n_chunks, stream));
+    }
     if (profiling) {
         CK(cudaEventRecord(ev1, stream));
         far_events.push_back({ev0, ev1});
@@ -732,7 +746,12 @@ int bem_ctx::apply_ahat64_multi(const double2* x, double2* y, int64_t n_rhs) {
         CK(cudaEventCreate(&ev1));
         CK(cudaEventRecord(ev0, stream));
     }
-    CK(launch_far64_multi(fa, n_tiles, n_chunks, stream));
+    if (opts.fp64_far == 0) {
+        if ((rc = far_df(pdm, tcm, n_rhs, 0, n_tiles, 0, n_tiles, chunk_tiles, n_chunks, 1, k0re, k0im, part, rstride)))
+            return rc;
+    } else {
+        CK(launch_far64_multi(fa, n_tiles, n_chunks, stream));
+    }
     if (profiling) {
         CK(cudaEventRecord(ev1, stream));
         far_events.push_back({ev0, ev1});
@@ -795,6 +814,7 @@ int bem_default_opts(bem_opts* o) {
     o->osrc_tol = 1e-11;
     o->osrc_solver = 0;
     o->osrc_wavenumber = 0;
+    o->fp64_far = 0;
     return BEM_OK;
 }
 
@@ -812,7 +832,7 @@ int bem_create(bem_ctx** out, int device, void* cuda_stream, const bem_opts* opt
     if (opts) c->opts = *opts;
     if (c->opts.n_gauss_singular < 2 || c->opts.n_gauss_singular > 20 || !(c->opts.osrc_tol > 0) ||
         !(c->opts.osrc_tol < 1) || c->opts.osrc_solver < 0 || c->opts.osrc_solver > 4 ||
-        c->opts.osrc_wavenumber < 0 || c->opts.osrc_wavenumber > 1) {
+        c->opts.osrc_wavenumber < 0 || c->opts.osrc_wavenumber > 1 || c->opts.fp64_far < 0 || c->opts.fp64_far > 1) {
         delete c;
         return BEM_ERR_INVALID_ARG;
     }

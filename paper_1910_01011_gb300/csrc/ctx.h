@@ -112,6 +112,16 @@ struct bem_ctx {
     size_t multi_buf_bytes = 0;
     void* multi64_buf = nullptr;  // FP64 multi-vector far field: densities, curls, partial potentials
     size_t multi64_buf_bytes = 0;
+    struct DfGeom {                // double-float far field: split geometry, tables, constants
+        bool ready = false;
+        void* buf = nullptr;
+        float4 *pgh = nullptr, *pgl = nullptr, *tgh = nullptr, *tgl = nullptr, *tch = nullptr, *tcl = nullptr;
+        float4 *sctab = nullptr, *kdf = nullptr;
+        float2* extab = nullptr;
+        float pi64[4] = {}, ln64[3] = {}, inv_pi64 = 0, inv_ln64 = 0, sixth[2] = {};
+    } dfg;
+    void* dfv_buf = nullptr;       // double-float densities and curls of the vectors of one call
+    size_t dfv_bytes = 0;
     int4* multi_work = nullptr;
     int64_t multi_n_work = 0;
     int multi_key[3] = {-1, -1, -1};  // (n_chunks, chunk_tiles, groups) the list was built for
@@ -170,6 +180,9 @@ struct bem_ctx {
     int apply_ahat(const double2* x, double2* y, int precision);
     int apply_ahat_multi(const double2* x, double2* y, int64_t n_rhs);
     int apply_ahat64_multi(const double2* x, double2* y, int64_t n_rhs);
+    int ensure_fardf();
+    int far_df(const double4* pd, const double4* cu, int64_t R, int tgt_b, int tgt_e, int src_b, int src_e,
+               int chunk_tiles, int n_chunks, int slot1, double kre, double kim, double* partial, int64_t rstride);
     int apply_prec(const double2* x, double2* y);
     int apply_prec_batch(const double2* x, double2* y, int64_t n_rhs);
     int apply_prec_ahat(const double2* x, double2* y, int precision);

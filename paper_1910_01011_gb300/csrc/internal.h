@@ -192,6 +192,30 @@ struct FarArgs64M {
 };
 cudaError_t launch_far64_multi(const FarArgs64M& a, int n_tgt_tiles, int n_chunks, cudaStream_t s);
 
+// The far field to FP64 accuracy in double-float FP32 arithmetic (k_fardf.cu):
+// the same work decomposition as FarArgs64M, every real as an (h, l) pair of
+// floats (geometry split once, densities split per call with a power-of-two
+// scale per vector).
+struct FarArgsDF {
+    const float4 *pgh, *pgl;   // [n_pts] point offset from its tile centre, weight
+    const float4 *tgh, *tgl;   // [n_slots] normal, h
+    const float4 *tch, *tcl;   // [n_tiles] tile centres
+    const int* tdom;
+    const int* tntri;
+    const int2* dom_tiles;
+    const float4* kdf;         // [n_dom] (Re k hi, lo, Im k hi, lo) of each domain
+    float4 k0df;               // slot-0 wavenumber
+    const float4 *pdh, *pdl;   // [R][n_pts] scaled densities
+    const float4 *cuh, *cul;   // [R][2 n_slots] scaled curls
+    const int* vexp;           // [R] each vector's scale is 2^-vexp
+    const float4* sctab;       // [128] (sin hi, lo, cos hi, lo) of j pi / 64
+    const float2* extab;       // [64] 2^(-j/64) hi, lo
+    float pi64[4], ln64[3], inv_pi64, inv_ln64, sixth[2];
+    int src_begin, src_end, tgt_begin, chunk_tiles, slot1, groups, R;
+    int64_t n_pts, n_slots, rstride;
+    double* partial;           // [R][n_chunks][2][NCOMP][n_pts]
+};
+
 struct GatherArgs {
     const int4* slot_v;         // [n_slots] vertex ids (-1 pad), .w = domain
     const int64_t* v_dof1;      // per global vertex

@@ -715,84 +715,14 @@ cudaError_t launch_far32_multi(const FarArgs32M& a, int64_t n_work, cudaStream_t
 
 // ----------------------------------------------------------------- FP64 far field
 
-__global__ void __launch_bounds__(TP) far64_kernel(FarArgs64 A) {
-    const int tid = threadIdx.x;
-    const int tt = A.tgt_begin + blockIdx.x;
-    const int sb = A.src_begin + blockIdx.y * A.chunk_tiles;
-    const int se = min(sb + A.chunk_tiles, A.src_end);
-    const int64_t p = (int64_t)tt * TP + tid;
-    const double4 g = A.pg[p];
-    const int mt = tid / QP;
-    const double4 ng = A.tg[(int64_t)tt * TT + mt];
-    const double4 ct = A.tc[tt];
-    const int mydom = A.tdom[tt];
-    const int2 dr = A.dom_tiles[mydom];
-    double2 ks[2] = {A.k0, A.kdom[mydom]};
-    double acc[2][NCOMP];
-    for (int sl = 0; sl < 2; sl++)
-        for (int c = 0; c < NCOMP; c++) acc[sl][c] = 0.0;
-    for (int s = sb; s < se; s++) {
-        const double4 cs = A.tc[s];
-        const double Dx = ct.x - cs.x, Dy = ct.y - cs.y, Dz = ct.z - cs.z;
-        const double Xx = g.x + Dx, Xy = g.y + Dy, Xz = g.z + Dz;  // x - c_source
-        const int ntri = A.tntri[s];
-        const int nsl = (A.slot1 && s >= dr.x && s < dr.y) ? 2 : 1;
-        for (int tl = 0; tl < ntri; tl++) {
-            if (s == tt && tl == mt) continue;
-            const int64_t ts = (int64_t)s * TT + tl;
-            const double4 tg = A.tg[ts];
-            const double4 cre = A.tcurl[2 * ts], cim = A.tcurl[2 * ts + 1];
-            const double fK = tg.w - (tg.x * Xx + tg.y * Xy + tg.z * Xz);
-            const double nn = ng.x * tg.x + ng.y * tg.y + ng.z * tg.z;
-            for (int sl = 0; sl < nsl; sl++) {
-                const double kr = ks[sl].x, ki = ks[sl].y;
-                double S1r = 0, S1i = 0, S2r = 0, S2i = 0, S3r = 0, S3i = 0;
-                for (int q = 0; q < QP; q++) {
-                    const double4 y = A.pg[ts * QP + q];
-                    const double4 d = A.pd[ts * QP + q];
-                    const double ex = Xx - y.x, ey = Xy - y.y, ez = Xz - y.z;  // x - y
-                    const double r = sqrt(ex * ex + ey * ey + ez * ez);
-                    const double rinv = 1.0 / r;
-                    double sn, cs2;
-                    sincos(kr * r, &sn, &cs2);
-                    const double a = exp(-ki * r) * rinv;
-                    const double Gr = a * cs2, Gi = a * sn;
-                    const double u = -ki - rinv;
-                    const double Fr = (Gr * u - Gi * kr) * rinv, Fi = (Gr * kr + Gi * u) * rinv;
-                    const double ndot = ng.x * ex + ng.y * ey + ng.z * ez;
-                    acc[sl][0] += Gr * d.x - Gi * d.y;
-                    acc[sl][1] += Gr * d.y + Gi * d.x;
-                    acc[sl][4] += ndot * (Fr * d.x - Fi * d.y);
-                    acc[sl][5] += ndot * (Fr * d.y + Fi * d.x);
-                    S1r += Fr * d.z - Fi * d.w;
-                    S1i += Fr * d.w + Fi * d.z;
-                    S2r += Gr * y.w;
-                    S2i += Gi * y.w;
-                    S3r += Gr * d.z - Gi * d.w;
-                    S3i += Gr * d.w + Gi * d.z;
-                }
-                acc[sl][2] += fK * S1r;
-                acc[sl][3] += fK * S1i;
-                acc[sl][6] += nn * S3r;
-                acc[sl][7] += nn * S3i;
-                acc[sl][8] += S2r * cre.x - S2i * cim.x;
-                acc[sl][9] += S2r * cre.y - S2i * cim.y;
-                acc[sl][10] += S2r * cre.z - S2i * cim.z;
-                acc[sl][11] += S2r * cim.x + S2i * cre.x;
-                acc[sl][12] += S2r * cim.y + S2i * cre.y;
-                acc[sl][13] += S2r * cim.z + S2i * cre.z;
-            }
-        }
-    }
-    double* out = A.partial + (int64_t)blockIdx.y * 2 * NCOMP * A.n_pts;
-    for (int sl = 0; sl < 2; sl++)
-        for (int c = 0; c < NCOMP; c++) out[(int64_t)(sl * NCOMP + c) * A.n_pts + p] = acc[sl][c];
-}
-
+// One vector at FP64: the multi-vector kernel with a single group.
 cudaError_t launch_far64(const FarArgs64& a, int n_tgt_tiles, int n_chunks, cudaStream_t s) {
-    if (n_tgt_tiles <= 0 || n_chunks <= 0) return cudaSuccess;
-    far64_kernel<<<dim3(n_tgt_tiles, n_chunks), TP, 0, s>>>(a);
-    return cudaGetLastError();
+    FarArgs64M m{};
+    m.pg = a.pg; m.tg = a.tg; m.tc = a.tc; m.tdom = a.tdom; m.tntri = a.tntri; m.pd = a.pd; m.tcurl = a.tcurl;
+    m.dom_tiles = a.dom_tiles; m.kdom = a.kdom; m.k0 = a.k0;
+    m.src_begin = a.src_begin; m.src_end = a.src_end; m.tgt_begin = a.tgt_begin; m.chunk_tiles = a.chunk_tiles;
+    m.slot1 = a.slot1; m.groups = 1; m.R = 1; m.n_pts = a.n_pts; m.n_slots = 0; m.rstride = 0; m.partial = a.partial;
+    return launch_far64_multi(m, n_tgt_tiles, n_chunks, s);
 }
 
 // Several vectors per FP64 far-field CTA.  The Green's function G, its radial
@@ -893,16 +823,20 @@ __device__ __forceinline__ void far64m_body(const FarArgs64M& A, int sl, int grp
     }
 }
 
-__global__ void __launch_bounds__(TP, 1) far64m_kernel(FarArgs64M A) {
+template <int RG>
+__global__ void __launch_bounds__(TP, RG == 1 ? 2 : 1) far64m_kernel(FarArgs64M A) {
     const int sl = blockIdx.z / A.groups, grp = blockIdx.z % A.groups;
     const double ki = sl ? A.kdom[A.tdom[A.tgt_begin + blockIdx.x]].y : A.k0.y;
-    if (ki != 0.0) far64m_body<RG64, true>(A, sl, grp);
-    else far64m_body<RG64, false>(A, sl, grp);
+    if (ki != 0.0) far64m_body<RG, true>(A, sl, grp);
+    else far64m_body<RG, false>(A, sl, grp);
 }
 
+// One vector (groups = R = 1) or groups of RG64; slot 1 only with a.slot1.
 cudaError_t launch_far64_multi(const FarArgs64M& a, int n_tgt_tiles, int n_chunks, cudaStream_t s) {
     if (n_tgt_tiles <= 0 || n_chunks <= 0 || a.groups <= 0) return cudaSuccess;
-    far64m_kernel<<<dim3(n_tgt_tiles, n_chunks, (a.slot1 ? 2 : 1) * a.groups), TP, 0, s>>>(a);
+    const dim3 grid(n_tgt_tiles, n_chunks, (a.slot1 ? 2 : 1) * a.groups);
+    if (a.R == 1) far64m_kernel<1><<<grid, TP, 0, s>>>(a);
+    else far64m_kernel<RG64><<<grid, TP, 0, s>>>(a);
     return cudaGetLastError();
 }
 

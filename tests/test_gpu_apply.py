@@ -151,6 +151,28 @@ def test_multi_rhs_fp64_far_field_matches_oracle(api, name):
             assert rel(Y[r], c.apply(X[r], precision=0)) < 1e-13, (R, r)
 
 
+@pytest.mark.parametrize("name", ["ragged", "shell", "phase"])
+def test_fp64_double_float_far_field_matches_native(api, name):
+    """The FP64 path's far field in double-float FP32 arithmetic (the default)
+    against the same field in native FP64 arithmetic: one vector and five in
+    one launch, on an attenuating interior wavenumber (3.7 + 0.2i, 66 + 0.5i)
+    and phases k|x - y| up to ~130 rad; both within the FP64 bar of the
+    oracle's dense A_hat."""
+    s = {"ragged": ragged_scene, "shell": lambda: scenes.shell_scene(1),
+         "phase": lambda: scenes.sphere_scene(2, k0=60.0, k1=66.0 + 0.5j)}[name]()
+    A = pmchwt.assemble(s)
+    cd = ctx_for(api, s)
+    cn = ctx_for(api, s, fp64_far=1)
+    X = np.stack([scenes.random_complex(A.shape[0], 80 + r) for r in range(4)] + [scenes.smooth_trace_vector(s, 2)])
+    for x in (X[0], X[4]):
+        yd, yn = cd.apply(x, precision=0), cn.apply(x, precision=0)
+        assert rel(yd, yn) < 1e-12
+        assert rel(yd, A @ x) < TOL[0]
+    Yd, Yn = cd.apply(X, precision=0), cn.apply(X, precision=0)
+    for r in range(X.shape[0]):
+        assert rel(Yd[r], Yn[r]) < 1e-12, r
+
+
 def test_large_phase_accuracy_fp32(api):
     """k|x-y| up to ~120 rad on a unit sphere: the FP32 path keeps the
     phase through the tile-local offsets (a plain FP32 distance would lose
