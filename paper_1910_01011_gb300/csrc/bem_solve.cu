@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "df_math.cuh"
 #include "internal.h"
 #include "krylov.h"
 
@@ -78,45 +79,57 @@ struct PistonArgs {
     const double4* tc;
     const int4* slot_v;
     const double* slot_n;
-    const double4* disc; // [n_elem * nq] (x, y, z, weight)
+    const float4 *disc_h, *disc_l;  // [n_elem * nq] (x, y, z, weight) as double-floats
     int n_elem, nq;
-    const double2* w;    // [n_rhs][n_elem] piston weights
+    const float4* w;     // [n_rhs][n_elem] piston weights (re hi, re lo, im hi, im lo)
     int n_rhs;
-    double2 k0;
+    float4 k0;           // (Re hi, lo, Im hi, lo)
     double2 pref;        // -i omega rho0 / (2 pi)
     int64_t n_slots;
     double lam[QP][3];
+    DfConsts c;
+    const float4* sctab; // double-float sin / cos table (df_math.cuh)
+    const float2* extab;
     double2* tri_out;    // [n_rhs][n_slots*3][2]
 };
 
 // Excitations per block row of piston_kernel (its accumulators live in
-// registers: 4 doubles per excitation and thread).
+// registers: 4 double-floats per excitation and thread).
 constexpr int PK_RC = 16;
 constexpr int PK_SLOTS = 16;  // slots per block; one thread per (slot, rule point)
 
+__device__ __forceinline__ void dacc(dfl& acc, dfl x) {  // acc += x (low part gathers the errors)
+    const dfl q = two_sum(acc.h, x.h);
+    acc.h = q.h;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(q.l, x.l));
+}
+
 // Rayleigh field of piston m (its disc points, weights folded in) at x and
-// its normal derivative along n: e = sum_j w_j exp(ik R_j)/R_j,
-// f = sum_j w_j exp(ik R_j)/R_j (ik - 1/R_j) (x - y_j).n / R_j.
+// its normal derivative along n, in double-float arithmetic:
+// e = sum_j w_j exp(ik R_j)/R_j, f = sum_j w_j exp(ik R_j)/R_j (ik - 1/R_j) (x - y_j).n / R_j.
 template <bool ATTEN>
-__device__ __forceinline__ void piston_field(const double4* __restrict__ disc, int nq, double2 k0, double x, double y,
-                                             double z, double nx, double ny, double nz, double& er, double& ei,
-                                             double& fr, double& fi) {
-    er = ei = fr = fi = 0;
-    for (int j = 0; j < nq; j++) {
-        const double4 d = disc[j];
-        const double ex = x - d.x, ey = y - d.y, ez = z - d.z;
-        const double R = sqrt(ex * ex + ey * ey + ez * ez);
-        const double Ri = 1.0 / R;
-        double sn, cs;
-        sincos(k0.x * R, &sn, &cs);
-        const double amp = (ATTEN ? exp(-k0.y * R) : 1.0) * Ri * d.w;
-        const double gr = amp * cs, gi = amp * sn;  // w exp(ikR)/R
-        er += gr;
-        ei += gi;
-        const double ur = -k0.y - Ri, ui = k0.x;
-        const double dn = (ex * nx + ey * ny + ez * nz) * Ri;
-        fr += (gr * ur - gi * ui) * dn;
-        fi += (gr * ui + gi * ur) * dn;
+__device__ __forceinline__ void piston_field(const PistonArgs& a, int m, const dfl (&x)[3], const dfl (&n)[3],
+                                             const float4* __restrict__ tab, const float2* __restrict__ etab,
+                                             dfl& er, dfl& ei, dfl& fr, dfl& fi) {
+    const dfl kr = {a.k0.x, a.k0.y}, ki = {a.k0.z, a.k0.w};
+    er = ei = fr = fi = dfl{0.0f, 0.0f};
+    for (int j = 0; j < a.nq; j++) {
+        const float4 dh = a.disc_h[(int64_t)m * a.nq + j], dl = a.disc_l[(int64_t)m * a.nq + j];
+        const dfl ex = dsub(x[0], dfl{dh.x, dl.x}), ey = dsub(x[1], dfl{dh.y, dl.y}), ez = dsub(x[2], dfl{dh.z, dl.z});
+        dfl R, Ri;
+        dsqrt_rinv(dadd(dadd(dsqr(ex), dsqr(ey)), dsqr(ez)), R, Ri);
+        dfl sn, cs;
+        dsincos(dmul(kr, R), a.c, tab, sn, cs);
+        dfl amp = dmul(Ri, dfl{dh.w, dl.w});
+        if (ATTEN) amp = dmul(amp, dexp_neg(dmul(ki, R), a.c, etab));
+        const dfl gr = dmul(amp, cs), gi = dmul(amp, sn);  // w exp(ikR)/R
+        dacc(er, gr);
+        dacc(ei, gi);
+        // d/dn: exp(ikR)/R (ik - 1/R) (x-y).n / R
+        const dfl ur = dsub(dneg(ki), Ri);
+        const dfl dn = dmul(dadd(dadd(dmul(ex, n[0]), dmul(ey, n[1])), dmul(ez, n[2])), Ri);
+        dacc(fr, dmul(dsub(dmul(gr, ur), dmul(gi, kr)), dn));
+        dacc(fi, dmul(dadd(dmul(gr, kr), dmul(gi, ur)), dn));
     }
 }
 
@@ -127,44 +140,61 @@ __device__ __forceinline__ void piston_field(const double4* __restrict__ disc, i
 // piston's field once at its rule point and accumulates it into the PK_RC
 // excitations of its block row; a piston whose weight is zero in all of them
 // is skipped (a block-uniform test), so the unit excitations of a
-// superposition basis cost one evaluation per piston.  The rule points of a
-// slot are summed against the P1 values in shared memory.
+// superposition basis cost one evaluation per piston.  The sums run in
+// double-float FP32 arithmetic (df_math.cuh: FP64 accuracy at the FP32
+// rate); the rule points of a slot are summed against the P1 values in
+// shared memory in FP64.
+template <bool ATTEN>
 __global__ void __launch_bounds__(PK_SLOTS * QP) piston_kernel(PistonArgs a) {
+    __shared__ float4 tab[128];
+    __shared__ float2 etab[64];
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) tab[i] = a.sctab[i];
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) etab[i] = a.extab[i];
+    __syncthreads();
     const int sl = threadIdx.x / QP, q = threadIdx.x % QP;
     const int64_t s = (int64_t)blockIdx.x * PK_SLOTS + sl;
     const int r0 = blockIdx.y * PK_RC, nrc = min(PK_RC, a.n_rhs - r0);
     const bool live = s < a.n_slots && a.slot_v[s].x >= 0;
-    double acc[PK_RC][4];
+    dfl acc[PK_RC][4];
 #pragma unroll
-    for (int c = 0; c < PK_RC; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0;
+    for (int c = 0; c < PK_RC; c++) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = dfl{0.0f, 0.0f};
     double gw = 0;
     if (live) {
         const double4 c0 = a.tc[s / TT];
-        const double nx = a.slot_n[3 * s], ny = a.slot_n[3 * s + 1], nz = a.slot_n[3 * s + 2];
         const double4 g = a.pg[s * QP + q];
         gw = g.w;
-        const double x = c0.x + g.x, y = c0.y + g.y, z = c0.z + g.z;
-        const double2* wr = a.w + (int64_t)r0 * a.n_elem;
+        const double xd[3] = {c0.x + g.x, c0.y + g.y, c0.z + g.z};
+        dfl x[3], n[3];
+        for (int k = 0; k < 3; k++) {
+            const float h = (float)xd[k];
+            x[k] = dfl{h, (float)(xd[k] - (double)h)};
+            const double nd = a.slot_n[3 * s + k];
+            const float nh = (float)nd;
+            n[k] = dfl{nh, (float)(nd - (double)nh)};
+        }
+        const float4* wr = a.w + (int64_t)r0 * a.n_elem;
         for (int m = 0; m < a.n_elem; m++) {
             bool any = false;
             for (int c = 0; c < nrc && !any; c++) {
-                const double2 wm = wr[(int64_t)c * a.n_elem + m];
-                any = wm.x != 0.0 || wm.y != 0.0;
+                const float4 wm = wr[(int64_t)c * a.n_elem + m];
+                any = wm.x != 0.0f || wm.z != 0.0f;
             }
             if (!any) continue;
-            double er, ei, fr, fi;
-            if (a.k0.y != 0.0)
-                piston_field<true>(a.disc + (int64_t)m * a.nq, a.nq, a.k0, x, y, z, nx, ny, nz, er, ei, fr, fi);
-            else
-                piston_field<false>(a.disc + (int64_t)m * a.nq, a.nq, a.k0, x, y, z, nx, ny, nz, er, ei, fr, fi);
+            dfl er, ei, fr, fi;
+            piston_field<ATTEN>(a, m, x, n, tab, etab, er, ei, fr, fi);
 #pragma unroll
             for (int c = 0; c < PK_RC; c++)
                 if (c < nrc) {
-                    const double2 wm = wr[(int64_t)c * a.n_elem + m];
-                    acc[c][0] += wm.x * er - wm.y * ei;
-                    acc[c][1] += wm.x * ei + wm.y * er;
-                    acc[c][2] += wm.x * fr - wm.y * fi;
-                    acc[c][3] += wm.x * fi + wm.y * fr;
+                    const float4 wm = wr[(int64_t)c * a.n_elem + m];
+                    const dfl wre = {wm.x, wm.y}, wim = {wm.z, wm.w};
+                    dmac(acc[c][0], wre, er, 1.0f);
+                    dmac(acc[c][0], wim, ei, -1.0f);
+                    dmac(acc[c][1], wre, ei, 1.0f);
+                    dmac(acc[c][1], wim, er, 1.0f);
+                    dmac(acc[c][2], wre, fr, 1.0f);
+                    dmac(acc[c][2], wim, fi, -1.0f);
+                    dmac(acc[c][3], wre, fi, 1.0f);
+                    dmac(acc[c][3], wim, fr, 1.0f);
                 }
         }
     }
@@ -176,10 +206,13 @@ __global__ void __launch_bounds__(PK_SLOTS * QP) piston_kernel(PistonArgs a) {
 #pragma unroll
     for (int c = 0; c < PK_RC; c++) {
         if (c >= nrc) break;
-        sh[sl][q][0] = a.pref.x * acc[c][0] - a.pref.y * acc[c][1];
-        sh[sl][q][1] = a.pref.x * acc[c][1] + a.pref.y * acc[c][0];
-        sh[sl][q][2] = a.pref.x * acc[c][2] - a.pref.y * acc[c][3];
-        sh[sl][q][3] = a.pref.x * acc[c][3] + a.pref.y * acc[c][2];
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = (double)acc[c][u].h + (double)acc[c][u].l;
+        sh[sl][q][0] = a.pref.x * v[0] - a.pref.y * v[1];
+        sh[sl][q][1] = a.pref.x * v[1] + a.pref.y * v[0];
+        sh[sl][q][2] = a.pref.x * v[2] - a.pref.y * v[3];
+        sh[sl][q][3] = a.pref.x * v[3] + a.pref.y * v[2];
         sh[sl][q][4] = gw;
         __syncthreads();
         if (live) {
@@ -215,8 +248,10 @@ struct SolveState {
     double2 *bt = nullptr, *bpb = nullptr, *bd = nullptr, *br = nullptr;
     int64_t batch_alloc = 0;
     double2* tri_rhs = nullptr; // [n_rhs][n_slots*6]
-    double4* disc = nullptr;
-    double2* wdev = nullptr;
+    double4* disc = nullptr;    // piston disc points [n_elem * nq] (x, y, z, weight)
+    double2* wdev = nullptr;    // piston weights [n_rhs][n_elem]
+    float4* disc_df = nullptr;  // the same as double-floats: [2][n_elem * nq] (hi, lo)
+    float4* w_df = nullptr;     // [n_rhs][n_elem] (re hi, re lo, im hi, im lo)
     int64_t n_rhs_alloc = 0;
     int64_t n_rhs_solved = 0;
     // superposition basis: the solution of every piston alone, [n_elem][N]
@@ -281,24 +316,55 @@ static int build_rhs(bem_ctx* ctx) {
                     d.w = w;
                 }
         }
-        ctx->dfree(S->disc);
-        ctx->dfree(S->wdev);
+        // double-float copies: disc points (hi, lo) and weights (re hi, re lo, im hi, im lo)
+        auto split = [](double v, float& h, float& l) {
+            h = (float)v;
+            l = (float)(v - (double)h);
+        };
+        std::vector<float4> dsplit(2 * disc.size());
+        for (size_t i = 0; i < disc.size(); i++) {
+            float4& h = dsplit[i];
+            float4& l = dsplit[disc.size() + i];
+            split(disc[i].x, h.x, l.x);
+            split(disc[i].y, h.y, l.y);
+            split(disc[i].z, h.z, l.z);
+            split(disc[i].w, h.w, l.w);
+        }
+        std::vector<float4> wsplit(ctx->tr_w.size() / 2);
+        for (size_t i = 0; i < wsplit.size(); i++) {
+            split(ctx->tr_w[2 * i], wsplit[i].x, wsplit[i].y);
+            split(ctx->tr_w[2 * i + 1], wsplit[i].z, wsplit[i].w);
+        }
+        if ((rc = ctx->ensure_fardf())) return rc;
+        for (void* p : {(void*)S->disc, (void*)S->wdev, (void*)S->disc_df, (void*)S->w_df}) ctx->dfree(p);
         S->disc = (double4*)ctx->dalloc(disc.size() * sizeof(double4), &rc); if (rc) return rc;
         S->wdev = (double2*)ctx->dalloc(ctx->tr_w.size() * sizeof(double), &rc); if (rc) return rc;
+        S->disc_df = (float4*)ctx->dalloc(dsplit.size() * sizeof(float4), &rc); if (rc) return rc;
+        S->w_df = (float4*)ctx->dalloc(std::max<size_t>(1, wsplit.size()) * sizeof(float4), &rc); if (rc) return rc;
         CK(cudaMemcpyAsync(S->disc, disc.data(), disc.size() * sizeof(double4), cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(S->wdev, ctx->tr_w.data(), ctx->tr_w.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(S->disc_df, dsplit.data(), dsplit.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(S->w_df, wsplit.data(), wsplit.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
         PistonArgs a{};
         a.pg = ctx->dev.pg64; a.tc = ctx->dev.tc; a.slot_v = ctx->dev.slot_v; a.slot_n = ctx->dev.slot_n;
-        a.disc = S->disc; a.n_elem = (int)ne; a.nq = nq; a.w = S->wdev; a.n_rhs = (int)nr;
-        a.k0 = make_double2(ctx->k0re, ctx->k0im);
+        a.disc_h = S->disc_df; a.disc_l = S->disc_df + disc.size(); a.n_elem = (int)ne; a.nq = nq; a.w = S->w_df;
+        a.n_rhs = (int)nr;
+        {
+            float h, l, hi, li;
+            split(ctx->k0re, h, l);
+            split(ctx->k0im, hi, li);
+            a.k0 = make_float4(h, l, hi, li);
+        }
+        a.c = ctx->dfg.c; a.sctab = ctx->dfg.sctab; a.extab = ctx->dfg.extab;
         a.pref = make_double2(0.0, -ctx->omega_rho0 / (2.0 * M_PI));
         a.n_slots = g.n_slots;
         for (int q = 0; q < QP; q++)
             for (int k = 0; k < 3; k++) a.lam[q][k] = ctx->quad.lam[q][k];
         a.tri_out = S->tri_rhs;
         CK(cudaMemsetAsync(S->tri_rhs, 0, nr * g.n_slots * 6 * sizeof(double2), ctx->stream));
-        piston_kernel<<<dim3((unsigned)((g.n_slots + PK_SLOTS - 1) / PK_SLOTS), (unsigned)((nr + PK_RC - 1) / PK_RC)),
-                        PK_SLOTS * QP, 0, ctx->stream>>>(a);
+        const dim3 grid((unsigned)((g.n_slots + PK_SLOTS - 1) / PK_SLOTS), (unsigned)((nr + PK_RC - 1) / PK_RC));
+        if (ctx->k0im != 0.0) piston_kernel<true><<<grid, PK_SLOTS * QP, 0, ctx->stream>>>(a);
+        else piston_kernel<false><<<grid, PK_SLOTS * QP, 0, ctx->stream>>>(a);
         ctx->launches++;
     } else {
         return ctx->fail(BEM_ERR_STATE, "no incident field set");

@@ -118,7 +118,7 @@ struct bem_ctx {
         float4 *pgh = nullptr, *pgl = nullptr, *tgh = nullptr, *tgl = nullptr, *tch = nullptr, *tcl = nullptr;
         float4 *sctab = nullptr, *kdf = nullptr;
         float2* extab = nullptr;
-        float pi64[4] = {}, ln64[3] = {}, inv_pi64 = 0, inv_ln64 = 0, sixth[2] = {};
+        gbem::DfConsts c{};
     } dfg;
     void* dfv_buf = nullptr;       // double-float densities and curls of the vectors of one call
     size_t dfv_bytes = 0;

@@ -192,6 +192,12 @@ struct FarArgs64M {
 };
 cudaError_t launch_far64_multi(const FarArgs64M& a, int n_tgt_tiles, int n_chunks, cudaStream_t s);
 
+// Split constants of the double-float sin, cos and exp (df_math.cuh): pi/64
+// in four FP32 parts, ln2/64 in three, 64/pi, 64/ln2 and -1/6 as (h, l).
+struct DfConsts {
+    float pi64[4], ln64[3], inv_pi64, inv_ln64, sixth[2];
+};
+
 // The far field to FP64 accuracy in double-float FP32 arithmetic (k_fardf.cu):
 // the same work decomposition as FarArgs64M, every real as an (h, l) pair of
 // floats (geometry split once, densities split per call with a power-of-two
@@ -210,7 +216,7 @@ struct FarArgsDF {
     const int* vexp;           // [R] each vector's scale is 2^-vexp
     const float4* sctab;       // [128] (sin hi, lo, cos hi, lo) of j pi / 64
     const float2* extab;       // [64] 2^(-j/64) hi, lo
-    float pi64[4], ln64[3], inv_pi64, inv_ln64, sixth[2];
+    DfConsts c;                // split constants of the double-float sin, cos and exp
     int src_begin, src_end, tgt_begin, chunk_tiles, slot1, groups, R;
     int64_t n_pts, n_slots, rstride;
     double* partial;           // [R][n_chunks][2][NCOMP][n_pts]

@@ -36,114 +36,10 @@
 #include <vector>
 
 #include "ctx.h"
+#include "df_math.cuh"
 #include "internal.h"
 
 namespace gbem {
-
-struct dfl {
-    float h, l;
-};
-
-__device__ __forceinline__ dfl two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-// |a| >= |b| (or a == 0)
-__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ dfl two_prod(float a, float b) {
-    const float p = __fmul_rn(a, b);
-    return {p, __fmaf_rn(a, b, -p)};
-}
-__device__ __forceinline__ dfl dneg(dfl a) { return {-a.h, -a.l}; }
-__device__ __forceinline__ dfl dadd(dfl a, dfl b) {
-    const dfl s = two_sum(a.h, b.h);
-    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
-}
-__device__ __forceinline__ dfl dsub(dfl a, dfl b) { return dadd(a, dneg(b)); }
-__device__ __forceinline__ dfl dmul(dfl a, dfl b) {
-    const dfl p = two_prod(a.h, b.h);
-    return fast_two_sum(p.h, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l)));
-}
-__device__ __forceinline__ dfl dsqr(dfl a) {
-    const dfl p = two_prod(a.h, a.h);
-    return fast_two_sum(p.h, __fmaf_rn(__fadd_rn(a.h, a.h), a.l, p.l));
-}
-// acc += s a b (s = +-1); acc's low part gathers the errors (renormalised at the end)
-__device__ __forceinline__ void dmac(dfl& acc, dfl a, dfl b, float s) {
-    const dfl p = two_prod(s * a.h, b.h);
-    const float t = __fmaf_rn(s * a.h, b.l, __fmaf_rn(s * a.l, b.h, p.l));
-    const dfl q = two_sum(acc.h, p.h);
-    acc.h = q.h;
-    acc.l = __fadd_rn(acc.l, __fadd_rn(q.l, t));
-}
-
-__device__ __forceinline__ dfl ld_h(const float4& h, const float4& l, int c) {
-    return c == 0 ? dfl{h.x, l.x} : c == 1 ? dfl{h.y, l.y} : c == 2 ? dfl{h.z, l.z} : dfl{h.w, l.w};
-}
-
-// r = sqrt(R) and 1/r for R > 0 (double-float): FP32 seeds, one Newton step each
-__device__ __forceinline__ void dsqrt_rinv(dfl R, dfl& r, dfl& ri) {
-    const float s = __fsqrt_rn(R.h);
-    const float y = __frcp_rn(s);
-    const dfl s2 = two_prod(s, s);
-    const float d = __fadd_rn(__fsub_rn(R.h, s2.h), __fsub_rn(R.l, s2.l));  // R - s^2 (first difference exact)
-    r = fast_two_sum(s, __fmul_rn(__fmul_rn(d, y), 0.5f));
-    const dfl ry = two_prod(r.h, y);
-    const float e = __fsub_rn(__fsub_rn(1.0f, ry.h), __fmaf_rn(r.l, y, ry.l));  // 1 - r y
-    ri = fast_two_sum(y, __fmul_rn(y, e));
-}
-
-// sin and cos of th >= 0 (double-float) by reduction to |d| <= pi/128
-__device__ __forceinline__ void dsincos(dfl th, const FarArgsDF& A, const float4* __restrict__ tab, dfl& sn, dfl& cs) {
-    const float nf = rintf(__fmul_rn(th.h, A.inv_pi64));
-    const float r1 = __fsub_rn(th.h, __fmul_rn(nf, A.pi64[0]));  // exact (n (pi/64)_1 is exact and near th)
-    const dfl p2 = two_prod(nf, A.pi64[1]);
-    const dfl s = two_sum(r1, -p2.h);
-    float lo = __fsub_rn(s.l, p2.l);
-    lo = __fmaf_rn(-nf, A.pi64[2], lo);
-    lo = __fmaf_rn(-nf, A.pi64[3], lo);
-    lo = __fadd_rn(lo, th.l);
-    const dfl d = fast_two_sum(s.h, lo);
-    const float4 t = tab[((int)nf) & 127];
-    const dfl sa = {t.x, t.y}, ca = {t.z, t.w};
-    const dfl d2 = dsqr(d);
-    // sin d = d - d^3 / 6 + d^5 / 120 - d^7 / 5040
-    const dfl d3 = dmul(d, d2);
-    dfl sd = dadd(d, dmul(d3, dfl{A.sixth[0], A.sixth[1]}));
-    sd.l = __fmaf_rn(__fmul_rn(d3.h, d2.h), __fmaf_rn(-d2.h, 1.0f / 5040.0f, 1.0f / 120.0f), sd.l);
-    // cos d = 1 - d^2 / 2 + d^4 / 24 - d^6 / 720
-    dfl cd = fast_two_sum(1.0f, -0.5f * d2.h);
-    cd.l = __fmaf_rn(__fmul_rn(d2.h, d2.h), __fmaf_rn(-d2.h, 1.0f / 720.0f, 1.0f / 24.0f), __fsub_rn(cd.l, 0.5f * d2.l));
-    sn = dadd(dmul(sa, cd), dmul(ca, sd));
-    cs = dsub(dmul(ca, cd), dmul(sa, sd));
-}
-
-// e^{-a} (double-float) by reduction to |t| <= ln2 / 128
-__device__ __forceinline__ dfl dexp_neg(dfl a, const FarArgsDF& A, const float2* __restrict__ etab) {
-    const float mf = rintf(__fmul_rn(a.h, A.inv_ln64));
-    const float r1 = __fsub_rn(a.h, __fmul_rn(mf, A.ln64[0]));
-    const dfl p2 = two_prod(mf, A.ln64[1]);
-    const dfl s = two_sum(r1, -p2.h);
-    float lo = __fsub_rn(s.l, p2.l);
-    lo = __fmaf_rn(-mf, A.ln64[2], lo);
-    lo = __fadd_rn(lo, a.l);
-    const dfl t = fast_two_sum(s.h, lo);
-    // e^{-t} = 1 - t + t^2 / 2 - t^3 / 6 + t^4 / 24
-    const dfl t2 = dsqr(t);
-    dfl e = dadd(dsub(dfl{1.0f, 0.0f}, t), dfl{0.5f * t2.h, 0.5f * t2.l});
-    e.l = __fmaf_rn(__fmul_rn(t.h, t2.h), __fmaf_rn(t.h, 1.0f / 24.0f, -1.0f / 6.0f), e.l);
-    const int m = (int)mf;
-    const float2 T = etab[m & 63];
-    const int k = m >> 6;  // 2^(-m/64) = 2^(-k) 2^(-(m & 63)/64)
-    if (k > 126) return {0.0f, 0.0f};
-    const float sc = __int_as_float((127 - k) << 23);
-    const dfl v = dmul(e, dfl{T.x, T.y});
-    return {v.h * sc, v.l * sc};
-}
 
 template <int RG, bool ATTEN>
 __device__ __forceinline__ void fardf_body(const FarArgsDF& A, int sl, int grp, const float4* __restrict__ tab,
@@ -194,8 +90,8 @@ __device__ __forceinline__ void fardf_body(const FarArgsDF& A, int sl, int grp, 
                 dfl r, ri;
                 dsqrt_rinv(dadd(dadd(dsqr(ex), dsqr(ey)), dsqr(ez)), r, ri);
                 dfl sn, cs2;
-                dsincos(dmul(kr, r), A, tab, sn, cs2);
-                const dfl a = ATTEN ? dmul(dexp_neg(dmul(ki, r), A, etab), ri) : ri;
+                dsincos(dmul(kr, r), A.c, tab, sn, cs2);
+                const dfl a = ATTEN ? dmul(dexp_neg(dmul(ki, r), A.c, etab), ri) : ri;
                 const dfl Gr = dmul(a, cs2), Gi = dmul(a, sn);
                 const dfl u = dsub(dneg(ki), ri);  // -Im k - 1/r
                 const dfl Fr = dmul(dsub(dmul(Gr, u), dmul(Gi, kr)), ri);
@@ -397,23 +293,24 @@ int bem_ctx::ensure_fardf() {
     CK(cudaMemcpyAsync(dfg.extab, ex.data(), ex.size() * sizeof(float2), cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(dfg.kdf, kd.data(), kd.size() * sizeof(float4), cudaMemcpyHostToDevice, stream));
     // pi/64 in four parts (the first with 7 significant bits), ln2/64 in three (the first with 10)
+    DfConsts& c = dfg.c;
     long double rest = PI / 64.0L;
-    dfg.pi64[0] = round_bits(rest, 7);
-    rest -= dfg.pi64[0];
+    c.pi64[0] = round_bits(rest, 7);
+    rest -= c.pi64[0];
     for (int i = 1; i < 4; i++) {
-        dfg.pi64[i] = (float)rest;
-        rest -= dfg.pi64[i];
+        c.pi64[i] = (float)rest;
+        rest -= c.pi64[i];
     }
     rest = LN2 / 64.0L;
-    dfg.ln64[0] = round_bits(rest, 10);
-    rest -= dfg.ln64[0];
+    c.ln64[0] = round_bits(rest, 10);
+    rest -= c.ln64[0];
     for (int i = 1; i < 3; i++) {
-        dfg.ln64[i] = (float)rest;
-        rest -= dfg.ln64[i];
+        c.ln64[i] = (float)rest;
+        rest -= c.ln64[i];
     }
-    dfg.inv_pi64 = (float)(64.0L / PI);
-    dfg.inv_ln64 = (float)(64.0L / LN2);
-    split_ld(-1.0L / 6.0L, dfg.sixth[0], dfg.sixth[1]);
+    c.inv_pi64 = (float)(64.0L / PI);
+    c.inv_ln64 = (float)(64.0L / LN2);
+    split_ld(-1.0L / 6.0L, c.sixth[0], c.sixth[1]);
     CK(cudaStreamSynchronize(stream));  // the host tables above are freed on return
     dfg.ready = true;
     return BEM_OK;
@@ -461,10 +358,7 @@ int bem_ctx::far_df(const double4* pd, const double4* cu, int64_t R, int tgt_b, 
     a.k0df = make_float4(kh, kl, ih, il);
     a.pdh = pdh; a.pdl = pdl; a.cuh = cuh; a.cul = cul; a.vexp = vexp;
     a.sctab = dfg.sctab; a.extab = dfg.extab;
-    for (int i = 0; i < 4; i++) a.pi64[i] = dfg.pi64[i];
-    for (int i = 0; i < 3; i++) a.ln64[i] = dfg.ln64[i];
-    a.inv_pi64 = dfg.inv_pi64; a.inv_ln64 = dfg.inv_ln64;
-    a.sixth[0] = dfg.sixth[0]; a.sixth[1] = dfg.sixth[1];
+    a.c = dfg.c;
     a.src_begin = src_b; a.src_end = src_e; a.tgt_begin = tgt_b; a.chunk_tiles = chunk_tiles; a.slot1 = slot1;
     a.R = (int)R; a.groups = R == 1 ? 1 : (int)((R + RG64 - 1) / RG64);
     a.n_pts = np; a.n_slots = g.n_slots; a.rstride = rstride; a.partial = partial;
