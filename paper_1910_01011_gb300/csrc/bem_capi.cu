@@ -220,7 +220,8 @@ int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_
         const int64_t gx = ((int64_t)(o.restart + 1) * R + 63) / 64;
         b += (int64_t)(o.restart + 3) * R * N * 8 +
              16 * std::max<int64_t>((int64_t)(o.restart + 1) * R * R * 8, R * 64 * std::max<int64_t>(gx, 608)) +
-             16 * (2 * (int64_t)(o.restart + 1) * R * R + R * R);
+             16 * (2 * (int64_t)(o.restart + 1) * R * R + R * R) +
+             16 * ((int64_t)(o.restart + 1) * R * o.restart * R + (int64_t)(o.restart + 1) * R * R);  // Hessenberg mirror
     }
     b += 4 * R * N * 16;
     if (o.precondition) {

@@ -236,6 +236,54 @@ __global__ void __launch_bounds__(KV_THREADS) kbd_dots(int64_t n, int K, int P, 
 }
 
 // C[k P + c] = sum_blk part[(k P + c) nsplit + blk]  (fixed order)
+// Back substitution Y = R^-1 G of the block GMRES least squares, by blocks of
+// BS_ROWS rows from the bottom: R upper triangular J x J (column-major,
+// leading dimension ld), G [J][P] row-major (overwritten), Y [J][P]; a zero
+// pivot gives a zero row of Y.  bs_block_kernel (one CTA, thread (r, c))
+// solves rows [i0, i1) against the block's own columns; bs_update_kernel
+// (thread per (row, column) above i0) subtracts those columns' part.
+constexpr int BS_ROWS = 32;
+__device__ __forceinline__ double2 cdiv(double2 g, double2 d) {
+    const double dd = d.x * d.x + d.y * d.y;
+    return dd > 0 ? make_double2((g.x * d.x + g.y * d.y) / dd, (g.y * d.x - g.x * d.y) / dd) : make_double2(0, 0);
+}
+__global__ void bs_block_kernel(const double2* __restrict__ R, int64_t ld, double2* __restrict__ G,
+                                double2* __restrict__ Y, int P, int i0, int i1) {
+    __shared__ double2 ys[32];
+    const int c = threadIdx.x, r = threadIdx.y;  // blockDim = (P, BS_ROWS)
+    for (int i = i1 - 1; i >= i0; i--) {
+        if (r == i - i0) {
+            const double2 y = cdiv(G[(int64_t)i * P + c], R[(int64_t)i * ld + i]);
+            Y[(int64_t)i * P + c] = y;
+            ys[c] = y;
+        }
+        __syncthreads();
+        if (r < i - i0) {
+            const double2 h = R[(int64_t)i * ld + i0 + r], y = ys[c];
+            double2& g = G[(int64_t)(i0 + r) * P + c];
+            g.x -= h.x * y.x - h.y * y.y;
+            g.y -= h.x * y.y + h.y * y.x;
+        }
+        __syncthreads();
+    }
+}
+__global__ void bs_update_kernel(const double2* __restrict__ R, int64_t ld, double2* __restrict__ G,
+                                 const double2* __restrict__ Y, int P, int i0, int i1) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = t / P;
+    const int c = (int)(t % P);
+    if (r >= i0) return;
+    double sr = 0, si = 0;
+    for (int i = i0; i < i1; i++) {
+        const double2 h = R[(int64_t)i * ld + r], y = Y[(int64_t)i * P + c];
+        sr += h.x * y.x - h.y * y.y;
+        si += h.x * y.y + h.y * y.x;
+    }
+    double2& g = G[r * P + c];
+    g.x -= sr;
+    g.y -= si;
+}
+
 __global__ void kbd_reduce(int KP, int nsplit, const double2* __restrict__ part, double2* __restrict__ C) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= KP) return;
@@ -917,7 +965,7 @@ int gmres_block_impl(Krylov& k, bem_ctx* ctx, const Krylov::Op& op, const double
         return BEM_OK;
     };
     const int KM = (m + 1) * P;
-    std::vector<double2> Hs((size_t)KM * m * P);     // rotated block Hessenberg (upper triangle), Hs[col * KM + row]
+    double2* Hs = k.hs_pin;  // rotated block Hessenberg (upper triangle), Hs[col * KM + row]; pinned, mirrored on the device
     std::vector<double2> Gr((size_t)KM * P);         // rotated right-hand sides, row-major Gr[row * P + c]
     std::vector<double2> rcs((size_t)m * P * P), rsn((size_t)m * P * P);  // P Givens rotations per basis column
     int total = 0;
@@ -1013,12 +1061,15 @@ int gmres_block_impl(Krylov& k, bem_ctx* ctx, const Krylov::Op& op, const double
                     rot(Gr.data(), P, row, 0, P, cs, sn);
                 }
             }
-            // keep the rotated columns (upper triangle) for the back substitution
+            // keep the rotated columns (upper triangle) for the back substitution,
+            // mirrored on the device while the next step runs
             for (int c = 0; c < P; c++) {
                 const int q = jj * P + c;
                 double2* col = &Hs[(size_t)q * KM];
                 for (int r = 0; r <= q; r++) col[r] = Hb[(size_t)r * P + c];
             }
+            cudaMemcpyAsync(k.hs_dev + (size_t)jj * P * KM, Hs + (size_t)jj * P * KM, (size_t)P * KM * sizeof(double2),
+                            cudaMemcpyHostToDevice, ctx->stream);
             // residual of each column: the last P rows of its rotated right-hand side
             bool all = true;
             for (int c = 0; c < P; c++) {
@@ -1084,22 +1135,18 @@ int gmres_block_impl(Krylov& k, bem_ctx* ctx, const Krylov::Op& op, const double
         // Y = H^-1 G (upper triangular, J unknowns per column), X += Z Y (FP64)
         const int J = j * P;
         if (J > 0) {
-            std::vector<double2> Yd((size_t)J * P);  // row-major [unknown][column]
-            for (int i = J - 1; i >= 0; i--) {
-                const double2 d = Hs[(size_t)i * KM + i];
-                const double dd = d.x * d.x + d.y * d.y;
-                for (int c = 0; c < P; c++) {
-                    double sr = Gr[(size_t)i * P + c].x, si = Gr[(size_t)i * P + c].y;
-                    for (int kk = i + 1; kk < J; kk++) {
-                        const double2 h = Hs[(size_t)kk * KM + i], y = Yd[(size_t)kk * P + c];
-                        sr -= h.x * y.x - h.y * y.y;
-                        si -= h.x * y.y + h.y * y.x;
-                    }
-                    Yd[(size_t)i * P + c] = dd > 0 ? make_double2((sr * d.x + si * d.y) / dd, (si * d.x - sr * d.y) / dd)
-                                                   : make_double2(0, 0);
-                }
+            // Y = H^-1 G on the device (H mirrored column by column as it was folded)
+            CK(cudaMemcpyAsync(k.gs_dev, Gr.data(), (size_t)J * P * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+            for (int i1 = J; i1 > 0; i1 -= BS_ROWS) {
+                const int i0 = std::max(0, i1 - BS_ROWS);
+                bs_block_kernel<<<1, dim3((unsigned)P, (unsigned)BS_ROWS), 0, ctx->stream>>>(k.hs_dev, KM, k.gs_dev, k.bC, P,
+                                                                                        i0, i1);
+                if (i0 > 0)
+                    bs_update_kernel<<<(unsigned)(((int64_t)i0 * P + 255) / 256), 256, 0, ctx->stream>>>(
+                        k.hs_dev, KM, k.gs_dev, k.bC, P, i0, i1);
+                ctx->launches += i0 > 0 ? 2 : 1;
             }
-            CK(cudaMemcpyAsync(k.bC, Yd.data(), Yd.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaGetLastError());
             if ((rc = block_combine(ctx, n, (const double2*)(prec ? k.Z : k.V), J, P, k.bC, 1.0, (const double2*)X, 1.0, X)))
                 return rc;
         }
@@ -1138,6 +1185,24 @@ int Krylov::gmres_block(bem_ctx* ctx, const Op& op, const double2* B, double2* X
         bpart = (double2*)ctx->dalloc(need_part * sizeof(double2), &rc);
         if (rc) { bpart = nullptr; bpart_n = 0; return rc; }
         bpart_n = need_part;
+    }
+    // the Hessenberg matrix, pinned on the host and mirrored on the device, and the back substitution's G
+    const size_t need_hs = (size_t)(m + 1) * P * m * P;
+    if (hs_n < need_hs) {
+        if (hs_pin) cudaFreeHost(hs_pin);
+        hs_pin = nullptr;
+        hs_n = 0;
+        dfree_buf(ctx, (void**)&hs_dev);
+        dfree_buf(ctx, (void**)&gs_dev);
+        if (cudaHostAlloc((void**)&hs_pin, need_hs * sizeof(double2), cudaHostAllocDefault) != cudaSuccess) {
+            hs_pin = nullptr;
+            return ctx->fail(BEM_ERR_CUDA, "block GMRES: pinned Hessenberg buffer");
+        }
+        hs_dev = (double2*)ctx->dalloc(need_hs * sizeof(double2), &rc);
+        if (rc) { hs_dev = nullptr; return rc; }
+        gs_dev = (double2*)ctx->dalloc((size_t)(m + 1) * P * P * sizeof(double2), &rc);
+        if (rc) { gs_dev = nullptr; return rc; }
+        hs_n = need_hs;
     }
     const size_t need_h = (size_t)2 * 2 * (m + 1) * P * P;  // two steps of two K x P coefficient sets
     if (hpin_n < need_h) {

@@ -29,6 +29,7 @@ struct Krylov {
     ~Krylov() {  // device buffers belong to the context's allocations; the host-side poll objects are ours
         if (n_run_host) cudaFreeHost(n_run_host);
         if (hpin) cudaFreeHost(hpin);
+        if (hs_pin) cudaFreeHost(hs_pin);
         for (auto& e : poll_ev)
             if (e) cudaEventDestroy(e);
     }
@@ -74,6 +75,9 @@ struct Krylov {
     size_t b32_n = 0;
     double2* hpin = nullptr;                  // pinned Hessenberg coefficients of two consecutive steps
     size_t hpin_n = 0;
+    double2* hs_pin = nullptr;                // rotated block Hessenberg matrix (pinned host copy)
+    double2 *hs_dev = nullptr, *gs_dev = nullptr;  // its device mirror; back-substitution right-hand sides
+    size_t hs_n = 0;
     static void dfree_buf(bem_ctx* ctx, void** p);
 };
 
