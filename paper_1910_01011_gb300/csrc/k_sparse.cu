@@ -57,7 +57,9 @@ struct OsrcState {
     int nblk = 0;
     // batched COCG state, [max_sys][n] complex; max_sys = 2 n_pade max_rhs
     double2 *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *b = nullptr;
-    double2* beta = nullptr;           // [max_sys][n_dom] shifts (per system and domain)
+    double2* beta = nullptr;           // shifts of the systems being solved: beta_pade or beta_close
+    double2* beta_pade = nullptr;      // [max_sys][n_dom] Pade shifts B_{s mod n_pade} of each domain
+    double2* beta_close = nullptr;     // [2 max_rhs][n_dom] closing systems: 0 and 1 / k_eps^2 alternately
     double* part = nullptr;            // [max_sys][nblk][4] partial sums
     double* scal = nullptr;            // [max_sys][8]: rho(2 parities) re/im, bnorm2, rnorm2, active
     // stage vectors, [max_rhs][2][n]
@@ -77,10 +79,11 @@ struct OsrcState {
     float2 *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // [max_sys][n]
     int64_t* dom_v0 = nullptr;         // [n_dom + 1] vertex offsets
     unsigned long long* stat = nullptr;  // [0]: iterations (sum over CTAs), [1]: CTAs that did not converge
-    // CUDA graphs of GRAPH_ITERS COCG iterations, per (number of systems, tolerance)
+    // CUDA graphs of GRAPH_ITERS COCG iterations, per (number of systems, tolerance, shift table)
     struct Graph {
         int n_sys;
         double tol;
+        const double2* beta;
         cudaGraphExec_t exec;
     };
     std::vector<Graph> graphs;
@@ -1164,11 +1167,11 @@ void destroy_osrc_state(bem_ctx* ctx) {
 static int ensure_osrc_batch(bem_ctx* ctx, OsrcState* o, int64_t R) {
     if (R <= o->max_rhs) return BEM_OK;
     CK(cudaStreamSynchronize(ctx->stream));
-    for (void* p : {(void*)o->x, (void*)o->r, (void*)o->z, (void*)o->p, (void*)o->q, (void*)o->b, (void*)o->beta,
-                    (void*)o->part, (void*)o->scal, (void*)o->u, (void*)o->g, (void*)o->x32, (void*)o->r32,
-                    (void*)o->z32, (void*)o->p32, (void*)o->q32})
+    for (void* p : {(void*)o->x, (void*)o->r, (void*)o->z, (void*)o->p, (void*)o->q, (void*)o->b, (void*)o->beta_pade,
+                    (void*)o->beta_close, (void*)o->part, (void*)o->scal, (void*)o->u, (void*)o->g, (void*)o->x32,
+                    (void*)o->r32, (void*)o->z32, (void*)o->p32, (void*)o->q32})
         ctx->dfree(p);
-    o->x = o->r = o->z = o->p = o->q = o->b = o->beta = o->u = o->g = nullptr;
+    o->x = o->r = o->z = o->p = o->q = o->b = o->beta = o->beta_pade = o->beta_close = o->u = o->g = nullptr;
     o->x32 = o->r32 = o->z32 = o->p32 = o->q32 = nullptr;
     o->part = o->scal = nullptr;
     for (auto& gr : o->graphs) cudaGraphExecDestroy(gr.exec);
@@ -1186,7 +1189,23 @@ static int ensure_osrc_batch(bem_ctx* ctx, OsrcState* o, int64_t R) {
     o->p = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
     o->q = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
     o->b = (double2*)ctx->dalloc(vec, &rc); if (rc) return rc;
-    o->beta = (double2*)ctx->dalloc((size_t)ms * o->n_dom * sizeof(double2), &rc); if (rc) return rc;
+    o->beta_pade = (double2*)ctx->dalloc((size_t)ms * o->n_dom * sizeof(double2), &rc); if (rc) return rc;
+    o->beta_close = (double2*)ctx->dalloc((size_t)2 * R * o->n_dom * sizeof(double2), &rc); if (rc) return rc;
+    {
+        // the shift tables, for every batch up to R (both repeat per right-hand side)
+        const int nd = o->n_dom, L = o->n_pade;
+        std::vector<double2> bp((size_t)ms * nd), bc((size_t)2 * R * nd);
+        for (int64_t s = 0; s < ms; s++)
+            for (int d = 0; d < nd; d++) bp[(size_t)s * nd + d] = o->B[(size_t)d * L + s % L];
+        for (int64_t rb = 0; rb < R; rb++)
+            for (int d = 0; d < nd; d++) {
+                bc[(size_t)(2 * rb) * nd + d] = make_double2(0, 0);
+                bc[(size_t)(2 * rb + 1) * nd + d] = o->inv_keps2[d];
+            }
+        CK(cudaMemcpyAsync(o->beta_pade, bp.data(), bp.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(o->beta_close, bc.data(), bc.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     o->part = (double*)ctx->dalloc((size_t)ms * o->nblk * 4 * sizeof(double), &rc); if (rc) return rc;
     o->scal = (double*)ctx->dalloc((size_t)ms * 8 * sizeof(double), &rc); if (rc) return rc;
     o->u = (double2*)ctx->dalloc((size_t)2 * R * n * sizeof(double2), &rc); if (rc) return rc;
@@ -1508,7 +1527,7 @@ static int cocg_solve_grid(bem_ctx* ctx, int n_sys) {
     // graph of GRAPH_ITERS iterations for this system count and tolerance
     cudaGraphExec_t exec = nullptr;
     for (auto& g : o->graphs)
-        if (g.n_sys == n_sys && g.tol == o->tol) exec = g.exec;
+        if (g.n_sys == n_sys && g.tol == o->tol && g.beta == o->beta) exec = g.exec;
     if (!exec) {
         if (!o->cap) CK(cudaStreamCreateWithFlags(&o->cap, cudaStreamNonBlocking));
         cudaGraph_t graph;
@@ -1517,7 +1536,7 @@ static int cocg_solve_grid(bem_ctx* ctx, int n_sys) {
         CK(cudaStreamEndCapture(o->cap, &graph));
         CK(cudaGraphInstantiate(&exec, graph, 0));
         CK(cudaGraphDestroy(graph));
-        o->graphs.push_back({n_sys, o->tol, exec});
+        o->graphs.push_back({n_sys, o->tol, o->beta, exec});
     }
     std::vector<double> sc(8 * n_sys);
     int it = 0;
@@ -1568,11 +1587,7 @@ int bem_ctx::apply_prec_batch(const double2* xin, double2* yout, int64_t R) {
     // Pade solves w_{rb,i,l} = (M - B_l S)^-1 row_i, systems ordered [rb][row][l],
     // the shift of system s on domain d at be[s][d]
     replicate_rows<<<dim3(nb, (unsigned)ns), SP_THREADS, 0, stream>>>(n, L, o->g, o->b);
-    const int nd = o->n_dom;
-    std::vector<double2> be((size_t)ns * nd);
-    for (int s = 0; s < ns; s++)
-        for (int d = 0; d < nd; d++) be[(size_t)s * nd + d] = o->B[(size_t)d * L + s % L];
-    CK(cudaMemcpyAsync(o->beta, be.data(), be.size() * sizeof(double2), cudaMemcpyHostToDevice, stream));
+    o->beta = o->beta_pade;  // (device tables built with the batch buffers: no host copy per application)
     if ((rc = cocg_solve(this, ns, L))) return rc;
     // brackets; row 1 scaled by i k (the DtN weak form)
     BracketArgs ba{};
@@ -1581,12 +1596,7 @@ int bem_ctx::apply_prec_batch(const double2* xin, double2* yout, int64_t R) {
     ba.out = o->b;
     bracket_kernel<<<dim3(nb, 2, (unsigned)R), SP_THREADS, 0, stream>>>(ba);
     // out1 = M^-1 (i k bracket_1);  out2 = (M - S/k_eps^2)^-1 bracket_2, then / (i k)
-    for (int64_t rb = 0; rb < R; rb++)
-        for (int d = 0; d < nd; d++) {
-            be[(size_t)(2 * rb) * nd + d] = make_double2(0, 0);
-            be[(size_t)(2 * rb + 1) * nd + d] = o->inv_keps2[d];
-        }
-    CK(cudaMemcpyAsync(o->beta, be.data(), (size_t)2 * R * nd * sizeof(double2), cudaMemcpyHostToDevice, stream));
+    o->beta = o->beta_close;
     if ((rc = cocg_solve(this, (int)(2 * R)))) return rc;
     BracketArgs cp{};  // scaled copy (no Pade terms): u_row = post_row * x_row
     cp.n = n; cp.rp = o->rp; cp.ci = o->ci; cp.vs = o->vs; cp.g = o->x; cp.w = nullptr; cp.L = 0;
