@@ -505,7 +505,8 @@ def serving_metrics(local, n_req=12, max_exc=16, rate=20.0, budget=150 << 30, to
         return {"p50_ms": float(np.percentile(lat, 50)) if lat else None,
                 "p99_ms": float(np.percentile(lat, 99)) if lat else None,
                 "wall_s": wall, "excitations_per_s": n_exc / wall, "requests_per_s": n_req / wall,
-                "batches": st["batches"] - warm["batches"], "peak_device_gib": st["peak_device_bytes"] / 2**30,
+                "batches": st["batches"] - warm["batches"], "joined_requests": st["joined"] - warm["joined"],
+                "peak_device_gib": st["peak_device_bytes"] / 2**30,
                 "evictions": st["evictions"], "warm_up_s": warm_s,
                 "iterations_per_excitation": {k: float(np.mean(v)) for k, v in its.items()},
                 "failed_requests": fails}

@@ -367,6 +367,10 @@ typedef struct {
     int64_t hbm_budget_bytes; /* device bytes all scenes may hold together (default 150 GiB; 0 = no limit) */
     bem_solve_opts solve;     /* options of every solve (default: mixed precision, batch_rhs = max_batch_rhs,
                                  block_gmres = 1, operator_mode = 2) */
+    int32_t join;             /* 1 (default): requests for a scene whose mixed-precision solve is running join
+                                 it at its next refinement boundary while the block (16 excitations with block
+                                 GMRES, else batch_rhs) has room and the budget holds the growth of the solve's
+                                 memory estimate.  0: they wait for the running solve to finish */
 } bem_server_opts;
 
 typedef struct {
@@ -384,6 +388,7 @@ typedef struct {
     int64_t device_bytes;     /* held by all scenes now */
     int64_t peak_device_bytes;
     int64_t evictions;
+    int64_t joined;           /* requests that joined a solve already running */
 } bem_server_stats;
 
 int bem_server_default_opts(bem_server_opts* opts);

@@ -46,7 +46,7 @@ class bem_solve_report(ctypes.Structure):
 
 class bem_server_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_batch_rhs", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
-                ("solve", bem_solve_opts)]
+                ("solve", bem_solve_opts), ("join", ctypes.c_int32)]
 
 
 class bem_server_stats(ctypes.Structure):
@@ -55,7 +55,7 @@ class bem_server_stats(ctypes.Structure):
                 ("mean_batch_exc", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("p50_wait_ms", ctypes.c_double), ("requests_per_s", ctypes.c_double),
                 ("excitations_per_s", ctypes.c_double), ("device_bytes", ctypes.c_int64),
-                ("peak_device_bytes", ctypes.c_int64), ("evictions", ctypes.c_int64)]
+                ("peak_device_bytes", ctypes.c_int64), ("evictions", ctypes.c_int64), ("joined", ctypes.c_int64)]
 
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3

@@ -286,11 +286,12 @@ class Server:
     and solved concurrently across scenes under one device-memory budget."""
 
     def __init__(self, device: int = 0, slots: int = 2, max_batch_rhs: int = 64, hbm_budget_bytes: int = 150 << 30,
-                 **solve):
+                 join: int = 1, **solve):
         self.lib = _lib.load()
         o = _lib.bem_server_opts()
         check(self.lib.bem_server_default_opts(ctypes.byref(o)))
         o.slots, o.max_batch_rhs, o.hbm_budget_bytes = int(slots), int(max_batch_rhs), int(hbm_budget_bytes)
+        o.join = int(join)
         names = {f[0] for f in o.solve._fields_}
         for k, v in solve.items():
             if k not in names:

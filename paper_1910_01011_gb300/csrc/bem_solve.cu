@@ -264,17 +264,24 @@ struct SolveState {
 }  // namespace gbem
 
 // Right-hand sides of every excitation into S->b (device).
-static int build_rhs(bem_ctx* ctx) {
+// r0 > 0 (excitations joined to a running solve): only excitations
+// [r0, r0 + count) are built, into storage already sized (capacity) by the
+// first call; the piston discs of that call are reused.
+static int build_rhs(bem_ctx* ctx, int64_t r0 = 0, int64_t count = -1, int64_t capacity = 0) {
     const Geometry& g = ctx->geo;
     SolveState* S = ctx->solve;
     const int64_t N = g.n_dof, nr = ctx->field_kind == 2 ? ctx->n_rhs : 1;
+    if (count < 0) count = nr - r0;
     int rc;
-    if (S->n_rhs_alloc < nr) {
+    if (r0 > 0 && (ctx->field_kind != 2 || S->n_rhs_alloc < r0 + count || !S->disc_df))
+        return ctx->fail(BEM_ERR_STATE, "joined excitations beyond the solve's capacity");
+    if (S->n_rhs_alloc < std::max(nr, capacity)) {
+        const int64_t cap = std::max(nr, capacity);
         for (void* p : {(void*)S->b, (void*)S->u, (void*)S->tri_rhs}) ctx->dfree(p);
-        S->b = (double2*)ctx->dalloc(nr * N * sizeof(double2), &rc); if (rc) return rc;
-        S->u = (double2*)ctx->dalloc(nr * N * sizeof(double2), &rc); if (rc) return rc;
-        S->tri_rhs = (double2*)ctx->dalloc(nr * g.n_slots * 6 * sizeof(double2), &rc); if (rc) return rc;
-        S->n_rhs_alloc = nr;
+        S->b = (double2*)ctx->dalloc(cap * N * sizeof(double2), &rc); if (rc) return rc;
+        S->u = (double2*)ctx->dalloc(cap * N * sizeof(double2), &rc); if (rc) return rc;
+        S->tri_rhs = (double2*)ctx->dalloc(cap * g.n_slots * 6 * sizeof(double2), &rc); if (rc) return rc;
+        S->n_rhs_alloc = cap;
     }
     if (ctx->field_kind == 1) {
         PlaneWaveArgs a{};
@@ -295,8 +302,8 @@ static int build_rhs(bem_ctx* ctx) {
         const int64_t ne = (int64_t)ctx->tr_r.size();
         std::vector<double> gx, gw;
         gauss_legendre01(n_r, gx, gw);
-        std::vector<double4> disc(ne * nq);
-        for (int64_t m = 0; m < ne; m++) {
+        std::vector<double4> disc(r0 > 0 ? 0 : ne * nq);
+        for (int64_t m = 0; m < (r0 > 0 ? 0 : ne); m++) {
             const double* c = &ctx->tr_c[3 * m];
             const double* nn = &ctx->tr_n[3 * m];
             const double a = ctx->tr_r[m];
@@ -336,19 +343,25 @@ static int build_rhs(bem_ctx* ctx) {
             split(ctx->tr_w[2 * i + 1], wsplit[i].z, wsplit[i].w);
         }
         if ((rc = ctx->ensure_fardf())) return rc;
-        for (void* p : {(void*)S->disc, (void*)S->wdev, (void*)S->disc_df, (void*)S->w_df}) ctx->dfree(p);
-        S->disc = (double4*)ctx->dalloc(disc.size() * sizeof(double4), &rc); if (rc) return rc;
+        if (r0 == 0) {
+            for (void* p : {(void*)S->disc, (void*)S->disc_df}) ctx->dfree(p);
+            S->disc = (double4*)ctx->dalloc(disc.size() * sizeof(double4), &rc); if (rc) return rc;
+            S->disc_df = (float4*)ctx->dalloc(dsplit.size() * sizeof(float4), &rc); if (rc) return rc;
+            CK(cudaMemcpyAsync(S->disc, disc.data(), disc.size() * sizeof(double4), cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(S->disc_df, dsplit.data(), dsplit.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                               ctx->stream));
+        }
+        // the weights of every excitation so far (joined ones included)
+        for (void* p : {(void*)S->wdev, (void*)S->w_df}) ctx->dfree(p);
         S->wdev = (double2*)ctx->dalloc(ctx->tr_w.size() * sizeof(double), &rc); if (rc) return rc;
-        S->disc_df = (float4*)ctx->dalloc(dsplit.size() * sizeof(float4), &rc); if (rc) return rc;
         S->w_df = (float4*)ctx->dalloc(std::max<size_t>(1, wsplit.size()) * sizeof(float4), &rc); if (rc) return rc;
-        CK(cudaMemcpyAsync(S->disc, disc.data(), disc.size() * sizeof(double4), cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(S->wdev, ctx->tr_w.data(), ctx->tr_w.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(S->disc_df, dsplit.data(), dsplit.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(S->w_df, wsplit.data(), wsplit.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
         PistonArgs a{};
         a.pg = ctx->dev.pg64; a.tc = ctx->dev.tc; a.slot_v = ctx->dev.slot_v; a.slot_n = ctx->dev.slot_n;
-        a.disc_h = S->disc_df; a.disc_l = S->disc_df + disc.size(); a.n_elem = (int)ne; a.nq = nq; a.w = S->w_df;
-        a.n_rhs = (int)nr;
+        a.disc_h = S->disc_df; a.disc_l = S->disc_df + ne * nq; a.n_elem = (int)ne; a.nq = nq;
+        a.w = S->w_df + r0 * ne;
+        a.n_rhs = (int)count;
         {
             float h, l, hi, li;
             split(ctx->k0re, h, l);
@@ -361,8 +374,8 @@ static int build_rhs(bem_ctx* ctx) {
         for (int q = 0; q < QP; q++)
             for (int k = 0; k < 3; k++) a.lam[q][k] = ctx->quad.lam[q][k];
         a.tri_out = S->tri_rhs;
-        CK(cudaMemsetAsync(S->tri_rhs, 0, nr * g.n_slots * 6 * sizeof(double2), ctx->stream));
-        const dim3 grid((unsigned)((g.n_slots + PK_SLOTS - 1) / PK_SLOTS), (unsigned)((nr + PK_RC - 1) / PK_RC));
+        CK(cudaMemsetAsync(S->tri_rhs, 0, count * g.n_slots * 6 * sizeof(double2), ctx->stream));
+        const dim3 grid((unsigned)((g.n_slots + PK_SLOTS - 1) / PK_SLOTS), (unsigned)((count + PK_RC - 1) / PK_RC));
         if (ctx->k0im != 0.0) piston_kernel<true><<<grid, PK_SLOTS * QP, 0, ctx->stream>>>(a);
         else piston_kernel<false><<<grid, PK_SLOTS * QP, 0, ctx->stream>>>(a);
         ctx->launches++;
@@ -370,11 +383,11 @@ static int build_rhs(bem_ctx* ctx) {
         return ctx->fail(BEM_ERR_STATE, "no incident field set");
     }
     CK(cudaGetLastError());
-    for (int64_t r = 0; r < nr; r++) {
+    for (int64_t r = 0; r < count; r++) {
         ReduceArgs ra{};
         ra.vc_ptr = ctx->dev.vc_ptr; ra.vc_idx = ctx->dev.vc_idx; ra.v_dof1 = ctx->dev.v_dof1;
         ra.v_dof2 = ctx->dev.v_dof2; ra.tri_out = S->tri_rhs + r * g.n_slots * 6; ra.v_begin = 0;
-        ra.v_end = g.n_vert; ra.y = S->b + r * N;
+        ra.v_end = g.n_vert; ra.y = S->b + (r0 + r) * N;
         CK(launch_reduce(ra, ctx->stream));
         ctx->launches++;
     }
@@ -542,13 +555,18 @@ static int ensure_batch_state(bem_ctx* ctx, int64_t R) {
 // Solve R = nb right-hand sides b[R][N] into u[R][N] with R GMRES runs in
 // lockstep (same method, tolerances and stopping rule per column as the
 // one-at-a-time path).
-static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, double2* u, int64_t R,
-                       bem_solve_report* rep, bool* converged) {
+// cap > R (a single-batch mixed solve with ctx->join_hook set): before each
+// refinement cycle the hook may hand over further excitations, which join as
+// new columns (their right-hand sides built into b, zero start) until the
+// block holds cap columns; R is then the final column count.
+static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, double2* u, int64_t& R,
+                       bem_solve_report* rep, bool* converged, int64_t cap = 0) {
     SolveState* S = ctx->solve;
     const int64_t N = ctx->geo.n_dof;
+    cap = std::max(cap, R);
     int rc;
-    if ((rc = ensure_batch_state(ctx, R))) return rc;
-    if ((rc = S->kry.ensure(ctx, N, o.restart, R))) return rc;
+    if ((rc = ensure_batch_state(ctx, cap))) return rc;
+    if ((rc = S->kry.ensure(ctx, N, o.restart, cap))) return rc;
     auto plain = [ctx, &o, N](const double2* X, double2* Y, int prec, int64_t nr) -> int {
         if (o.operator_mode == 1)
             return prec == BEM_PREC_FP64 ? ctx->apply_assembled64(X, Y, nr) : ctx->apply_assembled(X, Y, nr);
@@ -560,14 +578,14 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
         return BEM_OK;
     };
     const bool left = o.precondition && !o.flexible;
-    auto op_for = [ctx, left, plain, S, R](int prec) {
-        return [ctx, prec, left, plain, S, R](const double2* X, double2* Y) -> int {
+    auto op_for = [ctx, left, plain, S, &R](int prec) {
+        return [ctx, prec, left, plain, S, &R](const double2* X, double2* Y) -> int {
             if (!left) return plain(X, Y, prec, R);
             int e = plain(X, S->bt, prec, R);
             return e ? e : ctx->apply_prec_batch(S->bt, Y, R);
         };
     };
-    const Krylov::Op right = [ctx, R](const double2* X, double2* Y) -> int { return ctx->apply_prec_batch(X, Y, R); };
+    const Krylov::Op right = [ctx, &R](const double2* X, double2* Y) -> int { return ctx->apply_prec_batch(X, Y, R); };
     const Krylov::Op* rp = (o.precondition && o.flexible) ? &right : nullptr;
     auto rhs_of = [&](const double2* v) -> const double2* {
         if (!left) return v;
@@ -584,8 +602,8 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
         for (int64_t r = 0; r < R; r++) rel[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
         return BEM_OK;
     };
-    std::vector<double> bn(R), rel(R, 1.0), irel(R);
-    std::vector<int> its(R);
+    std::vector<double> bn(cap), rel(cap, 1.0), irel(cap);
+    std::vector<int> its(cap);
     if ((rc = S->kry.norms(ctx, b, R, bn.data()))) return rc;
     CK(cudaMemsetAsync(u, 0, R * N * sizeof(double2), ctx->stream));
     int it = 0;
@@ -609,10 +627,10 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
         double inner = o.tol;
         for (int attempt = 0; attempt < 4; attempt++) {
             if ((rc = inner_solve(op_for(BEM_PREC_FP64), sb, u, inner, attempt == 0, false))) return rc;
-            it += *std::max_element(its.begin(), its.end());
+            it += *std::max_element(its.begin(), its.begin() + R);
             for (int64_t r = 0; r < R; r++) rep->iterations += its[r];
             if ((rc = residual(rel, bn))) return rc;
-            worst = *std::max_element(rel.begin(), rel.end());
+            worst = *std::max_element(rel.begin(), rel.begin() + R);
             if (worst <= o.tol || it >= o.max_iter) break;
             inner *= 0.1;
         }
@@ -622,7 +640,25 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
         int ref = 0, inner_prec = BEM_PREC_FP32;
         double prev = 2.0;
         for (; ref <= o.max_refine; ref++) {
-            worst = *std::max_element(rel.begin(), rel.end());
+            if (R < cap && ctx->join_hook) {
+                // excitations that arrived while this block ran join it here
+                std::vector<double> w;
+                const int64_t k = ctx->join_hook(cap - R, w);
+                if (k > 0) {
+                    ctx->tr_w.insert(ctx->tr_w.end(), w.begin(), w.end());
+                    ctx->n_rhs += k;
+                    if ((rc = build_rhs(ctx, R, k))) return rc;
+                    if ((rc = S->kry.norms(ctx, b + R * N, k, bn.data() + R))) return rc;
+                    CK(cudaMemsetAsync(u + R * N, 0, k * N * sizeof(double2), ctx->stream));
+                    CK(cudaMemcpyAsync(S->br + R * N, b + R * N, k * N * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                       ctx->stream));
+                    for (int64_t r = R; r < R + k; r++) rel[r] = bn[r] > 0 ? 1.0 : 0.0;
+                    R += k;
+                    prev = 2.0;  // new columns start at residual 1: not a stalled refinement
+                    ref = std::min(ref, std::max(0, o.max_refine - 2));  // and get refinement cycles of their own
+                }
+            }
+            worst = *std::max_element(rel.begin(), rel.begin() + R);
             if (worst <= o.tol || it >= o.max_iter || ref == o.max_refine) break;
             // stalled refinement (reduced-precision operator error too large
             // for this conditioning): the remaining inner solves run in FP64
@@ -633,7 +669,7 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
             if ((rc = inner_solve(op_for(inner_prec), sr, S->bd, inner_tolerance(o, worst), true,
                                   inner_prec != BEM_PREC_FP64)))
                 return rc;
-            it += *std::max_element(its.begin(), its.end());
+            it += *std::max_element(its.begin(), its.begin() + R);
             for (int64_t r = 0; r < R; r++) rep->iterations += its[r];
             if ((rc = S->kry.axpby(ctx, 1.0, u, 1.0, S->bd, u, R * N))) return rc;
             if ((rc = residual(rel, bn))) return rc;
@@ -660,9 +696,15 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     if (rc) return rc;
     if ((rc = ctx->ensure_near())) return rc;
     if ((rc = ensure_solve_state(ctx))) return rc;
-    if ((rc = build_rhs(ctx))) return rc;
+    // a request loop may hand excitations to a running mixed solve (joined at
+    // refinement boundaries) while it is a single batch: room for a full block
+    const int64_t nr0 = ctx->field_kind == 2 ? ctx->n_rhs : 1;
+    const int64_t join_cap = std::max<int64_t>(1, solve_batch_width(o, std::max<int64_t>(o.batch_rhs, 1)));
+    const bool joinable = ctx->join_hook && o.precision == BEM_PREC_FP32 && ctx->field_kind == 2 && nr0 <= join_cap &&
+                          o.batch_rhs > 1;
+    if ((rc = build_rhs(ctx, 0, -1, joinable ? join_cap : 0))) return rc;
     SolveState* S = ctx->solve;
-    const int64_t N = ctx->geo.n_dof, nr = ctx->field_kind == 2 ? ctx->n_rhs : 1;
+    const int64_t N = ctx->geo.n_dof, nr = nr0;
     o.operator_mode = resolved_operator_mode(o.operator_mode, N);
     if ((rc = S->kry.ensure(ctx, N, o.restart))) return rc;
     // the preconditioner only has to be a fixed linear map to the accuracy the
@@ -699,17 +741,22 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     };
     const Krylov::Op right = [ctx](const double2* x, double2* y) -> int { return ctx->apply_prec(x, y); };
     const Krylov::Op* rp = (o.precondition && o.flexible) ? &right : nullptr;
-    if (o.batch_rhs > 1 && nr > 1) {
+    int64_t n_solved = nr;
+    if (joinable) {
+        int64_t Rb = nr;
+        if ((rc = solve_block(ctx, o, S->b, S->u, Rb, &R, &converged, join_cap))) return rc;
+        n_solved = Rb;
+    } else if (o.batch_rhs > 1 && nr > 1) {
         // blocks of up to batch_rhs excitations, GMRES in lockstep; block GMRES
         // takes at most BLOCK_COLS columns per block (its host-side band QR
         // update costs O(step x P^3)), the batch split evenly
         const int64_t width = solve_batch_width(o, nr);
         for (int64_t r0 = 0; r0 < nr; r0 += width) {
-            const int64_t Rb = std::min<int64_t>(width, nr - r0);
+            int64_t Rb = std::min<int64_t>(width, nr - r0);
             if ((rc = solve_block(ctx, o, S->b + r0 * N, S->u + r0 * N, Rb, &R, &converged))) return rc;
         }
     }
-    for (int64_t r = 0; r < (o.batch_rhs > 1 && nr > 1 ? 0 : nr); r++) {
+    for (int64_t r = 0; r < (joinable || (o.batch_rhs > 1 && nr > 1) ? 0 : nr); r++) {
         const double2* b = S->b + r * N;
         double2* u = S->u + r * N;
         double bnorm;
@@ -782,7 +829,7 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     }
     CK(cudaStreamSynchronize(ctx->stream));
     if ((rc = ctx->check_device_error())) return rc;
-    S->n_rhs_solved = nr;
+    S->n_rhs_solved = n_solved;
     R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (rep) *rep = R;
     if (!converged) return ctx->fail(BEM_ERR_NOT_CONVERGED, "GMRES did not reach the requested residual");

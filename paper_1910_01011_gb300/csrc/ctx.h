@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <functional>
 #include <string>
 #include <utility>
 #include <vector>
@@ -122,6 +123,10 @@ struct bem_ctx {
     } dfg;
     void* dfv_buf = nullptr;       // double-float densities and curls of the vectors of one call
     size_t dfv_bytes = 0;
+    // set by a request loop around bem_solve: at a refinement boundary of a
+    // single-batch mixed solve, hands over up to `room` more excitations
+    // (their weights appended to w, [k][n_elem] complex) and returns k
+    std::function<int64_t(int64_t room, std::vector<double>& w)> join_hook;
     int4* multi_work = nullptr;
     int64_t multi_n_work = 0;
     int multi_key[3] = {-1, -1, -1};  // (n_chunks, chunk_tiles, groups) the list was built for

@@ -34,6 +34,7 @@
 namespace gbem {
 void release_device_memory(bem_ctx* ctx);
 int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_opts& o);
+int64_t solve_batch_width(const bem_solve_opts& o, int64_t n_exc);
 int copy_solution(bem_ctx* ctx, int64_t rhs0, int64_t n, double2* host);
 }  // namespace gbem
 
@@ -84,13 +85,16 @@ struct bem_server {
     std::vector<std::thread> workers;
     // statistics
     std::vector<double> lat_ms, wait_ms;
-    int64_t done_req = 0, done_exc = 0, failed = 0, batches = 0, batch_exc_sum = 0, evictions = 0;
+    int64_t done_req = 0, done_exc = 0, failed = 0, batches = 0, batch_exc_sum = 0, evictions = 0, joined = 0;
     int64_t peak_pool = 0;
     Clock::time_point t_first, t_last;
     bool any = false;
 
     void worker();
     bool pick(std::vector<Request*>& group, Scene*& sc, int64_t& extra);
+    // joining running solves: mixed precision only (its refinement boundaries)
+    bool joins() const { return opts.join && opts.solve.precision == BEM_PREC_FP32 && opts.solve.batch_rhs > 1; }
+    int64_t join_cap() const { return solve_batch_width(opts.solve, opts.solve.batch_rhs); }
 };
 
 namespace {
@@ -208,8 +212,46 @@ void bem_server::worker() {
 
         bem_ctx* ctx = s->ctx;
         bem_solve_report rep{};
+        if (joins()) {
+            // later requests for this scene join at a refinement boundary (FIFO order, while they fit)
+            const int32_t scene_id = group.front()->scene;
+            ctx->join_hook = [this, scene_id, ctx, &group, &extra, n_cur = n](int64_t room,
+                                                                              std::vector<double>& w) mutable -> int64_t {
+                std::lock_guard<std::mutex> g(mu);
+                int64_t k = 0;
+                for (size_t qi = 0; qi < queue.size();) {
+                    Request* r = reqs[queue[qi]].get();
+                    if (r->scene != scene_id || r->retried || r->n_exc > room - k) {
+                        qi++;
+                        continue;
+                    }
+                    // the solve's estimate grows with the joined excitations: reserve the growth
+                    const int64_t add = std::max<int64_t>(
+                        0, estimate_solve_bytes(ctx, n_cur + k + r->n_exc, opts.solve) -
+                               estimate_solve_bytes(ctx, n_cur + k, opts.solve));
+                    if (opts.hbm_budget_bytes > 0 && pool.load() + reserved + add > opts.hbm_budget_bytes) {
+                        qi++;
+                        continue;
+                    }
+                    reserved += add;
+                    extra += add;
+                    r->state = BEM_REQ_RUNNING;
+                    r->t_start = Clock::now();
+                    w.insert(w.end(), r->w.begin(), r->w.end());
+                    k += r->n_exc;
+                    group.push_back(r);
+                    queue.erase(queue.begin() + qi);
+                    joined++;
+                }
+                n_cur += k;
+                return k;
+            };
+        }
         int rc = bem_set_excitations(ctx, (const bem_z*)W.data(), n);
         if (!rc) rc = bem_solve(ctx, &opts.solve, &rep);
+        ctx->join_hook = nullptr;
+        n = 0;
+        for (Request* r : group) n += r->n_exc;  // joined requests included
         const bool converged_fail = rc == BEM_ERR_NOT_CONVERGED;
         std::string err = rc ? bem_last_error(ctx) : std::string();
         std::vector<double2> U;
@@ -275,6 +317,7 @@ int bem_server_default_opts(bem_server_opts* o) {
     o->solve.batch_rhs = 64;
     o->solve.block_gmres = 1;
     o->solve.operator_mode = 2;
+    o->join = 1;
     return BEM_OK;
 }
 
@@ -284,7 +327,8 @@ int bem_server_create(bem_server** out, int device, const bem_server_opts* opts)
     bem_server_opts o;
     bem_server_default_opts(&o);
     if (opts) o = *opts;
-    if (o.slots < 1 || o.slots > 64 || o.max_batch_rhs < 1 || o.hbm_budget_bytes < 0) return BEM_ERR_INVALID_ARG;
+    if (o.slots < 1 || o.slots > 64 || o.max_batch_rhs < 1 || o.hbm_budget_bytes < 0 || o.join < 0 || o.join > 1)
+        return BEM_ERR_INVALID_ARG;
     int n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return BEM_ERR_CUDA;
     bem_server* s = new (std::nothrow) bem_server();
@@ -457,6 +501,7 @@ int bem_server_get_stats(bem_server* s, bem_server_stats* st) {
     st->device_bytes = s->pool.load();
     st->peak_device_bytes = std::max(s->peak_pool, s->pool.load());
     st->evictions = s->evictions;
+    st->joined = s->joined;
     return BEM_OK;
 }
 

@@ -181,3 +181,38 @@ def test_two_scenes_overlap_on_the_device(api):
     print("solo", solo, "together", both, "most running", most)
     assert most == 2
     assert both < 0.85 * sum(solo)
+
+
+def test_request_joins_a_running_solve(api):
+    """A request for a scene whose mixed solve is already running joins it at
+    its next refinement boundary instead of waiting for it to finish: the
+    server counts the join, the late request is solved in the same batch
+    (batch size 2 + 1), and every excitation of both requests matches the
+    oracle's dense solve.  (Joining is timed against a running solve; the
+    late request is submitted as soon as the first one runs, up to three
+    tries.)"""
+    import time
+    rng = np.random.default_rng(41)
+    wA = np.exp(2j * np.pi * rng.random((2, 6)))
+    wB = np.exp(2j * np.pi * rng.random((1, 6)))
+    for attempt in range(3):
+        srv, ids = make_server(api, ["two"], slots=1, max_batch_rhs=8)
+        sid = ids["two"]
+        h = srv.submit(sid, wA[:1])  # set-up outside the experiment
+        srv.wait(h)
+        srv.result(h, 1, sid)
+        hA = srv.submit(sid, wA)
+        while srv.poll(hA) == 0:
+            time.sleep(0.0002)
+        hB = srv.submit(sid, wB)
+        assert srv.wait(hA, 600) == 2 and srv.wait(hB, 600) == 2
+        UA, repA = srv.result(hA, 2, sid)
+        UB, repB = srv.result(hB, 1, sid)
+        st = srv.stats()
+        srv.close()
+        if st["joined"] >= 1:
+            break
+    assert st["joined"] >= 1 and repB["batch_exc"] == 3 and repA["batch_exc"] == 3
+    for U, W in ((UA, wA), (UB, wB)):
+        for r in range(W.shape[0]):
+            assert rel(U[r], oracle_solution("two", 0, W[r])) < 1e-6
