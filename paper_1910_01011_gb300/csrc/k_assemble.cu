@@ -18,6 +18,7 @@
 #include <cstdint>
 
 #include "ctx.h"
+#include "df_math.cuh"
 #include "internal.h"
 
 namespace gbem {
@@ -272,6 +273,173 @@ __global__ void __launch_bounds__(TT) assemble64_kernel(AssembleArgs a, const do
     }
 }
 
+// The same assembly with the kernel values and their P1 moments in
+// double-float FP32 arithmetic (df_math.cuh), about 1e-13 relative, and the
+// coefficient epilogue in FP64 from the converted moments: GB300 runs FP64 at
+// ~1/64 of the FP32 rate, and the 36 point pairs of a triangle pair dominate.
+struct AssembleDf {
+    const float4 *pgh, *pgl, *tgh, *tgl, *tch, *tcl;  // split geometry (bem_ctx::ensure_fardf)
+    const float4* kdf;        // [n_dom] (Re k hi, lo, Im k hi, lo)
+    float4 k0df;
+    const float4* sctab;
+    const float2* extab;
+    DfConsts c;
+    float lamh[QP][3], laml[QP][3];  // P1 values at the rule points
+    float i4h, i4l;                  // 1 / (4 pi)
+};
+
+template <bool ATTEN>
+__device__ __forceinline__ void assembledf_body(const AssembleArgs& a, const AssembleDf& d, double2* A64,
+                                                const float4* __restrict__ tab, const float2* __restrict__ etab) {
+    const int tt = blockIdx.x;
+    const int tl = threadIdx.x;
+    const int64_t ts = (int64_t)tt * TT + tl;
+    const int4 tv = a.slot_v[ts];
+    if (tv.x < 0) return;
+    const int dom = tv.w;
+    const int2 dr = a.dom_tiles[dom];
+    int sb = blockIdx.y * a.chunk_tiles, se = min(sb + a.chunk_tiles, a.n_tiles);
+    if (a.slot == 1) {
+        sb = max(sb, dr.x);
+        se = min(se, dr.y);
+    }
+    if (sb >= se) return;
+    const float4 kk = a.slot == 0 ? d.k0df : d.kdf[dom];
+    const dfl kr = {kk.x, kk.y}, ki = {kk.z, kk.w};
+    const SlotCoef cf = a.coef[dom * 2 + a.slot];
+    const float4 nh = d.tgh[ts], nl = d.tgl[ts];
+    const dfl ngx = {nh.x, nl.x}, ngy = {nh.y, nl.y}, ngz = {nh.z, nl.z};
+    const float4 cth = d.tch[tt], ctl = d.tcl[tt];
+    const int64_t ra[3] = {a.v_dof1[tv.x], a.v_dof1[tv.y], a.v_dof1[tv.z]};
+    const int64_t rb[3] = {a.v_dof2[tv.x], a.v_dof2[tv.y], a.v_dof2[tv.z]};
+    const dfl i4 = {d.i4h, d.i4l};
+    for (int s = sb; s < se; s++) {
+        const float4 csh = d.tch[s], csl = d.tcl[s];
+        const dfl Dx = dsub(dfl{cth.x, ctl.x}, dfl{csh.x, csl.x});
+        const dfl Dy = dsub(dfl{cth.y, ctl.y}, dfl{csh.y, csl.y});
+        const dfl Dz = dsub(dfl{cth.z, ctl.z}, dfl{csh.z, csl.z});
+        const int ntri = a.tntri[s];
+        for (int sl = 0; sl < ntri; sl++) {
+            const int64_t ss = (int64_t)s * TT + sl;
+            if (ss == ts) continue;
+            const float4 sgh = d.tgh[ss], sgl = d.tgl[ss];
+            const dfl snx = {sgh.x, sgl.x}, sny = {sgh.y, sgl.y}, snz = {sgh.z, sgl.z}, sh = {sgh.w, sgl.w};
+            dfl V[3][3][2], K[3][3][2], Kp[3][3][2];
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int b = 0; b < 3; b++)
+#pragma unroll
+                    for (int c = 0; c < 2; c++) V[i][b][c] = K[i][b][c] = Kp[i][b][c] = dfl{0.0f, 0.0f};
+            for (int qx = 0; qx < QP; qx++) {
+                const float4 xh = d.pgh[ts * QP + qx], xl = d.pgl[ts * QP + qx];
+                const dfl Xx = dadd(dfl{xh.x, xl.x}, Dx), Xy = dadd(dfl{xh.y, xl.y}, Dy), Xz = dadd(dfl{xh.z, xl.z}, Dz);
+                const dfl fK = dsub(sh, dadd(dadd(dmul(snx, Xx), dmul(sny, Xy)), dmul(snz, Xz)));
+                dfl hV[3][2], hK[3][2], hKp[3][2];
+#pragma unroll
+                for (int b = 0; b < 3; b++)
+#pragma unroll
+                    for (int c = 0; c < 2; c++) hV[b][c] = hK[b][c] = hKp[b][c] = dfl{0.0f, 0.0f};
+                for (int qy = 0; qy < QP; qy++) {
+                    const float4 yh = d.pgh[ss * QP + qy], yl = d.pgl[ss * QP + qy];
+                    const dfl ex = dsub(Xx, dfl{yh.x, yl.x}), ey = dsub(Xy, dfl{yh.y, yl.y}), ez = dsub(Xz, dfl{yh.z, yl.z});
+                    dfl r, ri;
+                    dsqrt_rinv(dadd(dadd(dsqr(ex), dsqr(ey)), dsqr(ez)), r, ri);
+                    dfl sn, cs;
+                    dsincos(dmul(kr, r), d.c, tab, sn, cs);
+                    const dfl am = ATTEN ? dmul(dexp_neg(dmul(ki, r), d.c, etab), ri) : ri;
+                    const dfl Gr = dmul(am, cs), Gi = dmul(am, sn);
+                    const dfl u = dsub(dneg(ki), ri);
+                    const dfl Fr = dmul(dsub(dmul(Gr, u), dmul(Gi, kr)), ri);
+                    const dfl Fi = dmul(dadd(dmul(Gr, kr), dmul(Gi, u)), ri);
+                    const dfl ndot = dadd(dadd(dmul(ngx, ex), dmul(ngy, ey)), dmul(ngz, ez));
+                    const dfl nFr = dmul(ndot, Fr), nFi = dmul(ndot, Fi);
+                    const dfl yw = {yh.w, yl.w};
+#pragma unroll
+                    for (int b = 0; b < 3; b++) {
+                        const dfl wl = dmul(yw, dfl{d.lamh[qy][b], d.laml[qy][b]});
+                        dmac(hV[b][0], wl, Gr, 1.0f);
+                        dmac(hV[b][1], wl, Gi, 1.0f);
+                        dmac(hK[b][0], wl, Fr, 1.0f);
+                        dmac(hK[b][1], wl, Fi, 1.0f);
+                        dmac(hKp[b][0], wl, nFr, 1.0f);
+                        dmac(hKp[b][1], wl, nFi, 1.0f);
+                    }
+                }
+                const dfl xw = dmul(dfl{xh.w, xl.w}, i4);
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    const dfl wx = dmul(xw, dfl{d.lamh[qx][i], d.laml[qx][i]});
+                    const dfl wk = dmul(wx, fK);
+#pragma unroll
+                    for (int b = 0; b < 3; b++)
+#pragma unroll
+                        for (int c = 0; c < 2; c++) {
+                            dmac(V[i][b][c], wx, hV[b][c], 1.0f);
+                            dmac(K[i][b][c], wk, hK[b][c], 1.0f);
+                            dmac(Kp[i][b][c], wx, hKp[b][c], 1.0f);
+                        }
+                }
+            }
+            // epilogue in FP64 (as assemble64_kernel) from the converted moments
+            double Vd[3][3][2];
+            double sr = 0, si = 0;
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int b = 0; b < 3; b++) {
+                    Vd[i][b][0] = (double)V[i][b][0].h + (double)V[i][b][0].l;
+                    Vd[i][b][1] = (double)V[i][b][1].h + (double)V[i][b][1].l;
+                    sr += Vd[i][b][0];
+                    si += Vd[i][b][1];
+                }
+            const double nn = ((double)ngx.h + ngx.l) * ((double)snx.h + snx.l) +
+                              ((double)ngy.h + ngy.l) * ((double)sny.h + sny.l) +
+                              ((double)ngz.h + ngz.l) * ((double)snz.h + snz.l);
+            const int4 sv = a.slot_v[ss];
+            const int vb[3] = {sv.x, sv.y, sv.z};
+            for (int b = 0; b < 3; b++) {
+                const int64_t ca = a.v_dof1[vb[b]], cb = a.v_dof2[vb[b]];
+                for (int i = 0; i < 3; i++) {
+                    double cc = 0;
+                    for (int c = 0; c < 3; c++) cc += a.slot_curl[ts * 9 + 3 * i + c] * a.slot_curl[ss * 9 + 3 * b + c];
+                    const double kvr = cf.k2re * Vd[i][b][0] - cf.k2im * Vd[i][b][1];
+                    const double kvi = cf.k2re * Vd[i][b][1] + cf.k2im * Vd[i][b][0];
+                    const double Kr = (double)K[i][b][0].h + (double)K[i][b][0].l;
+                    const double Ki = (double)K[i][b][1].h + (double)K[i][b][1].l;
+                    const double Pr = (double)Kp[i][b][0].h + (double)Kp[i][b][0].l;
+                    const double Pi = (double)Kp[i][b][1].h + (double)Kp[i][b][1].l;
+                    double* e;
+                    e = reinterpret_cast<double*>(&A64[ra[i] * a.n + ca]);
+                    atomicAdd(e, cf.cV * Vd[i][b][0]);
+                    atomicAdd(e + 1, cf.cV * Vd[i][b][1]);
+                    e = reinterpret_cast<double*>(&A64[ra[i] * a.n + cb]);
+                    atomicAdd(e, -cf.cK * Kr);
+                    atomicAdd(e + 1, -cf.cK * Ki);
+                    e = reinterpret_cast<double*>(&A64[rb[i] * a.n + ca]);
+                    atomicAdd(e, cf.cKp * Pr);
+                    atomicAdd(e + 1, cf.cKp * Pi);
+                    e = reinterpret_cast<double*>(&A64[rb[i] * a.n + cb]);
+                    atomicAdd(e, cf.cW * (cc * sr - nn * kvr));
+                    atomicAdd(e + 1, cf.cW * (cc * si - nn * kvi));
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TT) assembledf_kernel(AssembleArgs a, AssembleDf d, double2* A64) {
+    __shared__ float4 tab[128];
+    __shared__ float2 etab[64];
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) tab[i] = d.sctab[i];
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) etab[i] = d.extab[i];
+    __syncthreads();
+    const int4 tv = a.slot_v[(int64_t)blockIdx.x * TT + threadIdx.x];
+    const float4 kk = a.slot == 0 ? d.k0df : d.kdf[tv.x >= 0 ? tv.w : 0];
+    if (kk.z != 0.0f || kk.w != 0.0f) assembledf_body<true>(a, d, A64, tab, etab);
+    else assembledf_body<false>(a, d, A64, tab, etab);
+}
+
 __global__ void add_near64_kernel(int64_t n_pairs, const int32_t* pair_tgt, const int32_t* pair_src,
                                   const int4* slot_v, const int64_t* v_dof1, const int64_t* v_dof2,
                                   const double2* nb64, int64_t n, double2* A) {
@@ -406,9 +574,27 @@ int bem_ctx::ensure_assembled64() {
     for (int q = 0; q < QP; q++)
         for (int k = 0; k < 3; k++) a.lam64[q][k] = quad.lam[q][k];
     const dim3 grid(g.n_tiles, (g.n_tiles + a.chunk_tiles - 1) / a.chunk_tiles);
+    AssembleDf d{};
+    if (opts.fp64_far == 0) {  // double-float kernel values (the default), else native FP64
+        if ((rc = ensure_fardf())) return rc;
+        d.pgh = dfg.pgh; d.pgl = dfg.pgl; d.tgh = dfg.tgh; d.tgl = dfg.tgl; d.tch = dfg.tch; d.tcl = dfg.tcl;
+        d.kdf = dfg.kdf; d.sctab = dfg.sctab; d.extab = dfg.extab; d.c = dfg.c;
+        auto split = [](long double v, float& h, float& l) {
+            h = (float)v;
+            l = (float)(v - (long double)h);
+        };
+        float h, l, ih, il;
+        split((long double)k0re, h, l);
+        split((long double)k0im, ih, il);
+        d.k0df = make_float4(h, l, ih, il);
+        for (int q = 0; q < QP; q++)
+            for (int k = 0; k < 3; k++) split((long double)quad.lam[q][k], d.lamh[q][k], d.laml[q][k]);
+        split(1.0L / (4.0L * 3.141592653589793238462643383279502884L), d.i4h, d.i4l);
+    }
     for (int sl = 0; sl < 2; sl++) {
         a.slot = sl;
-        assemble64_kernel<<<grid, TT, 0, stream>>>(a, dev.pg64, dev.tg64, asm64);
+        if (opts.fp64_far == 0) assembledf_kernel<<<grid, TT, 0, stream>>>(a, d, asm64);
+        else assemble64_kernel<<<grid, TT, 0, stream>>>(a, dev.pg64, dev.tg64, asm64);
         CK(cudaGetLastError());
     }
     const int64_t np = pmchwt_near.n_pairs;
