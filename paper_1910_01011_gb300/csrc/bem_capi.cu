@@ -317,8 +317,16 @@ int bem_ctx::finalize() {
     for (int64_t s = 0; s < g.n_slots; s++)
         for (int64_t i = g.np_ptr[s]; i < g.np_ptr[s + 1]; i++) ptgt[i] = (int32_t)s;
     if ((rc = upload(this, &d.np_tgt, ptgt))) return rc;
-    for (int r = 0; r <= 3; r++)  // 0: the near-pair rule, 1-3: Sauter-Schwab
+    for (int r = 0; r <= 3; r++) {  // 0: the near-pair rule, 1-3: Sauter-Schwab
         if ((rc = upload(this, &d.ss_tab[r], quad.ss[r]))) return rc;
+        const size_t m = quad.ss[r].size();
+        std::vector<float> f(2 * m);  // double-float copy for the near build
+        for (size_t i = 0; i < m; i++) {
+            f[i] = (float)quad.ss[r][i];
+            f[m + i] = (float)(quad.ss[r][i] - (double)f[i]);
+        }
+        if ((rc = upload(this, &d.ss_tabf[r], f))) return rc;
+    }
     // working buffers
     d.pd32 = (float4*)dalloc(g.n_pts * sizeof(float4), &rc); if (rc) return rc;
     d.tcurl32 = (float4*)dalloc(2 * g.n_slots * sizeof(float4), &rc); if (rc) return rc;
@@ -392,6 +400,23 @@ int bem_ctx::build_near(NearSet& ns, int n_slot_k, double kre, double kim, const
         a.slot_dom = (const int*)dev.slot_v;
         a.n_slot_k = n_slot_k;
         a.raw = raw;
+        if (opts.fp64_far == 0) {  // double-float point evaluations (the default), else native FP64
+            if ((rc = ensure_fardf())) return rc;
+            a.use_df = 1;
+            for (int r = 0; r <= 3; r++) a.ss_tabf[r] = dev.ss_tabf[r];
+            a.sctab = dfg.sctab;
+            a.extab = dfg.extab;
+            a.c = dfg.c;
+            a.kdf = dfg.kdf;
+            auto split = [](long double v, float& h, float& l) {
+                h = (float)v;
+                l = (float)(v - (long double)h);
+            };
+            split((long double)kre, a.k0df.x, a.k0df.y);
+            split((long double)kim, a.k0df.z, a.k0df.w);
+            for (int q = 0; q < 3 * QP; q++) split((long double)a.rule[q], a.rule_h[q], a.rule_l[q]);
+            split(1.0L / (4.0L * 3.141592653589793238462643383279502884L), a.i4h, a.i4l);
+        }
         CK(launch_near_build(a, stream));
         NearCombineArgs c{};
         c.n_pairs = nb;

@@ -27,6 +27,7 @@ struct DeviceGeom {
     int64_t* np_ptr = nullptr;
     int32_t *np_src = nullptr, *np_code = nullptr, *np_tgt = nullptr;
     double* ss_tab[4] = {nullptr, nullptr, nullptr, nullptr};
+    float* ss_tabf[4] = {nullptr, nullptr, nullptr, nullptr};  // the same as (hi [5 n], lo [5 n]) floats
     // working buffers
     float4 *pd32 = nullptr, *tcurl32 = nullptr;
     double4 *pd64 = nullptr, *tcurl64 = nullptr;

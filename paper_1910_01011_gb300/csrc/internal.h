@@ -292,6 +292,17 @@ struct NearArgs {
     const int* slot_dom;        // via slot_v.w
     int n_slot_k;               // 1 or 2
     double2* raw;               // [pair][slot][27]: V, K, K' (SS minus regular)
+    // double-float point evaluations (use_df): tables as (hi, lo) floats,
+    // sin / cos / exp tables and constants, wavenumbers, regular rule, 1 / (4 pi)
+    int use_df;
+    const float* ss_tabf[4];
+    const float4* sctab;
+    const float2* extab;
+    DfConsts c;
+    const float4* kdf;
+    float4 k0df;
+    float rule_h[3 * QP], rule_l[3 * QP];
+    float i4h, i4l;
 };
 
 struct NearCombineArgs {
