@@ -91,13 +91,14 @@ def test_context_rebuilds_after_adding_a_domain():
 def test_fp64_assembled_operator_matches_oracle(name):
     """BEM_PREC_FP64_ASSEMBLED: A_hat assembled in complex128 and applied by
     the FP64-accurate split-FP32 product (the FP64 refinement residual), FP64
-    bar 1e-11, for 1, 2 and 5 right-hand sides (the three launch shapes)."""
+    bar 1e-11, for 1, 2, 5 and 9 right-hand sides (the launch shapes, 9 = a
+    group of eight and a ragged one)."""
     from paper_1910_01011_gb300 import api
     s = {"sphere": lambda: scenes.sphere_scene(2), "shell": lambda: scenes.shell_scene(1)}[name]()
     A = pmchwt.assemble(s)
     c = api.Context.from_scene(s)
     rng = np.random.default_rng(6)
-    for n_rhs in (1, 2, 5):
+    for n_rhs in (1, 2, 5, 9):
         X = rng.standard_normal((n_rhs, A.shape[0])) + 1j * rng.standard_normal((n_rhs, A.shape[0]))
         Y = c.apply(X, precision=api.FP64_ASSEMBLED)
         ref = X @ A.T
