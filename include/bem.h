@@ -202,10 +202,11 @@ typedef struct {
                               operators take at most 4 GiB (36 N^2 bytes, N <= 10,922), else
                               matrix-free */
     int32_t batch_rhs;     /* >1: excitations are solved in blocks of up to batch_rhs right-hand sides,
-                              R independent GMRES runs in lockstep whose operator and preconditioner
-                              applications act on all R columns at once (one GEMM per application with
-                              operator_mode 1); each column stops on its own residual.  0 or 1: one
-                              excitation after another (default).  The results do not depend on it. */
+                              R independent GMRES runs in lockstep (or one block GMRES, block_gmres) whose
+                              operator and preconditioner applications act on all R columns at once (one
+                              GEMM per application with operator_mode 1); each column stops on its own
+                              residual.  0 or 1: one excitation after another (default).  The results do
+                              not depend on it (within the tolerance). */
     int32_t flexible;      /* 1 (default): the preconditioner is applied on the right, u = P y, inside a
                               flexible GMRES that keeps the preconditioned basis, so its sparse solves may
                               stop at the loose tolerance prec_tol; GMRES then measures the residual of
