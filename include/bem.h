@@ -89,7 +89,7 @@ typedef struct {
                                   depends on it; k_j needed 1.3-2.1x fewer iterations on every scene measured */
     int32_t fp64_far;          /* far field of the FP64 matrix-free operator: 0 (default) double-float arithmetic
                                   on the FP32 pipes (pairs of FP32 numbers, ~1e-13 relative, phases below
-                                  ~6,000 rad), 1 native FP64 (GB300 runs FP64 at ~1/64 of the FP32 rate) */
+                                  ~100,000 rad), 1 native FP64 (GB300 runs FP64 at ~1/64 of the FP32 rate) */
 } bem_opts;
 
 /* Fill opts with the defaults above. */

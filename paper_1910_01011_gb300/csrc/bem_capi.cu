@@ -401,7 +401,7 @@ int bem_ctx::build_near(NearSet& ns, int n_slot_k, double kre, double kim, const
         a.n_slot_k = n_slot_k;
         a.raw = raw;
         if (opts.fp64_far == 0) {  // double-float point evaluations (the default), else native FP64
-            if ((rc = ensure_fardf())) return rc;
+            if ((rc = ensure_fardf()) || (rc = check_df_phase(kre, false))) return rc;
             a.use_df = 1;
             for (int r = 0; r <= 3; r++) a.ss_tabf[r] = dev.ss_tabf[r];
             a.sctab = dfg.sctab;

@@ -342,7 +342,7 @@ static int build_rhs(bem_ctx* ctx, int64_t r0 = 0, int64_t count = -1, int64_t c
             split(ctx->tr_w[2 * i], wsplit[i].x, wsplit[i].y);
             split(ctx->tr_w[2 * i + 1], wsplit[i].z, wsplit[i].w);
         }
-        if ((rc = ctx->ensure_fardf())) return rc;
+        if ((rc = ctx->ensure_fardf()) || (rc = ctx->check_df_phase(ctx->k0re, true))) return rc;
         if (r0 == 0) {
             for (void* p : {(void*)S->disc, (void*)S->disc_df}) ctx->dfree(p);
             S->disc = (double4*)ctx->dalloc(disc.size() * sizeof(double4), &rc); if (rc) return rc;

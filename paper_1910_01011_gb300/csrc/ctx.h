@@ -187,6 +187,8 @@ struct bem_ctx {
     int apply_ahat_multi(const double2* x, double2* y, int64_t n_rhs);
     int apply_ahat64_multi(const double2* x, double2* y, int64_t n_rhs);
     int ensure_fardf();
+    double df_extent(bool with_transducer) const;
+    int check_df_phase(double kre, bool with_transducer);
     int far_df(const double4* pd, const double4* cu, int64_t R, int tgt_b, int tgt_e, int src_b, int src_e,
                int chunk_tiles, int n_chunks, int slot1, double kre, double kim, double* partial, int64_t rstride);
     int apply_prec(const double2* x, double2* y);

@@ -6,8 +6,9 @@
 // explicit round-to-nearest intrinsics, so the compiler fuses nothing.
 //  * dsqrt_rinv: FP32 square root and reciprocal, one Newton step each.
 //  * dsincos: Cody and Waite's additive reduction of the phase by multiples of
-//    pi/64 held in four FP32 parts (the first with 7 significant bits, so the
-//    reduction is exact below ~6,000 rad), Taylor series of the remainder
+//    pi/64 held in four FP32 parts (the first with 3 significant bits, so its
+//    product with the multiple n is exact for n < 2^21, phases below ~100,000
+//    rad; the next two products are formed exactly), Taylor series of the remainder
 //    |d| <= pi/128 (d^3 and d^2 terms in double-float, the rest in FP32), and
 //    a 128-entry double-float table of sin, cos (j pi/64) combined by the
 //    addition theorem (table-driven method in the manner of Tang).
@@ -85,15 +86,17 @@ __device__ __forceinline__ void dsqrt_rinv(dfl R, dfl& r, dfl& ri) {
 __device__ __forceinline__ void dsincos(dfl th, const DfConsts& A, const float4* __restrict__ tab, dfl& sn, dfl& cs) {
     const float nf = rintf(__fmul_rn(th.h, A.inv_pi64));
     const float r1 = __fsub_rn(th.h, __fmul_rn(nf, A.pi64[0]));  // exact (n (pi/64)_1 is exact and near th)
-    const dfl p2 = two_prod(nf, A.pi64[1]);
+    const dfl p2 = two_prod(nf, A.pi64[1]);                       // n (pi/64)_2 and n (pi/64)_3 exactly
+    const dfl p3 = two_prod(nf, A.pi64[2]);
     const dfl s = two_sum(r1, -p2.h);
-    float lo = __fsub_rn(s.l, p2.l);
-    lo = __fmaf_rn(-nf, A.pi64[2], lo);
+    const dfl t = two_sum(s.h, -p3.h);
+    float lo = __fsub_rn(__fsub_rn(s.l, p2.l), p3.l);
+    lo = __fadd_rn(lo, t.l);
     lo = __fmaf_rn(-nf, A.pi64[3], lo);
     lo = __fadd_rn(lo, th.l);
-    const dfl d = fast_two_sum(s.h, lo);
-    const float4 t = tab[((int)nf) & 127];
-    const dfl sa = {t.x, t.y}, ca = {t.z, t.w};
+    const dfl d = two_sum(t.h, lo);
+    const float4 ta = tab[((int)nf) & 127];
+    const dfl sa = {ta.x, ta.y}, ca = {ta.z, ta.w};
     const dfl d2 = dsqr(d);
     // sin d = d - d^3 / 6 + d^5 / 120 - d^7 / 5040
     const dfl d3 = dmul(d, d2);

@@ -576,7 +576,7 @@ int bem_ctx::ensure_assembled64() {
     const dim3 grid(g.n_tiles, (g.n_tiles + a.chunk_tiles - 1) / a.chunk_tiles);
     AssembleDf d{};
     if (opts.fp64_far == 0) {  // double-float kernel values (the default), else native FP64
-        if ((rc = ensure_fardf())) return rc;
+        if ((rc = ensure_fardf()) || (rc = check_df_phase(k0re, false))) return rc;
         d.pgh = dfg.pgh; d.pgl = dfg.pgl; d.tgh = dfg.tgh; d.tgl = dfg.tgl; d.tch = dfg.tch; d.tcl = dfg.tcl;
         d.kdf = dfg.kdf; d.sctab = dfg.sctab; d.extab = dfg.extab; d.c = dfg.c;
         auto split = [](long double v, float& h, float& l) {

@@ -13,8 +13,8 @@
 //  * r = |x - y| and 1/r: FP32 square root and reciprocal, then one Newton
 //    step each in double-float (relative error ~4e-15);
 //  * e^{ikr}: the phase k r is reduced by multiples of pi/64 held in four
-//    FP32 parts (Cody and Waite's additive reduction; the first part has 7
-//    significant bits, so n (pi/64)_1 is exact for phases below ~6,000 rad),
+//    FP32 parts (Cody and Waite's additive reduction; the first part has 3
+//    significant bits, so n (pi/64)_1 is exact for phases below ~100,000 rad),
 //    then sin and cos of the remainder |d| <= pi/128 by their Taylor series
 //    (the d^3 and d^2 terms in double-float, the rest in FP32) combined with
 //    a 128-entry double-float table of sin and cos (j pi/64) by the addition
@@ -31,6 +31,7 @@
 // the same projection), at ~1e-13 relative instead of ~1e-16.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -248,6 +249,41 @@ float round_bits(long double v, int bits) {
 
 }  // namespace
 
+// Largest phase |Re k| |x - y| the double-float reduction handles (n (pi/64)_1
+// exact for n < 2^21), with a margin.
+constexpr double DF_PHASE_MAX = 1.0e5;
+
+// Extent of the mesh (and of the transducer's pistons if `with_transducer`):
+// the diagonal of the box around every tile's bounding sphere.
+double bem_ctx::df_extent(bool with_transducer) const {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int t = 0; t < geo.n_tiles; t++)
+        for (int c = 0; c < 3; c++) {
+            lo[c] = std::min(lo[c], geo.tile_c[4 * t + c] - geo.tile_c[4 * t + 3]);
+            hi[c] = std::max(hi[c], geo.tile_c[4 * t + c] + geo.tile_c[4 * t + 3]);
+        }
+    if (with_transducer)
+        for (size_t m = 0; m < tr_r.size(); m++)
+            for (int c = 0; c < 3; c++) {
+                lo[c] = std::min(lo[c], tr_c[3 * m + c] - tr_r[m]);
+                hi[c] = std::max(hi[c], tr_c[3 * m + c] + tr_r[m]);
+            }
+    double d2 = 0;
+    for (int c = 0; c < 3; c++) d2 += hi[c] > lo[c] ? (hi[c] - lo[c]) * (hi[c] - lo[c]) : 0.0;
+    return std::sqrt(d2);
+}
+
+// INVALID_ARG if a phase |Re k| |x - y| of this geometry (wavenumber kre, the
+// domains' own, and the exterior one) may exceed the double-float range.
+int bem_ctx::check_df_phase(double kre, bool with_transducer) {
+    double kmax = std::max(std::fabs(kre), std::fabs(k0re));
+    for (auto& d : doms) kmax = std::max(kmax, std::fabs(d.kre));
+    if (kmax * df_extent(with_transducer) > DF_PHASE_MAX)
+        return fail(BEM_ERR_INVALID_ARG, "phases k|x - y| beyond the double-float range (1e5 rad): set "
+                                         "bem_opts.fp64_far = 1 for native FP64 arithmetic");
+    return BEM_OK;
+}
+
 // Geometry, tables and constants of the double-float far field (once per geometry).
 int bem_ctx::ensure_fardf() {
     bem_ctx* const ctx = this;
@@ -292,10 +328,10 @@ int bem_ctx::ensure_fardf() {
     CK(cudaMemcpyAsync(dfg.sctab, sc.data(), sc.size() * sizeof(float4), cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(dfg.extab, ex.data(), ex.size() * sizeof(float2), cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(dfg.kdf, kd.data(), kd.size() * sizeof(float4), cudaMemcpyHostToDevice, stream));
-    // pi/64 in four parts (the first with 7 significant bits), ln2/64 in three (the first with 10)
+    // pi/64 in four parts (the first with 3 significant bits), ln2/64 in three (the first with 10)
     DfConsts& c = dfg.c;
     long double rest = PI / 64.0L;
-    c.pi64[0] = round_bits(rest, 7);
+    c.pi64[0] = round_bits(rest, 3);
     rest -= c.pi64[0];
     for (int i = 1; i < 4; i++) {
         c.pi64[i] = (float)rest;
@@ -325,6 +361,7 @@ int bem_ctx::far_df(const double4* pd, const double4* cu, int64_t R, int tgt_b, 
                     int64_t rstride) {
     bem_ctx* const ctx = this;
     int rc = ensure_fardf();
+    if (!rc) rc = check_df_phase(kre, false);
     if (rc) return rc;
     const Geometry& g = geo;
     const int64_t np = g.n_pts, ns2 = 2 * g.n_slots;

@@ -173,6 +173,24 @@ def test_fp64_double_float_far_field_matches_native(api, name):
         assert rel(Yd[r], Yn[r]) < 1e-12, r
 
 
+def test_fp64_double_float_far_field_large_phase(api):
+    """Phases k|x - y| up to ~10,000 rad (unit sphere, k0 = 5,000): the
+    double-float far field, near build and reduction stay at the FP64 bar
+    against native FP64 and the oracle; a geometry whose phases may pass
+    1e5 rad is refused (native FP64 remains available)."""
+    from paper_1910_01011_gb300._lib import BemError
+    s = scenes.sphere_scene(2, k0=5000.0, k1=5250.0)
+    A = pmchwt.assemble(s)
+    x = scenes.random_complex(A.shape[0], 12)
+    yd = ctx_for(api, s).apply(x, precision=0)
+    yn = ctx_for(api, s, fp64_far=1).apply(x, precision=0)
+    assert rel(yd, yn) < 1e-10
+    assert rel(yd, A @ x) < 1e-10
+    far = scenes.sphere_scene(2, k0=1.0e6, k1=1.05e6)
+    with pytest.raises(BemError):
+        ctx_for(api, far).apply(scenes.random_complex(A.shape[0], 13), precision=0)
+
+
 def test_large_phase_accuracy_fp32(api):
     """k|x-y| up to ~120 rad on a unit sphere: the FP32 path keeps the
     phase through the tile-local offsets (a plain FP32 distance would lose
