@@ -701,6 +701,8 @@ def main():
     ap.add_argument("--rhs", type=int, default=1,
                     help="right-hand sides per apply step; > 1 applies them in one matrix-free far-field launch "
                          "(far32m_kernel) and reports interaction-RHS per second (profiling of the multi-RHS path)")
+    ap.add_argument("--serving-max-exc", type=int, default=64,
+                    help="serving trace: excitations per request drawn from 1..this (default: the stated 1..64)")
     ap.add_argument("--clocks-log", default=None, help="keep the raw nvidia-smi clock samples in this CSV file")
     ap.add_argument("--osrc-solver", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="sparse solver of the preconditioner step: 0 automatic, 1 one CTA per system, 2 grid-wide, "
@@ -831,7 +833,7 @@ def main():
             # the minutes-long solve and serving measurements run on one GPU; replicas
             # of them on more GPUs would only repeat the same numbers
             extra("solve", rib_solve_metrics, local)
-            extra("serving", serving_metrics, local, 12, 16, 20.0, 150 << 30, 1e-6, rank, world)
+            extra("serving", serving_metrics, local, 12, args.serving_max_exc, 20.0, 150 << 30, 1e-6, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dt, sample = oracle_sample(s, args.ref_rows)
         line["cpu_baseline"] = {"value": n / dt / 1e9, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
