@@ -220,6 +220,13 @@ typedef struct {
                               column, each one application of the operator and preconditioner to R vectors);
                               blocks are at most 16 columns wide, a larger batch is split evenly.  Same
                               solution. */
+    int32_t recycle;       /* batched solves (batch_rhs > 1): keep up to this many solved pairs (b, u) of the
+                              context (orthonormalised: Q, U' with A U' = Q) and start every later solve of the
+                              same operator from u0 = U' Q^H b, so only the part of b outside the span of the
+                              earlier right-hand sides is left to GMRES (with as many pairs as pistons, any
+                              excitation of that transducer starts converged).  0 (default): off.  Kept across
+                              bem_set_transducer and bem_set_excitations; dropped when the operator changes
+                              (bem_set_exterior, bem_set_material).  Same solution. */
 } bem_solve_opts;
 
 typedef struct {

@@ -36,7 +36,8 @@ class bem_solve_opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("precondition", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int32), ("operator_mode", ctypes.c_int32), ("batch_rhs", ctypes.c_int32),
-                ("flexible", ctypes.c_int32), ("prec_tol", ctypes.c_double), ("block_gmres", ctypes.c_int32)]
+                ("flexible", ctypes.c_int32), ("prec_tol", ctypes.c_double), ("block_gmres", ctypes.c_int32),
+                ("recycle", ctypes.c_int32)]
 
 
 class bem_solve_report(ctypes.Structure):

@@ -152,6 +152,7 @@ static void release_device(bem_ctx* ctx) {
 namespace gbem {
 
 void invalidate_basis(bem_ctx* ctx);
+void invalidate_recycle(bem_ctx* ctx);
 
 // Eviction by the request loop: every device allocation of the context goes;
 // the host description (meshes, materials, transducer) stays and the device
@@ -246,6 +247,8 @@ int64_t estimate_solve_bytes(const bem_ctx* ctx, int64_t n_exc, const bem_solve_
     // double-float far field: split geometry and tables; split densities of R vectors
     if (o.operator_mode == 0 && ctx->opts.fp64_far == 0)
         b += 32 * (pts + slots + tiles) + 4096 + R * (pts * 32 + 2 * slots * 32 + 16);
+    // recycled solution space: Q, U' and their coefficients
+    if (o.recycle > 0) b += (int64_t)o.recycle * (2 * N * 16 + 64 * 16);
     // split vectors of the FP64-accurate residual product
     b += R * N * 16 + 4096;
     if (o.operator_mode == 1) {
@@ -883,6 +886,7 @@ int bem_set_exterior(bem_ctx* ctx, bem_z k0, double rho0) {
     ctx->k0im = k0.im;
     ctx->rho0 = rho0;
     invalidate_basis(ctx);
+    invalidate_recycle(ctx);
     if (ctx->ready) {
         ctx->near_ready = false;
         ctx->osrc_ready = false;
@@ -930,6 +934,7 @@ int bem_set_material(bem_ctx* ctx, int32_t id, bem_z k, double rho) {
     ctx->doms[id].kim = k.im;
     ctx->doms[id].rho = rho;
     invalidate_basis(ctx);
+    invalidate_recycle(ctx);
     if (ctx->ready) {
         ctx->near_ready = false;
         ctx->osrc_ready = false;

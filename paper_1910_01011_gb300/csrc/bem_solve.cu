@@ -259,7 +259,69 @@ struct SolveState {
     int64_t n_basis = 0;
     double2* wstage = nullptr;  // staging for superposition weights and outputs
     size_t wstage_bytes = 0;
+    // recycled solution space (bem_solve_opts.recycle): Q [rec_cap][N] orthonormal
+    // right-hand sides of earlier solves, U [rec_cap][N] with A_hat U = Q, rec_k in use
+    double2 *rec_Q = nullptr, *rec_U = nullptr, *rec_C = nullptr;  // rec_C: [rec_cap][REC_RMAX] coefficients
+    int64_t rec_cap = 0, rec_k = 0;
 };
+
+constexpr int REC_RMAX = 64;  // columns per coefficient pass of the recycled space
+
+// C[k][r] = sum_i conj(Q_k[i]) B_r[i] (k < gridDim.x, r < gridDim.y; row stride REC_RMAX)
+__global__ void rec_dots_kernel(const double2* __restrict__ Q, const double2* __restrict__ B, int64_t N,
+                                double2* __restrict__ C) {
+    const int k = blockIdx.x, r = blockIdx.y;
+    const double2* q = Q + (int64_t)k * N;
+    const double2* b = B + (int64_t)r * N;
+    double sr = 0, si = 0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const double2 a = q[i], x = b[i];
+        sr += a.x * x.x + a.y * x.y;
+        si += a.x * x.y - a.y * x.x;
+    }
+    __shared__ double red[2][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][w] = sr;
+        red[1][w] = si;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0, ti = 0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); j++) {
+            tr += red[0][j];
+            ti += red[1][j];
+        }
+        C[(int64_t)k * REC_RMAX + r] = make_double2(tr, ti);
+    }
+}
+
+// X_r[i] = base_r[i] + alpha sum_{k < K} U_k[i] C[k][r]   (base may be null)
+__global__ void rec_combine_kernel(const double2* __restrict__ U, int K, const double2* __restrict__ C, int64_t N,
+                                   double alpha, const double2* base, double2* X) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (i >= N) return;
+    double xr = 0, xi = 0;
+    for (int k = 0; k < K; k++) {
+        const double2 a = U[(int64_t)k * N + i], c = C[(int64_t)k * REC_RMAX + r];
+        xr += a.x * c.x - a.y * c.y;
+        xi += a.x * c.y + a.y * c.x;
+    }
+    double2 v = base ? base[(int64_t)r * N + i] : make_double2(0, 0);
+    v.x += alpha * xr;
+    v.y += alpha * xi;
+    X[(int64_t)r * N + i] = v;
+}
+
+__global__ void rec_scale_kernel(const double2* __restrict__ x, int64_t N, double s, double2* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) y[i] = make_double2(s * x[i].x, s * x[i].y);
+}
 
 }  // namespace gbem
 
@@ -430,6 +492,10 @@ namespace gbem {
 void invalidate_basis(bem_ctx* ctx) {
     if (ctx->solve) ctx->solve->n_basis = 0;
 }
+// The operator changed: earlier (b, u) pairs no longer solve it.
+void invalidate_recycle(bem_ctx* ctx) {
+    if (ctx->solve) ctx->solve->rec_k = 0;
+}
 }  // namespace gbem
 
 // Drop the solver objects after their device memory was released with the
@@ -555,6 +621,75 @@ static int ensure_batch_state(bem_ctx* ctx, int64_t R) {
 // Solve R = nb right-hand sides b[R][N] into u[R][N] with R GMRES runs in
 // lockstep (same method, tolerances and stopping rule per column as the
 // one-at-a-time path).
+// ---- recycled solution space (bem_solve_opts.recycle)
+
+// Storage for `cap` pairs; a different capacity starts an empty space.
+static int rec_ensure(bem_ctx* ctx, int64_t cap) {
+    SolveState* S = ctx->solve;
+    if (S->rec_cap == cap) return BEM_OK;
+    for (void* p : {(void*)S->rec_Q, (void*)S->rec_U, (void*)S->rec_C}) ctx->dfree(p);
+    S->rec_Q = S->rec_U = S->rec_C = nullptr;
+    S->rec_cap = S->rec_k = 0;
+    const int64_t N = ctx->geo.n_dof;
+    int rc;
+    S->rec_Q = (double2*)ctx->dalloc((size_t)cap * N * sizeof(double2), &rc); if (rc) return rc;
+    S->rec_U = (double2*)ctx->dalloc((size_t)cap * N * sizeof(double2), &rc); if (rc) return rc;
+    S->rec_C = (double2*)ctx->dalloc((size_t)cap * REC_RMAX * sizeof(double2), &rc); if (rc) return rc;
+    S->rec_cap = cap;
+    return BEM_OK;
+}
+
+// u_r = U' (Q^H b_r) for the R columns (the projection of b onto the earlier
+// right-hand sides, solved by the same combination of their solutions).
+static int rec_start(bem_ctx* ctx, const double2* b, double2* u, int64_t R) {
+    SolveState* S = ctx->solve;
+    const int64_t N = ctx->geo.n_dof;
+    const int K = (int)S->rec_k;
+    for (int64_t r0 = 0; r0 < R; r0 += REC_RMAX) {
+        const int Rc = (int)std::min<int64_t>(REC_RMAX, R - r0);
+        rec_dots_kernel<<<dim3((unsigned)K, (unsigned)Rc), 256, 0, ctx->stream>>>(S->rec_Q, b + r0 * N, N, S->rec_C);
+        rec_combine_kernel<<<dim3((unsigned)((N + 255) / 256), (unsigned)Rc), 256, 0, ctx->stream>>>(
+            S->rec_U, K, S->rec_C, N, 1.0, nullptr, u + r0 * N);
+        ctx->launches += 2;
+    }
+    CK(cudaGetLastError());
+    return BEM_OK;
+}
+
+// Fold the solved pairs (b_r, u_r) into the space while it has room: two
+// Gram-Schmidt passes of b_r against Q, the same combination applied to u_r,
+// then both scaled by 1 / |b_r'| (A U' = Q holds to the solve tolerance).  A
+// column within 1e-8 of the span adds nothing.  wb, wu: N-vector scratch.
+static int rec_append(bem_ctx* ctx, const double2* b, const double2* u, int64_t R, double2* wb, double2* wu) {
+    SolveState* S = ctx->solve;
+    const int64_t N = ctx->geo.n_dof;
+    const unsigned nb = (unsigned)((N + 255) / 256);
+    for (int64_t r = 0; r < R && S->rec_k < S->rec_cap; r++) {
+        double bn = 0;
+        int rc = S->kry.norms(ctx, b + r * N, 1, &bn);
+        if (rc) return rc;
+        if (!(bn > 0)) continue;
+        CK(cudaMemcpyAsync(wb, b + r * N, N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(wu, u + r * N, N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+        const int K = (int)S->rec_k;
+        for (int pass = 0; pass < 2 && K > 0; pass++) {
+            rec_dots_kernel<<<dim3((unsigned)K, 1), 256, 0, ctx->stream>>>(S->rec_Q, wb, N, S->rec_C);
+            rec_combine_kernel<<<dim3(nb, 1), 256, 0, ctx->stream>>>(S->rec_Q, K, S->rec_C, N, -1.0, wb, wb);
+            rec_combine_kernel<<<dim3(nb, 1), 256, 0, ctx->stream>>>(S->rec_U, K, S->rec_C, N, -1.0, wu, wu);
+            ctx->launches += 3;
+        }
+        double wn = 0;
+        if ((rc = S->kry.norms(ctx, wb, 1, &wn))) return rc;
+        if (!(wn > 1e-8 * bn)) continue;
+        rec_scale_kernel<<<nb, 256, 0, ctx->stream>>>(wb, N, 1.0 / wn, S->rec_Q + (int64_t)K * N);
+        rec_scale_kernel<<<nb, 256, 0, ctx->stream>>>(wu, N, 1.0 / wn, S->rec_U + (int64_t)K * N);
+        ctx->launches += 2;
+        CK(cudaGetLastError());
+        S->rec_k++;
+    }
+    return BEM_OK;
+}
+
 // cap > R (a single-batch mixed solve with ctx->join_hook set): before each
 // refinement cycle the hook may hand over further excitations, which join as
 // new columns (their right-hand sides built into b, zero start) until the
@@ -606,6 +741,10 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
     std::vector<int> its(cap);
     if ((rc = S->kry.norms(ctx, b, R, bn.data()))) return rc;
     CK(cudaMemsetAsync(u, 0, R * N * sizeof(double2), ctx->stream));
+    // recycled start: u = U' Q^H b, the part of b in the span of earlier right-hand sides
+    if (o.recycle > 0 && (rc = rec_ensure(ctx, o.recycle))) return rc;
+    const bool warm = o.recycle > 0 && S->rec_k > 0;
+    if (warm && (rc = rec_start(ctx, b, u, R))) return rc;
     int it = 0;
     double worst = 0;
     // block GMRES, or R GMRES runs in lockstep (also where the block's
@@ -626,7 +765,7 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
         if (rc) return rc;
         double inner = o.tol;
         for (int attempt = 0; attempt < 4; attempt++) {
-            if ((rc = inner_solve(op_for(BEM_PREC_FP64), sb, u, inner, attempt == 0, false))) return rc;
+            if ((rc = inner_solve(op_for(BEM_PREC_FP64), sb, u, inner, attempt == 0 && !warm, false))) return rc;
             it += *std::max_element(its.begin(), its.begin() + R);
             for (int64_t r = 0; r < R; r++) rep->iterations += its[r];
             if ((rc = residual(rel, bn))) return rc;
@@ -635,8 +774,12 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
             inner *= 0.1;
         }
     } else {
-        CK(cudaMemcpyAsync(S->br, b, R * N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
-        for (int64_t r = 0; r < R; r++) rel[r] = bn[r] > 0 ? 1.0 : 0.0;
+        if (warm) {
+            if ((rc = residual(rel, bn))) return rc;  // br = b - A_hat u0 (FP64)
+        } else {
+            CK(cudaMemcpyAsync(S->br, b, R * N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+            for (int64_t r = 0; r < R; r++) rel[r] = bn[r] > 0 ? 1.0 : 0.0;
+        }
         int ref = 0, inner_prec = BEM_PREC_FP32;
         double prev = 2.0;
         for (; ref <= o.max_refine; ref++) {
@@ -676,6 +819,10 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
         }
         rep->refinements += ref;
     }
+    if (o.recycle > 0 && worst <= o.tol) {  // keep the solved pairs for later solves of this operator
+        if ((rc = rec_ensure(ctx, o.recycle))) return rc;
+        if ((rc = rec_append(ctx, b, u, R, S->bt, S->bpb))) return rc;
+    }
     rep->residual = std::max(rep->residual, worst);
     *converged &= worst <= o.tol;
     return BEM_OK;
@@ -688,7 +835,7 @@ int bem_solve(bem_ctx* ctx, const bem_solve_opts* opts, bem_solve_report* rep) {
     if (opts) o = *opts;
     if (o.restart < 1 || o.max_iter < 1 || !(o.tol > 0) || (o.precision != BEM_PREC_FP64 && o.precision != BEM_PREC_FP32) ||
         o.operator_mode < 0 || o.operator_mode > 2 || o.batch_rhs < 0 || o.flexible < 0 || o.flexible > 1 ||
-        !(o.prec_tol >= 0) || o.prec_tol >= 1 || o.block_gmres < 0 || o.block_gmres > 1)
+        !(o.prec_tol >= 0) || o.prec_tol >= 1 || o.block_gmres < 0 || o.block_gmres > 1 || o.recycle < 0)
         return ctx->fail(BEM_ERR_INVALID_ARG, "bad solve options");
     CK(cudaSetDevice(ctx->device));
     const auto t0 = std::chrono::steady_clock::now();

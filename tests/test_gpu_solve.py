@@ -195,6 +195,42 @@ def test_automatic_operator_mode(api):
     assert rel(sols[1].ravel(), sols[0].ravel()) < 1e-8
 
 
+def test_recycled_solution_space(api):
+    """bem_solve_opts.recycle: solved pairs (b, u) of earlier batched solves
+    start later ones.  Six pistons: excitations in the span of earlier ones
+    start converged (no iteration); once six independent excitations were
+    solved, any excitation does; every solution meets the oracle's dense
+    solve; a material change drops the space (iterations again)."""
+    s = scenes.two_sphere_scene(1)
+    tr = small_transducer()
+    A = pmchwt.assemble(s)
+    rng = np.random.default_rng(31)
+    W1 = np.exp(2j * np.pi * rng.random((4, 6)))
+    W2 = (rng.standard_normal((3, 4)) + 1j * rng.standard_normal((3, 4))) @ W1  # in the span of W1
+    W3 = np.exp(2j * np.pi * rng.random((4, 6)))
+    W4 = np.exp(2j * np.pi * rng.random((2, 6)))
+    c = ctx_for(api, s)
+    c.set_transducer(tr["centres"], tr["normals"], tr["radii"], 2.6)
+    kw = dict(precision=1, batch_rhs=4, block_gmres=1, recycle=16, operator_mode=1)
+
+    def run(W, tol):
+        c.set_excitations(W)
+        rep = c.solve(tol=tol, **kw)
+        assert rep["converged"], rep
+        B = c.rhs(W.shape[0]).reshape(W.shape[0], -1)
+        for r in range(W.shape[0]):
+            assert rel(c.solution(r), np.linalg.solve(A, B[r])) < 1e-6, r
+        return rep["iterations"]
+
+    assert run(W1, 1e-10) > 0
+    assert run(W2, 1e-8) == 0
+    assert run(W3, 1e-10) > 0
+    assert run(W4, 1e-8) == 0
+    d = s.domains[0]
+    c.set_material(0, d.k, d.rho)  # same values: the operator is rebuilt, the space dropped
+    assert run(W4, 1e-8) > 0
+
+
 def test_solve_reports_not_converged(api):
     s = scenes.sphere_scene(2)
     c = ctx_for(api, s)
