@@ -374,7 +374,7 @@ typedef struct {
     int32_t max_batch_rhs;    /* excitations merged into one solve (default 64) */
     int64_t hbm_budget_bytes; /* device bytes all scenes may hold together (default 150 GiB; 0 = no limit) */
     bem_solve_opts solve;     /* options of every solve (default: mixed precision, batch_rhs = max_batch_rhs,
-                                 block_gmres = 1, operator_mode = 2) */
+                                 block_gmres = 1, operator_mode = 2, recycle = 256) */
     int32_t join;             /* 1 (default): requests for a scene whose mixed-precision solve is running join
                                  it at its next refinement boundary while the block (16 excitations with block
                                  GMRES, else batch_rhs) has room and the budget holds the growth of the solve's

@@ -640,17 +640,21 @@ static int rec_ensure(bem_ctx* ctx, int64_t cap) {
 }
 
 // u_r = U' (Q^H b_r) for the R columns (the projection of b onto the earlier
-// right-hand sides, solved by the same combination of their solutions).
-static int rec_start(bem_ctx* ctx, const double2* b, double2* u, int64_t R) {
+// right-hand sides, solved by the same combination of their solutions); with
+// res, also res_r = b_r - Q (Q^H b_r), its residual (A U' = Q to the earlier
+// solves' tolerance, which the refinement's FP64 residuals then correct).
+static int rec_start(bem_ctx* ctx, const double2* b, double2* u, int64_t R, double2* res) {
     SolveState* S = ctx->solve;
     const int64_t N = ctx->geo.n_dof;
     const int K = (int)S->rec_k;
     for (int64_t r0 = 0; r0 < R; r0 += REC_RMAX) {
         const int Rc = (int)std::min<int64_t>(REC_RMAX, R - r0);
+        const dim3 grid((unsigned)((N + 255) / 256), (unsigned)Rc);
         rec_dots_kernel<<<dim3((unsigned)K, (unsigned)Rc), 256, 0, ctx->stream>>>(S->rec_Q, b + r0 * N, N, S->rec_C);
-        rec_combine_kernel<<<dim3((unsigned)((N + 255) / 256), (unsigned)Rc), 256, 0, ctx->stream>>>(
-            S->rec_U, K, S->rec_C, N, 1.0, nullptr, u + r0 * N);
-        ctx->launches += 2;
+        rec_combine_kernel<<<grid, 256, 0, ctx->stream>>>(S->rec_U, K, S->rec_C, N, 1.0, nullptr, u + r0 * N);
+        if (res) rec_combine_kernel<<<grid, 256, 0, ctx->stream>>>(S->rec_Q, K, S->rec_C, N, -1.0, b + r0 * N,
+                                                                   res + r0 * N);
+        ctx->launches += res ? 3 : 2;
     }
     CK(cudaGetLastError());
     return BEM_OK;
@@ -744,7 +748,7 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
     // recycled start: u = U' Q^H b, the part of b in the span of earlier right-hand sides
     if (o.recycle > 0 && (rc = rec_ensure(ctx, o.recycle))) return rc;
     const bool warm = o.recycle > 0 && S->rec_k > 0;
-    if (warm && (rc = rec_start(ctx, b, u, R))) return rc;
+    if (warm && (rc = rec_start(ctx, b, u, R, o.precision == BEM_PREC_FP64 ? nullptr : S->br))) return rc;
     int it = 0;
     double worst = 0;
     // block GMRES, or R GMRES runs in lockstep (also where the block's
@@ -774,8 +778,10 @@ static int solve_block(bem_ctx* ctx, const bem_solve_opts& o, const double2* b, 
             inner *= 0.1;
         }
     } else {
-        if (warm) {
-            if ((rc = residual(rel, bn))) return rc;  // br = b - A_hat u0 (FP64)
+        if (warm) {  // br = b - Q Q^H b from rec_start
+            std::vector<double> rn(R);
+            if ((rc = S->kry.norms(ctx, S->br, R, rn.data()))) return rc;
+            for (int64_t r = 0; r < R; r++) rel[r] = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
         } else {
             CK(cudaMemcpyAsync(S->br, b, R * N * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
             for (int64_t r = 0; r < R; r++) rel[r] = bn[r] > 0 ? 1.0 : 0.0;

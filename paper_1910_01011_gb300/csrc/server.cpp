@@ -317,6 +317,7 @@ int bem_server_default_opts(bem_server_opts* o) {
     o->solve.batch_rhs = 64;
     o->solve.block_gmres = 1;
     o->solve.operator_mode = 2;
+    o->solve.recycle = 256;
     o->join = 1;
     return BEM_OK;
 }
